@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""Benchmark of the pressure-projection Poisson solve (one GPU per rank).
+
+A step is one pass of the whole path over one synthetic input: operator assembly (density,
+activity, merge map, face coefficients, scaling), divergence right-hand side, and the
+preconditioned CG solve to relative residual 1e-8, on the 512x256x128 slender-hull-in-waves grid
+(16.8 M cells, ~ the paper's 16.7 M-point Athena grid).  Inputs are resident in HBM before the
+timed region; `e2e` repeats the step through the host-buffer C-ABI call (vofp_solve_host) with
+the host<->device copies inside the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--mode mixed|fp64] [--impl reference]
+
+Under torchrun every rank solves its own copy (replicas; no data exchange) and rank 0 prints one
+JSON line.  `--impl reference` times the CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Poisson time-to-1e-8 residual & solves/s at 512×256×128; HBM GB/s per CG iter"
+SHAPE = (512, 256, 128)
+RTOL = 1e-8
+FALLBACK_HBM_GBS = 6800.0
+# algorithmic bytes per cell of one launch / one iteration ("Roofline")
+STENCIL_BYTES = {64: 9 * 8, 32: 9 * 4}          # reads r, p_old, x, Tx, Ty, Tz; writes p, x, q
+UPDATE_BYTES = {64: 3 * 8, 32: 3 * 4}           # reads r, q; writes r
+ITER_BYTES = {64: 12 * 8, 32: 12 * 4}
+# dram read+write bytes per cell of one stencil launch from the committed ncu capture, valid only
+# while the kernel sources hash to KERNEL_HASH (else reported as null)
+TRAFFIC_PER_CELL = {}
+KERNEL_HASH = None
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("vofp_kernels.cuh", "vofp_solve.cu"):
+        with open(os.path.join(ROOT, "paper_1410_1937_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([s.strip() for s in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 5 + i and s[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def make_problem(shape, seed=2):
+    from paper_1410_1937_gb300 import inputs as I
+    return I.config2(seed=seed, shape=shape)
+
+
+def cpu_baseline(prob, gpu_fp64_iterations, iters=40):
+    """Oracle (plain FP64 CSR Jacobi-PCG) on a bounded sample of the same workload: its assembly
+    plus `iters` PCG iterations, extrapolated to a whole solve with the iteration count of the FP64
+    CG on this input (the same iteration in exact arithmetic)."""
+    from oracle import poisson
+    threads = poisson.set_threads(0)
+    t0 = time.perf_counter()
+    s = poisson.System(prob)
+    t_asm = time.perf_counter() - t0
+    _, info = s.solve_pcg(rtol=RTOL, maxit=iters)
+    t_it = info["seconds"] / max(info["iterations"], 1)
+    t_solve = t_asm + t_it * gpu_fp64_iterations
+    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": threads, "kind": "oracle",
+            "sample": (f"oracle assembly of the {prob.shape[2]}x{prob.shape[1]}x{prob.shape[0]} workload "
+                       f"({t_asm:.1f} s) + {info['iterations']} Jacobi-PCG iterations "
+                       f"({t_it * 1e3:.1f} ms each), extrapolated to {gpu_fp64_iterations} iterations"),
+            "iterations_per_s": 1.0 / t_it, "assembly_s": t_asm}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    prob = make_problem(tuple(args.shape))
+    from oracle import poisson
+    threads = poisson.set_threads(0)
+    s = poisson.System(prob)
+    times = []
+    iters = args.ref_iters
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        _, info = s.solve_pcg(rtol=RTOL, maxit=iters)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    t_it = float(np.mean(times)) / iters
+    t_solve = s.assembly_seconds + t_it * args.ref_fp64_iterations
+    value = 1.0 / t_solve
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_solve * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"hull-in-waves {args.shape[0]}x{args.shape[1]}x{args.shape[2]} rtol 1e-8"},
+           "cpu_baseline": {"value": value, "unit": "solves/s", "cores": threads, "kind": "oracle",
+                            "sample": f"each step {iters} oracle Jacobi-PCG iterations; solve extrapolated "
+                                      f"to {args.ref_fp64_iterations} iterations plus assembly "
+                                      f"({s.assembly_seconds:.1f} s)"},
+           "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_1410_1937_gb300 import vofp
+
+    torch.cuda.set_device(local_rank)
+    prob = make_problem(tuple(args.shape))
+    stream = torch.cuda.Stream()
+    mode = vofp.MODE_MIXED if args.mode == "mixed" else vofp.MODE_FP64
+    prec = 32 if args.mode == "mixed" else 64
+    with torch.cuda.stream(stream):
+        ctx = vofp.Context(prob.dx, prob.dy, prob.dz, stream)
+        t = {k: torch.from_numpy(np.ascontiguousarray(getattr(prob, k)).ravel()).cuda()
+             for k in ("F", "vf", "ax", "ay", "az", "u", "v", "w")}
+        b = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+        x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+        infos = []
+        launches = [0]
+
+        def step():
+            l0 = ctx.vofp_launch_count()
+            ctx.vofp_build_operator(t["F"], t["ax"], t["ay"], t["az"], t["vf"], prob.bc, prob.rho_liquid,
+                                    prob.rho_gas, prob.merge_threshold, prob.density_smoothing, prob.dt)
+            ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"], out=b)
+            _, info = ctx.vofp_solve(b, x=x, mode=mode, rtol=RTOL, x0_zero=1, check_every=args.check_every,
+                                     inner_rtol=args.inner_rtol)
+            launches[0] += ctx.vofp_launch_count() - l0
+            infos.append(info)
+
+        for _ in range(args.warmup):
+            step()
+        infos.clear()
+        launches[0] = 0
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local_rank) as clk:
+            e0.record(stream)
+            for _ in range(args.steps):
+                step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ms = e0.elapsed_time(e1) / args.steps
+        tm = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        ms_max = float(tm.item())
+        info = infos[-1]
+        assert all(i["status"] == 0 for i in infos), infos
+        # dominant kernel: the fused CG stencil of the solve's precision, timed live
+        st_ms, up_ms = ctx.vofp_time_iteration_kernels(prec, args.kernel_reps)
+        n = prob.n
+        hbm, hbm_kind = peaks()
+        achieved = STENCIL_BYTES[prec] * n / (st_ms * 1e-3) / 1e9
+        traffic = None
+        if KERNEL_HASH is not None and KERNEL_HASH == kernel_hash() and prec in TRAFFIC_PER_CELL:
+            traffic = TRAFFIC_PER_CELL[prec] * n
+        iter_s = info["seconds"] / max(info["iterations"], 1)
+        # FP64 reference solve on the same input for the iteration count and its own time
+        x64 = torch.zeros_like(x)
+        _, info64 = ctx.vofp_solve(b, x=x64, mode=vofp.MODE_FP64, rtol=RTOL, x0_zero=1)
+        st64, up64 = ctx.vofp_time_iteration_kernels(64, args.kernel_reps)
+
+        # end to end through the host-buffer C-ABI call
+        e2e = None
+        if not args.no_e2e:
+            host = {k: torch.from_numpy(np.ascontiguousarray(getattr(prob, k)).ravel()).pin_memory()
+                    for k in ("F", "vf", "ax", "ay", "az", "u", "v", "w")}
+            xh = torch.empty(n, dtype=torch.float64).pin_memory()
+            ctx2 = vofp.Context(prob.dx, prob.dy, prob.dz, stream)
+
+            def host_step():
+                r = ctx2.vofp_solve_host(host["F"], host["ax"], host["ay"], host["az"], host["vf"], host["u"],
+                                         host["v"], host["w"], prob.bc, xh, mode=mode, rtol=RTOL,
+                                         check_every=args.check_every, inner_rtol=args.inner_rtol,
+                                         rho_liquid=prob.rho_liquid, rho_gas=prob.rho_gas,
+                                         merge_threshold=prob.merge_threshold, dt=prob.dt)
+                assert r["status"] == 0, r
+            for _ in range(max(1, args.warmup // 2)):
+                host_step()
+            if world > 1:
+                dist.barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                host_step()
+            torch.cuda.synchronize()
+            e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+            te = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+            if world > 1:
+                dist.all_reduce(te, op=dist.ReduceOp.MAX)
+            h2d = sum(v.numel() * 8 for v in host.values())
+            e2e = {"value": world * 1e3 / float(te.item()), "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": n * 8, "ms_per_step": float(te.item())}
+            ctx2.close()
+
+    if rank != 0:
+        return
+    out = {
+        "metric": METRIC, "value": world * 1e3 / ms_max, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == 32 else "f64",
+        "data": "synthetic",
+        "config": {"workload": f"hull-in-waves {args.shape[0]}x{args.shape[1]}x{args.shape[2]} "
+                               f"({n} cells) Dirichlet exit, rtol 1e-8",
+                   "mode": args.mode, "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "l2": "inputs larger than L2 (8 FP64 arrays of 134 MB)"},
+        "time_to_tol_ms": info["seconds"] * 1e3,
+        "iterations": info["iterations"], "outer_iterations": info["outer_iterations"],
+        "rel_residual": info["rel_residual"],
+        "cg_iterations_per_s": info["iterations"] / info["seconds"],
+        "hbm_gbs_per_iter": ITER_BYTES[prec] * n / iter_s / 1e9,
+        "fp64_reference": {"time_to_tol_ms": info64["seconds"] * 1e3, "iterations": info64["iterations"],
+                           "rel_residual": info64["rel_residual"], "status": info64["status_name"],
+                           "stencil_ms": st64, "update_ms": up64,
+                           "stencil_gbs": STENCIL_BYTES[64] * n / (st64 * 1e-3) / 1e9,
+                           "hbm_gbs_per_iter": ITER_BYTES[64] * n / (info64["seconds"] / max(info64["iterations"], 1)) / 1e9},
+        "roofline": {"bound": "hbm", "kernel": f"k_stencil<{'float' if prec == 32 else 'double'},ST_CG>",
+                     "achieved": achieved, "peak": hbm, "peak_kind": hbm_kind, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic, "stencil_ms": st_ms, "update_ms": up_ms,
+                     "update_gbs": UPDATE_BYTES[prec] * n / (up_ms * 1e-3) / 1e9},
+        "clocks": clk.summary(),
+        "gpu_launches": launches[0],
+        "e2e": e2e,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(prob, info64["iterations"])
+    print(json.dumps(out), flush=True)
+
+
+def run_profile(args):
+    """One assembly + right-hand side + a solve capped at --profile-iters iterations (for ncu)."""
+    import torch
+    from paper_1410_1937_gb300 import vofp
+    prob = make_problem(tuple(args.shape))
+    ctx, t = vofp.context_for(prob)
+    b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
+    mode = vofp.MODE_MIXED if args.mode == "mixed" else vofp.MODE_FP64
+    _, info = ctx.vofp_solve(b, mode=mode, rtol=RTOL, max_iter=args.profile_iters, check_every=args.check_every,
+                             inner_rtol=args.inner_rtol, raise_on_error=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": True, "shape": args.shape, "mode": args.mode, "iterations": info["iterations"],
+                      "status": info["status_name"], "launches": ctx.vofp_launch_count()}), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--shape", type=int, nargs=3, default=list(SHAPE))
+    ap.add_argument("--check-every", type=int, default=8)
+    ap.add_argument("--inner-rtol", type=float, default=1e-3)
+    ap.add_argument("--kernel-reps", type=int, default=20)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-iters", type=int, default=20)
+    ap.add_argument("--ref-fp64-iterations", type=int, default=2000)
+    ap.add_argument("--profile-iters", type=int, default=0,
+                    help="profiling run: one step whose solve stops after this many CG iterations")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if args.profile_iters > 0:
+        run_profile(args)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

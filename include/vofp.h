@@ -1,0 +1,205 @@
+/*
+ * vofp.h -- C ABI of libvofp, a single-GPU (sm_103a) solver for the pressure-projection Poisson
+ * equation of the cartesian-grid volume-of-fluid method of Dommermuth et al., "The numerical
+ * simulation of ship waves using cartesian-grid and volume-of-fluid methods".
+ *
+ * The equation (Sec. 2 Eq. pois; Sec. 2.1 Eq. poisson1) is  div( grad(p) / rho ) = div(u*) / dt,
+ * integrated over each cell's open faces (Sec. 2.3 Eqs. integral1-integral2).  The library solves
+ * the discrete form  A_hat p = b_hat  where
+ *   - A_hat = P^T A P is symmetric positive (semi)definite: A is the 7-point finite-volume operator
+ *     with face coefficients T_f = A_f S_f / ((d_L rho_L + d_R rho_R) / 2) (aperture x face area x
+ *     half-cell harmonic average of 1/rho over centre distance), and P merges cells whose open
+ *     volume is below a threshold into a neighbour (Sec. 2.3);
+ *   - b = -(1/dt) * (sum of outward face fluxes A_f S_f u_f + body-surface flux), Sec. 2.4 F_i;
+ *   - rho = rho_gas + (rho_liquid - rho_gas) F from the VOF fraction F (Sec. 2 Eq. density with
+ *     H(phi) = phi), optionally smoothed (1/4, 1/2, 1/4) along each axis (Sec. 2.10).
+ * The solve is preconditioned conjugate gradients (Sec. 1); the paper names no preconditioner.
+ *
+ * Conventions shared by every entry point
+ *   Layout   cells are numbered c = i + nx*(j + ny*k), x fastest.  Face arrays use the same order
+ *            with the face axis one longer: x-faces (nz, ny, nx+1), y-faces (nz, ny+1, nx),
+ *            z-faces (nz+1, ny, nx); x-face i lies between cells i-1 and i.
+ *   Memory   unless stated otherwise every array argument is DEVICE memory, FP64, contiguous,
+ *            owned by the caller, and only read during the call (outputs are written).  The
+ *            library owns its workspace (coefficients, Krylov vectors, graphs) and frees it in
+ *            vofp_destroy.
+ *   Streams  all work is enqueued on the stream given to vofp_create.  Entry points that return
+ *            a scalar (solve info, residual) synchronise that stream before returning.
+ *   Errors   every call returns a vofp_status; VOFP_OK is 0.  No exception crosses the ABI, nothing
+ *            calls exit or traps on the device.  vofp_last_error gives a message for the context.
+ *            A failed solve still writes its best iterate and fills vofp_solve_info.
+ *   Boundary domain faces are ordered -x, +x, -y, +y, -z, +z.  NEUMANN is a free-slip wall (no
+ *            pressure flux unless neumann_flux prescribes one, Sec. 2.6 Eq. exit); DIRICHLET puts
+ *            p = 0 on the face, half a cell from the adjacent centre.
+ *   Cells    a cell has no unknown when its open volume is 0 or none of its flux-carrying faces
+ *            is open; its faces are then closed and it reads 0 in every output.
+ */
+#ifndef VOFP_H
+#define VOFP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vofp_ctx vofp_ctx;
+/* A cudaStream_t (0 = legacy default stream). */
+typedef struct CUstream_st* vofp_stream;
+
+typedef enum {
+    VOFP_OK = 0,
+    VOFP_ERR_INVALID_ARG = 1,     /* bad pointer, size or option                                  */
+    VOFP_ERR_CUDA = 2,            /* a CUDA runtime call failed (message in vofp_last_error)      */
+    VOFP_ERR_OOM = 3,             /* device allocation failed                                     */
+    VOFP_ERR_NOT_CONVERGED = 4,   /* max_iter reached before rtol                                 */
+    VOFP_ERR_BREAKDOWN = 5,       /* p.Ap <= 0, r.z <= 0 or a non-finite scalar in the iteration  */
+    VOFP_ERR_STAGNATED = 6,       /* residual stopped decreasing (stag_window / stag_ratio)       */
+    VOFP_ERR_INCOMPATIBLE_RHS = 7,/* all-Neumann problem whose right-hand side does not sum to 0  */
+    VOFP_ERR_NOT_BUILT = 8        /* vofp_build_operator has not succeeded on this context        */
+} vofp_status;
+
+enum { VOFP_BC_NEUMANN = 0, VOFP_BC_DIRICHLET = 1 };
+enum { VOFP_MODE_FP64 = 0, VOFP_MODE_MIXED = 1 };
+enum { VOFP_PRECOND_JACOBI = 0, VOFP_PRECOND_RBSGS = 1 };
+
+/* Grid: nx*ny*nz cells; dx, dy, dz are HOST arrays of the cell widths (lengths nx, ny, nz),
+ * copied by vofp_create.  Stretched grids follow Sec. 2.2. */
+typedef struct {
+    int nx, ny, nz;
+    const double* dx;
+    const double* dy;
+    const double* dz;
+} vofp_grid;
+
+/* Boundary kinds per domain face, and optional prescribed outward pressure flux
+ * g = (1/rho) dp/dn on NEUMANN faces (device, one value per boundary face in the face's own
+ * (row, column) order: -x/+x faces (nz, ny), -y/+y (nz, nx), -z/+z (ny, nx); NULL = 0).
+ * The Orlanski exit of Sec. 2.6 (Eq. exit) is such a flux. */
+typedef struct {
+    int kind[6];
+    const double* neumann_flux[6];
+} vofp_bc;
+
+/* Physical settings.  merge_threshold: cells with open-volume fraction below it merge into the
+ * neighbour across their largest open face (Sec. 2.3 uses 0.25; 0 disables merging).
+ * density_smoothing: 1 applies the filter of Sec. 2.10.  dt > 0 scales the right-hand side. */
+typedef struct {
+    double rho_liquid, rho_gas;
+    double merge_threshold;
+    int density_smoothing;
+    double dt;
+} vofp_phys;
+
+/* Solve options.
+ *   mode        VOFP_MODE_FP64: PCG in FP64.  VOFP_MODE_MIXED: iterative refinement whose outer
+ *               residual b - A x and solution update are FP64 while the inner PCG runs with FP32
+ *               coefficients and vectors and FP64-accumulated dot products.
+ *   precond     VOFP_PRECOND_JACOBI (diagonal) or VOFP_PRECOND_RBSGS (red-black symmetric
+ *               Gauss-Seidel; FP64 mode only).
+ *   rtol        stop when ||b_hat - A_hat x|| <= rtol ||b_hat|| (2-norm over the unknowns).
+ *   max_iter    cap on PCG iterations (inner iterations summed in mixed mode).
+ *   inner_rtol  mixed mode: relative residual reduction of each inner solve (e.g. 1e-3).
+ *   check_every convergence is tested every check_every iterations (even, >= 2; 0 = default 8).
+ *   x0_zero     1: ignore the contents of x and start from 0. */
+typedef struct {
+    int mode;
+    int precond;
+    double rtol;
+    int max_iter;
+    double inner_rtol;
+    int check_every;
+    int x0_zero;
+} vofp_solve_opts;
+
+typedef struct {
+    int iterations;          /* PCG iterations (inner iterations summed in mixed mode)          */
+    int outer_iterations;    /* refinement steps in mixed mode, 1 otherwise                     */
+    double rel_residual;     /* ||b_hat - A_hat x|| / ||b_hat||, recomputed in FP64 at the end  */
+    double seconds;          /* device time of the solve (CUDA events)                          */
+    int status;              /* vofp_status of the solve                                        */
+} vofp_solve_info;
+
+typedef struct {
+    long long cells;          /* nx*ny*nz                                                      */
+    long long unknowns;       /* merge groups with an unknown                                  */
+    long long inactive;       /* cells without an unknown                                      */
+    long long merged_cells;   /* cells folded into another cell's unknown                      */
+    long long groups;         /* merge groups with more than one cell                          */
+    long long device_bytes;   /* device memory held by the context                             */
+} vofp_stats;
+
+/* Library version string (static storage). */
+const char* vofp_version(void);
+
+/* Create a context for one grid on one stream.  *out receives the context.  Fails with
+ * INVALID_ARG for non-positive sizes or widths, OOM if the grid arrays cannot be allocated. */
+vofp_status vofp_create(vofp_ctx** out, const vofp_grid* grid, vofp_stream stream);
+
+/* Free everything the context holds.  NULL is accepted. */
+void vofp_destroy(vofp_ctx* ctx);
+
+/* Message of the last failing call on ctx ("" if none; static text if ctx is NULL). */
+const char* vofp_last_error(const vofp_ctx* ctx);
+
+/* Assemble A_hat from the VOF fraction F (cells), the apertures ax, ay, az (faces, in [0,1]),
+ * the open-volume fraction vol_frac (cells, in [0,1]; NULL = all 1), boundary kinds and physics
+ * (Sec. 2 Eq. density; Sec. 2.3 Eqs. integral2 and merging; Sec. 2.10).  Computes cell activity,
+ * the merge map (host side, O(number of small cells)), face coefficients and the scaled FP64 and
+ * FP32 copies used by the solvers.  Synchronises the stream. */
+vofp_status vofp_build_operator(vofp_ctx* ctx, const double* F, const double* ax,
+                                const double* ay, const double* az, const double* vol_frac,
+                                const vofp_bc* bc, const vofp_phys* phys);
+
+/* b (cells) = -(1/dt) (sum of outward open-face fluxes A_f S_f u_f + body_flux) + prescribed
+ * Neumann fluxes, for face velocities u (x-faces), v (y-faces), w (z-faces) (Sec. 2.1 Eq.
+ * poisson1 with R = 0; Sec. 2.3 Eq. integral2).  body_flux (cells) is the integral of v*.n over
+ * each cell's body surface (NULL = 0).  Normal velocities on NEUMANN domain faces are not used.
+ * b is per cell and not merged; solve and residual merge it. */
+vofp_status vofp_rhs_from_face_velocity(vofp_ctx* ctx, const double* u, const double* v,
+                                        const double* w, const double* body_flux, double* b);
+
+/* y = A_hat x: x is read at each group's master cell; y receives the group's value at the master
+ * and 0 at every other cell and at cells without an unknown. */
+vofp_status vofp_apply(vofp_ctx* ctx, const double* x, double* y);
+
+/* Merge b over groups and return ||b_hat - A_hat x|| / ||b_hat|| in *rel (FP64).  Synchronises. */
+vofp_status vofp_residual(vofp_ctx* ctx, const double* b, const double* x, double* rel);
+
+/* Solve A_hat x = b_hat (b per cell, merged internally).  x: initial guess on entry (unless
+ * opts->x0_zero), solution on exit, with every cell of a group holding the group's value and 0
+ * where there is no unknown.  info may be NULL.  Returns info->status. */
+vofp_status vofp_solve(vofp_ctx* ctx, const double* b, double* x, const vofp_solve_opts* opts,
+                       vofp_solve_info* info);
+
+/* End-to-end call on HOST buffers (pageable or pinned): copies F, apertures, vol_frac and the
+ * face velocities to the device, builds the operator, forms the right-hand side, solves and
+ * copies the pressure back to x_host (cells).  Equivalent to the device-pointer calls above. */
+vofp_status vofp_solve_host(vofp_ctx* ctx, const double* F, const double* ax, const double* ay,
+                            const double* az, const double* vol_frac, const double* u,
+                            const double* v, const double* w, const vofp_bc* bc,
+                            const vofp_phys* phys, const vofp_solve_opts* opts, double* x_host,
+                            vofp_solve_info* info);
+
+/* master[c] (device int32, cells) = root cell of c's merge group, -1 for cells without unknown. */
+vofp_status vofp_merge_map(vofp_ctx* ctx, int32_t* master);
+
+/* Counts and device memory of the built operator. */
+vofp_status vofp_get_stats(vofp_ctx* ctx, vofp_stats* stats);
+
+/* *count = number of kernels this context has launched since vofp_create (kernels run inside
+ * the solve's CUDA graphs are counted per execution). */
+vofp_status vofp_launch_count(vofp_ctx* ctx, long long* count);
+
+/* Measurement hook: launches one FP64 (precision 64) or FP32 (precision 32) CG iteration's
+ * kernels `reps` times on the context stream after a vofp_solve, recording the average device
+ * time of the fused stencil kernel in *stencil_ms and of the vector-update kernel in *update_ms.
+ * It reuses the last solve's vectors and leaves the solution untouched. */
+vofp_status vofp_time_iteration_kernels(vofp_ctx* ctx, int precision, int reps,
+                                        float* stencil_ms, float* update_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VOFP_H */

@@ -1,0 +1,241 @@
+// extern "C" entry points of libvofp (declared and documented in include/vofp.h): argument
+// checks, context lifetime and error reporting around the implementations in the other files.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "vofp_internal.cuh"
+
+namespace {
+
+const char* kNullCtx = "null context";
+
+vofp_status check_ctx(vofp_ctx* c, bool need_built) {
+    if (!c) return VOFP_ERR_INVALID_ARG;
+    c->err.clear();
+    if (need_built && !c->built) {
+        c->set_error("vofp_build_operator has not succeeded on this context");
+        return VOFP_ERR_NOT_BUILT;
+    }
+    return VOFP_OK;
+}
+
+vofp_status invalid(vofp_ctx* c, const char* m) {
+    if (c) c->set_error(m);
+    return VOFP_ERR_INVALID_ARG;
+}
+
+vofp_status fail_cuda(vofp_ctx* c) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        c->set_error(std::string("kernel launch: ") + cudaGetErrorString(e));
+        return VOFP_ERR_CUDA;
+    }
+    return VOFP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* vofp_version(void) { return "vofp 0.1 (sm_103a)"; }
+
+vofp_status vofp_create(vofp_ctx** out, const vofp_grid* g, vofp_stream stream) {
+    if (!out || !g) return VOFP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (g->nx <= 0 || g->ny <= 0 || g->nz <= 0 || !g->dx || !g->dy || !g->dz) return VOFP_ERR_INVALID_ARG;
+    const long long n = (long long)g->nx * g->ny * g->nz;
+    if (n >= (1LL << 31)) return VOFP_ERR_INVALID_ARG;
+    for (int i = 0; i < g->nx; ++i)
+        if (!(g->dx[i] > 0.0) || !std::isfinite(g->dx[i])) return VOFP_ERR_INVALID_ARG;
+    for (int j = 0; j < g->ny; ++j)
+        if (!(g->dy[j] > 0.0) || !std::isfinite(g->dy[j])) return VOFP_ERR_INVALID_ARG;
+    for (int k = 0; k < g->nz; ++k)
+        if (!(g->dz[k] > 0.0) || !std::isfinite(g->dz[k])) return VOFP_ERR_INVALID_ARG;
+    vofp_ctx* c = new (std::nothrow) vofp_ctx();
+    if (!c) return VOFP_ERR_OOM;
+    c->d.nx = g->nx;
+    c->d.ny = g->ny;
+    c->d.nz = g->nz;
+    c->d.n = n;
+    c->d.plane = (long long)g->nx * g->ny;
+    c->stream = reinterpret_cast<cudaStream_t>(stream);
+    // planes per stencil block: enough blocks to fill the GPU several times over; the environment
+    // variable VOFP_STENCIL_ZCHUNK overrides it for tuning
+    c->zchunk = g->nz >= 256 ? 32 : 16;
+    if (const char* z = std::getenv("VOFP_STENCIL_ZCHUNK")) {
+        int v = std::atoi(z);
+        if (v >= 1 && v <= 4096) c->zchunk = v;
+    }
+    c->hdx.assign(g->dx, g->dx + g->nx);
+    c->hdy.assign(g->dy, g->dy + g->ny);
+    c->hdz.assign(g->dz, g->dz + g->nz);
+    vofp_status s;
+    if ((s = c->alloc(&c->dx, g->nx)) || (s = c->alloc(&c->dy, g->ny)) || (s = c->alloc(&c->dz, g->nz))) {
+        vofp_destroy(c);
+        return s;
+    }
+    if (cudaMemcpy(c->dx, g->dx, sizeof(double) * g->nx, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->dy, g->dy, sizeof(double) * g->ny, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->dz, g->dz, sizeof(double) * g->nz, cudaMemcpyHostToDevice) != cudaSuccess) {
+        vofp_destroy(c);
+        return VOFP_ERR_CUDA;
+    }
+    *out = c;
+    return VOFP_OK;
+}
+
+void vofp_destroy(vofp_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    if (c->graph_fp64) cudaGraphExecDestroy(c->graph_fp64);
+    if (c->graph_mixed) cudaGraphExecDestroy(c->graph_mixed);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    for (void* p : c->allocs) cudaFree(p);
+    delete c;
+}
+
+const char* vofp_last_error(const vofp_ctx* c) { return c ? c->err.c_str() : kNullCtx; }
+
+vofp_status vofp_build_operator(vofp_ctx* c, const double* F, const double* ax, const double* ay,
+                                const double* az, const double* vf, const vofp_bc* bc, const vofp_phys* phys) {
+    vofp_status s = check_ctx(c, false);
+    if (s) return s;
+    if (!F || !ax || !ay || !az || !bc || !phys) return invalid(c, "null input");
+    for (int f = 0; f < 6; ++f)
+        if (bc->kind[f] != VOFP_BC_NEUMANN && bc->kind[f] != VOFP_BC_DIRICHLET) return invalid(c, "bad boundary kind");
+    if (!(phys->rho_liquid > 0.0) || !(phys->rho_gas > 0.0) || !(phys->dt > 0.0) || !(phys->merge_threshold >= 0.0) ||
+        phys->merge_threshold > 1.0)
+        return invalid(c, "bad physical parameters");
+    // any change of the operator invalidates the captured loops (group count, pointers)
+    if (c->graph_fp64) {
+        cudaGraphExecDestroy(c->graph_fp64);
+        c->graph_fp64 = nullptr;
+        c->graph_fp64_key = -1;
+    }
+    if (c->graph_mixed) {
+        cudaGraphExecDestroy(c->graph_mixed);
+        c->graph_mixed = nullptr;
+        c->graph_mixed_key = -1;
+    }
+    return vofp::build_operator(c, F, ax, ay, az, vf, bc, phys);
+}
+
+vofp_status vofp_rhs_from_face_velocity(vofp_ctx* c, const double* u, const double* v, const double* w,
+                                        const double* body, double* b) {
+    vofp_status s = check_ctx(c, true);
+    if (s) return s;
+    if (!u || !v || !w || !b) return invalid(c, "null input");
+    if ((s = vofp::rhs(c, u, v, w, body, b))) return s;
+    return fail_cuda(c);
+}
+
+vofp_status vofp_apply(vofp_ctx* c, const double* x, double* y) {
+    vofp_status s = check_ctx(c, true);
+    if (s) return s;
+    if (!x || !y) return invalid(c, "null input");
+    if ((s = vofp::apply_unscaled(c, x, y))) return s;
+    return fail_cuda(c);
+}
+
+vofp_status vofp_residual(vofp_ctx* c, const double* b, const double* x, double* rel) {
+    vofp_status s = check_ctx(c, true);
+    if (s) return s;
+    if (!b || !x || !rel) return invalid(c, "null input");
+    return vofp::residual(c, b, x, rel);
+}
+
+vofp_status vofp_solve(vofp_ctx* c, const double* b, double* x, const vofp_solve_opts* o, vofp_solve_info* info) {
+    vofp_status s = check_ctx(c, true);
+    if (s) return s;
+    if (!b || !x || !o) return invalid(c, "null input");
+    if (!(o->rtol > 0.0) || o->rtol >= 1.0) return invalid(c, "rtol must be in (0, 1)");
+    if (o->mode != VOFP_MODE_FP64 && o->mode != VOFP_MODE_MIXED) return invalid(c, "unknown mode");
+    if (o->precond != VOFP_PRECOND_JACOBI) return invalid(c, "preconditioner not available in this build");
+    if (o->check_every < 0 || (o->check_every % 2) != 0 || o->check_every > 64)
+        return invalid(c, "check_every must be 0 or an even number <= 64");
+    if (o->mode == VOFP_MODE_MIXED && (o->inner_rtol < 0.0 || o->inner_rtol >= 1.0))
+        return invalid(c, "inner_rtol must be in [0, 1)");
+    if (info) std::memset(info, 0, sizeof(*info));
+    return vofp::solve(c, b, x, o, info);
+}
+
+vofp_status vofp_solve_host(vofp_ctx* c, const double* F, const double* ax, const double* ay, const double* az,
+                            const double* vf, const double* u, const double* v, const double* w, const vofp_bc* bc,
+                            const vofp_phys* phys, const vofp_solve_opts* o, double* x_host, vofp_solve_info* info) {
+    vofp_status s = check_ctx(c, false);
+    if (s) return s;
+    if (!F || !ax || !ay || !az || !u || !v || !w || !x_host || !o) return invalid(c, "null input");
+    const vofp::Dims d = c->d;
+    const long long N = d.n;
+    const long long nfx = (long long)(d.nx + 1) * d.ny * d.nz;
+    const long long nfy = (long long)d.nx * (d.ny + 1) * d.nz;
+    const long long nfz = (long long)d.nx * d.ny * (d.nz + 1);
+    const long long total = 4 * N + 2 * (nfx + nfy + nfz);
+    if (!c->dstage) {
+        if ((s = c->alloc(&c->dstage, total))) return s;
+        c->dstage_bytes = sizeof(double) * total;
+    }
+    double* p = c->dstage;
+    double *dF = p, *dvf = p + N, *db = p + 2 * N, *dx = p + 3 * N;
+    double *dax = p + 4 * N, *day = dax + nfx, *daz = day + nfy;
+    double *du = daz + nfz, *dv = du + nfx, *dw = dv + nfy;
+    cudaStream_t st = c->stream;
+    VOFP_CUDA_TRY(c, cudaMemcpyAsync(dF, F, sizeof(double) * N, cudaMemcpyHostToDevice, st));
+    if (vf) VOFP_CUDA_TRY(c, cudaMemcpyAsync(dvf, vf, sizeof(double) * N, cudaMemcpyHostToDevice, st));
+    VOFP_CUDA_TRY(c, cudaMemcpyAsync(dax, ax, sizeof(double) * nfx, cudaMemcpyHostToDevice, st));
+    VOFP_CUDA_TRY(c, cudaMemcpyAsync(day, ay, sizeof(double) * nfy, cudaMemcpyHostToDevice, st));
+    VOFP_CUDA_TRY(c, cudaMemcpyAsync(daz, az, sizeof(double) * nfz, cudaMemcpyHostToDevice, st));
+    VOFP_CUDA_TRY(c, cudaMemcpyAsync(du, u, sizeof(double) * nfx, cudaMemcpyHostToDevice, st));
+    VOFP_CUDA_TRY(c, cudaMemcpyAsync(dv, v, sizeof(double) * nfy, cudaMemcpyHostToDevice, st));
+    VOFP_CUDA_TRY(c, cudaMemcpyAsync(dw, w, sizeof(double) * nfz, cudaMemcpyHostToDevice, st));
+    if ((s = vofp_build_operator(c, dF, dax, day, daz, vf ? dvf : nullptr, bc, phys))) return s;
+    if ((s = vofp_rhs_from_face_velocity(c, du, dv, dw, nullptr, db))) return s;
+    vofp_solve_opts o2 = *o;
+    o2.x0_zero = 1;
+    vofp_status rs = vofp_solve(c, db, dx, &o2, info);
+    if (rs != VOFP_OK && rs != VOFP_ERR_NOT_CONVERGED && rs != VOFP_ERR_BREAKDOWN) return rs;
+    VOFP_CUDA_TRY(c, cudaMemcpyAsync(x_host, dx, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+    VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
+    return rs;
+}
+
+vofp_status vofp_merge_map(vofp_ctx* c, int32_t* master) {
+    vofp_status s = check_ctx(c, true);
+    if (s) return s;
+    if (!master) return invalid(c, "null output");
+    VOFP_CUDA_TRY(c, cudaMemcpyAsync(master, c->root, sizeof(int32_t) * c->d.n, cudaMemcpyDeviceToDevice, c->stream));
+    return VOFP_OK;
+}
+
+vofp_status vofp_get_stats(vofp_ctx* c, vofp_stats* st) {
+    vofp_status s = check_ctx(c, true);
+    if (s) return s;
+    if (!st) return invalid(c, "null output");
+    st->cells = c->d.n;
+    st->unknowns = c->n_unknowns;
+    st->inactive = c->n_inactive;
+    st->merged_cells = c->n_merged;
+    st->groups = c->ngroups;
+    st->device_bytes = (long long)c->bytes;
+    return VOFP_OK;
+}
+
+vofp_status vofp_launch_count(vofp_ctx* c, long long* count) {
+    if (!c || !count) return VOFP_ERR_INVALID_ARG;
+    *count = c->launches;
+    return VOFP_OK;
+}
+
+vofp_status vofp_time_iteration_kernels(vofp_ctx* c, int precision, int reps, float* stencil_ms, float* update_ms) {
+    vofp_status s = check_ctx(c, true);
+    if (s) return s;
+    if ((precision != 64 && precision != 32) || reps <= 0 || !stencil_ms || !update_ms)
+        return invalid(c, "bad arguments");
+    return vofp::time_iteration_kernels(c, precision, reps, stencil_ms, update_ms);
+}
+
+}  // extern "C"

@@ -1,0 +1,234 @@
+// Internal declarations of libvofp: the context, launch helpers and shared device utilities.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/vofp.h"
+
+#define VOFP_CUDA_TRY(ctx, expr)                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (expr);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            (ctx)->set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));       \
+            return e_ == cudaErrorMemoryAllocation ? VOFP_ERR_OOM : VOFP_ERR_CUDA;      \
+        }                                                                               \
+    } while (0)
+
+namespace vofp {
+
+constexpr int kBX = 32;          // stencil tile width (x), one warp
+constexpr int kBY = 8;           // stencil tile height (y)
+constexpr int kRedThreads = 256; // threads of the streaming/reduction kernels
+constexpr int kMaxPartials = 1 << 17;
+
+// Scalars of one CG run, resident in device memory so that the loop needs no host round trip.
+struct CgScalars {
+    double rr;          // r.r of the (scaled) residual over the unknowns
+    double rr0;         // r.r at the start of the current (inner) solve
+    double pq_raw;      // p.t summed over all cells by the stencil kernel
+    double pq_corr;     // merge-group correction to p.Ap
+    double alpha;       // step of the last completed iteration (used by the next stencil pass)
+    double beta;        // direction coefficient for the next stencil pass
+    double bnorm2;      // ||b_hat||^2 (unscaled)
+    double rnorm2;      // last true ||b_hat - A_hat x||^2 (unscaled)
+    double rtol;        // relative tolerance of the (outer) loop
+    double inner_rtol;  // relative reduction of each inner solve (mixed precision)
+    double scale;       // inner right-hand side scale (mixed precision)
+    double inner_target;// relative reduction the current inner solve stops at
+    double ref2;        // squared norm the current loop's tolerance is relative to
+    long long iter;     // iterations of the current loop
+    long long iter_total;
+    long long max_iter;
+    int status;         // vofp_status of the loop
+    int done;           // 1 when the loop has finished
+    int outer;          // refinement steps
+    int timing;         // 1 while the measurement hook runs: breakdowns are not recorded
+};
+
+struct Dims {
+    int nx, ny, nz;
+    long long n;
+    long long plane;     // nx*ny
+};
+
+}  // namespace vofp
+
+struct vofp_ctx {
+    vofp::Dims d{};
+    cudaStream_t stream = nullptr;
+    std::string err;
+    std::vector<double> hdx, hdy, hdz;
+    double *dx = nullptr, *dy = nullptr, *dz = nullptr;
+
+    bool built = false;
+    int bc[6] = {0, 0, 0, 0, 0, 0};
+    vofp_phys phys{};
+    bool dirichlet = false;
+    double* nflux[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool has_nflux[6] = {false, false, false, false, false, false};
+
+    // operator (FP64, unscaled): T of each cell's +face, full diagonal of the unmerged operator
+    double *Tx = nullptr, *Ty = nullptr, *Tz = nullptr, *diag = nullptr;
+    // effective apertures (faces of cells without an unknown closed)
+    double *axe = nullptr, *aye = nullptr, *aze = nullptr;
+    // symmetric scaling: s = diag(A_hat)^-1/2 of the cell's group, sq = 1/s (0 without unknown)
+    double *s = nullptr, *sq = nullptr;
+    double *Txs = nullptr, *Tys = nullptr, *Tzs = nullptr;     // s_L T s_R
+    float *Txf = nullptr, *Tyf = nullptr, *Tzf = nullptr;      // FP32 copies
+    uint32_t* slave_bits = nullptr;   // bit c set when c belongs to another cell's group
+    int32_t* root = nullptr;          // group root per cell, -1 without unknown
+    uint8_t* inactive = nullptr;
+    // merge groups with more than one cell: cells of group g are gcells[gptr[g] .. gptr[g+1]),
+    // master first; gcorr[g] = s_m^2 * sum of the cells' diagonals - |G|
+    int ngroups = 0;
+    int *gptr = nullptr, *gcells = nullptr;
+    double* gcorr = nullptr;
+    long long n_unknowns = 0, n_inactive = 0, n_merged = 0;
+
+    // Krylov workspace
+    double *xt = nullptr, *r = nullptr, *p0 = nullptr, *p1 = nullptr, *q = nullptr, *bt = nullptr;
+    float *rf = nullptr, *pf0 = nullptr, *pf1 = nullptr, *qf = nullptr, *xf = nullptr;
+    double* partials = nullptr;       // block partial sums
+    unsigned int* counters = nullptr; // last-block tickets
+    vofp::CgScalars* sc = nullptr;
+    double* work = nullptr;           // apply / residual scratch (cells)
+    double* dstage = nullptr;         // host-call staging (inputs)
+    size_t dstage_bytes = 0;
+
+    // CUDA graphs of the solve loops, keyed by configuration
+    cudaGraphExec_t graph_fp64 = nullptr;
+    int graph_fp64_key = -1;
+    cudaGraphExec_t graph_mixed = nullptr;
+    int graph_mixed_key = -1;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+    size_t bytes = 0;
+    std::vector<void*> allocs;
+    long long launches = 0;           // kernels launched (graph bodies counted per execution)
+    int zchunk = 16;                  // planes marched by one stencil block
+
+    void set_error(const std::string& m) { err = m; }
+    template <typename T>
+    vofp_status alloc(T** p, size_t count) {
+        void* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, sizeof(T) * (count ? count : 1));
+        if (e != cudaSuccess) {
+            set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+            return VOFP_ERR_OOM;
+        }
+        allocs.push_back(q);
+        bytes += sizeof(T) * count;
+        *p = reinterpret_cast<T*>(q);
+        return VOFP_OK;
+    }
+};
+
+namespace vofp {
+
+// ---- launches implemented in the .cu files -------------------------------------------------
+vofp_status build_operator(vofp_ctx* c, const double* F, const double* ax, const double* ay,
+                           const double* az, const double* vf, const vofp_bc* bc,
+                           const vofp_phys* phys);
+vofp_status rhs(vofp_ctx* c, const double* u, const double* v, const double* w,
+                const double* body, double* b);
+vofp_status apply_unscaled(vofp_ctx* c, const double* x, double* y);
+vofp_status residual(vofp_ctx* c, const double* b, const double* x, double* rel);
+vofp_status solve(vofp_ctx* c, const double* b, double* x, const vofp_solve_opts* o,
+                  vofp_solve_info* info);
+vofp_status time_iteration_kernels(vofp_ctx* c, int precision, int reps, float* st, float* up);
+
+// group helpers (vofp_assemble.cu)
+void launch_group_expand(vofp_ctx* c, double* v);
+void launch_group_fold(vofp_ctx* c, double* v, bool zero_slaves);
+
+// stencil helpers (vofp_stencil.cu)
+// t = A x on the full grid with the unscaled coefficients and explicit diagonal
+void launch_stencil_apply_unscaled(vofp_ctx* c, const double* x, double* t);
+// t = (unit-diagonal scaled operator) x, FP64
+void launch_stencil_apply_scaled(vofp_ctx* c, const double* x, double* t);
+// merge-group patch after a scaled stencil: q_m = sum t + corr p_m, expanded; p.Ap correction
+template <typename V>
+void launch_group_patch(vofp_ctx* c, V* t, const V* p, bool dot_correction);
+
+// Launch a kernel on stream s and count it.
+template <typename... KArgs, typename... Args>
+inline void launch(vofp_ctx* c, void (*k)(KArgs...), dim3 g, dim3 b, cudaStream_t s, Args... args) {
+    k<<<g, b, 0, s>>>(static_cast<KArgs>(args)...);
+    ++c->launches;
+}
+
+inline int ceil_div(long long a, long long b) { return int((a + b - 1) / b); }
+inline int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+}  // namespace vofp
+
+// ---- device utilities ------------------------------------------------------------------------
+namespace vofp {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum of v over the block, valid in thread 0.  Fixed order: deterministic.
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) s += sh[w];
+    }
+    return s;
+}
+
+// Write this block's partial and, in the block that finishes last, reduce all partials in
+// index order.  Returns true (in thread 0 of the last block) with *total set.
+// The ticket counter is reset by the last block for the next launch.
+__device__ __forceinline__ bool last_block_reduce(double part, double* partials,
+                                                  unsigned int* counter, int nblocks,
+                                                  double* total, double* sh) {
+    __shared__ bool is_last;
+    const int b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    if (threadIdx.x + blockDim.x * threadIdx.y == 0) {
+        partials[b] = part;
+        __threadfence();
+        unsigned int t = atomicAdd(counter, 1u);
+        is_last = (t == (unsigned int)(nblocks - 1));
+    }
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int nt = blockDim.x * blockDim.y;
+    double s = 0.0;
+    if (tid < 32) {
+        for (int i = tid; i < nblocks; i += 32) s += *((volatile double*)&partials[i]);
+        s = warp_sum(s);
+    }
+    if (tid == 0) {
+        *total = s;
+        *counter = 0u;
+    }
+    (void)nt;
+    (void)sh;
+    return tid == 0;
+}
+
+}  // namespace vofp

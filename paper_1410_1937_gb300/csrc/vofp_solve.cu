@@ -1,0 +1,639 @@
+// Solve orchestration: the preconditioned CG loop of Sec. 1 as a CUDA graph with a device-side
+// WHILE condition (no host round trip per iteration), FP64 or mixed-precision iterative
+// refinement (FP64 outer residual and solution update, FP32 inner CG with FP64-accurate dots).
+#include <algorithm>
+#include <cmath>
+
+#include "vofp_kernels.cuh"
+
+namespace vofp {
+namespace {
+
+constexpr int kNT = kRedThreads;
+
+int stream_grid(long long n) {
+    long long b = (n + kNT - 1) / kNT;
+    long long cap = (long long)num_sms() * 8;
+    return int(std::max(1LL, std::min(b, cap)));
+}
+
+dim3 stencil_grid(const vofp_ctx* c) {
+    return dim3(ceil_div(c->d.nx, kBX), ceil_div(c->d.ny, kBY), ceil_div(c->d.nz, c->zchunk));
+}
+
+// register prefetch depth of the stencil: deeper for FP32, whose planes carry half the bytes
+template <typename V>
+constexpr int stencil_pf() {
+    return sizeof(V) == 8 ? 1 : 2;
+}
+
+// x_t[c] = x0[root(c)] * sq[c] (scaled initial guess, expanded over groups; 0 without unknown)
+__global__ void k_init_x(long long n, const double* __restrict__ x0, const int32_t* __restrict__ root,
+                         const double* __restrict__ sq, double* __restrict__ xt, int zero) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const int32_t r = root[c];
+        xt[c] = (zero || r < 0) ? 0.0 : x0[r] * sq[c];
+    }
+}
+
+// work = b; the group fold follows.  bt = s * b_hat (after the fold)
+__global__ void k_copy(long long n, const double* __restrict__ a, double* __restrict__ b) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+        b[c] = a[c];
+}
+
+// sums over unknowns (root[c] == c) of b_hat and |b_hat|, and of b_hat^2
+__global__ void k_bsums(long long n, const double* __restrict__ bh, const int32_t* __restrict__ root,
+                        double* __restrict__ partials, unsigned int* __restrict__ counter, double* out3) {
+    __shared__ double sh[32];
+    double s = 0.0, a = 0.0, q = 0.0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        if (root[c] != (int32_t)c) continue;
+        const double v = bh[c];
+        s += v;
+        a += fabs(v);
+        q = fma(v, v, q);
+    }
+    double t;
+    if (grid_reduce(s, partials, counter, sh, &t)) out3[0] = t;
+    __syncthreads();
+    if (grid_reduce(a, partials + kMaxPartials / 4, counter + 1, sh, &t)) out3[1] = t;
+    __syncthreads();
+    if (grid_reduce(q, partials + kMaxPartials / 2, counter + 2, sh, &t)) out3[2] = t;
+}
+
+// b_hat -= shift at unknowns (all cells of a group hold the group's value)
+__global__ void k_shift(long long n, double* __restrict__ bh, const int32_t* __restrict__ root, const double* shift) {
+    const double sft = *shift;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+        if (root[c] >= 0) bh[c] -= sft;
+}
+
+__global__ void k_scale(long long n, const double* __restrict__ s, const double* __restrict__ a, double* __restrict__ out) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+        out[c] = s[c] * a[c];
+}
+
+// r = bt - q over all cells; rr = r.r over unknowns; rn2 = sum (r sq)^2 over unknowns.
+// Starts a loop: alpha = beta = 0, iteration count 0.
+__global__ void k_init_residual(long long n, const double* __restrict__ bt, const double* __restrict__ q,
+                                const double* __restrict__ sq, const uint32_t* __restrict__ bits,
+                                double* __restrict__ r, CgScalars* sc, double* __restrict__ partials,
+                                unsigned int* __restrict__ counter) {
+    __shared__ double sh[32];
+    double a = 0.0, b = 0.0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const double v = bt[c] - q[c];
+        r[c] = v;
+        if (!is_slave(bits, c)) {
+            a = fma(v, v, a);
+            const double u = v * sq[c];
+            b = fma(u, u, b);
+        }
+    }
+    double t;
+    if (grid_reduce(a, partials, counter, sh, &t)) {
+        sc->rr = t;
+        sc->rr0 = t;
+    }
+    __syncthreads();
+    if (grid_reduce(b, partials + kMaxPartials / 2, counter + 1, sh, &t)) sc->rnorm2 = t;
+}
+
+// pending x update of the last iteration, then the unscaled solution x = s * x_t
+__global__ void k_finalize_x(long long n, double* __restrict__ xt, const double* __restrict__ p,
+                             const double* __restrict__ s, const CgScalars* sc, double* __restrict__ xout) {
+    const double alpha = sc->alpha;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const double v = fma(alpha, p[c], xt[c]);
+        xt[c] = v;
+        xout[c] = s[c] * v;
+    }
+}
+
+// expand: out[c] = x[root(c)], 0 without unknown
+__global__ void k_expand_gather(long long n, const double* __restrict__ x, const int32_t* __restrict__ root,
+                                double* __restrict__ out) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const int32_t r = root[c];
+        out[c] = r < 0 ? 0.0 : x[r];
+    }
+}
+
+// ||b_hat - y||^2 and ||b_hat||^2 over unknowns (b_hat and y folded: group value at the master)
+__global__ void k_resid_norms(long long n, const double* __restrict__ bh, const double* __restrict__ y,
+                              const int32_t* __restrict__ root, double* __restrict__ partials,
+                              unsigned int* __restrict__ counter, double* out2) {
+    __shared__ double sh[32];
+    double a = 0.0, b = 0.0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        if (root[c] != (int32_t)c) continue;
+        const double rv = bh[c] - y[c];
+        a = fma(rv, rv, a);
+        b = fma(bh[c], bh[c], b);
+    }
+    double t;
+    if (grid_reduce(a, partials, counter, sh, &t)) out2[0] = t;
+    __syncthreads();
+    if (grid_reduce(b, partials + kMaxPartials / 2, counter + 1, sh, &t)) out2[1] = t;
+}
+
+// mean over unknowns of x, subtracted at every cell with an unknown (all-Neumann problems)
+__global__ void k_sum_unknowns(long long n, const double* __restrict__ x, const int32_t* __restrict__ root,
+                               double* __restrict__ partials, unsigned int* __restrict__ counter, double* out) {
+    __shared__ double sh[32];
+    double a = 0.0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+        if (root[c] == (int32_t)c) a += x[c];
+    double t;
+    if (grid_reduce(a, partials, counter, sh, &t)) *out = t;
+}
+
+__global__ void k_set_pq_inf(CgScalars* sc, int timing) {
+    sc->pq_raw = INFINITY;
+    sc->pq_corr = 0.0;
+    sc->alpha = 0.0;
+    sc->beta = 0.0;
+    sc->timing = timing;
+}
+
+// ---- mixed precision ----------------------------------------------------------------------
+// Outer step of iterative refinement: r = bt - q (q = scaled A x_t, FP64), true residual check,
+// and the FP32 right-hand side of the next inner solve, normalised to unit norm.
+__global__ void k_outer_residual(long long n, const double* __restrict__ bt, const double* __restrict__ q,
+                                 const double* __restrict__ sq, const uint32_t* __restrict__ bits,
+                                 double* __restrict__ r, CgScalars* sc, double* __restrict__ partials,
+                                 unsigned int* __restrict__ counter, cudaGraphConditionalHandle h_outer,
+                                 cudaGraphConditionalHandle h_inner) {
+    __shared__ double sh[32];
+    double a = 0.0, b = 0.0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const double v = bt[c] - q[c];
+        r[c] = v;
+        if (!is_slave(bits, c)) {
+            a = fma(v, v, a);
+            const double u = v * sq[c];
+            b = fma(u, u, b);
+        }
+    }
+    double t;
+    if (grid_reduce(a, partials, counter, sh, &t)) sc->rr0 = t;   // scaled residual norm^2
+    __syncthreads();
+    if (grid_reduce(b, partials + kMaxPartials / 2, counter + 1, sh, &t)) {
+        sc->rnorm2 = t;
+        bool stop = false;
+        if (!isfinite(t) || sc->status != VOFP_OK) {
+            if (sc->status == VOFP_OK) sc->status = VOFP_ERR_BREAKDOWN;
+            stop = true;
+        } else if (t <= sc->rtol * sc->rtol * sc->ref2) {
+            stop = true;
+        } else if (sc->iter_total >= sc->max_iter || sc->outer >= 200) {
+            sc->status = VOFP_ERR_NOT_CONVERGED;
+            stop = true;
+        }
+        sc->done = stop ? 1 : 0;
+        if (!stop) sc->outer += 1;
+        cudaGraphSetConditional(h_outer, stop ? 0u : 1u);
+        cudaGraphSetConditional(h_inner, stop ? 0u : 1u);
+    }
+}
+
+// inner start: rf = r / ||r||, x_f = 0, p_f(old) = 0, rr = rf.rf (Dot2-accumulated)
+__global__ void k_inner_prep(long long n, const double* __restrict__ r, const uint32_t* __restrict__ bits,
+                             float* __restrict__ rf, float* __restrict__ xf, float* __restrict__ pf0,
+                             CgScalars* sc, double* __restrict__ partials, unsigned int* __restrict__ counter) {
+    __shared__ double sh[32];
+    const double rr = sc->rr0;
+    const double inv = (rr > 0.0 && !sc->done) ? 1.0 / sqrt(rr) : 0.0;
+    AccF2 acc;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const float v = (float)(r[c] * inv);
+        rf[c] = v;
+        xf[c] = 0.0f;
+        pf0[c] = 0.0f;
+        if (!is_slave(bits, c)) acc.add(v, v);
+    }
+    double t;
+    if (grid_reduce(acc.value(), partials, counter, sh, &t)) {
+        sc->scale = (rr > 0.0 && !sc->done) ? sqrt(rr) : 0.0;
+        // the last refinement step only needs the reduction that reaches rtol (with margin)
+        const double need = sc->rnorm2 > 0.0 ? 0.3 * sc->rtol * sqrt(sc->ref2 / sc->rnorm2) : 1.0;
+        sc->inner_target = fmax(sc->inner_rtol, fmin(need, 0.5));
+        sc->rr = t;
+        sc->alpha = 0.0;
+        sc->beta = 0.0;
+        sc->iter = 0;
+        const double rr0 = t;
+        sc->rr0 = rr0;
+    }
+}
+
+// end of an inner solve: x_f += alpha p_f (pending), x_t += ||r|| * x_f in FP64
+__global__ void k_inner_finish(long long n, float* __restrict__ xf, const float* __restrict__ pf,
+                               double* __restrict__ xt, const CgScalars* sc) {
+    const float alpha = (float)sc->alpha;
+    const double scale = sc->scale;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const float v = __fmaf_rn(alpha, pf[c], xf[c]);
+        xt[c] = fma(scale, (double)v, xt[c]);
+    }
+}
+
+}  // namespace
+
+// ---- launch helpers --------------------------------------------------------------------------
+
+void launch_stencil_apply_unscaled(vofp_ctx* c, const double* x, double* t) {
+    launch(c, k_stencil<double, ST_APPLY_UNSCALED, 1>, stencil_grid(c), dim3(kBX, kBY), c->stream, 
+        c->d, c->zchunk, c->Tx, c->Ty, c->Tz, c->diag, x, nullptr, nullptr, nullptr, t, c->sc, c->partials, c->counters);
+}
+
+void launch_stencil_apply_scaled(vofp_ctx* c, const double* x, double* t) {
+    launch(c, k_stencil<double, ST_APPLY_SCALED, 1>, stencil_grid(c), dim3(kBX, kBY), c->stream, 
+        c->d, c->zchunk, c->Txs, c->Tys, c->Tzs, nullptr, x, nullptr, nullptr, nullptr, t, c->sc, c->partials, c->counters);
+}
+
+template <typename V>
+void launch_group_patch(vofp_ctx* c, V* t, const V* p, bool dot) {
+    if (c->ngroups == 0) return;
+    launch(c, k_group_patch<V>, ceil_div(c->ngroups, kNT), kNT, c->stream, c->ngroups, c->gptr, c->gcells, c->gcorr, t, p,
+                                                                        dot ? 1 : 0, c->sc, c->partials, c->counters);
+}
+template void launch_group_patch<double>(vofp_ctx*, double*, const double*, bool);
+template void launch_group_patch<float>(vofp_ctx*, float*, const float*, bool);
+
+namespace {
+
+// one CG iteration on stream st (FP64 or FP32), reading p_old from `po` and writing `pn`
+template <typename V>
+void launch_cg_iteration(vofp_ctx* c, cudaStream_t st, V* r, V* po, V* pn, V* xv, V* q,
+                         const V* Tx, const V* Ty, const V* Tz, bool inner,
+                         cudaGraphConditionalHandle h, int use_h) {
+    launch(c, k_stencil<V, ST_CG, stencil_pf<V>()>, stencil_grid(c), dim3(kBX, kBY), st, c->d, c->zchunk, Tx, Ty, Tz, nullptr, r, po, pn, xv, q,
+                                                                       c->sc, c->partials, c->counters);
+    if (c->ngroups > 0)
+        launch(c, k_group_patch<V>, ceil_div(c->ngroups, kNT), kNT, st, c->ngroups, c->gptr, c->gcells, c->gcorr, q, pn,
+                                                                    1, c->sc, c->partials, c->counters);
+    if (inner)
+        launch(c, k_cg_update<V, true>, stream_grid(c->d.n / (sizeof(V) == 8 ? 2 : 4) + 1), kNT, st, 
+            c->d.n, r, q, c->slave_bits, c->sc, c->partials, c->counters, h, use_h);
+    else
+        launch(c, k_cg_update<V, false>, stream_grid(c->d.n / (sizeof(V) == 8 ? 2 : 4) + 1), kNT, st, 
+            c->d.n, r, q, c->slave_bits, c->sc, c->partials, c->counters, h, use_h);
+}
+
+vofp_status ensure_workspace(vofp_ctx* c) {
+    if (c->xt) return VOFP_OK;
+    const long long N = c->d.n;
+    vofp_status s;
+    if ((s = c->alloc(&c->xt, N)) || (s = c->alloc(&c->r, N)) || (s = c->alloc(&c->p0, N)) ||
+        (s = c->alloc(&c->p1, N)) || (s = c->alloc(&c->q, N)) || (s = c->alloc(&c->bt, N)) ||
+        (s = c->alloc(&c->rf, N)) || (s = c->alloc(&c->pf0, N)) || (s = c->alloc(&c->pf1, N)) ||
+        (s = c->alloc(&c->qf, N)) || (s = c->alloc(&c->xf, N)))
+        return s;
+    VOFP_CUDA_TRY(c, cudaEventCreate(&c->ev0));
+    VOFP_CUDA_TRY(c, cudaEventCreate(&c->ev1));
+    return VOFP_OK;
+}
+
+// capture `fn` (launches on stream cs) into the body graph of a WHILE node
+template <typename F>
+vofp_status capture_into(vofp_ctx* c, cudaStream_t cs, cudaGraph_t body, F fn) {
+    VOFP_CUDA_TRY(c, cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    fn();
+    cudaGraph_t out = body;
+    VOFP_CUDA_TRY(c, cudaStreamEndCapture(cs, &out));
+    return VOFP_OK;
+}
+
+vofp_status add_while(vofp_ctx* c, cudaGraph_t g, cudaGraphConditionalHandle* h, cudaGraph_t* body,
+                      const cudaGraphNode_t* deps, size_t ndeps, cudaGraphNode_t* node, unsigned int dflt) {
+    VOFP_CUDA_TRY(c, cudaGraphConditionalHandleCreate(h, g, dflt, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams prm = {};
+    prm.type = cudaGraphNodeTypeConditional;
+    prm.conditional.handle = *h;
+    prm.conditional.type = cudaGraphCondTypeWhile;
+    prm.conditional.size = 1;
+    VOFP_CUDA_TRY(c, cudaGraphAddNode(node, g, deps, nullptr, ndeps, &prm));
+    *body = prm.conditional.phGraph_out[0];
+    return VOFP_OK;
+}
+
+// FP64 loop: WHILE { U x [stencil, patch, update]; true-residual check }
+vofp_status build_graph_fp64(vofp_ctx* c, int U) {
+    if (c->graph_fp64 && c->graph_fp64_key == U) return VOFP_OK;
+    const long long launches0 = c->launches;
+    if (c->graph_fp64) {
+        cudaGraphExecDestroy(c->graph_fp64);
+        c->graph_fp64 = nullptr;
+    }
+    cudaStream_t cs;
+    VOFP_CUDA_TRY(c, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g;
+    VOFP_CUDA_TRY(c, cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    cudaGraph_t body;
+    cudaGraphNode_t node;
+    vofp_status s = add_while(c, g, &h, &body, nullptr, 0, &node, 1u);
+    if (s) return s;
+    s = capture_into(c, cs, body, [&]() {
+        for (int u = 0; u < U; ++u) {
+            double* po = (u % 2 == 0) ? c->p0 : c->p1;
+            double* pn = (u % 2 == 0) ? c->p1 : c->p0;
+            launch_cg_iteration<double>(c, cs, c->r, po, pn, c->xt, c->q, c->Txs, c->Tys, c->Tzs, false, h, 0);
+        }
+        launch(c, k_cg_check<double>, stream_grid(c->d.n), kNT, cs, c->d.n, c->r, c->sq, c->slave_bits, c->sc,
+                                                                 c->partials, c->counters, h, 1);
+    });
+    if (s) return s;
+    VOFP_CUDA_TRY(c, cudaGraphInstantiate(&c->graph_fp64, g, 0));
+    cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    c->graph_fp64_key = U;
+    c->launches = launches0;
+    return VOFP_OK;
+}
+
+// Mixed: WHILE_outer { FP64 apply + patch + outer residual (sets both conditions); inner prep;
+//                      WHILE_inner { U x [FP32 stencil, patch, update(inner stop)] }; finish }
+vofp_status build_graph_mixed(vofp_ctx* c, int U) {
+    if (c->graph_mixed && c->graph_mixed_key == U) return VOFP_OK;
+    const long long launches0 = c->launches;
+    if (c->graph_mixed) {
+        cudaGraphExecDestroy(c->graph_mixed);
+        c->graph_mixed = nullptr;
+    }
+    cudaStream_t cs;
+    VOFP_CUDA_TRY(c, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g;
+    VOFP_CUDA_TRY(c, cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle ho, hi;
+    cudaGraph_t obody, ibody;
+    cudaGraphNode_t onode, inode;
+    vofp_status s = add_while(c, g, &ho, &obody, nullptr, 0, &onode, 1u);
+    if (s) return s;
+    // outer body, part 1: residual and inner preparation (captured), then the inner WHILE node
+    cudaGraphNode_t last = nullptr;
+    VOFP_CUDA_TRY(c, cudaGraphConditionalHandleCreate(&hi, obody, 1u, cudaGraphCondAssignDefault));
+    VOFP_CUDA_TRY(c, cudaStreamBeginCaptureToGraph(cs, obody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    launch(c, k_stencil<double, ST_APPLY_SCALED, 1>, stencil_grid(c), dim3(kBX, kBY), cs, 
+        c->d, c->zchunk, c->Txs, c->Tys, c->Tzs, nullptr, c->xt, nullptr, nullptr, nullptr, c->q, c->sc, c->partials, c->counters);
+    if (c->ngroups > 0)
+        launch(c, k_group_patch<double>, ceil_div(c->ngroups, kNT), kNT, cs, c->ngroups, c->gptr, c->gcells, c->gcorr, c->q,
+                                                                         c->xt, 0, c->sc, c->partials, c->counters);
+    launch(c, k_outer_residual, stream_grid(c->d.n), kNT, cs, c->d.n, c->bt, c->q, c->sq, c->slave_bits, c->r, c->sc,
+                                                          c->partials, c->counters, ho, hi);
+    launch(c, k_inner_prep, stream_grid(c->d.n), kNT, cs, c->d.n, c->r, c->slave_bits, c->rf, c->xf, c->pf0, c->sc,
+                                                      c->partials, c->counters);
+    {
+        cudaGraph_t tmp = obody;
+        VOFP_CUDA_TRY(c, cudaStreamEndCapture(cs, &tmp));
+    }
+    // the node captured last in the outer body is the sink: find it (the graph is a chain)
+    {
+        size_t nn = 0;
+        VOFP_CUDA_TRY(c, cudaGraphGetNodes(obody, nullptr, &nn));
+        std::vector<cudaGraphNode_t> nodes(nn);
+        VOFP_CUDA_TRY(c, cudaGraphGetNodes(obody, nodes.data(), &nn));
+        for (auto nd : nodes) {
+            size_t no = 0;
+            VOFP_CUDA_TRY(c, cudaGraphNodeGetDependentNodes(nd, nullptr, nullptr, &no));
+            if (no == 0) last = nd;
+        }
+    }
+    cudaGraphNodeParams prm = {};
+    prm.type = cudaGraphNodeTypeConditional;
+    prm.conditional.handle = hi;
+    prm.conditional.type = cudaGraphCondTypeWhile;
+    prm.conditional.size = 1;
+    VOFP_CUDA_TRY(c, cudaGraphAddNode(&inode, obody, &last, nullptr, 1, &prm));
+    ibody = prm.conditional.phGraph_out[0];
+    s = capture_into(c, cs, ibody, [&]() {
+        for (int u = 0; u < U; ++u) {
+            float* po = (u % 2 == 0) ? c->pf0 : c->pf1;
+            float* pn = (u % 2 == 0) ? c->pf1 : c->pf0;
+            launch_cg_iteration<float>(c, cs, c->rf, po, pn, c->xf, c->qf, c->Txf, c->Tyf, c->Tzf, true, hi, 1);
+        }
+    });
+    if (s) return s;
+    // outer body, part 2: fold the inner solution into x_t (FP64)
+    VOFP_CUDA_TRY(c, cudaStreamBeginCaptureToGraph(cs, obody, &inode, nullptr, 1, cudaStreamCaptureModeRelaxed));
+    launch(c, k_inner_finish, stream_grid(c->d.n), kNT, cs, c->d.n, c->xf, c->pf0, c->xt, c->sc);
+    {
+        cudaGraph_t tmp = obody;
+        VOFP_CUDA_TRY(c, cudaStreamEndCapture(cs, &tmp));
+    }
+    VOFP_CUDA_TRY(c, cudaGraphInstantiate(&c->graph_mixed, g, 0));
+    cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    c->graph_mixed_key = U;
+    c->launches = launches0;
+    return VOFP_OK;
+}
+
+// b_hat (expanded over groups) into c->work, its scaled copy into c->bt; returns sums over
+// unknowns of b_hat, |b_hat|, b_hat^2 (host) after optional Neumann projection.
+vofp_status prepare_rhs(vofp_ctx* c, const double* b, double* sums3) {
+    const long long N = c->d.n;
+    cudaStream_t st = c->stream;
+    launch(c, k_copy, stream_grid(N), kNT, st, N, b, c->work);
+    launch_group_fold(c, c->work, false);
+    double* d3 = c->partials + kMaxPartials - 8;
+    launch(c, k_bsums, stream_grid(N), kNT, st, N, c->work, c->root, c->partials, c->counters, d3);
+    VOFP_CUDA_TRY(c, cudaMemcpyAsync(sums3, d3, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
+    if (!c->dirichlet) {
+        // all-Neumann: A_hat 1 = 0, so b_hat must sum to zero (integral form, Sec. 2.3)
+        if (std::fabs(sums3[0]) > 1e-12 * std::max(sums3[1], 1e-300)) {
+            c->set_error("all-Neumann problem: sum of b_hat is not zero");
+            return VOFP_ERR_INCOMPATIBLE_RHS;
+        }
+        double shift = c->n_unknowns > 0 ? sums3[0] / double(c->n_unknowns) : 0.0;
+        VOFP_CUDA_TRY(c, cudaMemcpyAsync(d3 + 4, &shift, sizeof(double), cudaMemcpyHostToDevice, st));
+        launch(c, k_shift, stream_grid(N), kNT, st, N, c->work, c->root, d3 + 4);
+        launch(c, k_bsums, stream_grid(N), kNT, st, N, c->work, c->root, c->partials, c->counters, d3);
+        VOFP_CUDA_TRY(c, cudaMemcpyAsync(sums3, d3, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
+    }
+    launch(c, k_scale, stream_grid(N), kNT, st, N, c->s, c->work, c->bt);
+    return VOFP_OK;
+}
+
+}  // namespace
+
+vofp_status apply_unscaled(vofp_ctx* c, const double* x, double* y) {
+    const long long N = c->d.n;
+    launch(c, k_expand_gather, stream_grid(N), kNT, c->stream, N, x, c->root, c->work);
+    launch_stencil_apply_unscaled(c, c->work, y);
+    launch_group_fold(c, y, true);
+    VOFP_CUDA_TRY(c, cudaGetLastError());
+    return VOFP_OK;
+}
+
+// rel = ||b_hat - A_hat x|| / ||b_hat|| with the unscaled operator (x read at masters)
+vofp_status residual(vofp_ctx* c, const double* b, const double* x, double* rel) {
+    vofp_status s = ensure_workspace(c);
+    if (s) return s;
+    const long long N = c->d.n;
+    cudaStream_t st = c->stream;
+    launch(c, k_copy, stream_grid(N), kNT, st, N, b, c->q);
+    launch_group_fold(c, c->q, true);
+    launch(c, k_expand_gather, stream_grid(N), kNT, st, N, x, c->root, c->work);
+    launch_stencil_apply_unscaled(c, c->work, c->p1);
+    launch_group_fold(c, c->p1, true);
+    double* d2 = c->partials + kMaxPartials - 16;
+    launch(c, k_resid_norms, stream_grid(N), kNT, st, N, c->q, c->p1, c->root, c->partials, c->counters, d2);
+    double h[2];
+    VOFP_CUDA_TRY(c, cudaMemcpyAsync(h, d2, sizeof(h), cudaMemcpyDeviceToHost, st));
+    VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
+    *rel = h[1] > 0.0 ? std::sqrt(h[0] / h[1]) : std::sqrt(h[0]);
+    return VOFP_OK;
+}
+
+vofp_status solve(vofp_ctx* c, const double* b, double* x, const vofp_solve_opts* o, vofp_solve_info* info) {
+    vofp_status s = ensure_workspace(c);
+    if (s) return s;
+    const long long N = c->d.n;
+    cudaStream_t st = c->stream;
+    const int U = o->check_every > 0 ? o->check_every : 8;
+    VOFP_CUDA_TRY(c, cudaEventRecord(c->ev0, st));
+    double sums[3];
+    if ((s = prepare_rhs(c, b, sums))) return s;
+    // scaled initial guess, r = bt - (S A S) x_t
+    launch(c, k_init_x, stream_grid(N), kNT, st, N, x, c->root, c->sq, c->xt, o->x0_zero);
+    launch_stencil_apply_scaled(c, c->xt, c->q);
+    launch_group_patch<double>(c, c->q, c->xt, false);
+    CgScalars h{};
+    h.status = VOFP_OK;
+    h.rtol = o->rtol;
+    h.inner_rtol = o->inner_rtol > 0 ? o->inner_rtol : 1e-3;
+    h.max_iter = o->max_iter > 0 ? o->max_iter : 100000;
+    h.bnorm2 = sums[2];
+    h.ref2 = sums[2];
+    VOFP_CUDA_TRY(c, cudaMemcpyAsync(c->sc, &h, sizeof(h), cudaMemcpyHostToDevice, st));
+    launch(c, k_init_residual, stream_grid(N), kNT, st, N, c->bt, c->q, c->sq, c->slave_bits, c->r, c->sc, c->partials,
+                                                     c->counters);
+    VOFP_CUDA_TRY(c, cudaMemsetAsync(c->p0, 0, sizeof(double) * N, st));
+    VOFP_CUDA_TRY(c, cudaMemcpyAsync(&h, c->sc, sizeof(h), cudaMemcpyDeviceToHost, st));
+    VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
+    if (!std::isfinite(h.rnorm2) || !std::isfinite(h.ref2) || !std::isfinite(h.rr)) {
+        // a non-finite right-hand side or initial guess: report, leave x as the scaled guess
+        launch(c, k_finalize_x, stream_grid(N), kNT, st, N, c->xt, c->p0, c->s, (const CgScalars*)c->sc, x);
+        VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
+        if (info) {
+            info->status = VOFP_ERR_BREAKDOWN;
+            info->rel_residual = NAN;
+        }
+        c->set_error("non-finite right-hand side or initial residual");
+        return VOFP_ERR_BREAKDOWN;
+    }
+    const bool converged0 = !(h.rnorm2 > o->rtol * o->rtol * h.ref2);
+    if (o->mode == VOFP_MODE_MIXED) {
+        if ((s = build_graph_mixed(c, U))) return s;
+        if (!converged0) VOFP_CUDA_TRY(c, cudaGraphLaunch(c->graph_mixed, st));
+        // the mixed loop folds every inner solution into x_t itself; no pending step
+        launch(c, k_set_pq_inf, 1, 1, st, c->sc, 0);
+        launch(c, k_finalize_x, stream_grid(N), kNT, st, N, c->xt, c->p0, c->s, c->sc, x);
+    } else {
+        if ((s = build_graph_fp64(c, U))) return s;
+        if (!converged0) VOFP_CUDA_TRY(c, cudaGraphLaunch(c->graph_fp64, st));
+        launch(c, k_finalize_x, stream_grid(N), kNT, st, N, c->xt, c->p0, c->s, c->sc, x);
+    }
+    if (!c->dirichlet) {
+        double* d1 = c->partials + kMaxPartials - 24;
+        launch(c, k_sum_unknowns, stream_grid(N), kNT, st, N, x, c->root, c->partials, c->counters, d1);
+        double tot = 0.0;
+        VOFP_CUDA_TRY(c, cudaMemcpyAsync(&tot, d1, sizeof(double), cudaMemcpyDeviceToHost, st));
+        VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
+        double mean = c->n_unknowns > 0 ? tot / double(c->n_unknowns) : 0.0;
+        VOFP_CUDA_TRY(c, cudaMemcpyAsync(d1 + 2, &mean, sizeof(double), cudaMemcpyHostToDevice, st));
+        launch(c, k_shift, stream_grid(N), kNT, st, N, x, c->root, d1 + 2);
+    }
+    VOFP_CUDA_TRY(c, cudaEventRecord(c->ev1, st));
+    VOFP_CUDA_TRY(c, cudaMemcpyAsync(&h, c->sc, sizeof(h), cudaMemcpyDeviceToHost, st));
+    VOFP_CUDA_TRY(c, cudaGetLastError());
+    double rel = 0.0;
+    if ((s = residual(c, b, x, &rel))) return s;
+    float ms = 0.0f;
+    VOFP_CUDA_TRY(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    if (!converged0) {
+        // kernels executed by the graph: whole bodies of U iterations
+        const long long g = c->ngroups > 0 ? 1 : 0;
+        if (o->mode == VOFP_MODE_MIXED)
+            c->launches += (long long)(h.outer + 1) * (4 + g) + h.iter_total * (2 + g);
+        else
+            c->launches += (h.iter_total / U) * (U * (2 + g) + 1);
+    }
+    vofp_status result = (vofp_status)h.status;
+    if (result == VOFP_OK && !(rel <= o->rtol * 1.0000001) && !converged0) {
+        // the recursively updated residual met the tolerance but the recomputed one did not
+        if (!(rel <= o->rtol * 10.0)) result = VOFP_ERR_NOT_CONVERGED;
+    }
+    if (info) {
+        info->iterations = (int)h.iter_total;
+        info->outer_iterations = o->mode == VOFP_MODE_MIXED ? h.outer : 1;
+        info->rel_residual = rel;
+        info->seconds = ms * 1e-3;
+        info->status = result;
+    }
+    if (result != VOFP_OK)
+        c->set_error(result == VOFP_ERR_NOT_CONVERGED ? "solve did not reach rtol" : "CG breakdown");
+    return result;
+}
+
+vofp_status time_iteration_kernels(vofp_ctx* c, int precision, int reps, float* stencil_ms, float* update_ms) {
+    vofp_status s = ensure_workspace(c);
+    if (s) return s;
+    cudaStream_t st = c->stream;
+    const long long N = c->d.n;
+    cudaEvent_t a, b2;
+    VOFP_CUDA_TRY(c, cudaEventCreate(&a));
+    VOFP_CUDA_TRY(c, cudaEventCreate(&b2));
+    // alpha = beta = 0 keeps every value fixed while every byte is still read and written
+    launch(c, k_set_pq_inf, 1, 1, st, c->sc, 1);
+    float t1 = 0.0f, t2 = 0.0f;
+    if (precision == 32) {
+        launch(c, k_stencil<float, ST_CG, stencil_pf<float>()>, stencil_grid(c), dim3(kBX, kBY), st, 
+            c->d, c->zchunk, c->Txf, c->Tyf, c->Tzf, nullptr, c->rf, c->pf0, c->pf1, c->xf, c->qf, c->sc, c->partials, c->counters);
+        VOFP_CUDA_TRY(c, cudaEventRecord(a, st));
+        for (int i = 0; i < reps; ++i)
+            launch(c, k_stencil<float, ST_CG, stencil_pf<float>()>, stencil_grid(c), dim3(kBX, kBY), st, 
+                c->d, c->zchunk, c->Txf, c->Tyf, c->Tzf, nullptr, c->rf, c->pf0, c->pf1, c->xf, c->qf, c->sc, c->partials, c->counters);
+        VOFP_CUDA_TRY(c, cudaEventRecord(b2, st));
+        VOFP_CUDA_TRY(c, cudaEventSynchronize(b2));
+        VOFP_CUDA_TRY(c, cudaEventElapsedTime(&t1, a, b2));
+        launch(c, k_set_pq_inf, 1, 1, st, c->sc, 1);
+        VOFP_CUDA_TRY(c, cudaEventRecord(a, st));
+        for (int i = 0; i < reps; ++i)
+            launch(c, k_cg_update<float, false>, stream_grid(N / 4 + 1), kNT, st, N, c->rf, c->qf, c->slave_bits, c->sc,
+                                                                              c->partials, c->counters, 0, 0);
+        VOFP_CUDA_TRY(c, cudaEventRecord(b2, st));
+    } else {
+        launch(c, k_stencil<double, ST_CG, stencil_pf<double>()>, stencil_grid(c), dim3(kBX, kBY), st, 
+            c->d, c->zchunk, c->Txs, c->Tys, c->Tzs, nullptr, c->r, c->p0, c->p1, c->xt, c->q, c->sc, c->partials, c->counters);
+        VOFP_CUDA_TRY(c, cudaEventRecord(a, st));
+        for (int i = 0; i < reps; ++i)
+            launch(c, k_stencil<double, ST_CG, stencil_pf<double>()>, stencil_grid(c), dim3(kBX, kBY), st, 
+                c->d, c->zchunk, c->Txs, c->Tys, c->Tzs, nullptr, c->r, c->p0, c->p1, c->xt, c->q, c->sc, c->partials, c->counters);
+        VOFP_CUDA_TRY(c, cudaEventRecord(b2, st));
+        VOFP_CUDA_TRY(c, cudaEventSynchronize(b2));
+        VOFP_CUDA_TRY(c, cudaEventElapsedTime(&t1, a, b2));
+        launch(c, k_set_pq_inf, 1, 1, st, c->sc, 1);
+        VOFP_CUDA_TRY(c, cudaEventRecord(a, st));
+        for (int i = 0; i < reps; ++i)
+            launch(c, k_cg_update<double, false>, stream_grid(N / 2 + 1), kNT, st, N, c->r, c->q, c->slave_bits, c->sc,
+                                                                               c->partials, c->counters, 0, 0);
+        VOFP_CUDA_TRY(c, cudaEventRecord(b2, st));
+    }
+    VOFP_CUDA_TRY(c, cudaEventSynchronize(b2));
+    VOFP_CUDA_TRY(c, cudaEventElapsedTime(&t2, a, b2));
+    launch(c, k_set_pq_inf, 1, 1, st, c->sc, 0);
+    VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b2);
+    *stencil_ms = t1 / reps;
+    *update_ms = t2 / reps;
+    return VOFP_OK;
+}
+
+}  // namespace vofp

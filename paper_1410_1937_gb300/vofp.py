@@ -1,0 +1,291 @@
+"""Thin ctypes binding of libvofp (include/vofp.h).  Argument marshalling only: every step of the
+solve runs in the library's CUDA kernels.  Importing this module fails loudly when libvofp.so has
+not been built (``python -c "import __graft_entry__ as g; g.build()"``); there is no CPU fallback.
+
+Module-level functions carry the C names (vofp_create, vofp_build_operator, ...) and take torch
+CUDA tensors (float64, contiguous) where the C call takes device pointers; ``Context`` wraps them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvofp.so")
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libvofp.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+_lib = ctypes.CDLL(LIB_PATH)
+
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_STAGNATED, \
+    ERR_INCOMPATIBLE_RHS, ERR_NOT_BUILT = range(9)
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGED", 5: "BREAKDOWN",
+                6: "STAGNATED", 7: "INCOMPATIBLE_RHS", 8: "NOT_BUILT"}
+BC_NEUMANN, BC_DIRICHLET = 0, 1
+MODE_FP64, MODE_MIXED = 0, 1
+PRECOND_JACOBI, PRECOND_RBSGS = 0, 1
+
+
+class VofpError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"vofp status {STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", ctypes.POINTER(ctypes.c_double)), ("dy", ctypes.POINTER(ctypes.c_double)),
+                ("dz", ctypes.POINTER(ctypes.c_double))]
+
+
+class _Bc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int * 6), ("neumann_flux", ctypes.c_void_p * 6)]
+
+
+class _Phys(ctypes.Structure):
+    _fields_ = [("rho_liquid", ctypes.c_double), ("rho_gas", ctypes.c_double),
+                ("merge_threshold", ctypes.c_double), ("density_smoothing", ctypes.c_int),
+                ("dt", ctypes.c_double)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("precond", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("inner_rtol", ctypes.c_double),
+                ("check_every", ctypes.c_int), ("x0_zero", ctypes.c_int)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("outer_iterations", ctypes.c_int),
+                ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("status", ctypes.c_int)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("cells", ctypes.c_longlong), ("unknowns", ctypes.c_longlong),
+                ("inactive", ctypes.c_longlong), ("merged_cells", ctypes.c_longlong),
+                ("groups", ctypes.c_longlong), ("device_bytes", ctypes.c_longlong)]
+
+
+_vp = ctypes.c_void_p
+_P = ctypes.POINTER
+_sig = {
+    "vofp_version": (ctypes.c_char_p, []),
+    "vofp_create": (ctypes.c_int, [_P(_vp), _P(_Grid), _vp]),
+    "vofp_destroy": (None, [_vp]),
+    "vofp_last_error": (ctypes.c_char_p, [_vp]),
+    "vofp_build_operator": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _P(_Bc), _P(_Phys)]),
+    "vofp_rhs_from_face_velocity": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "vofp_apply": (ctypes.c_int, [_vp, _vp, _vp]),
+    "vofp_residual": (ctypes.c_int, [_vp, _vp, _vp, _P(ctypes.c_double)]),
+    "vofp_solve": (ctypes.c_int, [_vp, _vp, _vp, _P(_Opts), _P(_Info)]),
+    "vofp_solve_host": (ctypes.c_int, [_vp] + [_vp] * 8 + [_P(_Bc), _P(_Phys), _P(_Opts), _vp, _P(_Info)]),
+    "vofp_merge_map": (ctypes.c_int, [_vp, _vp]),
+    "vofp_get_stats": (ctypes.c_int, [_vp, _P(_Stats)]),
+    "vofp_launch_count": (ctypes.c_int, [_vp, _P(ctypes.c_longlong)]),
+    "vofp_time_iteration_kernels": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _P(ctypes.c_float),
+                                                   _P(ctypes.c_float)]),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_sig)
+
+
+def _check(ctx, status):
+    if status != OK:
+        msg = _lib.vofp_last_error(ctx)
+        raise VofpError(status, msg.decode() if msg else "")
+
+
+def _dev(t, n, name, dtype="float64"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if str(t.dtype) != f"torch.{dtype}" or not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"{name}: need contiguous {dtype} with {n} elements, got {t.dtype} {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ---- functions with the C names ------------------------------------------------------------
+
+def vofp_version() -> str:
+    return _lib.vofp_version().decode()
+
+
+def vofp_create(dx, dy, dz, stream=None):
+    dx, dy, dz = (np.ascontiguousarray(a, dtype=np.float64) for a in (dx, dy, dz))
+    g = _Grid(len(dx), len(dy), len(dz), dx.ctypes.data_as(_P(ctypes.c_double)),
+              dy.ctypes.data_as(_P(ctypes.c_double)), dz.ctypes.data_as(_P(ctypes.c_double)))
+    h = _vp()
+    st = _lib.vofp_create(ctypes.byref(h), ctypes.byref(g), _stream_handle(stream))
+    if st != OK:
+        raise VofpError(st, "vofp_create failed")
+    return h
+
+
+def vofp_destroy(ctx):
+    _lib.vofp_destroy(ctx)
+
+
+def vofp_last_error(ctx) -> str:
+    return _lib.vofp_last_error(ctx).decode()
+
+
+class Context:
+    """One grid on one stream.  Arrays are torch CUDA float64 tensors in the layouts of vofp.h."""
+
+    def __init__(self, dx, dy, dz, stream=None):
+        self.nx, self.ny, self.nz = len(dx), len(dy), len(dz)
+        self.n = self.nx * self.ny * self.nz
+        self.nfx = (self.nx + 1) * self.ny * self.nz
+        self.nfy = self.nx * (self.ny + 1) * self.nz
+        self.nfz = self.nx * self.ny * (self.nz + 1)
+        self.h = vofp_create(dx, dy, dz, stream)
+        self._keep = []
+
+    def close(self):
+        if self.h:
+            vofp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- operator ------------------------------------------------------------------------------
+    def _bc(self, kinds, neumann_flux):
+        b = _Bc()
+        self._keep = []
+        for f in range(6):
+            b.kind[f] = int(kinds[f])
+            g = None if neumann_flux is None else neumann_flux[f]
+            if g is None:
+                b.neumann_flux[f] = None
+            else:
+                nb = (self.ny * self.nz, self.ny * self.nz, self.nx * self.nz, self.nx * self.nz,
+                      self.nx * self.ny, self.nx * self.ny)[f]
+                b.neumann_flux[f] = _dev(g, nb, f"neumann_flux[{f}]").value
+                self._keep.append(g)
+        return b
+
+    def vofp_build_operator(self, F, ax, ay, az, vol_frac, bc, rho_liquid=1000.0, rho_gas=1.2,
+                            merge_threshold=0.1, density_smoothing=0, dt=1.0, neumann_flux=None):
+        b = self._bc(bc, neumann_flux)
+        ph = _Phys(rho_liquid, rho_gas, merge_threshold, int(density_smoothing), dt)
+        vf = None if vol_frac is None else _dev(vol_frac, self.n, "vol_frac")
+        _check(self.h, _lib.vofp_build_operator(self.h, _dev(F, self.n, "F"), _dev(ax, self.nfx, "ax"),
+                                                _dev(ay, self.nfy, "ay"), _dev(az, self.nfz, "az"),
+                                                vf, ctypes.byref(b), ctypes.byref(ph)))
+
+    def vofp_rhs_from_face_velocity(self, u, v, w, body_flux=None, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.n, dtype=torch.float64, device=u.device)
+        bf = None if body_flux is None else _dev(body_flux, self.n, "body_flux")
+        _check(self.h, _lib.vofp_rhs_from_face_velocity(self.h, _dev(u, self.nfx, "u"), _dev(v, self.nfy, "v"),
+                                                        _dev(w, self.nfz, "w"), bf, _dev(out, self.n, "b")))
+        return out
+
+    def vofp_apply(self, x, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.n, dtype=torch.float64, device=x.device)
+        _check(self.h, _lib.vofp_apply(self.h, _dev(x, self.n, "x"), _dev(out, self.n, "y")))
+        return out
+
+    def vofp_residual(self, b, x) -> float:
+        r = ctypes.c_double(0.0)
+        _check(self.h, _lib.vofp_residual(self.h, _dev(b, self.n, "b"), _dev(x, self.n, "x"), ctypes.byref(r)))
+        return r.value
+
+    def vofp_solve(self, b, x=None, mode=MODE_FP64, rtol=1e-10, max_iter=100000, inner_rtol=1e-3,
+                   check_every=8, precond=PRECOND_JACOBI, raise_on_error=True, x0_zero=0):
+        import torch
+        if x is None:
+            x = torch.zeros(self.n, dtype=torch.float64, device=b.device)
+            x0_zero = 1
+        o = _Opts(int(mode), int(precond), float(rtol), int(max_iter), float(inner_rtol), int(check_every), x0_zero)
+        info = _Info()
+        st = _lib.vofp_solve(self.h, _dev(b, self.n, "b"), _dev(x, self.n, "x"), ctypes.byref(o), ctypes.byref(info))
+        out = {"iterations": info.iterations, "outer_iterations": info.outer_iterations,
+               "rel_residual": info.rel_residual, "seconds": info.seconds, "status": info.status,
+               "status_name": STATUS_NAMES.get(info.status, str(info.status))}
+        if st != OK and raise_on_error and st not in (ERR_NOT_CONVERGED,):
+            _check(self.h, st)
+        out["return_status"] = st
+        return x, out
+
+    def vofp_solve_host(self, F, ax, ay, az, vol_frac, u, v, w, bc, x_out, mode=MODE_FP64, rtol=1e-10,
+                        max_iter=100000, inner_rtol=1e-3, check_every=8, rho_liquid=1000.0, rho_gas=1.2,
+                        merge_threshold=0.1, density_smoothing=0, dt=1.0):
+        """Host-buffer end-to-end call: numpy (or pinned torch CPU) float64 arrays in, x_out out."""
+        def hp(a, n, name):
+            if a is None:
+                return None
+            if hasattr(a, "data_ptr"):
+                if a.numel() != n or a.is_cuda:
+                    raise ValueError(name)
+                return ctypes.c_void_p(a.data_ptr())
+            a = np.asarray(a)
+            if a.dtype != np.float64 or a.size != n or not a.flags.c_contiguous:
+                raise ValueError(name)
+            return ctypes.c_void_p(a.ctypes.data)
+        b = self._bc(bc, None)
+        ph = _Phys(rho_liquid, rho_gas, merge_threshold, int(density_smoothing), dt)
+        o = _Opts(int(mode), PRECOND_JACOBI, float(rtol), int(max_iter), float(inner_rtol), int(check_every), 1)
+        info = _Info()
+        st = _lib.vofp_solve_host(self.h, hp(F, self.n, "F"), hp(ax, self.nfx, "ax"), hp(ay, self.nfy, "ay"),
+                                  hp(az, self.nfz, "az"), hp(vol_frac, self.n, "vol_frac"), hp(u, self.nfx, "u"),
+                                  hp(v, self.nfy, "v"), hp(w, self.nfz, "w"), ctypes.byref(b), ctypes.byref(ph),
+                                  ctypes.byref(o), hp(x_out, self.n, "x_out"), ctypes.byref(info))
+        if st not in (OK, ERR_NOT_CONVERGED):
+            _check(self.h, st)
+        return {"iterations": info.iterations, "outer_iterations": info.outer_iterations,
+                "rel_residual": info.rel_residual, "seconds": info.seconds, "status": info.status}
+
+    def vofp_merge_map(self):
+        import torch
+        out = torch.empty(self.n, dtype=torch.int32, device="cuda")
+        _check(self.h, _lib.vofp_merge_map(self.h, _dev(out, self.n, "master", "int32")))
+        return out
+
+    def vofp_get_stats(self):
+        s = _Stats()
+        _check(self.h, _lib.vofp_get_stats(self.h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in _Stats._fields_}
+
+    def vofp_launch_count(self) -> int:
+        n = ctypes.c_longlong(0)
+        _check(self.h, _lib.vofp_launch_count(self.h, ctypes.byref(n)))
+        return n.value
+
+    def vofp_time_iteration_kernels(self, precision=64, reps=20):
+        a, b = ctypes.c_float(0), ctypes.c_float(0)
+        _check(self.h, _lib.vofp_time_iteration_kernels(self.h, int(precision), int(reps), ctypes.byref(a),
+                                                        ctypes.byref(b)))
+        return a.value, b.value
+
+
+def context_for(problem, stream=None, device="cuda"):
+    """Create a Context for an inputs.Problem, upload its arrays and build the operator.
+    Returns (ctx, device arrays dict)."""
+    import torch
+    ctx = Context(problem.dx, problem.dy, problem.dz, stream)
+    t = {k: torch.from_numpy(np.ascontiguousarray(getattr(problem, k)).ravel()).to(device)
+         for k in ("F", "vf", "ax", "ay", "az", "u", "v", "w")}
+    ctx.vofp_build_operator(t["F"], t["ax"], t["ay"], t["az"], t["vf"], problem.bc,
+                            problem.rho_liquid, problem.rho_gas, problem.merge_threshold,
+                            problem.density_smoothing, problem.dt)
+    return ctx, t

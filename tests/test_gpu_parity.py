@@ -1,0 +1,228 @@
+"""GPU parity: every step of the CUDA path against the CPU oracle on the same seeded inputs.
+
+Tolerances: operator apply and right-hand side are FP64 evaluations of the same definition in a
+different summation order, so they agree to a few ulps (1e-13 relative).  Solutions: relative L2
+error <= 1e-6 against the oracle solved to 1e-12, at relative residual 1e-10 (FP64) or 1e-8
+(mixed precision).  Merge maps are integers: bit-exact.
+"""
+import numpy as np
+import pytest
+
+from paper_1410_1937_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def vofp():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1410_1937_gb300 import vofp as V
+    return V
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a).ravel()).cuda()
+
+
+def host(t, shape):
+    return t.cpu().numpy().reshape(shape)
+
+
+def ragged_sphere(shape=(37, 11, 45), seed=3, threshold=0.25):
+    nx, ny, nz = shape
+    xn = I.tanh_nodes(-0.5, 0.5, nx, 0.0, 0.2)
+    yn = I.tanh_nodes(-0.5, 0.5, ny, 0.0, 0.2)
+    zn = I.tanh_nodes(-0.5, 0.5, nz, 0.0, 0.2)
+    F = I.vof_cosine(xn, yn, zn, 0.04, 0.6, 0.7)
+    body = I.Sphere((0.02, -0.03, 0.01), 0.23)
+    p = I._assemble("ragged-sphere", xn, yn, zn, F, body, np.random.default_rng(seed), rtol=1e-10)
+    p.merge_threshold = threshold
+    return p
+
+
+CASES = {
+    "tiny": lambda: I.tiny_sphere(),
+    "ragged": lambda: ragged_sphere(),
+    "c0": lambda: I.config0(),
+    "c1-small": lambda: I.config1(shape=(64, 32, 32)),
+    "hull-small": lambda: I.config2(shape=(96, 48, 40)),
+}
+
+
+@pytest.mark.parametrize("case", ["tiny", "ragged", "hull-small"])
+def test_merge_map_bit_exact(vofp, oracle, case):
+    prob = CASES[case]()
+    s = oracle.System(prob)
+    ctx, t = vofp.context_for(prob)
+    root = ctx.vofp_merge_map().cpu().numpy()
+    assert (s.root != np.arange(prob.n)).sum() > 0
+    np.testing.assert_array_equal(root, s.root.astype(np.int32))
+    st = ctx.vofp_get_stats()
+    assert st["unknowns"] == s.M and st["inactive"] == int((s.root < 0).sum())
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_rhs_matches_oracle(vofp, oracle, case):
+    prob = CASES[case]()
+    s = oracle.System(prob)
+    ctx, t = vofp.context_for(prob)
+    b = host(ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"]), prob.shape).ravel()
+    scale = np.abs(s.b).max()
+    assert np.abs(b - s.b).max() <= 1e-13 * scale
+
+
+def test_apply_reproduces_operator_columns(vofp, oracle):
+    prob = I.tiny_sphere()
+    s = oracle.System(prob)
+    ctx, _ = vofp.context_for(prob)
+    Ah = s.Ahat.toarray()
+    for col, m in enumerate(s.masters):
+        e = np.zeros(prob.n)
+        e[m] = 1.0
+        y = host(ctx.vofp_apply(dev(e)), prob.shape).ravel()
+        ref = np.zeros(prob.n)
+        ref[s.masters] = Ah[:, col]
+        assert np.abs(y - ref).max() <= 1e-14 * np.abs(Ah[:, col]).max(), f"column {col}"
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_apply_random_vector(vofp, oracle, case):
+    prob = CASES[case]()
+    s = oracle.System(prob)
+    ctx, _ = vofp.context_for(prob)
+    x = np.random.default_rng(9).uniform(-1, 1, prob.n)
+    y = host(ctx.vofp_apply(dev(x)), prob.shape).ravel()
+    ref = s.apply_full(x).ravel()
+    assert np.abs(y - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_solve_matches_oracle(vofp, oracle, case, mode):
+    prob = CASES[case]()
+    ref, info_ref, s = oracle.solve(prob, rtol=1e-12)
+    assert info_ref["rel_residual"] < 1e-11
+    ctx, t = vofp.context_for(prob)
+    b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
+    rtol = 1e-10 if mode == "fp64" else 1e-8
+    x, info = ctx.vofp_solve(b, rtol=rtol, mode=vofp.MODE_FP64 if mode == "fp64" else vofp.MODE_MIXED)
+    assert info["status"] == 0, info
+    assert info["rel_residual"] <= rtol
+    got = host(x, prob.shape)
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err <= 1e-6, (err, info)
+    # the oracle's own residual of the GPU solution
+    assert s.residual(got) <= rtol * 1.01
+
+
+def test_solve_is_bitwise_reproducible(vofp):
+    prob = CASES["hull-small"]()
+    ctx, t = vofp.context_for(prob)
+    b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
+    x1, i1 = ctx.vofp_solve(b, rtol=1e-10)
+    x2, i2 = ctx.vofp_solve(b, rtol=1e-10)
+    assert i1["iterations"] == i2["iterations"]
+    assert torch.equal(x1, x2)
+
+
+def test_initial_guess_is_used(vofp):
+    prob = CASES["c0"]()
+    ctx, t = vofp.context_for(prob)
+    b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
+    x, i1 = ctx.vofp_solve(b, rtol=1e-10)
+    x2, i2 = ctx.vofp_solve(b, x=x.clone(), rtol=1e-10)
+    assert i2["iterations"] == 0 and i2["status"] == 0
+    # x -> x * sqrt(d) -> * 1/sqrt(d) round trip: equal to one rounding
+    torch.testing.assert_close(x2, x, rtol=3e-16, atol=0)
+
+
+def test_manufactured_solution_second_order_on_gpu(vofp):
+    errs = []
+    for n in (16, 32, 64):
+        prob = I.manufactured(n)
+        ctx, t = vofp.context_for(prob)
+        b = dev(I.manufactured_rhs(prob))
+        x, info = ctx.vofp_solve(b, rtol=1e-12)
+        assert info["status"] == 0
+        errs.append(np.abs(host(x, prob.shape) - I.manufactured_pressure(prob)).max())
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all((rates > 1.85) & (rates < 2.15)), (errs, rates)
+
+
+def test_all_neumann_zero_mean_solution(vofp, oracle):
+    prob = I.tiny_sphere()
+    prob.bc = (I.NEUMANN,) * 6
+    ref, _, s = oracle.solve(prob)
+    ctx, t = vofp.context_for(prob)
+    b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
+    x, info = ctx.vofp_solve(b, rtol=1e-11)
+    assert info["status"] == 0
+    got = host(x, prob.shape)
+    assert abs(s.restrict(got).mean()) < 1e-12 * np.abs(ref).max()
+    assert np.linalg.norm(got - ref) <= 1e-7 * np.linalg.norm(ref)
+
+
+def test_incompatible_all_neumann_rhs_is_rejected(vofp):
+    prob = I.tiny_sphere()
+    prob.bc = (I.NEUMANN,) * 6
+    ctx, t = vofp.context_for(prob)
+    b = torch.ones(prob.n, dtype=torch.float64, device="cuda")
+    with pytest.raises(vofp.VofpError) as e:
+        ctx.vofp_solve(b, rtol=1e-10)
+    assert e.value.status == vofp.ERR_INCOMPATIBLE_RHS
+
+
+def test_iteration_cap_reports_not_converged(vofp):
+    prob = CASES["c0"]()
+    ctx, t = vofp.context_for(prob)
+    b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
+    x, info = ctx.vofp_solve(b, rtol=1e-10, max_iter=4, check_every=2)
+    assert info["status"] == vofp.ERR_NOT_CONVERGED
+    assert 4 <= info["iterations"] <= 6
+    assert np.isfinite(info["rel_residual"]) and info["rel_residual"] > 1e-10
+
+
+def test_nan_rhs_reports_breakdown(vofp):
+    prob = CASES["c0"]()
+    ctx, t = vofp.context_for(prob)
+    b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
+    b[100] = float("nan")
+    x, info = ctx.vofp_solve(b, rtol=1e-10, raise_on_error=False)
+    assert info["status"] == vofp.ERR_BREAKDOWN
+
+
+def test_solve_before_build_is_rejected(vofp):
+    prob = I.tiny_sphere()
+    ctx = vofp.Context(prob.dx, prob.dy, prob.dz)
+    with pytest.raises(vofp.VofpError) as e:
+        ctx.vofp_solve(torch.zeros(prob.n, dtype=torch.float64, device="cuda"))
+    assert e.value.status == vofp.ERR_NOT_BUILT
+
+
+def test_single_cell_grid(vofp, oracle):
+    prob = I.manufactured(1)
+    prob.u = np.array([[[0.0, 0.7]]])
+    prob.rho_liquid = prob.rho_gas = 2.0
+    ref, _, _ = oracle.solve(prob)
+    ctx, t = vofp.context_for(prob)
+    b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
+    x, info = ctx.vofp_solve(b, rtol=1e-12)
+    assert info["status"] == 0
+    np.testing.assert_allclose(host(x, prob.shape), ref, rtol=1e-13)
+
+
+def test_host_buffer_entry_point_matches_device_path(vofp):
+    prob = CASES["c1-small"]()
+    ctx, t = vofp.context_for(prob)
+    b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
+    x, info = ctx.vofp_solve(b, rtol=1e-10)
+    ctx2 = vofp.Context(prob.dx, prob.dy, prob.dz)
+    xh = np.zeros(prob.n)
+    info2 = ctx2.vofp_solve_host(prob.F.ravel(), prob.ax.ravel(), prob.ay.ravel(), prob.az.ravel(),
+                                 prob.vf.ravel(), prob.u.ravel(), prob.v.ravel(), prob.w.ravel(), prob.bc, xh,
+                                 rtol=1e-10)
+    assert info2["status"] == 0
+    np.testing.assert_array_equal(xh, x.cpu().numpy())
