@@ -188,6 +188,20 @@ vofp_status vofp_merge_map(vofp_ctx* ctx, int32_t* master);
 /* Counts and device memory of the built operator. */
 vofp_status vofp_get_stats(vofp_ctx* ctx, vofp_stats* stats);
 
+/* Same result as vofp_residual, for callers that must not allocate device memory after set-up:
+ * code whose device memory belongs to another allocator (a framework's caching pool), a fixed
+ * memory budget, or a loop that cannot take the device-wide synchronisation of cudaMalloc and
+ * cudaFree.  vofp_residual may allocate the solver workspace on its first use; this call never
+ * calls cudaMalloc, cudaFree or any allocating routine.  The paper has no counterpart: it is a
+ * property of this library's interface.
+ * Scratch: one file-scope device array of about 1 MB (every GPU that loads the library keeps it
+ * until the process exits), enough for operators with at most 65536 merge groups; an operator with
+ * more groups is rejected with VOFP_ERR_INVALID_ARG and a message.  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  All calls share the array: calls that overlap on the GPU
+ * (other streams or threads) race.  Synchronises the context stream; *rel is a host double. */
+vofp_status vofp_residual_noalloc(vofp_ctx* ctx, const double* b, const double* x, double* rel);
+
 /* *count = number of kernels this context has launched since vofp_create (kernels run inside
  * the solve's CUDA graphs are counted per execution). */
 vofp_status vofp_launch_count(vofp_ctx* ctx, long long* count);

@@ -82,6 +82,7 @@ _sig = {
     "vofp_solve_host": (ctypes.c_int, [_vp] + [_vp] * 8 + [_P(_Bc), _P(_Phys), _P(_Opts), _vp, _P(_Info)]),
     "vofp_merge_map": (ctypes.c_int, [_vp, _vp]),
     "vofp_get_stats": (ctypes.c_int, [_vp, _P(_Stats)]),
+    "vofp_residual_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _P(ctypes.c_double)]),
     "vofp_launch_count": (ctypes.c_int, [_vp, _P(ctypes.c_longlong)]),
     "vofp_time_iteration_kernels": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _P(ctypes.c_float),
                                                    _P(ctypes.c_float)]),
@@ -208,6 +209,13 @@ class Context:
     def vofp_residual(self, b, x) -> float:
         r = ctypes.c_double(0.0)
         _check(self.h, _lib.vofp_residual(self.h, _dev(b, self.n, "b"), _dev(x, self.n, "x"), ctypes.byref(r)))
+        return r.value
+
+    def vofp_residual_noalloc(self, b, x) -> float:
+        """vofp_residual without any device allocation (fixed static scratch; see vofp.h)."""
+        r = ctypes.c_double(0.0)
+        _check(self.h, _lib.vofp_residual_noalloc(self.h, _dev(b, self.n, "b"), _dev(x, self.n, "x"),
+                                                  ctypes.byref(r)))
         return r.value
 
     def vofp_solve(self, b, x=None, mode=MODE_FP64, rtol=1e-10, max_iter=100000, inner_rtol=1e-3,
