@@ -33,10 +33,18 @@ METRIC = "Poisson time-to-1e-8 residual & solves/s at 512×256×128; HBM GB/s pe
 SHAPE = (512, 256, 128)
 RTOL = 1e-8
 FALLBACK_HBM_GBS = 6800.0
-# algorithmic bytes per cell of one launch / one iteration ("Roofline")
-STENCIL_BYTES = {64: 9 * 8, 32: 9 * 4}          # reads r, p_old, x, Tx, Ty, Tz; writes p, x, q
-UPDATE_BYTES = {64: 3 * 8, 32: 3 * 4}           # reads r, q; writes r
-ITER_BYTES = {64: 12 * 8, 32: 12 * 4}
+# algorithmic bytes per cell of one launch / one iteration ("Roofline"), in units of
+# one vector element (8 B for FP64, 4 B for FP32)
+#   stencil: reads r, p_old, x, Tx, Ty, Tz; writes p, x, q (red-black: writes on the black half only)
+#   update:  reads r, q; writes r
+#   red half-stencil (red-black): reads r, p_old, Tx, Ty, Tz; writes r on the red half
+STENCIL_ELEMS = {"jacobi": 9.0, "rbsgs": 7.5}
+UPDATE_ELEMS = 3.0
+RED_ELEMS = 5.5
+
+
+def iter_elems(precond):
+    return STENCIL_ELEMS[precond] + UPDATE_ELEMS + (RED_ELEMS if precond == "rbsgs" else 0.0)
 # dram read+write bytes per cell of one stencil launch from the committed ncu capture, valid only
 # while the kernel sources hash to KERNEL_HASH (else reported as null)
 TRAFFIC_PER_CELL = {}
@@ -170,6 +178,8 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream()
     mode = vofp.MODE_MIXED if args.mode == "mixed" else vofp.MODE_FP64
     prec = 32 if args.mode == "mixed" else 64
+    pc = vofp.PRECOND_RBSGS if args.precond == "rbsgs" else vofp.PRECOND_JACOBI
+    vb = prec // 8
     with torch.cuda.stream(stream):
         ctx = vofp.Context(prob.dx, prob.dy, prob.dz, stream)
         t = {k: torch.from_numpy(np.ascontiguousarray(getattr(prob, k)).ravel()).cuda()
@@ -185,7 +195,7 @@ def run_ours(args, rank, world, local_rank):
                                     prob.rho_gas, prob.merge_threshold, prob.density_smoothing, prob.dt)
             ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"], out=b)
             _, info = ctx.vofp_solve(b, x=x, mode=mode, rtol=RTOL, x0_zero=1, check_every=args.check_every,
-                                     inner_rtol=args.inner_rtol)
+                                     inner_rtol=args.inner_rtol, host_loop=int(args.host_loop), precond=pc)
             launches[0] += ctx.vofp_launch_count() - l0
             infos.append(info)
 
@@ -213,18 +223,26 @@ def run_ours(args, rank, world, local_rank):
         info = infos[-1]
         assert all(i["status"] == 0 for i in infos), infos
         # dominant kernel: the fused CG stencil of the solve's precision, timed live
-        st_ms, up_ms = ctx.vofp_time_iteration_kernels(prec, args.kernel_reps)
+        st_ms, up_ms, red_ms = ctx.vofp_time_iteration_kernels(prec, args.kernel_reps, precond=pc)
         n = prob.n
         hbm, hbm_kind = peaks()
-        achieved = STENCIL_BYTES[prec] * n / (st_ms * 1e-3) / 1e9
+        achieved = STENCIL_ELEMS[args.precond] * vb * n / (st_ms * 1e-3) / 1e9
         traffic = None
-        if KERNEL_HASH is not None and KERNEL_HASH == kernel_hash() and prec in TRAFFIC_PER_CELL:
-            traffic = TRAFFIC_PER_CELL[prec] * n
+        if KERNEL_HASH is not None and KERNEL_HASH == kernel_hash() and (prec, args.precond) in TRAFFIC_PER_CELL:
+            traffic = TRAFFIC_PER_CELL[(prec, args.precond)] * n
         iter_s = info["seconds"] / max(info["iterations"], 1)
-        # FP64 reference solve on the same input for the iteration count and its own time
-        x64 = torch.zeros_like(x)
-        _, info64 = ctx.vofp_solve(b, x=x64, mode=vofp.MODE_FP64, rtol=RTOL, x0_zero=1)
-        st64, up64 = ctx.vofp_time_iteration_kernels(64, args.kernel_reps)
+        # every solver variant once on the same input (plain FP64 Jacobi-PCG is the reference)
+        variants = {}
+        for vm, vmode in (("fp64", vofp.MODE_FP64), ("mixed", vofp.MODE_MIXED)):
+            for vp, vpc in (("jacobi", vofp.PRECOND_JACOBI), ("rbsgs", vofp.PRECOND_RBSGS)):
+                xv = torch.zeros_like(x)
+                _, iv = ctx.vofp_solve(b, x=xv, mode=vmode, rtol=RTOL, x0_zero=1, precond=vpc,
+                                       inner_rtol=args.inner_rtol)
+                variants[f"{vm}+{vp}"] = {"time_to_tol_ms": iv["seconds"] * 1e3, "iterations": iv["iterations"],
+                                          "outer_iterations": iv["outer_iterations"],
+                                          "rel_residual": iv["rel_residual"], "status": iv["status_name"]}
+        info64 = variants["fp64+jacobi"]
+        st64, up64, _ = ctx.vofp_time_iteration_kernels(64, args.kernel_reps)
 
         # end to end through the host-buffer C-ABI call
         e2e = None
@@ -239,7 +257,7 @@ def run_ours(args, rank, world, local_rank):
                                          host["v"], host["w"], prob.bc, xh, mode=mode, rtol=RTOL,
                                          check_every=args.check_every, inner_rtol=args.inner_rtol,
                                          rho_liquid=prob.rho_liquid, rho_gas=prob.rho_gas,
-                                         merge_threshold=prob.merge_threshold, dt=prob.dt)
+                                         merge_threshold=prob.merge_threshold, dt=prob.dt, precond=pc)
                 assert r["status"] == 0, r
             for _ in range(max(1, args.warmup // 2)):
                 host_step()
@@ -268,22 +286,26 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic",
         "config": {"workload": f"hull-in-waves {args.shape[0]}x{args.shape[1]}x{args.shape[2]} "
                                f"({n} cells) Dirichlet exit, rtol 1e-8",
-                   "mode": args.mode, "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "mode": args.mode, "precond": args.precond,
+                   "parallelism": "replicas" if world > 1 else "single-gpu",
                    "l2": "inputs larger than L2 (8 FP64 arrays of 134 MB)"},
         "time_to_tol_ms": info["seconds"] * 1e3,
         "iterations": info["iterations"], "outer_iterations": info["outer_iterations"],
         "rel_residual": info["rel_residual"],
         "cg_iterations_per_s": info["iterations"] / info["seconds"],
-        "hbm_gbs_per_iter": ITER_BYTES[prec] * n / iter_s / 1e9,
-        "fp64_reference": {"time_to_tol_ms": info64["seconds"] * 1e3, "iterations": info64["iterations"],
-                           "rel_residual": info64["rel_residual"], "status": info64["status_name"],
+        "hbm_gbs_per_iter": iter_elems(args.precond) * vb * n / iter_s / 1e9,
+        "variants": variants,
+        "fp64_reference": {"time_to_tol_ms": info64["time_to_tol_ms"], "iterations": info64["iterations"],
+                           "rel_residual": info64["rel_residual"], "status": info64["status"],
                            "stencil_ms": st64, "update_ms": up64,
-                           "stencil_gbs": STENCIL_BYTES[64] * n / (st64 * 1e-3) / 1e9,
-                           "hbm_gbs_per_iter": ITER_BYTES[64] * n / (info64["seconds"] / max(info64["iterations"], 1)) / 1e9},
-        "roofline": {"bound": "hbm", "kernel": f"k_stencil<{'float' if prec == 32 else 'double'},ST_CG>",
+                           "stencil_fp64_tflops": 9.31 * 2 * n / (st64 * 1e-3) / 1e12,
+                           "hbm_gbs_per_iter": iter_elems("jacobi") * 8 * n / (info64["time_to_tol_ms"] * 1e-3 /
+                                                                               max(info64["iterations"], 1)) / 1e9},
+        "roofline": {"bound": "hbm", "kernel": f"k_stencil<{'float' if prec == 32 else 'double'},ST_CG>"
+                                               f"{' red-black' if args.precond == 'rbsgs' else ''}",
                      "achieved": achieved, "peak": hbm, "peak_kind": hbm_kind, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "stencil_ms": st_ms, "update_ms": up_ms,
-                     "update_gbs": UPDATE_BYTES[prec] * n / (up_ms * 1e-3) / 1e9},
+                     "red_ms": red_ms, "update_gbs": UPDATE_ELEMS * vb * n / (up_ms * 1e-3) / 1e9},
         "clocks": clk.summary(),
         "gpu_launches": launches[0],
         "e2e": e2e,
@@ -301,10 +323,13 @@ def run_profile(args):
     ctx, t = vofp.context_for(prob)
     b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
     mode = vofp.MODE_MIXED if args.mode == "mixed" else vofp.MODE_FP64
+    # host-driven loop: every kernel is an ordinary launch that profilers can see
+    pc = vofp.PRECOND_RBSGS if args.precond == "rbsgs" else vofp.PRECOND_JACOBI
     _, info = ctx.vofp_solve(b, mode=mode, rtol=RTOL, max_iter=args.profile_iters, check_every=args.check_every,
-                             inner_rtol=args.inner_rtol, raise_on_error=False)
+                             inner_rtol=args.inner_rtol, raise_on_error=False, host_loop=1, precond=pc)
     torch.cuda.synchronize()
-    print(json.dumps({"profile": True, "shape": args.shape, "mode": args.mode, "iterations": info["iterations"],
+    print(json.dumps({"profile": True, "shape": args.shape, "mode": args.mode, "precond": args.precond,
+                      "iterations": info["iterations"],
                       "status": info["status_name"], "launches": ctx.vofp_launch_count()}), flush=True)
 
 
@@ -315,11 +340,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precond", default="rbsgs", choices=["jacobi", "rbsgs"])
     ap.add_argument("--shape", type=int, nargs=3, default=list(SHAPE))
     ap.add_argument("--check-every", type=int, default=8)
     ap.add_argument("--inner-rtol", type=float, default=1e-3)
     ap.add_argument("--kernel-reps", type=int, default=20)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="drive the CG loop from the host (same kernels; lets ncu list every launch)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-iters", type=int, default=20)
     ap.add_argument("--ref-fp64-iterations", type=int, default=2000)

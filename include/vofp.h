@@ -102,7 +102,11 @@ typedef struct {
  *   max_iter    cap on PCG iterations (inner iterations summed in mixed mode).
  *   inner_rtol  mixed mode: relative residual reduction of each inner solve (e.g. 1e-3).
  *   check_every convergence is tested every check_every iterations (even, >= 2; 0 = default 8).
- *   x0_zero     1: ignore the contents of x and start from 0. */
+ *   x0_zero     1: ignore the contents of x and start from 0.
+ *   host_loop   0: the loop runs as a CUDA graph with a device-side WHILE condition (no host round
+ *               trip per iteration).  1: the host launches each kernel and reads the convergence
+ *               flag every check_every iterations (same kernels and results; visible to profilers
+ *               that do not trace conditional graph bodies). */
 typedef struct {
     int mode;
     int precond;
@@ -111,6 +115,7 @@ typedef struct {
     double inner_rtol;
     int check_every;
     int x0_zero;
+    int host_loop;
 } vofp_solve_opts;
 
 typedef struct {
@@ -206,12 +211,14 @@ vofp_status vofp_residual_noalloc(vofp_ctx* ctx, const double* b, const double* 
  * the solve's CUDA graphs are counted per execution). */
 vofp_status vofp_launch_count(vofp_ctx* ctx, long long* count);
 
-/* Measurement hook: launches one FP64 (precision 64) or FP32 (precision 32) CG iteration's
- * kernels `reps` times on the context stream after a vofp_solve, recording the average device
- * time of the fused stencil kernel in *stencil_ms and of the vector-update kernel in *update_ms.
- * It reuses the last solve's vectors and leaves the solution untouched. */
-vofp_status vofp_time_iteration_kernels(vofp_ctx* ctx, int precision, int reps,
-                                        float* stencil_ms, float* update_ms);
+/* Measurement hook: after a vofp_solve, launches one CG iteration's kernels `reps` times each on
+ * the context stream -- FP64 (precision 64) or FP32 (precision 32), Jacobi or red-black (precond)
+ * -- and records the average device time of the fused stencil kernel in *stencil_ms, of the
+ * vector-update kernel in *update_ms and (red-black only, else 0) of the red half-stencil in
+ * *red_ms (may be NULL).  Step sizes are held at zero, so every byte is read and written but the
+ * vectors keep their values; the solution returned by the solve is untouched. */
+vofp_status vofp_time_iteration_kernels(vofp_ctx* ctx, int precision, int precond, int reps,
+                                        float* stencil_ms, float* update_ms, float* red_ms);
 
 #ifdef __cplusplus
 }

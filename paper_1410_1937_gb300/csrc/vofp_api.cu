@@ -1,7 +1,6 @@
 // extern "C" entry points of libvofp (declared and documented in include/vofp.h): argument
 // checks, context lifetime and error reporting around the implementations in the other files.
 #include <cmath>
-#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -61,13 +60,6 @@ vofp_status vofp_create(vofp_ctx** out, const vofp_grid* g, vofp_stream stream) 
     c->d.n = n;
     c->d.plane = (long long)g->nx * g->ny;
     c->stream = reinterpret_cast<cudaStream_t>(stream);
-    // planes per stencil block: enough blocks to fill the GPU several times over; the environment
-    // variable VOFP_STENCIL_ZCHUNK overrides it for tuning
-    c->zchunk = g->nz >= 256 ? 32 : 16;
-    if (const char* z = std::getenv("VOFP_STENCIL_ZCHUNK")) {
-        int v = std::atoi(z);
-        if (v >= 1 && v <= 4096) c->zchunk = v;
-    }
     c->hdx.assign(g->dx, g->dx + g->nx);
     c->hdy.assign(g->dy, g->dy + g->ny);
     c->hdz.assign(g->dz, g->dz + g->nz);
@@ -154,7 +146,7 @@ vofp_status vofp_solve(vofp_ctx* c, const double* b, double* x, const vofp_solve
     if (!b || !x || !o) return invalid(c, "null input");
     if (!(o->rtol > 0.0) || o->rtol >= 1.0) return invalid(c, "rtol must be in (0, 1)");
     if (o->mode != VOFP_MODE_FP64 && o->mode != VOFP_MODE_MIXED) return invalid(c, "unknown mode");
-    if (o->precond != VOFP_PRECOND_JACOBI) return invalid(c, "preconditioner not available in this build");
+    if (o->precond != VOFP_PRECOND_JACOBI && o->precond != VOFP_PRECOND_RBSGS) return invalid(c, "unknown preconditioner");
     if (o->check_every < 0 || (o->check_every % 2) != 0 || o->check_every > 64)
         return invalid(c, "check_every must be 0 or an even number <= 64");
     if (o->mode == VOFP_MODE_MIXED && (o->inner_rtol < 0.0 || o->inner_rtol >= 1.0))
@@ -230,12 +222,17 @@ vofp_status vofp_launch_count(vofp_ctx* c, long long* count) {
     return VOFP_OK;
 }
 
-vofp_status vofp_time_iteration_kernels(vofp_ctx* c, int precision, int reps, float* stencil_ms, float* update_ms) {
+vofp_status vofp_time_iteration_kernels(vofp_ctx* c, int precision, int precond, int reps, float* stencil_ms,
+                                        float* update_ms, float* red_ms) {
     vofp_status s = check_ctx(c, true);
     if (s) return s;
-    if ((precision != 64 && precision != 32) || reps <= 0 || !stencil_ms || !update_ms)
+    if ((precision != 64 && precision != 32) || (precond != VOFP_PRECOND_JACOBI && precond != VOFP_PRECOND_RBSGS) ||
+        reps <= 0 || !stencil_ms || !update_ms)
         return invalid(c, "bad arguments");
-    return vofp::time_iteration_kernels(c, precision, reps, stencil_ms, update_ms);
+    float red = 0.0f;
+    s = vofp::time_iteration_kernels(c, precision, precond == VOFP_PRECOND_RBSGS, reps, stencil_ms, update_ms, &red);
+    if (red_ms) *red_ms = red;
+    return s;
 }
 
 }  // extern "C"

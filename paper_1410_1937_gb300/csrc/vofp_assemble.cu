@@ -24,11 +24,14 @@ __device__ __forceinline__ long long fy_idx(const Dims& d, int i, int j, int k) 
 __device__ __forceinline__ long long fz_idx(const Dims& d, int i, int j, int k) {
     return i + (long long)d.nx * (j + (long long)d.ny * k);
 }
+// cell counts stay below 2^31 (checked by vofp_create): 32-bit division is enough
 __device__ __forceinline__ void cell_ijk(const Dims& d, long long c, int& i, int& j, int& k) {
-    i = int(c % d.nx);
-    long long t = c / d.nx;
-    j = int(t % d.ny);
-    k = int(t / d.ny);
+    const unsigned int uc = (unsigned int)c, nx = (unsigned int)d.nx, ny = (unsigned int)d.ny;
+    const unsigned int t = uc / nx;
+    i = int(uc - t * nx);
+    const unsigned int kk = t / ny;
+    j = int(t - kk * ny);
+    k = int(kk);
 }
 
 // rho = rho_g + (rho_l - rho_g) F   (Eq. density with H(phi) = phi)
@@ -326,6 +329,35 @@ __global__ void k_slave_bits(Dims d, const int32_t* __restrict__ root, uint32_t*
     }
 }
 
+// red cells: (i+j+k) even, own root, and not the master of a multi-cell group (a master always
+// touches one of its members, so a neighbour whose root is c marks c as a master)
+__global__ void k_red_bits(Dims d, const int32_t* __restrict__ root, const uint32_t* __restrict__ slave,
+                           uint32_t* __restrict__ red, uint32_t* __restrict__ excl, unsigned int* count) {
+    const long long nw = (d.n + 31) / 32;
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < nw;
+         w += (long long)gridDim.x * blockDim.x) {
+        uint32_t v = 0;
+        for (int b = 0; b < 32; ++b) {
+            const long long c = w * 32 + b;
+            if (c >= d.n || root[c] != (int32_t)c) continue;
+            int i, j, k;
+            cell_ijk(d, c, i, j, k);
+            if (((i + j + k) & 1) != 0) continue;
+            bool master = false;
+            if (i > 0) master |= root[c - 1] == (int32_t)c;
+            if (i < d.nx - 1) master |= root[c + 1] == (int32_t)c;
+            if (j > 0) master |= root[c - d.nx] == (int32_t)c;
+            if (j < d.ny - 1) master |= root[c + d.nx] == (int32_t)c;
+            if (k > 0) master |= root[c - d.plane] == (int32_t)c;
+            if (k < d.nz - 1) master |= root[c + d.plane] == (int32_t)c;
+            if (!master) v |= (1u << b);
+        }
+        red[w] = v;
+        excl[w] = v | slave[w];
+        if (v) atomicAdd(count, (unsigned int)__popc(v));
+    }
+}
+
 struct Flux6 {
     const double* g[6];
 };
@@ -478,6 +510,7 @@ vofp_status build_operator(vofp_ctx* c, const double* F, const double* ax, const
             (s = c->alloc(&c->Txs, N)) || (s = c->alloc(&c->Tys, N)) || (s = c->alloc(&c->Tzs, N)) ||
             (s = c->alloc(&c->Txf, N)) || (s = c->alloc(&c->Tyf, N)) || (s = c->alloc(&c->Tzf, N)) ||
             (s = c->alloc(&c->slave_bits, (N + 31) / 32)) || (s = c->alloc(&c->root, N)) ||
+            (s = c->alloc(&c->red_bits, (N + 31) / 32)) || (s = c->alloc(&c->excl_bits, (N + 31) / 32)) ||
             (s = c->alloc(&c->inactive, N)) || (s = c->alloc(&c->work, N)) ||
             (s = c->alloc(&c->partials, kMaxPartials)) || (s = c->alloc(&c->counters, 64)) ||
             (s = c->alloc(&c->sc, 4)))
@@ -642,6 +675,16 @@ vofp_status build_operator(vofp_ctx* c, const double* F, const double* ax, const
                                                                   c->Tx, c->Ty, c->Tz, c->s, c->sq, c->gcorr);
     launch(c, k_scaled_coeffs, gN, kNT, st, d, c->s, c->Tx, c->Ty, c->Tz, c->Txs, c->Tys, c->Tzs, c->Txf, c->Tyf, c->Tzf);
     launch(c, k_slave_bits, grid_for((N + 31) / 32), kNT, st, d, c->root, c->slave_bits);
+    {
+        unsigned int* nred = c->counters + 35;
+        VOFP_CUDA_TRY(c, cudaMemsetAsync(nred, 0, sizeof(unsigned int), st));
+        launch(c, k_red_bits, grid_for((N + 31) / 32), kNT, st, d, (const int32_t*)c->root,
+               (const uint32_t*)c->slave_bits, c->red_bits, c->excl_bits, nred);
+        unsigned int h = 0;
+        VOFP_CUDA_TRY(c, cudaMemcpyAsync(&h, nred, sizeof(h), cudaMemcpyDeviceToHost, st));
+        VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
+        c->n_red = h;
+    }
     VOFP_CUDA_TRY(c, cudaGetLastError());
     VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
     c->built = true;

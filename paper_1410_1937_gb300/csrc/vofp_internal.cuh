@@ -42,7 +42,8 @@ struct CgScalars {
     long long iter_total;
     long long max_iter;
     int status;         // vofp_status of the loop
-    int done;           // 1 when the loop has finished
+    int done;           // 1 when the (outer) loop has finished
+    int inner_done;     // 1 when the current inner loop has finished
     int outer;          // refinement steps
     int timing;         // 1 while the measurement hook runs: breakdowns are not recorded
 };
@@ -78,6 +79,12 @@ struct vofp_ctx {
     double *Txs = nullptr, *Tys = nullptr, *Tzs = nullptr;     // s_L T s_R
     float *Txf = nullptr, *Tyf = nullptr, *Tzf = nullptr;      // FP32 copies
     uint32_t* slave_bits = nullptr;   // bit c set when c belongs to another cell's group
+    // red-black elimination (Eisenstat form of red-black symmetric Gauss-Seidel): bit c of red_bits
+    // is set for "red" cells -- (i+j+k) even, with an unknown, in no merge group -- whose unknowns
+    // are eliminated; excl_bits = slave_bits | red_bits marks cells left out of the reduced dots
+    uint32_t* red_bits = nullptr;
+    uint32_t* excl_bits = nullptr;
+    long long n_red = 0;
     int32_t* root = nullptr;          // group root per cell, -1 without unknown
     uint8_t* inactive = nullptr;
     // merge groups with more than one cell: cells of group g are gcells[gptr[g] .. gptr[g+1]),
@@ -107,7 +114,6 @@ struct vofp_ctx {
     size_t bytes = 0;
     std::vector<void*> allocs;
     long long launches = 0;           // kernels launched (graph bodies counted per execution)
-    int zchunk = 16;                  // planes marched by one stencil block
 
     void set_error(const std::string& m) { err = m; }
     template <typename T>
@@ -137,7 +143,8 @@ vofp_status apply_unscaled(vofp_ctx* c, const double* x, double* y);
 vofp_status residual(vofp_ctx* c, const double* b, const double* x, double* rel);
 vofp_status solve(vofp_ctx* c, const double* b, double* x, const vofp_solve_opts* o,
                   vofp_solve_info* info);
-vofp_status time_iteration_kernels(vofp_ctx* c, int precision, int reps, float* st, float* up);
+vofp_status time_iteration_kernels(vofp_ctx* c, int precision, bool rb, int reps, float* st, float* up,
+                                   float* red);
 
 // group helpers (vofp_assemble.cu)
 void launch_group_expand(vofp_ctx* c, double* v);

@@ -107,7 +107,7 @@ __device__ __forceinline__ bool grid_reduce(double part, double* partials, unsig
 }
 
 // Fused direction update + stencil + dot (ST_CG), or a plain operator apply.
-// A block of kBX x kBY threads owns a kBX x kBY column tile and marches `zchunk` planes in z.
+// A block of kBX x kBY threads marches kBX x kBY column tiles in z over its share of tile-planes.
 // Plane k (with a one-cell halo) and the own columns of planes k-1 and k+1 sit in four rotating
 // shared buffers (one barrier per plane); the raw inputs of planes k+1 .. k+PF are prefetched
 // into registers one barrier ahead, so global loads overlap the arithmetic of the plane before.
@@ -120,134 +120,222 @@ struct StCoef {
     V txp, txm, typ, tym, tzp, xo, dg;
 };
 
-template <typename V, int MODE, int PF>
+template <typename V, int MODE, int PF, bool RB = false>
 __global__ void __launch_bounds__(kBX* kBY, 4)
-k_stencil(const Dims d, const int zchunk, const V* __restrict__ Tx, const V* __restrict__ Ty,
+k_stencil(const Dims d, const int per_block, const V* __restrict__ Tx, const V* __restrict__ Ty,
           const V* __restrict__ Tz, const double* __restrict__ diag, const V* __restrict__ src,
           const V* __restrict__ pold, V* __restrict__ pnew, V* __restrict__ xv, V* __restrict__ out,
-          CgScalars* __restrict__ sc, double* __restrict__ partials, unsigned int* __restrict__ counter) {
+          CgScalars* __restrict__ sc, double* __restrict__ partials, unsigned int* __restrict__ counter,
+          const uint32_t* __restrict__ red) {
     using Acc = typename AccFor<V>::type;
     constexpr bool CG = MODE == ST_CG;
     __shared__ V tile[4][kBY + 2][kBX + 2];
     __shared__ double sh[32];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + kBX * ty;
-    const int i0 = blockIdx.x * kBX, j0 = blockIdx.y * kBY;
-    const int i = i0 + tx, j = j0 + ty;
-    const int k0 = blockIdx.z * zchunk;
-    const int k1 = min(k0 + zchunk, d.nz);
-    const bool inside = i < d.nx && j < d.ny;
-    const long long own = inside ? i + (long long)d.nx * j : 0;
-    // this thread's halo element: rows j0-1 and j0+kBY, then columns i0-1 and i0+kBX
-    int hi = 0, hj = 0;
-    long long hoff = -1;
-    const bool has_halo = tid < kHalo;
-    if (has_halo) {
-        int gi, gj;
-        if (tid < kBX) {
-            gi = i0 + tid; gj = j0 - 1; hi = tid + 1; hj = 0;
-        } else if (tid < 2 * kBX) {
-            gi = i0 + tid - kBX; gj = j0 + kBY; hi = tid - kBX + 1; hj = kBY + 1;
-        } else if (tid < 2 * kBX + kBY) {
-            gi = i0 - 1; gj = j0 + tid - 2 * kBX; hi = 0; hj = tid - 2 * kBX + 1;
-        } else {
-            gi = i0 + kBX; gj = j0 + tid - 2 * kBX - kBY; hi = kBX + 1; hj = tid - 2 * kBX - kBY + 1;
-        }
-        if (gi >= 0 && gi < d.nx && gj >= 0 && gj < d.ny) hoff = gi + (long long)d.nx * gj;
-    }
     V beta = V(0), alpha = V(0);
     if (CG) {
         beta = (V)sc->beta;
         alpha = (V)sc->alpha;
     }
-    auto load = [&](int kk, V& r_, V& p_, V& hr, V& hp) {
-        r_ = V(0); p_ = V(0); hr = V(0); hp = V(0);
-        if (kk < 0 || kk >= d.nz) return;
-        const long long base = (long long)kk * d.plane;
-        if (inside) {
-            r_ = src[base + own];
-            if (CG) p_ = pold[base + own];
-        }
-        if (hoff >= 0) {
-            hr = src[base + hoff];
-            if (CG) hp = pold[base + hoff];
-        }
-    };
-    auto store = [&](int b, V r_, V p_, V hr, V hp) {
-        tile[b][ty + 1][tx + 1] = CG ? fmav(beta, p_, r_) : r_;
-        if (has_halo) tile[b][hj][hi] = CG ? fmav(beta, hp, hr) : hr;
-    };
-    auto loadc = [&](int kk, StCoef<V>& c) {
-        c.txp = c.txm = c.typ = c.tym = c.tzp = c.xo = c.dg = V(0);
-        if (!inside || kk >= k1) return;
-        const long long cc = (long long)kk * d.plane + own;
-        c.txp = Tx[cc];
-        c.txm = i > 0 ? Tx[cc - 1] : V(0);
-        c.typ = Ty[cc];
-        c.tym = j > 0 ? Ty[cc - d.nx] : V(0);
-        c.tzp = Tz[cc];
-        if (CG) c.xo = xv[cc];
-        if (MODE == ST_APPLY_UNSCALED) c.dg = (V)diag[cc];
-    };
-
-    V rr_[PF], pp_[PF], hr_[PF], hp_[PF];
-    {
-        V a, b, c2, e;
-        load(k0 - 1, a, b, c2, e);
-        store(0, a, b, c2, e);
-    }
-    V po_cur;
-    {
-        V a, c2, e;
-        load(k0, a, po_cur, c2, e);
-        store(1, a, po_cur, c2, e);
-    }
-#pragma unroll
-    for (int q = 0; q < PF; ++q) {
-        if (k0 + 1 + q <= k1) load(k0 + 1 + q, rr_[q], pp_[q], hr_[q], hp_[q]);
-        else rr_[q] = pp_[q] = hr_[q] = hp_[q] = V(0);
-    }
-    StCoef<V> cc;
-    loadc(k0, cc);
-    V tzm1 = (inside && k0 > 0) ? Tz[(long long)(k0 - 1) * d.plane + own] : V(0);
     Acc acc;
-    for (int k = k0; k < k1; ++k) {
-        const int rel = k - k0 + 1;
-        const int bm = (rel + 3) & 3, b0 = rel & 3, bp = (rel + 1) & 3;
-        store(bp, rr_[0], pp_[0], hr_[0], hp_[0]);
-        const V po_next = pp_[0];
-#pragma unroll
-        for (int q = 0; q < PF - 1; ++q) {
-            rr_[q] = rr_[q + 1]; pp_[q] = pp_[q + 1]; hr_[q] = hr_[q + 1]; hp_[q] = hp_[q + 1];
-        }
-        const int kn = k + 1 + PF;
-        if (kn <= k1) load(kn, rr_[PF - 1], pp_[PF - 1], hr_[PF - 1], hp_[PF - 1]);
-        StCoef<V> cn;
-        loadc(k + 1, cn);
-        __syncthreads();
-        if (inside) {
-            const long long c = (long long)k * d.plane + own;
-            const V v = tile[b0][ty + 1][tx + 1];
-            V t = (MODE == ST_APPLY_UNSCALED) ? cc.dg * v : v;
-            t = fmav(-cc.txp, tile[b0][ty + 1][tx + 2], t);
-            t = fmav(-cc.txm, tile[b0][ty + 1][tx], t);
-            t = fmav(-cc.typ, tile[b0][ty + 2][tx + 1], t);
-            t = fmav(-cc.tym, tile[b0][ty][tx + 1], t);
-            t = fmav(-cc.tzp, tile[bp][ty + 1][tx + 1], t);
-            t = fmav(-tzm1, tile[bm][ty + 1][tx + 1], t);
-            out[c] = t;
-            if (CG) {
-                pnew[c] = v;
-                xv[c] = fmav(alpha, po_cur, cc.xo);
-                acc.add(v, t);
+    // This block's share of the work: the tile-planes [w0, w1) in tile-major order, so every block
+    // marches the same number of planes (one wave, no tail) in at most a few column segments.
+    const int tiles_x = (d.nx + kBX - 1) / kBX;
+    const long long ntiles = (long long)tiles_x * ((d.ny + kBY - 1) / kBY);
+    const long long total = ntiles * d.nz;
+    const long long w0 = min((long long)blockIdx.x * per_block, total);
+    const long long w1 = min(w0 + per_block, total);
+    for (long long w = w0; w < w1;) {
+        const long long tile_id = w / d.nz;
+        const int k0 = int(w - tile_id * d.nz);
+        const int k1 = (int)min((long long)d.nz, (long long)k0 + (w1 - w));
+        w += k1 - k0;
+        const int i0 = int(tile_id % tiles_x) * kBX, j0 = int(tile_id / tiles_x) * kBY;
+        const int i = i0 + tx, j = j0 + ty;
+        const bool inside = i < d.nx && j < d.ny;
+        const long long own = inside ? i + (long long)d.nx * j : 0;
+        // this thread's halo element: rows j0-1 and j0+kBY, then columns i0-1 and i0+kBX
+        int hi = 0, hj = 0;
+        long long hoff = -1;
+        const bool has_halo = tid < kHalo;
+        if (has_halo) {
+            int gi, gj;
+            if (tid < kBX) {
+                gi = i0 + tid; gj = j0 - 1; hi = tid + 1; hj = 0;
+            } else if (tid < 2 * kBX) {
+                gi = i0 + tid - kBX; gj = j0 + kBY; hi = tid - kBX + 1; hj = kBY + 1;
+            } else if (tid < 2 * kBX + kBY) {
+                gi = i0 - 1; gj = j0 + tid - 2 * kBX; hi = 0; hj = tid - 2 * kBX + 1;
+            } else {
+                gi = i0 + kBX; gj = j0 + tid - 2 * kBX - kBY; hi = kBX + 1; hj = tid - 2 * kBX - kBY + 1;
             }
+            if (gi >= 0 && gi < d.nx && gj >= 0 && gj < d.ny) hoff = gi + (long long)d.nx * gj;
         }
-        tzm1 = cc.tzp;
-        cc = cn;
-        po_cur = po_next;
+        auto load = [&](int kk, V& r_, V& p_, V& hr, V& hp) {
+            r_ = V(0); p_ = V(0); hr = V(0); hp = V(0);
+            if (kk < 0 || kk >= d.nz) return;
+            const long long base = (long long)kk * d.plane;
+            if (inside) {
+                r_ = src[base + own];
+                if (CG) p_ = pold[base + own];
+            }
+            if (hoff >= 0) {
+                hr = src[base + hoff];
+                if (CG) hp = pold[base + hoff];
+            }
+        };
+        auto store = [&](int b, V r_, V p_, V hr, V hp) {
+            tile[b][ty + 1][tx + 1] = CG ? fmav(beta, p_, r_) : r_;
+            if (has_halo) tile[b][hj][hi] = CG ? fmav(beta, hp, hr) : hr;
+        };
+        auto loadc = [&](int kk, StCoef<V>& c) {
+            c.txp = c.txm = c.typ = c.tym = c.tzp = c.xo = c.dg = V(0);
+            if (!inside || kk >= k1) return;
+            const long long cc = (long long)kk * d.plane + own;
+            c.txp = Tx[cc];
+            c.txm = i > 0 ? Tx[cc - 1] : V(0);
+            c.typ = Ty[cc];
+            c.tym = j > 0 ? Ty[cc - d.nx] : V(0);
+            c.tzp = Tz[cc];
+            if (CG) c.xo = xv[cc];
+            if (MODE == ST_APPLY_UNSCALED) c.dg = (V)diag[cc];
+        };
+
+        // the previous segment's last readers of the buffers must be done before they are refilled
+        __syncthreads();
+        V rr_[PF], pp_[PF], hr_[PF], hp_[PF];
+        {
+            V a, b, c2, e;
+            load(k0 - 1, a, b, c2, e);
+            store(0, a, b, c2, e);
+        }
+        V po_cur;
+        {
+            V a, c2, e;
+            load(k0, a, po_cur, c2, e);
+            store(1, a, po_cur, c2, e);
+        }
+#pragma unroll
+        for (int q = 0; q < PF; ++q) {
+            if (k0 + 1 + q <= k1) load(k0 + 1 + q, rr_[q], pp_[q], hr_[q], hp_[q]);
+            else rr_[q] = pp_[q] = hr_[q] = hp_[q] = V(0);
+        }
+        StCoef<V> cc;
+        loadc(k0, cc);
+        V tzm1 = (inside && k0 > 0) ? Tz[(long long)(k0 - 1) * d.plane + own] : V(0);
+        for (int k = k0; k < k1; ++k) {
+            const int rel = k - k0 + 1;
+            const int bm = (rel + 3) & 3, b0 = rel & 3, bp = (rel + 1) & 3;
+            store(bp, rr_[0], pp_[0], hr_[0], hp_[0]);
+            const V po_next = pp_[0];
+#pragma unroll
+            for (int q = 0; q < PF - 1; ++q) {
+                rr_[q] = rr_[q + 1]; pp_[q] = pp_[q + 1]; hr_[q] = hr_[q + 1]; hp_[q] = hp_[q + 1];
+            }
+            const int kn = k + 1 + PF;
+            if (kn <= k1) load(kn, rr_[PF - 1], pp_[PF - 1], hr_[PF - 1], hp_[PF - 1]);
+            StCoef<V> cn;
+            loadc(k + 1, cn);
+            __syncthreads();
+            // red-black mode: red cells hold E p (written by k_red) and are not rows of the system
+            const bool row = inside && !(RB && ((red[((long long)k * d.plane + own) >> 5] >>
+                                                  (((long long)k * d.plane + own) & 31)) & 1u));
+            if (row) {
+                const long long c = (long long)k * d.plane + own;
+                const V v = tile[b0][ty + 1][tx + 1];
+                V t = (MODE == ST_APPLY_UNSCALED) ? cc.dg * v : v;
+                t = fmav(-cc.txp, tile[b0][ty + 1][tx + 2], t);
+                t = fmav(-cc.txm, tile[b0][ty + 1][tx], t);
+                t = fmav(-cc.typ, tile[b0][ty + 2][tx + 1], t);
+                t = fmav(-cc.tym, tile[b0][ty][tx + 1], t);
+                t = fmav(-cc.tzp, tile[bp][ty + 1][tx + 1], t);
+                t = fmav(-tzm1, tile[bm][ty + 1][tx + 1], t);
+                out[c] = t;
+                if (CG) {
+                    pnew[c] = v;
+                    xv[c] = fmav(alpha, po_cur, cc.xo);
+                    acc.add(v, t);
+                }
+            }
+            tzm1 = cc.tzp;
+            cc = cn;
+            po_cur = po_next;
+        }
     }
     if (CG) {
         double tot;
         if (grid_reduce(acc.value(), partials, counter, sh, &tot)) sc->pq_raw = tot;
+    }
+}
+
+// Red-black elimination (Eisenstat's form of red-black symmetric Gauss-Seidel).  On the scaled
+// operator I - E the red block is the identity, so red unknowns are eliminated exactly:
+// x_R = b_R + E_RS x_S, and CG runs on the Schur complement S = I_SS - E_SS - E_SR E_RS of the
+// remaining (black and merge-group) unknowns.  Each iteration first writes w_R = E_RS p into the
+// red entries of r (red cells have no other use for them), then the unchanged stencil applies
+// I - E to that vector on the black rows.
+// k_red: for every red cell, r_c = sum over its six faces of T_f * (r_nb + beta p_old,nb), the
+// direction of the black neighbour formed with the same fused multiply-add as the stencil.
+template <typename V>
+__global__ void __launch_bounds__(kRedThreads)
+k_red(const Dims d, const V* __restrict__ Tx, const V* __restrict__ Ty, const V* __restrict__ Tz,
+      const uint32_t* __restrict__ red, V* __restrict__ r, const V* __restrict__ pold,
+      const CgScalars* __restrict__ sc) {
+    const V beta = (V)sc->beta;
+    const long long rows = (long long)d.ny * d.nz;
+    const int half = (d.nx + 1) / 2;
+    for (long long row = blockIdx.y; row < rows; row += gridDim.y) {
+        const int j = int(row % d.ny), k = int(row / d.ny);
+        const int par = (j + k) & 1;
+        for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < half; m += gridDim.x * blockDim.x) {
+            const int i = 2 * m + par;
+            if (i >= d.nx) continue;
+            const long long c = i + (long long)d.nx * row;
+            if (!((red[c >> 5] >> (c & 31)) & 1u)) continue;
+            V acc = V(0);
+            if (i > 0) acc = fmav(Tx[c - 1], fmav(beta, pold[c - 1], r[c - 1]), acc);
+            if (i < d.nx - 1) acc = fmav(Tx[c], fmav(beta, pold[c + 1], r[c + 1]), acc);
+            if (j > 0) acc = fmav(Ty[c - d.nx], fmav(beta, pold[c - d.nx], r[c - d.nx]), acc);
+            if (j < d.ny - 1) acc = fmav(Ty[c], fmav(beta, pold[c + d.nx], r[c + d.nx]), acc);
+            if (k > 0) acc = fmav(Tz[c - d.plane], fmav(beta, pold[c - d.plane], r[c - d.plane]), acc);
+            if (k < d.nz - 1) acc = fmav(Tz[c], fmav(beta, pold[c + d.plane], r[c + d.plane]), acc);
+            r[c] = acc;
+        }
+    }
+}
+
+// Set-up and reconstruction gathers on the scaled FP64 operator (not in the iteration loop):
+//   to_red = 1: for red cells    dst_c = base_c + sum_nb T_f src_nb   (others untouched)
+//   to_red = 0: for non-red cells dst_c = base_c + sum over red nb of T_f src_nb, and 0 at red cells
+// base may be null (0).
+__global__ void __launch_bounds__(kRedThreads)
+k_rb_gather(const Dims d, const double* __restrict__ Tx, const double* __restrict__ Ty,
+            const double* __restrict__ Tz, const uint32_t* __restrict__ red, const double* __restrict__ src,
+            const double* __restrict__ base, double* __restrict__ dst, int to_red) {
+    const long long rows = (long long)d.ny * d.nz;
+    auto is_red = [&](long long c) { return (red[c >> 5] >> (c & 31)) & 1u; };
+    for (long long row = blockIdx.y; row < rows; row += gridDim.y) {
+        const int j = int(row % d.ny), k = int(row / d.ny);
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.nx; i += gridDim.x * blockDim.x) {
+            const long long c = i + (long long)d.nx * row;
+            const bool rc = is_red(c);
+            if (to_red && !rc) continue;
+            if (!to_red && rc) {
+                dst[c] = 0.0;
+                continue;
+            }
+            double acc = base ? base[c] : 0.0;
+            auto term = [&](long long n, double T) {
+                if (to_red || is_red(n)) acc = fma(T, src[n], acc);
+            };
+            if (i > 0) term(c - 1, Tx[c - 1]);
+            if (i < d.nx - 1) term(c + 1, Tx[c]);
+            if (j > 0) term(c - d.nx, Ty[c - d.nx]);
+            if (j < d.ny - 1) term(c + d.nx, Ty[c]);
+            if (k > 0) term(c - d.plane, Tz[c - d.plane]);
+            if (k < d.nz - 1) term(c + d.plane, Tz[c]);
+            dst[c] = acc;
+        }
     }
 }
 
@@ -292,12 +380,22 @@ k_cg_update(long long n, V* __restrict__ r, const V* __restrict__ q, const uint3
             cudaGraphConditionalHandle handle, int use_handle) {
     using Acc = typename AccFor<V>::type;
     __shared__ double sh[32];
-    const double rr = sc->rr;
-    const double pq = sc->pq_raw + sc->pq_corr;
-    // rr == 0: the residual vanished exactly (later unrolled iterations are no-ops, not breakdowns)
-    const bool ok = sc->status == VOFP_OK && (pq > 0.0) && isfinite(pq) && isfinite(rr) && rr > 0.0;
-    const bool broke = !ok && !(rr == 0.0 && sc->status == VOFP_OK);
-    const double alpha_d = ok ? rr / pq : 0.0;
+    __shared__ double s_alpha;
+    __shared__ int s_flags;
+    // the scalar step is computed once per block (FP64 division is slow on this part)
+    if (threadIdx.x == 0) {
+        const double rr = sc->rr;
+        const double pq = sc->pq_raw + sc->pq_corr;
+        // rr == 0: the residual vanished exactly (later unrolled iterations are no-ops)
+        const bool ok = sc->status == VOFP_OK && (pq > 0.0) && isfinite(pq) && isfinite(rr) && rr > 0.0;
+        const bool broke = !ok && !(rr == 0.0 && sc->status == VOFP_OK);
+        s_alpha = ok ? rr / pq : 0.0;
+        s_flags = (ok ? 1 : 0) | (broke ? 2 : 0);
+    }
+    __syncthreads();
+    const double alpha_d = s_alpha;
+    const bool ok = s_flags & 1;
+    const bool broke = (s_flags & 2) != 0;
     const V alpha = (V)alpha_d;
     Acc acc;
     constexpr int VW = sizeof(V) == 8 ? 2 : 4;
@@ -356,6 +454,7 @@ k_cg_update(long long n, V* __restrict__ r, const V* __restrict__ q, const uint3
     }
     double tot;
     if (grid_reduce(acc.value(), partials, counter, sh, &tot)) {
+        const double rr = sc->rr;
         sc->rr = tot;
         sc->beta = (rr > 0.0) ? tot / rr : 0.0;
         sc->alpha = alpha_d;
@@ -369,7 +468,7 @@ k_cg_update(long long n, V* __restrict__ r, const V* __restrict__ q, const uint3
         if (INNER) {
             bool stop = broke || !isfinite(tot) || tot <= sc->inner_target * sc->inner_target * sc->rr0 ||
                         sc->iter >= sc->max_iter || sc->iter_total >= sc->max_iter;
-            if (stop) sc->done = 1;
+            if (stop) sc->inner_done = 1;
             if (use_handle && stop) cudaGraphSetConditional(handle, 0);
         }
     }

@@ -13,13 +13,24 @@ constexpr int kNT = kRedThreads;
 
 int stream_grid(long long n) {
     long long b = (n + kNT - 1) / kNT;
-    long long cap = (long long)num_sms() * 8;
+    long long cap = (long long)num_sms() * 4;
     return int(std::max(1LL, std::min(b, cap)));
 }
 
-dim3 stencil_grid(const vofp_ctx* c) {
-    return dim3(ceil_div(c->d.nx, kBX), ceil_div(c->d.ny, kBY), ceil_div(c->d.nz, c->zchunk));
+// persistent stencil grid: 4 resident blocks per SM, each marching an equal share of tile-planes
+int stencil_blocks(const vofp_ctx* c) {
+    const long long tiles = (long long)ceil_div(c->d.nx, kBX) * ceil_div(c->d.ny, kBY);
+    const long long total = tiles * c->d.nz;
+    const long long want = (long long)num_sms() * 4;
+    return (int)std::max(1LL, std::min(want, total));
 }
+int stencil_per_block(const vofp_ctx* c) {
+    const long long tiles = (long long)ceil_div(c->d.nx, kBX) * ceil_div(c->d.ny, kBY);
+    const long long total = tiles * c->d.nz;
+    const int nb = stencil_blocks(c);
+    return (int)((total + nb - 1) / nb);
+}
+dim3 stencil_grid(const vofp_ctx* c) { return dim3(stencil_blocks(c)); }
 
 // register prefetch depth of the stencil: deeper for FP32, whose planes carry half the bytes
 template <typename V>
@@ -157,6 +168,16 @@ __global__ void k_set_pq_inf(CgScalars* sc, int timing) {
     sc->timing = timing;
 }
 
+// v_m = sum over the group of v, written to every cell of the group
+__global__ void k_group_fold_d(int ng, const int* __restrict__ gptr, const int* __restrict__ gcells,
+                               double* __restrict__ v) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    double sum = 0.0;
+    for (int t = gptr[g]; t < gptr[g + 1]; ++t) sum += v[gcells[t]];
+    for (int t = gptr[g]; t < gptr[g + 1]; ++t) v[gcells[t]] = sum;
+}
+
 // ---- mixed precision ----------------------------------------------------------------------
 // Outer step of iterative refinement: r = bt - q (q = scaled A x_t, FP64), true residual check,
 // and the FP32 right-hand side of the next inner solve, normalised to unit norm.
@@ -164,7 +185,7 @@ __global__ void k_outer_residual(long long n, const double* __restrict__ bt, con
                                  const double* __restrict__ sq, const uint32_t* __restrict__ bits,
                                  double* __restrict__ r, CgScalars* sc, double* __restrict__ partials,
                                  unsigned int* __restrict__ counter, cudaGraphConditionalHandle h_outer,
-                                 cudaGraphConditionalHandle h_inner) {
+                                 cudaGraphConditionalHandle h_inner, int use_handles) {
     __shared__ double sh[32];
     double a = 0.0, b = 0.0;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
@@ -193,8 +214,10 @@ __global__ void k_outer_residual(long long n, const double* __restrict__ bt, con
         }
         sc->done = stop ? 1 : 0;
         if (!stop) sc->outer += 1;
-        cudaGraphSetConditional(h_outer, stop ? 0u : 1u);
-        cudaGraphSetConditional(h_inner, stop ? 0u : 1u);
+        if (use_handles) {
+            cudaGraphSetConditional(h_outer, stop ? 0u : 1u);
+            cudaGraphSetConditional(h_inner, stop ? 0u : 1u);
+        }
     }
 }
 
@@ -223,6 +246,7 @@ __global__ void k_inner_prep(long long n, const double* __restrict__ r, const ui
         sc->alpha = 0.0;
         sc->beta = 0.0;
         sc->iter = 0;
+        sc->inner_done = 0;
         const double rr0 = t;
         sc->rr0 = rr0;
     }
@@ -239,18 +263,92 @@ __global__ void k_inner_finish(long long n, float* __restrict__ xf, const float*
     }
 }
 
+// dst = a + b at cells outside the red set, 0 at red cells; ||dst||^2 over cells outside `excl`
+// to sc->rr0 (the reduced right-hand side of a red-black inner solve and its norm)
+__global__ void k_reduced_rhs(long long n, const double* __restrict__ a, const double* __restrict__ b,
+                              const uint32_t* __restrict__ red, const uint32_t* __restrict__ excl,
+                              double* __restrict__ dst, CgScalars* sc, double* __restrict__ partials,
+                              unsigned int* __restrict__ counter, int norm) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const double v = is_slave(red, c) ? 0.0 : a[c] + b[c];
+        dst[c] = v;
+        if (!is_slave(excl, c)) acc = fma(v, v, acc);
+    }
+    if (norm) {
+        double t;
+        if (grid_reduce(acc, partials, counter, sh, &t)) sc->rr0 = t;
+    }
+}
+
+// x = s * x_t at every cell (after the red unknowns are reconstructed)
+__global__ void k_unscale(long long n, const double* __restrict__ xt, const double* __restrict__ s,
+                          double* __restrict__ xout) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+        xout[c] = s[c] * xt[c];
+}
+
+// end of a red-black inner solve: x_f += alpha p_f at every cell (red entries of p_f are 0)
+__global__ void k_inner_xf(long long n, float* __restrict__ xf, const float* __restrict__ pf, const CgScalars* sc) {
+    const float alpha = (float)sc->alpha;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+        xf[c] = __fmaf_rn(alpha, pf[c], xf[c]);
+}
+
+// correction d of A d = r from the reduced solution: d_S = scale x_f, d_R = r_R + scale E_RS x_f
+// (FP64 coefficients); x_t += d
+__global__ void __launch_bounds__(kRedThreads)
+k_inner_finish_rb(const Dims d, const double* __restrict__ Tx, const double* __restrict__ Ty,
+                  const double* __restrict__ Tz, const uint32_t* __restrict__ red, const float* __restrict__ xf,
+                  const double* __restrict__ r, double* __restrict__ xt, const CgScalars* sc) {
+    const double scale = sc->scale;
+    const long long rows = (long long)d.ny * d.nz;
+    for (long long row = blockIdx.y; row < rows; row += gridDim.y) {
+        const int j = int(row % d.ny), k = int(row / d.ny);
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.nx; i += gridDim.x * blockDim.x) {
+            const long long c = i + (long long)d.nx * row;
+            if (!is_slave(red, c)) {
+                xt[c] = fma(scale, (double)xf[c], xt[c]);
+                continue;
+            }
+            double acc = 0.0;
+            if (i > 0) acc = fma(Tx[c - 1], (double)xf[c - 1], acc);
+            if (i < d.nx - 1) acc = fma(Tx[c], (double)xf[c + 1], acc);
+            if (j > 0) acc = fma(Ty[c - d.nx], (double)xf[c - d.nx], acc);
+            if (j < d.ny - 1) acc = fma(Ty[c], (double)xf[c + d.nx], acc);
+            if (k > 0) acc = fma(Tz[c - d.plane], (double)xf[c - d.plane], acc);
+            if (k < d.nz - 1) acc = fma(Tz[c], (double)xf[c + d.plane], acc);
+            if (scale > 0.0) xt[c] += r[c] + scale * acc;
+        }
+    }
+}
+
+dim3 rows_grid(const vofp_ctx* c, int threads) {
+    const long long rows = (long long)c->d.ny * c->d.nz;
+    const int gx = ceil_div(c->d.nx, threads);
+    return dim3(gx, (unsigned)std::max(1LL, std::min(rows, (long long)num_sms() * 32)));
+}
+dim3 red_grid(const vofp_ctx* c) {
+    const long long rows = (long long)c->d.ny * c->d.nz;
+    const int gx = ceil_div((c->d.nx + 1) / 2, kNT);
+    return dim3(gx, (unsigned)std::max(1LL, std::min(rows, (long long)num_sms() * 32)));
+}
+
 }  // namespace
 
 // ---- launch helpers --------------------------------------------------------------------------
 
 void launch_stencil_apply_unscaled(vofp_ctx* c, const double* x, double* t) {
     launch(c, k_stencil<double, ST_APPLY_UNSCALED, 1>, stencil_grid(c), dim3(kBX, kBY), c->stream, 
-        c->d, c->zchunk, c->Tx, c->Ty, c->Tz, c->diag, x, nullptr, nullptr, nullptr, t, c->sc, c->partials, c->counters);
+        c->d, stencil_per_block(c), c->Tx, c->Ty, c->Tz, c->diag, x, nullptr, nullptr, nullptr, t, c->sc, c->partials, c->counters,
+        (const uint32_t*)nullptr);
 }
 
 void launch_stencil_apply_scaled(vofp_ctx* c, const double* x, double* t) {
     launch(c, k_stencil<double, ST_APPLY_SCALED, 1>, stencil_grid(c), dim3(kBX, kBY), c->stream, 
-        c->d, c->zchunk, c->Txs, c->Tys, c->Tzs, nullptr, x, nullptr, nullptr, nullptr, t, c->sc, c->partials, c->counters);
+        c->d, stencil_per_block(c), c->Txs, c->Tys, c->Tzs, nullptr, x, nullptr, nullptr, nullptr, t, c->sc, c->partials, c->counters,
+        (const uint32_t*)nullptr);
 }
 
 template <typename V>
@@ -264,22 +362,48 @@ template void launch_group_patch<float>(vofp_ctx*, float*, const float*, bool);
 
 namespace {
 
-// one CG iteration on stream st (FP64 or FP32), reading p_old from `po` and writing `pn`
+// one CG iteration on stream st (FP64 or FP32), reading p_old from `po` and writing `pn`; in
+// red-black mode the red half-stencil runs first and the stencil skips red rows
 template <typename V>
 void launch_cg_iteration(vofp_ctx* c, cudaStream_t st, V* r, V* po, V* pn, V* xv, V* q,
-                         const V* Tx, const V* Ty, const V* Tz, bool inner,
+                         const V* Tx, const V* Ty, const V* Tz, bool inner, bool rb,
                          cudaGraphConditionalHandle h, int use_h) {
-    launch(c, k_stencil<V, ST_CG, stencil_pf<V>()>, stencil_grid(c), dim3(kBX, kBY), st, c->d, c->zchunk, Tx, Ty, Tz, nullptr, r, po, pn, xv, q,
-                                                                       c->sc, c->partials, c->counters);
+    const uint32_t* bits = rb ? c->excl_bits : c->slave_bits;
+    if (rb) {
+        launch(c, k_red<V>, red_grid(c), dim3(kNT), st, c->d, Tx, Ty, Tz, (const uint32_t*)c->red_bits, r,
+               (const V*)po, (const CgScalars*)c->sc);
+        launch(c, k_stencil<V, ST_CG, stencil_pf<V>(), true>, stencil_grid(c), dim3(kBX, kBY), st, c->d,
+               stencil_per_block(c), Tx, Ty, Tz, (const double*)nullptr, (const V*)r, (const V*)po, pn, xv, q, c->sc,
+               c->partials, c->counters, (const uint32_t*)c->red_bits);
+    } else {
+        launch(c, k_stencil<V, ST_CG, stencil_pf<V>(), false>, stencil_grid(c), dim3(kBX, kBY), st, c->d,
+               stencil_per_block(c), Tx, Ty, Tz, (const double*)nullptr, (const V*)r, (const V*)po, pn, xv, q, c->sc,
+               c->partials, c->counters, (const uint32_t*)nullptr);
+    }
     if (c->ngroups > 0)
         launch(c, k_group_patch<V>, ceil_div(c->ngroups, kNT), kNT, st, c->ngroups, c->gptr, c->gcells, c->gcorr, q, pn,
-                                                                    1, c->sc, c->partials, c->counters);
+               1, c->sc, c->partials, c->counters);
     if (inner)
-        launch(c, k_cg_update<V, true>, stream_grid(c->d.n / (sizeof(V) == 8 ? 2 : 4) + 1), kNT, st, 
-            c->d.n, r, q, c->slave_bits, c->sc, c->partials, c->counters, h, use_h);
+        launch(c, k_cg_update<V, true>, stream_grid(c->d.n / (sizeof(V) == 8 ? 2 : 4) + 1), kNT, st,
+               c->d.n, r, (const V*)q, bits, c->sc, c->partials, c->counters, h, use_h);
     else
-        launch(c, k_cg_update<V, false>, stream_grid(c->d.n / (sizeof(V) == 8 ? 2 : 4) + 1), kNT, st, 
-            c->d.n, r, q, c->slave_bits, c->sc, c->partials, c->counters, h, use_h);
+        launch(c, k_cg_update<V, false>, stream_grid(c->d.n / (sizeof(V) == 8 ? 2 : 4) + 1), kNT, st,
+               c->d.n, r, (const V*)q, bits, c->sc, c->partials, c->counters, h, use_h);
+}
+
+// kernels of one iteration (for the launch count of graph executions)
+int iteration_kernels(const vofp_ctx* c, bool rb) { return 2 + (c->ngroups > 0 ? 1 : 0) + (rb ? 1 : 0); }
+
+// Mixed precision, red-black: the reduced right-hand side r_S + E_SR r_R of the correction
+// equation (folded over merge groups) into c->q, its norm into sc->rr0.
+void launch_reduced_rhs(vofp_ctx* c, cudaStream_t st) {
+    launch(c, k_rb_gather, rows_grid(c, kNT), dim3(kNT), st, c->d, (const double*)c->Txs, (const double*)c->Tys,
+           (const double*)c->Tzs, (const uint32_t*)c->red_bits, (const double*)c->r, (const double*)nullptr, c->q, 0);
+    if (c->ngroups > 0)
+        launch(c, k_group_fold_d, ceil_div(c->ngroups, kNT), kNT, st, c->ngroups, (const int*)c->gptr,
+               (const int*)c->gcells, c->q);
+    launch(c, k_reduced_rhs, stream_grid(c->d.n), kNT, st, c->d.n, (const double*)c->r, (const double*)c->q,
+           (const uint32_t*)c->red_bits, (const uint32_t*)c->excl_bits, c->q, c->sc, c->partials, c->counters, 1);
 }
 
 vofp_status ensure_workspace(vofp_ctx* c) {
@@ -319,9 +443,71 @@ vofp_status add_while(vofp_ctx* c, cudaGraph_t g, cudaGraphConditionalHandle* h,
     return VOFP_OK;
 }
 
-// FP64 loop: WHILE { U x [stencil, patch, update]; true-residual check }
-vofp_status build_graph_fp64(vofp_ctx* c, int U) {
-    if (c->graph_fp64 && c->graph_fp64_key == U) return VOFP_OK;
+// Launch sequences shared by the graph capture and the host-driven loop.
+// FP64 body: U iterations, then the true-residual check (sets the WHILE condition).
+void launch_fp64_body(vofp_ctx* c, cudaStream_t st, int U, bool rb, cudaGraphConditionalHandle h, int use_h) {
+    for (int u = 0; u < U; ++u) {
+        double* po = (u % 2 == 0) ? c->p0 : c->p1;
+        double* pn = (u % 2 == 0) ? c->p1 : c->p0;
+        launch_cg_iteration<double>(c, st, c->r, po, pn, c->xt, c->q, c->Txs, c->Tys, c->Tzs, false, rb, h, 0);
+    }
+    launch(c, k_cg_check<double>, stream_grid(c->d.n), kNT, st, c->d.n, (const double*)c->r, (const double*)c->sq,
+           (const uint32_t*)(rb ? c->excl_bits : c->slave_bits), c->sc, c->partials, c->counters, h, use_h);
+}
+int fp64_body_kernels(const vofp_ctx* c, int U, bool rb) { return U * iteration_kernels(c, rb) + 1; }
+
+// Mixed outer step, first part: FP64 residual of the full system, outer test, inner right-hand side.
+void launch_outer_head(vofp_ctx* c, cudaStream_t st, bool rb, cudaGraphConditionalHandle ho,
+                       cudaGraphConditionalHandle hi, int use_h) {
+    launch(c, k_stencil<double, ST_APPLY_SCALED, 1>, stencil_grid(c), dim3(kBX, kBY), st, c->d, stencil_per_block(c),
+           (const double*)c->Txs, (const double*)c->Tys, (const double*)c->Tzs, (const double*)nullptr,
+           (const double*)c->xt, (const double*)nullptr, (double*)nullptr, (double*)nullptr, c->q, c->sc, c->partials,
+           c->counters, (const uint32_t*)nullptr);
+    if (c->ngroups > 0)
+        launch(c, k_group_patch<double>, ceil_div(c->ngroups, kNT), kNT, st, c->ngroups, (const int*)c->gptr,
+               (const int*)c->gcells, (const double*)c->gcorr, c->q, (const double*)c->xt, 0, c->sc, c->partials,
+               c->counters);
+    launch(c, k_outer_residual, stream_grid(c->d.n), kNT, st, c->d.n, (const double*)c->bt, (const double*)c->q,
+           (const double*)c->sq, (const uint32_t*)c->slave_bits, c->r, c->sc, c->partials, c->counters, ho, hi, use_h);
+    if (rb) {
+        launch_reduced_rhs(c, st);
+        launch(c, k_inner_prep, stream_grid(c->d.n), kNT, st, c->d.n, (const double*)c->q,
+               (const uint32_t*)c->excl_bits, c->rf, c->xf, c->pf0, c->sc, c->partials, c->counters);
+    } else {
+        launch(c, k_inner_prep, stream_grid(c->d.n), kNT, st, c->d.n, (const double*)c->r,
+               (const uint32_t*)c->slave_bits, c->rf, c->xf, c->pf0, c->sc, c->partials, c->counters);
+    }
+}
+int outer_head_kernels(const vofp_ctx* c, bool rb) {
+    const int g = c->ngroups > 0 ? 1 : 0;
+    return 1 + g + 1 + (rb ? 2 + g : 0) + 1;
+}
+void launch_inner_body(vofp_ctx* c, cudaStream_t st, int U, bool rb, cudaGraphConditionalHandle hi, int use_h) {
+    for (int u = 0; u < U; ++u) {
+        float* po = (u % 2 == 0) ? c->pf0 : c->pf1;
+        float* pn = (u % 2 == 0) ? c->pf1 : c->pf0;
+        launch_cg_iteration<float>(c, st, c->rf, po, pn, c->xf, c->qf, c->Txf, c->Tyf, c->Tzf, true, rb, hi, use_h);
+    }
+}
+// Mixed outer step, last part: fold the inner solution into x_t (FP64).
+void launch_outer_tail(vofp_ctx* c, cudaStream_t st, bool rb) {
+    if (rb) {
+        launch(c, k_inner_xf, stream_grid(c->d.n), kNT, st, c->d.n, c->xf, (const float*)c->pf0, (const CgScalars*)c->sc);
+        launch(c, k_inner_finish_rb, rows_grid(c, kNT), dim3(kNT), st, c->d, (const double*)c->Txs,
+               (const double*)c->Tys, (const double*)c->Tzs, (const uint32_t*)c->red_bits, (const float*)c->xf,
+               (const double*)c->r, c->xt, (const CgScalars*)c->sc);
+    } else {
+        launch(c, k_inner_finish, stream_grid(c->d.n), kNT, st, c->d.n, c->xf, (const float*)c->pf0, c->xt,
+               (const CgScalars*)c->sc);
+    }
+}
+int outer_tail_kernels(bool rb) { return rb ? 2 : 1; }
+
+int graph_key(int U, bool rb) { return U * 2 + (rb ? 1 : 0); }
+
+// FP64 loop: WHILE { U x [red half-stencil (RB), stencil, patch, update]; true-residual check }
+vofp_status build_graph_fp64(vofp_ctx* c, int U, bool rb) {
+    if (c->graph_fp64 && c->graph_fp64_key == graph_key(U, rb)) return VOFP_OK;
     const long long launches0 = c->launches;
     if (c->graph_fp64) {
         cudaGraphExecDestroy(c->graph_fp64);
@@ -336,28 +522,20 @@ vofp_status build_graph_fp64(vofp_ctx* c, int U) {
     cudaGraphNode_t node;
     vofp_status s = add_while(c, g, &h, &body, nullptr, 0, &node, 1u);
     if (s) return s;
-    s = capture_into(c, cs, body, [&]() {
-        for (int u = 0; u < U; ++u) {
-            double* po = (u % 2 == 0) ? c->p0 : c->p1;
-            double* pn = (u % 2 == 0) ? c->p1 : c->p0;
-            launch_cg_iteration<double>(c, cs, c->r, po, pn, c->xt, c->q, c->Txs, c->Tys, c->Tzs, false, h, 0);
-        }
-        launch(c, k_cg_check<double>, stream_grid(c->d.n), kNT, cs, c->d.n, c->r, c->sq, c->slave_bits, c->sc,
-                                                                 c->partials, c->counters, h, 1);
-    });
+    s = capture_into(c, cs, body, [&]() { launch_fp64_body(c, cs, U, rb, h, 1); });
     if (s) return s;
     VOFP_CUDA_TRY(c, cudaGraphInstantiate(&c->graph_fp64, g, 0));
     cudaGraphDestroy(g);
     cudaStreamDestroy(cs);
-    c->graph_fp64_key = U;
+    c->graph_fp64_key = graph_key(U, rb);
     c->launches = launches0;
     return VOFP_OK;
 }
 
-// Mixed: WHILE_outer { FP64 apply + patch + outer residual (sets both conditions); inner prep;
-//                      WHILE_inner { U x [FP32 stencil, patch, update(inner stop)] }; finish }
-vofp_status build_graph_mixed(vofp_ctx* c, int U) {
-    if (c->graph_mixed && c->graph_mixed_key == U) return VOFP_OK;
+// Mixed: WHILE_outer { FP64 residual, outer test, inner right-hand side (sets both conditions);
+//                      WHILE_inner { U x FP32 iterations (inner stop) }; fold the correction }
+vofp_status build_graph_mixed(vofp_ctx* c, int U, bool rb) {
+    if (c->graph_mixed && c->graph_mixed_key == graph_key(U, rb)) return VOFP_OK;
     const long long launches0 = c->launches;
     if (c->graph_mixed) {
         cudaGraphExecDestroy(c->graph_mixed);
@@ -372,19 +550,10 @@ vofp_status build_graph_mixed(vofp_ctx* c, int U) {
     cudaGraphNode_t onode, inode;
     vofp_status s = add_while(c, g, &ho, &obody, nullptr, 0, &onode, 1u);
     if (s) return s;
-    // outer body, part 1: residual and inner preparation (captured), then the inner WHILE node
     cudaGraphNode_t last = nullptr;
     VOFP_CUDA_TRY(c, cudaGraphConditionalHandleCreate(&hi, obody, 1u, cudaGraphCondAssignDefault));
     VOFP_CUDA_TRY(c, cudaStreamBeginCaptureToGraph(cs, obody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    launch(c, k_stencil<double, ST_APPLY_SCALED, 1>, stencil_grid(c), dim3(kBX, kBY), cs, 
-        c->d, c->zchunk, c->Txs, c->Tys, c->Tzs, nullptr, c->xt, nullptr, nullptr, nullptr, c->q, c->sc, c->partials, c->counters);
-    if (c->ngroups > 0)
-        launch(c, k_group_patch<double>, ceil_div(c->ngroups, kNT), kNT, cs, c->ngroups, c->gptr, c->gcells, c->gcorr, c->q,
-                                                                         c->xt, 0, c->sc, c->partials, c->counters);
-    launch(c, k_outer_residual, stream_grid(c->d.n), kNT, cs, c->d.n, c->bt, c->q, c->sq, c->slave_bits, c->r, c->sc,
-                                                          c->partials, c->counters, ho, hi);
-    launch(c, k_inner_prep, stream_grid(c->d.n), kNT, cs, c->d.n, c->r, c->slave_bits, c->rf, c->xf, c->pf0, c->sc,
-                                                      c->partials, c->counters);
+    launch_outer_head(c, cs, rb, ho, hi, 1);
     {
         cudaGraph_t tmp = obody;
         VOFP_CUDA_TRY(c, cudaStreamEndCapture(cs, &tmp));
@@ -408,17 +577,10 @@ vofp_status build_graph_mixed(vofp_ctx* c, int U) {
     prm.conditional.size = 1;
     VOFP_CUDA_TRY(c, cudaGraphAddNode(&inode, obody, &last, nullptr, 1, &prm));
     ibody = prm.conditional.phGraph_out[0];
-    s = capture_into(c, cs, ibody, [&]() {
-        for (int u = 0; u < U; ++u) {
-            float* po = (u % 2 == 0) ? c->pf0 : c->pf1;
-            float* pn = (u % 2 == 0) ? c->pf1 : c->pf0;
-            launch_cg_iteration<float>(c, cs, c->rf, po, pn, c->xf, c->qf, c->Txf, c->Tyf, c->Tzf, true, hi, 1);
-        }
-    });
+    s = capture_into(c, cs, ibody, [&]() { launch_inner_body(c, cs, U, rb, hi, 1); });
     if (s) return s;
-    // outer body, part 2: fold the inner solution into x_t (FP64)
     VOFP_CUDA_TRY(c, cudaStreamBeginCaptureToGraph(cs, obody, &inode, nullptr, 1, cudaStreamCaptureModeRelaxed));
-    launch(c, k_inner_finish, stream_grid(c->d.n), kNT, cs, c->d.n, c->xf, c->pf0, c->xt, c->sc);
+    launch_outer_tail(c, cs, rb);
     {
         cudaGraph_t tmp = obody;
         VOFP_CUDA_TRY(c, cudaStreamEndCapture(cs, &tmp));
@@ -426,7 +588,7 @@ vofp_status build_graph_mixed(vofp_ctx* c, int U) {
     VOFP_CUDA_TRY(c, cudaGraphInstantiate(&c->graph_mixed, g, 0));
     cudaGraphDestroy(g);
     cudaStreamDestroy(cs);
-    c->graph_mixed_key = U;
+    c->graph_mixed_key = graph_key(U, rb);
     c->launches = launches0;
     return VOFP_OK;
 }
@@ -457,6 +619,38 @@ vofp_status prepare_rhs(vofp_ctx* c, const double* b, double* sums3) {
     }
     launch(c, k_scale, stream_grid(N), kNT, st, N, c->s, c->work, c->bt);
     return VOFP_OK;
+}
+
+// The same loops driven from the host: every kernel is an ordinary launch on the context
+// stream and the host reads the convergence flags every U iterations.
+vofp_status host_loop(vofp_ctx* c, bool mixed, bool rb, int U) {
+    cudaStream_t st = c->stream;
+    int flags[2] = {0, 0};
+    auto read_flags = [&]() -> vofp_status {
+        VOFP_CUDA_TRY(c, cudaMemcpyAsync(&flags[0], &c->sc->done, sizeof(int), cudaMemcpyDeviceToHost, st));
+        VOFP_CUDA_TRY(c, cudaMemcpyAsync(&flags[1], &c->sc->inner_done, sizeof(int), cudaMemcpyDeviceToHost, st));
+        VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
+        return VOFP_OK;
+    };
+    vofp_status s;
+    if (!mixed) {
+        for (;;) {
+            launch_fp64_body(c, st, U, rb, (cudaGraphConditionalHandle)0, 0);
+            if ((s = read_flags())) return s;
+            if (flags[0]) return VOFP_OK;
+        }
+    }
+    for (;;) {
+        launch_outer_head(c, st, rb, (cudaGraphConditionalHandle)0, (cudaGraphConditionalHandle)0, 0);
+        if ((s = read_flags())) return s;
+        if (flags[0]) return VOFP_OK;
+        for (;;) {
+            launch_inner_body(c, st, U, rb, (cudaGraphConditionalHandle)0, 0);
+            if ((s = read_flags())) return s;
+            if (flags[1]) break;
+        }
+        launch_outer_tail(c, st, rb);
+    }
 }
 
 }  // namespace
@@ -499,10 +693,39 @@ vofp_status solve(vofp_ctx* c, const double* b, double* x, const vofp_solve_opts
     VOFP_CUDA_TRY(c, cudaEventRecord(c->ev0, st));
     double sums[3];
     if ((s = prepare_rhs(c, b, sums))) return s;
+    const bool rb = o->precond == VOFP_PRECOND_RBSGS;
+    const bool mixed = o->mode == VOFP_MODE_MIXED;
+    // red-black vectors keep 0 at red cells that the stencil never writes
+    VOFP_CUDA_TRY(c, cudaMemsetAsync(c->p1, 0, sizeof(double) * N, st));
+    VOFP_CUDA_TRY(c, cudaMemsetAsync(c->pf1, 0, sizeof(float) * N, st));
+    VOFP_CUDA_TRY(c, cudaMemsetAsync(c->qf, 0, sizeof(float) * N, st));
     // scaled initial guess, r = bt - (S A S) x_t
     launch(c, k_init_x, stream_grid(N), kNT, st, N, x, c->root, c->sq, c->xt, o->x0_zero);
-    launch_stencil_apply_scaled(c, c->xt, c->q);
-    launch_group_patch<double>(c, c->q, c->xt, false);
+    const double* rhs_loop = c->bt;
+    if (rb && !mixed) {
+        // reduced system: b_S' = b_S + E_SR b_R (folded over groups) into c->work, and
+        // S x_t = (I - E)(w) on non-red rows with w = x_t there and w_R = E_RS x_t
+        launch(c, k_rb_gather, rows_grid(c, kNT), dim3(kNT), st, c->d, (const double*)c->Txs, (const double*)c->Tys,
+               (const double*)c->Tzs, (const uint32_t*)c->red_bits, (const double*)c->bt, (const double*)nullptr,
+               c->q, 0);
+        if (c->ngroups > 0)
+            launch(c, k_group_fold_d, ceil_div(c->ngroups, kNT), kNT, st, c->ngroups, (const int*)c->gptr,
+                   (const int*)c->gcells, c->q);
+        launch(c, k_reduced_rhs, stream_grid(N), kNT, st, N, (const double*)c->bt, (const double*)c->q,
+               (const uint32_t*)c->red_bits, (const uint32_t*)c->excl_bits, c->work, c->sc, c->partials, c->counters,
+               0);
+        launch(c, k_copy, stream_grid(N), kNT, st, N, (const double*)c->xt, c->p1);
+        launch(c, k_rb_gather, rows_grid(c, kNT), dim3(kNT), st, c->d, (const double*)c->Txs, (const double*)c->Tys,
+               (const double*)c->Tzs, (const uint32_t*)c->red_bits, (const double*)c->xt, (const double*)nullptr,
+               c->p1, 1);
+        launch_stencil_apply_scaled(c, c->p1, c->q);
+        launch_group_patch<double>(c, c->q, c->xt, false);
+        rhs_loop = c->work;
+        VOFP_CUDA_TRY(c, cudaMemsetAsync(c->p1, 0, sizeof(double) * N, st));
+    } else {
+        launch_stencil_apply_scaled(c, c->xt, c->q);
+        launch_group_patch<double>(c, c->q, c->xt, false);
+    }
     CgScalars h{};
     h.status = VOFP_OK;
     h.rtol = o->rtol;
@@ -511,8 +734,8 @@ vofp_status solve(vofp_ctx* c, const double* b, double* x, const vofp_solve_opts
     h.bnorm2 = sums[2];
     h.ref2 = sums[2];
     VOFP_CUDA_TRY(c, cudaMemcpyAsync(c->sc, &h, sizeof(h), cudaMemcpyHostToDevice, st));
-    launch(c, k_init_residual, stream_grid(N), kNT, st, N, c->bt, c->q, c->sq, c->slave_bits, c->r, c->sc, c->partials,
-                                                     c->counters);
+    launch(c, k_init_residual, stream_grid(N), kNT, st, N, rhs_loop, (const double*)c->q, (const double*)c->sq,
+           (const uint32_t*)((rb && !mixed) ? c->excl_bits : c->slave_bits), c->r, c->sc, c->partials, c->counters);
     VOFP_CUDA_TRY(c, cudaMemsetAsync(c->p0, 0, sizeof(double) * N, st));
     VOFP_CUDA_TRY(c, cudaMemcpyAsync(&h, c->sc, sizeof(h), cudaMemcpyDeviceToHost, st));
     VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
@@ -528,16 +751,28 @@ vofp_status solve(vofp_ctx* c, const double* b, double* x, const vofp_solve_opts
         return VOFP_ERR_BREAKDOWN;
     }
     const bool converged0 = !(h.rnorm2 > o->rtol * o->rtol * h.ref2);
-    if (o->mode == VOFP_MODE_MIXED) {
-        if ((s = build_graph_mixed(c, U))) return s;
-        if (!converged0) VOFP_CUDA_TRY(c, cudaGraphLaunch(c->graph_mixed, st));
+    if (o->host_loop && !converged0) {
+        if ((s = host_loop(c, mixed, rb, U))) return s;
+    }
+    if (mixed) {
+        if (!o->host_loop && (s = build_graph_mixed(c, U, rb))) return s;
+        if (!converged0 && !o->host_loop) VOFP_CUDA_TRY(c, cudaGraphLaunch(c->graph_mixed, st));
         // the mixed loop folds every inner solution into x_t itself; no pending step
         launch(c, k_set_pq_inf, 1, 1, st, c->sc, 0);
-        launch(c, k_finalize_x, stream_grid(N), kNT, st, N, c->xt, c->p0, c->s, c->sc, x);
+        launch(c, k_finalize_x, stream_grid(N), kNT, st, N, c->xt, (const double*)c->p0, (const double*)c->s,
+               (const CgScalars*)c->sc, x);
     } else {
-        if ((s = build_graph_fp64(c, U))) return s;
-        if (!converged0) VOFP_CUDA_TRY(c, cudaGraphLaunch(c->graph_fp64, st));
-        launch(c, k_finalize_x, stream_grid(N), kNT, st, N, c->xt, c->p0, c->s, c->sc, x);
+        if (!o->host_loop && (s = build_graph_fp64(c, U, rb))) return s;
+        if (!converged0 && !o->host_loop) VOFP_CUDA_TRY(c, cudaGraphLaunch(c->graph_fp64, st));
+        launch(c, k_finalize_x, stream_grid(N), kNT, st, N, c->xt, (const double*)c->p0, (const double*)c->s,
+               (const CgScalars*)c->sc, x);
+        if (rb) {
+            // eliminated unknowns: x_R = b_R + E_RS x_S, then unscale every cell
+            launch(c, k_rb_gather, rows_grid(c, kNT), dim3(kNT), st, c->d, (const double*)c->Txs,
+                   (const double*)c->Tys, (const double*)c->Tzs, (const uint32_t*)c->red_bits, (const double*)c->xt,
+                   (const double*)c->bt, c->xt, 1);
+            launch(c, k_unscale, stream_grid(N), kNT, st, N, (const double*)c->xt, (const double*)c->s, x);
+        }
     }
     if (!c->dirichlet) {
         double* d1 = c->partials + kMaxPartials - 24;
@@ -556,13 +791,13 @@ vofp_status solve(vofp_ctx* c, const double* b, double* x, const vofp_solve_opts
     if ((s = residual(c, b, x, &rel))) return s;
     float ms = 0.0f;
     VOFP_CUDA_TRY(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
-    if (!converged0) {
+    if (!converged0 && !o->host_loop) {
         // kernels executed by the graph: whole bodies of U iterations
-        const long long g = c->ngroups > 0 ? 1 : 0;
-        if (o->mode == VOFP_MODE_MIXED)
-            c->launches += (long long)(h.outer + 1) * (4 + g) + h.iter_total * (2 + g);
+        if (mixed)
+            c->launches += (long long)(h.outer + 1) * outer_head_kernels(c, rb) +
+                           (long long)h.outer * outer_tail_kernels(rb) + h.iter_total * iteration_kernels(c, rb);
         else
-            c->launches += (h.iter_total / U) * (U * (2 + g) + 1);
+            c->launches += (h.iter_total / U) * fp64_body_kernels(c, U, rb);
     }
     vofp_status result = (vofp_status)h.status;
     if (result == VOFP_OK && !(rel <= o->rtol * 1.0000001) && !converged0) {
@@ -581,7 +816,8 @@ vofp_status solve(vofp_ctx* c, const double* b, double* x, const vofp_solve_opts
     return result;
 }
 
-vofp_status time_iteration_kernels(vofp_ctx* c, int precision, int reps, float* stencil_ms, float* update_ms) {
+vofp_status time_iteration_kernels(vofp_ctx* c, int precision, bool rb, int reps, float* stencil_ms,
+                                   float* update_ms, float* red_ms) {
     vofp_status s = ensure_workspace(c);
     if (s) return s;
     cudaStream_t st = c->stream;
@@ -589,50 +825,77 @@ vofp_status time_iteration_kernels(vofp_ctx* c, int precision, int reps, float* 
     cudaEvent_t a, b2;
     VOFP_CUDA_TRY(c, cudaEventCreate(&a));
     VOFP_CUDA_TRY(c, cudaEventCreate(&b2));
-    // alpha = beta = 0 keeps every value fixed while every byte is still read and written
-    launch(c, k_set_pq_inf, 1, 1, st, c->sc, 1);
-    float t1 = 0.0f, t2 = 0.0f;
+    float t1 = 0.0f, t2 = 0.0f, t3 = 0.0f;
+    auto timed = [&](auto&& body, float* out) -> vofp_status {
+        // alpha = beta = 0 keeps every value fixed while every byte is still read and written
+        launch(c, k_set_pq_inf, 1, 1, st, c->sc, 1);
+        body();   // warm-up launch
+        VOFP_CUDA_TRY(c, cudaEventRecord(a, st));
+        for (int i = 0; i < reps; ++i) body();
+        VOFP_CUDA_TRY(c, cudaEventRecord(b2, st));
+        VOFP_CUDA_TRY(c, cudaEventSynchronize(b2));
+        VOFP_CUDA_TRY(c, cudaEventElapsedTime(out, a, b2));
+        *out /= reps;
+        return VOFP_OK;
+    };
+    const uint32_t* bits = rb ? c->excl_bits : c->slave_bits;
+    const uint32_t* red = rb ? c->red_bits : nullptr;
     if (precision == 32) {
-        launch(c, k_stencil<float, ST_CG, stencil_pf<float>()>, stencil_grid(c), dim3(kBX, kBY), st, 
-            c->d, c->zchunk, c->Txf, c->Tyf, c->Tzf, nullptr, c->rf, c->pf0, c->pf1, c->xf, c->qf, c->sc, c->partials, c->counters);
-        VOFP_CUDA_TRY(c, cudaEventRecord(a, st));
-        for (int i = 0; i < reps; ++i)
-            launch(c, k_stencil<float, ST_CG, stencil_pf<float>()>, stencil_grid(c), dim3(kBX, kBY), st, 
-                c->d, c->zchunk, c->Txf, c->Tyf, c->Tzf, nullptr, c->rf, c->pf0, c->pf1, c->xf, c->qf, c->sc, c->partials, c->counters);
-        VOFP_CUDA_TRY(c, cudaEventRecord(b2, st));
-        VOFP_CUDA_TRY(c, cudaEventSynchronize(b2));
-        VOFP_CUDA_TRY(c, cudaEventElapsedTime(&t1, a, b2));
-        launch(c, k_set_pq_inf, 1, 1, st, c->sc, 1);
-        VOFP_CUDA_TRY(c, cudaEventRecord(a, st));
-        for (int i = 0; i < reps; ++i)
-            launch(c, k_cg_update<float, false>, stream_grid(N / 4 + 1), kNT, st, N, c->rf, c->qf, c->slave_bits, c->sc,
-                                                                              c->partials, c->counters, 0, 0);
-        VOFP_CUDA_TRY(c, cudaEventRecord(b2, st));
+        auto stn = [&]() {
+            if (rb)
+                launch(c, k_stencil<float, ST_CG, stencil_pf<float>(), true>, stencil_grid(c), dim3(kBX, kBY), st, c->d,
+                       stencil_per_block(c), (const float*)c->Txf, (const float*)c->Tyf, (const float*)c->Tzf,
+                       (const double*)nullptr, (const float*)c->rf, (const float*)c->pf0, c->pf1, c->xf, c->qf, c->sc,
+                       c->partials, c->counters, red);
+            else
+                launch(c, k_stencil<float, ST_CG, stencil_pf<float>(), false>, stencil_grid(c), dim3(kBX, kBY), st,
+                       c->d, stencil_per_block(c), (const float*)c->Txf, (const float*)c->Tyf, (const float*)c->Tzf,
+                       (const double*)nullptr, (const float*)c->rf, (const float*)c->pf0, c->pf1, c->xf, c->qf, c->sc,
+                       c->partials, c->counters, red);
+        };
+        auto upd = [&]() {
+            launch(c, k_cg_update<float, false>, stream_grid(N / 4 + 1), kNT, st, N, c->rf, (const float*)c->qf, bits,
+                   c->sc, c->partials, c->counters, (cudaGraphConditionalHandle)0, 0);
+        };
+        auto rd = [&]() {
+            launch(c, k_red<float>, red_grid(c), dim3(kNT), st, c->d, (const float*)c->Txf, (const float*)c->Tyf,
+                   (const float*)c->Tzf, (const uint32_t*)c->red_bits, c->rf, (const float*)c->pf0,
+                   (const CgScalars*)c->sc);
+        };
+        if ((s = timed(stn, &t1)) || (s = timed(upd, &t2))) return s;
+        if (rb && (s = timed(rd, &t3))) return s;
     } else {
-        launch(c, k_stencil<double, ST_CG, stencil_pf<double>()>, stencil_grid(c), dim3(kBX, kBY), st, 
-            c->d, c->zchunk, c->Txs, c->Tys, c->Tzs, nullptr, c->r, c->p0, c->p1, c->xt, c->q, c->sc, c->partials, c->counters);
-        VOFP_CUDA_TRY(c, cudaEventRecord(a, st));
-        for (int i = 0; i < reps; ++i)
-            launch(c, k_stencil<double, ST_CG, stencil_pf<double>()>, stencil_grid(c), dim3(kBX, kBY), st, 
-                c->d, c->zchunk, c->Txs, c->Tys, c->Tzs, nullptr, c->r, c->p0, c->p1, c->xt, c->q, c->sc, c->partials, c->counters);
-        VOFP_CUDA_TRY(c, cudaEventRecord(b2, st));
-        VOFP_CUDA_TRY(c, cudaEventSynchronize(b2));
-        VOFP_CUDA_TRY(c, cudaEventElapsedTime(&t1, a, b2));
-        launch(c, k_set_pq_inf, 1, 1, st, c->sc, 1);
-        VOFP_CUDA_TRY(c, cudaEventRecord(a, st));
-        for (int i = 0; i < reps; ++i)
-            launch(c, k_cg_update<double, false>, stream_grid(N / 2 + 1), kNT, st, N, c->r, c->q, c->slave_bits, c->sc,
-                                                                               c->partials, c->counters, 0, 0);
-        VOFP_CUDA_TRY(c, cudaEventRecord(b2, st));
+        auto stn = [&]() {
+            if (rb)
+                launch(c, k_stencil<double, ST_CG, stencil_pf<double>(), true>, stencil_grid(c), dim3(kBX, kBY), st,
+                       c->d, stencil_per_block(c), (const double*)c->Txs, (const double*)c->Tys, (const double*)c->Tzs,
+                       (const double*)nullptr, (const double*)c->r, (const double*)c->p0, c->p1, c->xt, c->q, c->sc,
+                       c->partials, c->counters, red);
+            else
+                launch(c, k_stencil<double, ST_CG, stencil_pf<double>(), false>, stencil_grid(c), dim3(kBX, kBY), st,
+                       c->d, stencil_per_block(c), (const double*)c->Txs, (const double*)c->Tys, (const double*)c->Tzs,
+                       (const double*)nullptr, (const double*)c->r, (const double*)c->p0, c->p1, c->xt, c->q, c->sc,
+                       c->partials, c->counters, red);
+        };
+        auto upd = [&]() {
+            launch(c, k_cg_update<double, false>, stream_grid(N / 2 + 1), kNT, st, N, c->r, (const double*)c->q, bits,
+                   c->sc, c->partials, c->counters, (cudaGraphConditionalHandle)0, 0);
+        };
+        auto rd = [&]() {
+            launch(c, k_red<double>, red_grid(c), dim3(kNT), st, c->d, (const double*)c->Txs, (const double*)c->Tys,
+                   (const double*)c->Tzs, (const uint32_t*)c->red_bits, c->r, (const double*)c->p0,
+                   (const CgScalars*)c->sc);
+        };
+        if ((s = timed(stn, &t1)) || (s = timed(upd, &t2))) return s;
+        if (rb && (s = timed(rd, &t3))) return s;
     }
-    VOFP_CUDA_TRY(c, cudaEventSynchronize(b2));
-    VOFP_CUDA_TRY(c, cudaEventElapsedTime(&t2, a, b2));
     launch(c, k_set_pq_inf, 1, 1, st, c->sc, 0);
     VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
     cudaEventDestroy(a);
     cudaEventDestroy(b2);
-    *stencil_ms = t1 / reps;
-    *update_ms = t2 / reps;
+    *stencil_ms = t1;
+    *update_ms = t2;
+    *red_ms = t3;
     return VOFP_OK;
 }
 

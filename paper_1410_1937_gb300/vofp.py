@@ -52,7 +52,7 @@ class _Phys(ctypes.Structure):
 class _Opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("precond", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("inner_rtol", ctypes.c_double),
-                ("check_every", ctypes.c_int), ("x0_zero", ctypes.c_int)]
+                ("check_every", ctypes.c_int), ("x0_zero", ctypes.c_int), ("host_loop", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -84,8 +84,8 @@ _sig = {
     "vofp_get_stats": (ctypes.c_int, [_vp, _P(_Stats)]),
     "vofp_residual_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _P(ctypes.c_double)]),
     "vofp_launch_count": (ctypes.c_int, [_vp, _P(ctypes.c_longlong)]),
-    "vofp_time_iteration_kernels": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _P(ctypes.c_float),
-                                                   _P(ctypes.c_float)]),
+    "vofp_time_iteration_kernels": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                   _P(ctypes.c_float), _P(ctypes.c_float), _P(ctypes.c_float)]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -219,12 +219,13 @@ class Context:
         return r.value
 
     def vofp_solve(self, b, x=None, mode=MODE_FP64, rtol=1e-10, max_iter=100000, inner_rtol=1e-3,
-                   check_every=8, precond=PRECOND_JACOBI, raise_on_error=True, x0_zero=0):
+                   check_every=8, precond=PRECOND_JACOBI, raise_on_error=True, x0_zero=0, host_loop=0):
         import torch
         if x is None:
             x = torch.zeros(self.n, dtype=torch.float64, device=b.device)
             x0_zero = 1
-        o = _Opts(int(mode), int(precond), float(rtol), int(max_iter), float(inner_rtol), int(check_every), x0_zero)
+        o = _Opts(int(mode), int(precond), float(rtol), int(max_iter), float(inner_rtol), int(check_every), x0_zero,
+                  int(host_loop))
         info = _Info()
         st = _lib.vofp_solve(self.h, _dev(b, self.n, "b"), _dev(x, self.n, "x"), ctypes.byref(o), ctypes.byref(info))
         out = {"iterations": info.iterations, "outer_iterations": info.outer_iterations,
@@ -237,7 +238,7 @@ class Context:
 
     def vofp_solve_host(self, F, ax, ay, az, vol_frac, u, v, w, bc, x_out, mode=MODE_FP64, rtol=1e-10,
                         max_iter=100000, inner_rtol=1e-3, check_every=8, rho_liquid=1000.0, rho_gas=1.2,
-                        merge_threshold=0.1, density_smoothing=0, dt=1.0):
+                        merge_threshold=0.1, density_smoothing=0, dt=1.0, precond=PRECOND_JACOBI):
         """Host-buffer end-to-end call: numpy (or pinned torch CPU) float64 arrays in, x_out out."""
         def hp(a, n, name):
             if a is None:
@@ -252,7 +253,7 @@ class Context:
             return ctypes.c_void_p(a.ctypes.data)
         b = self._bc(bc, None)
         ph = _Phys(rho_liquid, rho_gas, merge_threshold, int(density_smoothing), dt)
-        o = _Opts(int(mode), PRECOND_JACOBI, float(rtol), int(max_iter), float(inner_rtol), int(check_every), 1)
+        o = _Opts(int(mode), int(precond), float(rtol), int(max_iter), float(inner_rtol), int(check_every), 1, 0)
         info = _Info()
         st = _lib.vofp_solve_host(self.h, hp(F, self.n, "F"), hp(ax, self.nfx, "ax"), hp(ay, self.nfy, "ay"),
                                   hp(az, self.nfz, "az"), hp(vol_frac, self.n, "vol_frac"), hp(u, self.nfx, "u"),
@@ -279,11 +280,12 @@ class Context:
         _check(self.h, _lib.vofp_launch_count(self.h, ctypes.byref(n)))
         return n.value
 
-    def vofp_time_iteration_kernels(self, precision=64, reps=20):
-        a, b = ctypes.c_float(0), ctypes.c_float(0)
-        _check(self.h, _lib.vofp_time_iteration_kernels(self.h, int(precision), int(reps), ctypes.byref(a),
-                                                        ctypes.byref(b)))
-        return a.value, b.value
+    def vofp_time_iteration_kernels(self, precision=64, reps=20, precond=PRECOND_JACOBI):
+        """Average device ms of the (stencil, update, red half-stencil) kernels of one iteration."""
+        a, b, r = ctypes.c_float(0), ctypes.c_float(0), ctypes.c_float(0)
+        _check(self.h, _lib.vofp_time_iteration_kernels(self.h, int(precision), int(precond), int(reps),
+                                                        ctypes.byref(a), ctypes.byref(b), ctypes.byref(r)))
+        return a.value, b.value, r.value
 
 
 def context_for(problem, stream=None, device="cuda"):

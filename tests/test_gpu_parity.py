@@ -101,14 +101,16 @@ def test_apply_random_vector(vofp, oracle, case):
 
 @pytest.mark.parametrize("case", list(CASES))
 @pytest.mark.parametrize("mode", ["fp64", "mixed"])
-def test_solve_matches_oracle(vofp, oracle, case, mode):
+@pytest.mark.parametrize("precond", ["jacobi", "rbsgs"])
+def test_solve_matches_oracle(vofp, oracle, case, mode, precond):
     prob = CASES[case]()
     ref, info_ref, s = oracle.solve(prob, rtol=1e-12)
     assert info_ref["rel_residual"] < 1e-11
     ctx, t = vofp.context_for(prob)
     b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
     rtol = 1e-10 if mode == "fp64" else 1e-8
-    x, info = ctx.vofp_solve(b, rtol=rtol, mode=vofp.MODE_FP64 if mode == "fp64" else vofp.MODE_MIXED)
+    x, info = ctx.vofp_solve(b, rtol=rtol, mode=vofp.MODE_FP64 if mode == "fp64" else vofp.MODE_MIXED,
+                             precond=vofp.PRECOND_JACOBI if precond == "jacobi" else vofp.PRECOND_RBSGS)
     assert info["status"] == 0, info
     assert info["rel_residual"] <= rtol
     got = host(x, prob.shape)
@@ -118,6 +120,23 @@ def test_solve_matches_oracle(vofp, oracle, case, mode):
     assert s.residual(got) <= rtol * 1.01
 
 
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_red_black_elimination_cuts_iterations(vofp, mode):
+    prob = CASES["hull-small"]()
+    ctx, t = vofp.context_for(prob)
+    assert 0 < ctx.vofp_get_stats()["cells"]
+    b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
+    m = vofp.MODE_FP64 if mode == "fp64" else vofp.MODE_MIXED
+    _, ij = ctx.vofp_solve(b, rtol=1e-10 if mode == "fp64" else 1e-8, mode=m)
+    x, ir = ctx.vofp_solve(b, rtol=1e-10 if mode == "fp64" else 1e-8, mode=m, precond=vofp.PRECOND_RBSGS)
+    assert ij["status"] == 0 and ir["status"] == 0
+    # CG on the red-black Schur complement: about half the iterations of Jacobi-PCG
+    assert ir["iterations"] < 0.7 * ij["iterations"], (ij, ir)
+    x2, ih = ctx.vofp_solve(b, rtol=1e-10 if mode == "fp64" else 1e-8, mode=m, precond=vofp.PRECOND_RBSGS,
+                            host_loop=1)
+    assert ih["iterations"] == ir["iterations"] and torch.equal(x, x2)
+
+
 def test_solve_is_bitwise_reproducible(vofp):
     prob = CASES["hull-small"]()
     ctx, t = vofp.context_for(prob)
@@ -125,6 +144,19 @@ def test_solve_is_bitwise_reproducible(vofp):
     x1, i1 = ctx.vofp_solve(b, rtol=1e-10)
     x2, i2 = ctx.vofp_solve(b, rtol=1e-10)
     assert i1["iterations"] == i2["iterations"]
+    assert torch.equal(x1, x2)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_host_loop_matches_graph_loop(vofp, mode):
+    prob = CASES["hull-small"]()
+    ctx, t = vofp.context_for(prob)
+    b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
+    m = vofp.MODE_FP64 if mode == "fp64" else vofp.MODE_MIXED
+    x1, i1 = ctx.vofp_solve(b, rtol=1e-9, mode=m)
+    x2, i2 = ctx.vofp_solve(b, rtol=1e-9, mode=m, host_loop=1)
+    assert i1["status"] == 0 and i2["status"] == 0
+    assert i1["iterations"] == i2["iterations"] and i1["outer_iterations"] == i2["outer_iterations"]
     assert torch.equal(x1, x2)
 
 
