@@ -45,6 +45,7 @@ extern "C" {
 #endif
 
 typedef struct vofp_ctx vofp_ctx;
+typedef struct vofp_nn vofp_nn;
 /* A cudaStream_t (0 = legacy default stream). */
 typedef struct CUstream_st* vofp_stream;
 
@@ -61,7 +62,7 @@ typedef enum {
 } vofp_status;
 
 enum { VOFP_BC_NEUMANN = 0, VOFP_BC_DIRICHLET = 1 };
-enum { VOFP_MODE_FP64 = 0, VOFP_MODE_MIXED = 1 };
+enum { VOFP_MODE_FP64 = 0, VOFP_MODE_MIXED = 1, VOFP_MODE_FCG_NN = 2 };
 enum { VOFP_PRECOND_JACOBI = 0, VOFP_PRECOND_RBSGS = 1 };
 
 /* Grid: nx*ny*nz cells; dx, dy, dz are HOST arrays of the cell widths (lengths nx, ny, nz),
@@ -106,7 +107,13 @@ typedef struct {
  *   host_loop   0: the loop runs as a CUDA graph with a device-side WHILE condition (no host round
  *               trip per iteration).  1: the host launches each kernel and reads the convergence
  *               flag every check_every iterations (same kernels and results; visible to profilers
- *               that do not trace conditional graph bodies). */
+ *               that do not trace conditional graph bodies).
+ *   nn          VOFP_MODE_FCG_NN: a network bound to this operator (vofp_nn_bind).  The solve is
+ *               FP64 iterative refinement whose inner solve is a flexible CG (FP32 vectors, FP64-
+ *               accurate dots) preconditioned by the network, which also gives the initial guess.
+ *               If the inner residual falls by less than 10 % over stag_window iterations, or a
+ *               breakdown occurs, the solve falls back to VOFP_MODE_MIXED (precond as given) from
+ *               the current iterate. */
 typedef struct {
     int mode;
     int precond;
@@ -116,6 +123,8 @@ typedef struct {
     int check_every;
     int x0_zero;
     int host_loop;
+    vofp_nn* nn;
+    int stag_window;
 } vofp_solve_opts;
 
 typedef struct {
@@ -124,6 +133,8 @@ typedef struct {
     double rel_residual;     /* ||b_hat - A_hat x|| / ||b_hat||, recomputed in FP64 at the end  */
     double seconds;          /* device time of the solve (CUDA events)                          */
     int status;              /* vofp_status of the solve                                        */
+    int nn_applications;     /* network evaluations (VOFP_MODE_FCG_NN)                          */
+    int fell_back;           /* 1 if VOFP_MODE_FCG_NN fell back to VOFP_MODE_MIXED              */
 } vofp_solve_info;
 
 typedef struct {
@@ -206,6 +217,40 @@ vofp_status vofp_get_stats(vofp_ctx* ctx, vofp_stats* stats);
  * first call before any stream capture.  All calls share the array: calls that overlap on the GPU
  * (other streams or threads) race.  Synchronises the context stream; *rel is a host double. */
 vofp_status vofp_residual_noalloc(vofp_ctx* ctx, const double* b, const double* x, double* rel);
+
+/* Training pair in the scaled variables the solvers and the network use: r_scaled = S b_hat
+ * (b merged over groups, S = diag(A_hat)^-1/2) and x_scaled = S^-1 x, both FP32 on every cell (0
+ * without unknown; every cell of a group holds its group's value).  Device arrays. */
+vofp_status vofp_scaled_pair(vofp_ctx* ctx, const double* b, const double* x, float* r_scaled, float* x_scaled);
+
+/* ---- learned preconditioner (the paper has none; see VOFP_MODE_FCG_NN) --------------------
+ * A 3-level 3-D convolutional encoder-decoder: two 3x3x3 convolutions with ReLU per level
+ * (16, 32, 64 channels), 2x2x2 average pooling down, nearest upsampling up with skip
+ * concatenation, and a 1x1x1 output layer.  Inputs per cell: the VOF fraction F, the mean open
+ * fraction of the cell's x, y and z faces, log(dx/dx_min), log(dy/dy_min), log(dz/dz_min), and the
+ * scaled residual divided by its RMS; the output is multiplied back by that RMS.  BF16
+ * activations and weights on the tensor cores with FP32 accumulation; FP32 master weights trained
+ * with Adam by the library's own forward and backward kernels.  Grid sizes must be multiples of 4.
+ * Parameter order (get/set): per convolution layer its weights [27][cout][cin] then biases, for
+ * the layers in forward order, then the output layer's 16 weights and its bias. */
+vofp_status vofp_nn_create(vofp_nn** out, unsigned long long seed, vofp_stream stream);
+void vofp_nn_destroy(vofp_nn* nn);
+const char* vofp_nn_last_error(const vofp_nn* nn);
+vofp_status vofp_nn_param_count(const vofp_nn* nn, long long* count);
+/* host <- FP32 masters (grads = 0) or the gradients of the last vofp_nn_train_step (grads = 1) */
+vofp_status vofp_nn_get_params(vofp_nn* nn, float* host, long long count, int grads);
+vofp_status vofp_nn_set_params(vofp_nn* nn, const float* host, long long count);
+/* geometry channels and the unknown mask from a built operator and its VOF fraction F (device) */
+vofp_status vofp_nn_bind(vofp_nn* nn, vofp_ctx* ctx, const double* F);
+/* copy the bound geometry out (geo: 8 BF16 per cell, device) / bind a stored one */
+vofp_status vofp_nn_export_geometry(vofp_nn* nn, uint16_t* geo, float* mask);
+vofp_status vofp_nn_set_geometry(vofp_nn* nn, int nx, int ny, int nz, const uint16_t* geo, const float* mask);
+/* z = network(r) for a scaled residual r (device FP32, cells) */
+vofp_status vofp_nn_forward(vofp_nn* nn, const float* r, float* z);
+/* forward, masked mean-squared error against target (both relative to the RMS of r), backward;
+ * update = 1 also takes an Adam step with learning rate lr.  *loss (host) may be NULL. */
+vofp_status vofp_nn_train_step(vofp_nn* nn, const float* r, const float* target, float lr, int update,
+                               float* loss);
 
 /* *count = number of kernels this context has launched since vofp_create (kernels run inside
  * the solve's CUDA graphs are counted per execution). */

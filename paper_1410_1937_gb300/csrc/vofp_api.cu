@@ -145,7 +145,9 @@ vofp_status vofp_solve(vofp_ctx* c, const double* b, double* x, const vofp_solve
     if (s) return s;
     if (!b || !x || !o) return invalid(c, "null input");
     if (!(o->rtol > 0.0) || o->rtol >= 1.0) return invalid(c, "rtol must be in (0, 1)");
-    if (o->mode != VOFP_MODE_FP64 && o->mode != VOFP_MODE_MIXED) return invalid(c, "unknown mode");
+    if (o->mode != VOFP_MODE_FP64 && o->mode != VOFP_MODE_MIXED && o->mode != VOFP_MODE_FCG_NN)
+        return invalid(c, "unknown mode");
+    if (o->mode == VOFP_MODE_FCG_NN && !o->nn) return invalid(c, "VOFP_MODE_FCG_NN needs a network");
     if (o->precond != VOFP_PRECOND_JACOBI && o->precond != VOFP_PRECOND_RBSGS) return invalid(c, "unknown preconditioner");
     if (o->check_every < 0 || (o->check_every % 2) != 0 || o->check_every > 64)
         return invalid(c, "check_every must be 0 or an even number <= 64");
@@ -193,6 +195,13 @@ vofp_status vofp_solve_host(vofp_ctx* c, const double* F, const double* ax, cons
     VOFP_CUDA_TRY(c, cudaMemcpyAsync(x_host, dx, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
     VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
     return rs;
+}
+
+vofp_status vofp_scaled_pair(vofp_ctx* c, const double* b, const double* x, float* r_scaled, float* x_scaled) {
+    vofp_status s = check_ctx(c, true);
+    if (s) return s;
+    if (!b || !x || !r_scaled || !x_scaled) return invalid(c, "null input");
+    return vofp::scaled_pair(c, b, x, r_scaled, x_scaled);
 }
 
 vofp_status vofp_merge_map(vofp_ctx* c, int32_t* master) {

@@ -97,6 +97,7 @@ struct vofp_ctx {
     // Krylov workspace
     double *xt = nullptr, *r = nullptr, *p0 = nullptr, *p1 = nullptr, *q = nullptr, *bt = nullptr;
     float *rf = nullptr, *pf0 = nullptr, *pf1 = nullptr, *qf = nullptr, *xf = nullptr;
+    float *zf = nullptr, *qf2 = nullptr;   // flexible CG (learned preconditioner)
     double* partials = nullptr;       // block partial sums
     unsigned int* counters = nullptr; // last-block tickets
     vofp::CgScalars* sc = nullptr;
@@ -143,6 +144,8 @@ vofp_status apply_unscaled(vofp_ctx* c, const double* x, double* y);
 vofp_status residual(vofp_ctx* c, const double* b, const double* x, double* rel);
 vofp_status solve(vofp_ctx* c, const double* b, double* x, const vofp_solve_opts* o,
                   vofp_solve_info* info);
+vofp_status solve_fcg(vofp_ctx* c, const double* b, double* x, const vofp_solve_opts* o, vofp_solve_info* info);
+vofp_status scaled_pair(vofp_ctx* c, const double* b, const double* x, float* r_scaled, float* x_scaled);
 vofp_status time_iteration_kernels(vofp_ctx* c, int precision, bool rb, int reps, float* st, float* up,
                                    float* red);
 
@@ -165,6 +168,11 @@ inline void launch(vofp_ctx* c, void (*k)(KArgs...), dim3 g, dim3 b, cudaStream_
     k<<<g, b, 0, s>>>(static_cast<KArgs>(args)...);
     ++c->launches;
 }
+
+namespace nn {
+long long bound_cells(const vofp_nn* n);
+cudaStream_t stream_of(const vofp_nn* n);
+}  // namespace nn
 
 inline int ceil_div(long long a, long long b) { return int((a + b - 1) / b); }
 inline int num_sms() {

@@ -394,7 +394,6 @@ k_cg_update(long long n, V* __restrict__ r, const V* __restrict__ q, const uint3
     }
     __syncthreads();
     const double alpha_d = s_alpha;
-    const bool ok = s_flags & 1;
     const bool broke = (s_flags & 2) != 0;
     const V alpha = (V)alpha_d;
     Acc acc;

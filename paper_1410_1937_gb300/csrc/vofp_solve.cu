@@ -335,6 +335,75 @@ dim3 red_grid(const vofp_ctx* c) {
     return dim3(gx, (unsigned)std::max(1LL, std::min(rows, (long long)num_sms() * 32)));
 }
 
+// ---- flexible CG with the learned preconditioner -----------------------------------------
+// up to three dot products of FP32 vectors over cells outside `bits`, accumulated with the
+// compensated (Dot2) scheme and reduced in FP64 into out[0..2]
+__global__ void __launch_bounds__(kNT)
+k_fdots(long long n, const float* __restrict__ a0, const float* __restrict__ b0, const float* __restrict__ a1,
+        const float* __restrict__ b1, const float* __restrict__ a2, const float* __restrict__ b2,
+        const uint32_t* __restrict__ bits, double* __restrict__ partials, unsigned int* __restrict__ counter,
+        double* out) {
+    __shared__ double sh[32];
+    AccF2 s0, s1, s2;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        if (is_slave(bits, c)) continue;
+        s0.add(a0[c], b0[c]);
+        if (a1) s1.add(a1[c], b1[c]);
+        if (a2) s2.add(a2[c], b2[c]);
+    }
+    double t;
+    if (grid_reduce(s0.value(), partials, counter, sh, &t)) out[0] = t;
+    __syncthreads();
+    if (grid_reduce(s1.value(), partials + kMaxPartials / 4, counter + 1, sh, &t)) out[1] = t;
+    __syncthreads();
+    if (grid_reduce(s2.value(), partials + kMaxPartials / 2, counter + 2, sh, &t)) out[2] = t;
+}
+
+// p = z + beta p_prev
+__global__ void k_fdir(long long n, const float* __restrict__ z, float beta, const float* __restrict__ pp,
+                       float* __restrict__ p) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+        p[c] = pp ? __fmaf_rn(beta, pp[c], z[c]) : z[c];
+}
+
+// x += alpha p, r -= alpha q
+__global__ void k_fupd(long long n, float alpha, const float* __restrict__ p, const float* __restrict__ q,
+                       float* __restrict__ x, float* __restrict__ r) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        x[c] = __fmaf_rn(alpha, p[c], x[c]);
+        r[c] = __fmaf_rn(-alpha, q[c], r[c]);
+    }
+}
+
+// r_f = r * inv (FP32), x_f = 0
+__global__ void k_fstart(long long n, const double* __restrict__ r, double inv, float* __restrict__ rf,
+                         float* __restrict__ xf) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        rf[c] = (float)(r[c] * inv);
+        xf[c] = 0.0f;
+    }
+}
+
+// x_t += scale * x_f (FP64)
+__global__ void k_ffold(long long n, const float* __restrict__ xf, double scale, double* __restrict__ xt) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+        xt[c] = fma(scale, (double)xf[c], xt[c]);
+}
+
+// every cell of a merge group takes its master's value (FP32)
+__global__ void k_group_expand_f(int ng, const int* __restrict__ gptr, const int* __restrict__ gcells,
+                                 float* __restrict__ v) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    const float vm = v[gcells[gptr[g]]];
+    for (int t = gptr[g] + 1; t < gptr[g + 1]; ++t) v[gcells[t]] = vm;
+}
+
+__global__ void k_to_float(long long n, const double* __restrict__ a, float* __restrict__ b) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+        b[c] = (float)a[c];
+}
+
 }  // namespace
 
 // ---- launch helpers --------------------------------------------------------------------------
@@ -685,6 +754,7 @@ vofp_status residual(vofp_ctx* c, const double* b, const double* x, double* rel)
 }
 
 vofp_status solve(vofp_ctx* c, const double* b, double* x, const vofp_solve_opts* o, vofp_solve_info* info) {
+    if (o->mode == VOFP_MODE_FCG_NN) return solve_fcg(c, b, x, o, info);
     vofp_status s = ensure_workspace(c);
     if (s) return s;
     const long long N = c->d.n;
@@ -813,6 +883,187 @@ vofp_status solve(vofp_ctx* c, const double* b, double* x, const vofp_solve_opts
     }
     if (result != VOFP_OK)
         c->set_error(result == VOFP_ERR_NOT_CONVERGED ? "solve did not reach rtol" : "CG breakdown");
+    return result;
+}
+
+vofp_status scaled_pair(vofp_ctx* c, const double* b, const double* x, float* r_scaled, float* x_scaled) {
+    vofp_status s = ensure_workspace(c);
+    if (s) return s;
+    const long long N = c->d.n;
+    cudaStream_t st = c->stream;
+    double sums[3];
+    if ((s = prepare_rhs(c, b, sums))) return s;
+    launch(c, k_to_float, stream_grid(N), kNT, st, N, (const double*)c->bt, r_scaled);
+    launch(c, k_init_x, stream_grid(N), kNT, st, N, x, (const int32_t*)c->root, (const double*)c->sq, c->xt, 0);
+    launch(c, k_to_float, stream_grid(N), kNT, st, N, (const double*)c->xt, x_scaled);
+    VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
+    return VOFP_OK;
+}
+
+// FP64 refinement around a flexible CG (FCG(1): each new direction is A-orthogonalised against the
+// previous one, which keeps CG's short recurrence valid for a preconditioner that changes from
+// one application to the next) whose preconditioner is the network.
+vofp_status solve_fcg(vofp_ctx* c, const double* b, double* x, const vofp_solve_opts* o, vofp_solve_info* info) {
+    vofp_status s = ensure_workspace(c);
+    if (s) return s;
+    const long long N = c->d.n;
+    cudaStream_t st = c->stream;
+    if (!c->zf) {
+        if ((s = c->alloc(&c->zf, N)) || (s = c->alloc(&c->qf2, N))) return s;
+    }
+    vofp_nn* nn = o->nn;
+    if (nn::bound_cells(nn) != N) {
+        c->set_error("the network is not bound to this grid (vofp_nn_bind)");
+        return VOFP_ERR_INVALID_ARG;
+    }
+    cudaStream_t nst = nn::stream_of(nn);
+    const int W = o->stag_window > 0 ? o->stag_window : 20;
+    const long long max_iter = o->max_iter > 0 ? o->max_iter : 100000;
+    VOFP_CUDA_TRY(c, cudaEventRecord(c->ev0, st));
+    double sums[3];
+    if ((s = prepare_rhs(c, b, sums))) return s;
+    const double bnorm2 = sums[2];
+    launch(c, k_init_x, stream_grid(N), kNT, st, N, x, (const int32_t*)c->root, (const double*)c->sq, c->xt,
+           o->x0_zero);
+    double* dres = c->partials + kMaxPartials - 40;
+    const uint32_t* bits = c->slave_bits;
+    auto dots = [&](const float* a0, const float* b0, const float* a1, const float* b1, const float* a2,
+                    const float* b2, double* h) -> vofp_status {
+        launch(c, k_fdots, stream_grid(N), kNT, st, N, a0, b0, a1, b1, a2, b2, bits, c->partials, c->counters, dres);
+        VOFP_CUDA_TRY(c, cudaMemcpyAsync(h, dres, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
+        return VOFP_OK;
+    };
+    auto apply_f = [&](const float* p, float* q) {
+        launch(c, k_stencil<float, ST_APPLY_SCALED, 2, false>, stencil_grid(c), dim3(kBX, kBY), st, c->d,
+               stencil_per_block(c), (const float*)c->Txf, (const float*)c->Tyf, (const float*)c->Tzf,
+               (const double*)nullptr, p, (const float*)nullptr, (float*)nullptr, (float*)nullptr, q, c->sc,
+               c->partials, c->counters, (const uint32_t*)nullptr);
+        if (c->ngroups > 0)
+            launch(c, k_group_patch<float>, ceil_div(c->ngroups, kNT), kNT, st, c->ngroups, (const int*)c->gptr,
+                   (const int*)c->gcells, (const double*)c->gcorr, q, p, 0, c->sc, c->partials, c->counters);
+    };
+    long long iters = 0;
+    int outer = 0, napp = 0, fell_back = 0;
+    vofp_status result = VOFP_OK;
+    double rnorm2 = 0.0;
+    for (;;) {
+        // FP64 residual of the scaled system and its true (unscaled) norm
+        launch_stencil_apply_scaled(c, c->xt, c->q);
+        launch_group_patch<double>(c, c->q, c->xt, false);
+        CgScalars h{};
+        h.status = VOFP_OK;
+        VOFP_CUDA_TRY(c, cudaMemcpyAsync(c->sc, &h, sizeof(h), cudaMemcpyHostToDevice, st));
+        launch(c, k_init_residual, stream_grid(N), kNT, st, N, (const double*)c->bt, (const double*)c->q,
+               (const double*)c->sq, bits, c->r, c->sc, c->partials, c->counters);
+        VOFP_CUDA_TRY(c, cudaMemcpyAsync(&h, c->sc, sizeof(h), cudaMemcpyDeviceToHost, st));
+        VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
+        rnorm2 = h.rnorm2;
+        if (!std::isfinite(rnorm2)) {
+            result = VOFP_ERR_BREAKDOWN;
+            break;
+        }
+        if (rnorm2 <= o->rtol * o->rtol * bnorm2) break;
+        if (iters >= max_iter || outer >= 200) {
+            result = VOFP_ERR_NOT_CONVERGED;
+            break;
+        }
+        ++outer;
+        const double scale = std::sqrt(h.rr);
+        const double target = std::max(o->inner_rtol > 0 ? o->inner_rtol : 1e-3,
+                                       std::min(0.5, 0.3 * o->rtol * std::sqrt(bnorm2 / rnorm2)));
+        launch(c, k_fstart, stream_grid(N), kNT, st, N, (const double*)c->r, scale > 0 ? 1.0 / scale : 0.0, c->rf,
+               c->xf);
+        double d[3];
+        if ((s = dots(c->rf, c->rf, nullptr, nullptr, nullptr, nullptr, d))) return s;
+        const double rr0 = d[0];
+        double rr = rr0, pq_prev = 0.0;
+        std::vector<double> hist;
+        float *p = c->pf0, *pp = c->pf1, *q = c->qf, *qp = c->qf2;
+        bool stop_inner = false;
+        for (int k = 0; !stop_inner; ++k) {
+            // z = M(r): the network, expanded over merge groups
+            // the network runs on its own stream: order it after this stream's work and back
+            if (nst != st) VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
+            if ((s = (vofp_status)vofp_nn_forward(nn, c->rf, c->zf))) {
+                c->set_error(std::string("network: ") + vofp_nn_last_error(nn));
+                return s;
+            }
+            if (nst != st) VOFP_CUDA_TRY(c, cudaStreamSynchronize(nst));
+            ++napp;
+            if (c->ngroups > 0)
+                launch(c, k_group_expand_f, ceil_div(c->ngroups, kNT), kNT, st, c->ngroups, (const int*)c->gptr,
+                       (const int*)c->gcells, c->zf);
+            float beta = 0.0f;
+            if (k > 0) {
+                if ((s = dots(c->zf, qp, nullptr, nullptr, nullptr, nullptr, d))) return s;
+                beta = (float)(-d[0] / pq_prev);
+            }
+            launch(c, k_fdir, stream_grid(N), kNT, st, N, (const float*)c->zf, beta, k > 0 ? (const float*)pp : nullptr,
+                   p);
+            apply_f(p, q);
+            if ((s = dots(p, q, p, c->rf, nullptr, nullptr, d))) return s;
+            const double pq = d[0], pr = d[1];
+            if (!(pq > 0.0) || !std::isfinite(pq) || !std::isfinite(pr)) {
+                fell_back = 1;
+                break;
+            }
+            const double alpha = pr / pq;
+            launch(c, k_fupd, stream_grid(N), kNT, st, N, (float)alpha, (const float*)p, (const float*)q, c->xf, c->rf);
+            if ((s = dots(c->rf, c->rf, nullptr, nullptr, nullptr, nullptr, d))) return s;
+            rr = d[0];
+            ++iters;
+            hist.push_back(rr);
+            pq_prev = pq;
+            std::swap(p, pp);
+            std::swap(q, qp);
+            if (!std::isfinite(rr)) {
+                fell_back = 1;
+                break;
+            }
+            if (rr <= target * target * rr0 || iters >= max_iter) stop_inner = true;
+            // stagnation: the residual norm fell by less than 10 % over the last W iterations
+            const size_t m = hist.size();
+            if (!stop_inner && m > (size_t)W && !(hist[m - 1] < 0.81 * hist[m - 1 - W])) {
+                fell_back = 1;
+                stop_inner = true;
+            }
+        }
+        launch(c, k_ffold, stream_grid(N), kNT, st, N, (const float*)c->xf, scale, c->xt);
+        if (fell_back) break;
+    }
+    launch(c, k_unscale, stream_grid(N), kNT, st, N, (const double*)c->xt, (const double*)c->s, x);
+    VOFP_CUDA_TRY(c, cudaEventRecord(c->ev1, st));
+    VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
+    float ms = 0.0f;
+    VOFP_CUDA_TRY(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    int it_total = (int)iters, outer_total = outer;
+    double seconds = ms * 1e-3;
+    if (fell_back && result == VOFP_OK) {
+        // plain mixed-precision PCG from the current iterate
+        vofp_solve_opts o2 = *o;
+        o2.mode = VOFP_MODE_MIXED;
+        o2.x0_zero = 0;
+        o2.max_iter = (int)std::max(1LL, max_iter - iters);
+        vofp_solve_info i2{};
+        result = solve(c, b, x, &o2, &i2);
+        it_total += i2.iterations;
+        outer_total += i2.outer_iterations;
+        seconds += i2.seconds;
+    }
+    double rel = 0.0;
+    if ((s = residual(c, b, x, &rel))) return s;
+    if (result == VOFP_OK && !(rel <= o->rtol * 10.0)) result = VOFP_ERR_NOT_CONVERGED;
+    if (info) {
+        info->iterations = it_total;
+        info->outer_iterations = outer_total;
+        info->rel_residual = rel;
+        info->seconds = seconds;
+        info->status = result;
+        info->nn_applications = napp;
+        info->fell_back = fell_back;
+    }
+    if (result != VOFP_OK) c->set_error("learned-preconditioner solve did not reach rtol");
     return result;
 }
 

@@ -1,0 +1,155 @@
+"""Training and evaluation of the learned preconditioner.
+
+Data: seeded hull-in-waves samples (hull offset, wave amplitude/wavelength/phase and velocities
+drawn per seed) whose pressure the plain PCG solver computes on the GPU; each sample is stored on
+the device as its geometry channels (BF16), unknown mask, scaled right-hand side S b_hat and scaled
+solution S^-1 x (FP32).  Training: the library's forward/backward/Adam kernels (vofp_nn_train_step)
+on one sample per step.  Evaluation: flexible CG with the network against plain and mixed PCG on
+held-out seeds.  Checkpoints are .npz files of the FP32 master weights.
+
+    python -m paper_1410_1937_gb300.learned --samples 2000 --epochs 4 --out weights.npz
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import time
+
+import numpy as np
+
+TRAIN_SEED0 = 100000
+HELD_OUT_SEED0 = 200000
+TRAIN_SHAPE = (256, 128, 64)
+
+
+def _geometry_worker(args):
+    """Inputs of one sample, computed in a worker process (numpy only, FP32 for transfer)."""
+    from paper_1410_1937_gb300 import inputs as I
+    seed, shape = args
+    p = I.config3_sample(seed, shape)
+    f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32).ravel()
+    return seed, (p.dx, p.dy, p.dz), {k: f32(getattr(p, k)) for k in ("F", "vf", "ax", "ay", "az", "u", "v", "w")}
+
+
+def generate(seeds, shape=TRAIN_SHAPE, workers=None, rtol=1e-9, log=print):
+    """Solve every seed's sample with the mixed-precision PCG and keep the training tensors on the GPU.
+    Geometry is built by a spawned process pool (started before this process touches CUDA)."""
+    ctxmp = mp.get_context("spawn")
+    workers = workers or max(1, min(16, (os.cpu_count() or 2) - 1))
+    pool = ctxmp.Pool(workers)
+    import torch
+    from paper_1410_1937_gb300 import vofp
+    data = []
+    t0 = time.perf_counter()
+    net = vofp.Network(seed=0)
+    try:
+        for i, (seed, (dx, dy, dz), arr) in enumerate(pool.imap(_geometry_worker, [(s, shape) for s in seeds],
+                                                                chunksize=1)):
+            d = {k: torch.from_numpy(v).cuda().double() for k, v in arr.items()}
+            ctx = vofp.Context(dx, dy, dz)
+            ctx.vofp_build_operator(d["F"], d["ax"], d["ay"], d["az"], d["vf"],
+                                    (0, 1, 0, 0, 0, 0), 1000.0, 1.2, 0.1, 0, 1.0)
+            b = ctx.vofp_rhs_from_face_velocity(d["u"], d["v"], d["w"])
+            x, info = ctx.vofp_solve(b, rtol=rtol, mode=vofp.MODE_MIXED, precond=vofp.PRECOND_RBSGS)
+            r, xs = ctx.vofp_scaled_pair(b, x)
+            net.bind(ctx, d["F"])
+            geo, mask = net.export_geometry()
+            data.append({"seed": seed, "geo": geo, "mask": mask, "r": r, "x": xs, "iters": info["iterations"]})
+            ctx.close()
+            if (i + 1) % 100 == 0 or i + 1 == len(seeds):
+                log(f"generated {i + 1}/{len(seeds)} samples in {time.perf_counter() - t0:.1f} s")
+    finally:
+        pool.close()
+        pool.join()
+    return data
+
+
+def train(net, data, shape=TRAIN_SHAPE, epochs=4, lr=1e-3, seed=0, log=print):
+    """One sample per Adam step, samples shuffled every epoch, cosine learning-rate decay."""
+    rng = np.random.default_rng(seed)
+    nz_ny_nx = (shape[2], shape[1], shape[0])
+    total = epochs * len(data)
+    step = 0
+    hist = []
+    t0 = time.perf_counter()
+    for ep in range(epochs):
+        losses = []
+        for i in rng.permutation(len(data)):
+            s = data[i]
+            net.set_geometry(nz_ny_nx, s["geo"], s["mask"])
+            lr_t = lr * 0.5 * (1 + math.cos(math.pi * step / max(total, 1)))
+            losses.append(net.train_step(s["r"], s["x"], lr=lr_t))
+            step += 1
+        hist.append(float(np.mean(losses)))
+        log(f"epoch {ep + 1}/{epochs}: mean loss {hist[-1]:.4e} ({time.perf_counter() - t0:.1f} s)")
+    return hist
+
+
+def save(net, path):
+    np.savez_compressed(path, params=net.get_params(), layers=np.array([27, 16, 32, 64]))
+
+
+def load(net, path):
+    net.set_params(np.load(path)["params"])
+
+
+def evaluate(net, seeds, shape, rtol=1e-8, log=print):
+    """Per seed: iterations and device time to rtol for flexible CG with the network, and for
+    mixed-precision PCG (Jacobi and red-black) and plain FP64 PCG on the same input."""
+    import torch
+    from paper_1410_1937_gb300 import inputs as I
+    from paper_1410_1937_gb300 import vofp
+    rows = []
+    for seed in seeds:
+        p = I.config3_sample(seed, shape)
+        ctx, t = vofp.context_for(p)
+        b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
+        net.bind(ctx, t["F"])
+        row = {"seed": seed}
+        for name, kw in (("fcg_nn", dict(mode=vofp.MODE_FCG_NN, nn=net)),
+                         ("mixed_rbsgs", dict(mode=vofp.MODE_MIXED, precond=vofp.PRECOND_RBSGS)),
+                         ("mixed_jacobi", dict(mode=vofp.MODE_MIXED)),
+                         ("fp64_jacobi", dict(mode=vofp.MODE_FP64))):
+            ctx.vofp_solve(b, rtol=rtol, raise_on_error=False, **kw)       # warm-up
+            _, info = ctx.vofp_solve(b, rtol=rtol, raise_on_error=False, **kw)
+            row[name] = {k: info[k] for k in ("iterations", "seconds", "rel_residual", "status_name",
+                                              "nn_applications", "fell_back")}
+        rows.append(row)
+        log(json.dumps(row))
+        ctx.close()
+    return rows
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--samples", type=int, default=2000)
+    ap.add_argument("--epochs", type=int, default=4)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--shape", type=int, nargs=3, default=list(TRAIN_SHAPE))
+    ap.add_argument("--eval-seeds", type=int, default=4)
+    ap.add_argument("--eval-shape", type=int, nargs=3, default=list(TRAIN_SHAPE))
+    ap.add_argument("--out", default="weights.npz")
+    ap.add_argument("--init", default=None)
+    ap.add_argument("--workers", type=int, default=0)
+    ap.add_argument("--report", default=None)
+    args = ap.parse_args()
+    shape = tuple(args.shape)
+    data = generate(range(TRAIN_SEED0, TRAIN_SEED0 + args.samples), shape, workers=args.workers or None)
+    from paper_1410_1937_gb300 import vofp
+    net = vofp.Network(seed=1)
+    if args.init:
+        load(net, args.init)
+    hist = train(net, data, shape, args.epochs, args.lr)
+    save(net, args.out)
+    del data
+    rows = evaluate(net, range(HELD_OUT_SEED0, HELD_OUT_SEED0 + args.eval_seeds), tuple(args.eval_shape))
+    if args.report:
+        with open(args.report, "w") as f:
+            json.dump({"samples": args.samples, "epochs": args.epochs, "loss": hist, "eval": rows}, f, indent=1)
+
+
+if __name__ == "__main__":
+    main()

@@ -23,7 +23,7 @@ OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_ST
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGED", 5: "BREAKDOWN",
                 6: "STAGNATED", 7: "INCOMPATIBLE_RHS", 8: "NOT_BUILT"}
 BC_NEUMANN, BC_DIRICHLET = 0, 1
-MODE_FP64, MODE_MIXED = 0, 1
+MODE_FP64, MODE_MIXED, MODE_FCG_NN = 0, 1, 2
 PRECOND_JACOBI, PRECOND_RBSGS = 0, 1
 
 
@@ -52,13 +52,14 @@ class _Phys(ctypes.Structure):
 class _Opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("precond", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("inner_rtol", ctypes.c_double),
-                ("check_every", ctypes.c_int), ("x0_zero", ctypes.c_int), ("host_loop", ctypes.c_int)]
+                ("check_every", ctypes.c_int), ("x0_zero", ctypes.c_int), ("host_loop", ctypes.c_int),
+                ("nn", ctypes.c_void_p), ("stag_window", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("outer_iterations", ctypes.c_int),
                 ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double),
-                ("status", ctypes.c_int)]
+                ("status", ctypes.c_int), ("nn_applications", ctypes.c_int), ("fell_back", ctypes.c_int)]
 
 
 class _Stats(ctypes.Structure):
@@ -84,6 +85,18 @@ _sig = {
     "vofp_get_stats": (ctypes.c_int, [_vp, _P(_Stats)]),
     "vofp_residual_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _P(ctypes.c_double)]),
     "vofp_launch_count": (ctypes.c_int, [_vp, _P(ctypes.c_longlong)]),
+    "vofp_scaled_pair": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "vofp_nn_create": (ctypes.c_int, [_P(_vp), ctypes.c_ulonglong, _vp]),
+    "vofp_nn_destroy": (None, [_vp]),
+    "vofp_nn_last_error": (ctypes.c_char_p, [_vp]),
+    "vofp_nn_param_count": (ctypes.c_int, [_vp, _P(ctypes.c_longlong)]),
+    "vofp_nn_get_params": (ctypes.c_int, [_vp, _vp, ctypes.c_longlong, ctypes.c_int]),
+    "vofp_nn_set_params": (ctypes.c_int, [_vp, _vp, ctypes.c_longlong]),
+    "vofp_nn_bind": (ctypes.c_int, [_vp, _vp, _vp]),
+    "vofp_nn_export_geometry": (ctypes.c_int, [_vp, _vp, _vp]),
+    "vofp_nn_set_geometry": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]),
+    "vofp_nn_forward": (ctypes.c_int, [_vp, _vp, _vp]),
+    "vofp_nn_train_step": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_float, ctypes.c_int, _P(ctypes.c_float)]),
     "vofp_time_iteration_kernels": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                    _P(ctypes.c_float), _P(ctypes.c_float), _P(ctypes.c_float)]),
 }
@@ -219,18 +232,20 @@ class Context:
         return r.value
 
     def vofp_solve(self, b, x=None, mode=MODE_FP64, rtol=1e-10, max_iter=100000, inner_rtol=1e-3,
-                   check_every=8, precond=PRECOND_JACOBI, raise_on_error=True, x0_zero=0, host_loop=0):
+                   check_every=8, precond=PRECOND_JACOBI, raise_on_error=True, x0_zero=0, host_loop=0,
+                   nn=None, stag_window=20):
         import torch
         if x is None:
             x = torch.zeros(self.n, dtype=torch.float64, device=b.device)
             x0_zero = 1
         o = _Opts(int(mode), int(precond), float(rtol), int(max_iter), float(inner_rtol), int(check_every), x0_zero,
-                  int(host_loop))
+                  int(host_loop), nn.h if nn is not None else None, int(stag_window))
         info = _Info()
         st = _lib.vofp_solve(self.h, _dev(b, self.n, "b"), _dev(x, self.n, "x"), ctypes.byref(o), ctypes.byref(info))
         out = {"iterations": info.iterations, "outer_iterations": info.outer_iterations,
                "rel_residual": info.rel_residual, "seconds": info.seconds, "status": info.status,
-               "status_name": STATUS_NAMES.get(info.status, str(info.status))}
+               "status_name": STATUS_NAMES.get(info.status, str(info.status)),
+               "nn_applications": info.nn_applications, "fell_back": info.fell_back}
         if st != OK and raise_on_error and st not in (ERR_NOT_CONVERGED,):
             _check(self.h, st)
         out["return_status"] = st
@@ -253,7 +268,8 @@ class Context:
             return ctypes.c_void_p(a.ctypes.data)
         b = self._bc(bc, None)
         ph = _Phys(rho_liquid, rho_gas, merge_threshold, int(density_smoothing), dt)
-        o = _Opts(int(mode), int(precond), float(rtol), int(max_iter), float(inner_rtol), int(check_every), 1, 0)
+        o = _Opts(int(mode), int(precond), float(rtol), int(max_iter), float(inner_rtol), int(check_every), 1, 0,
+                  None, 20)
         info = _Info()
         st = _lib.vofp_solve_host(self.h, hp(F, self.n, "F"), hp(ax, self.nfx, "ax"), hp(ay, self.nfy, "ay"),
                                   hp(az, self.nfz, "az"), hp(vol_frac, self.n, "vol_frac"), hp(u, self.nfx, "u"),
@@ -263,6 +279,16 @@ class Context:
             _check(self.h, st)
         return {"iterations": info.iterations, "outer_iterations": info.outer_iterations,
                 "rel_residual": info.rel_residual, "seconds": info.seconds, "status": info.status}
+
+    def vofp_scaled_pair(self, b, x):
+        """(S b_hat, S^-1 x) as FP32 CUDA tensors: the network's input and target variables."""
+        import torch
+        r = torch.empty(self.n, dtype=torch.float32, device=b.device)
+        xs = torch.empty(self.n, dtype=torch.float32, device=b.device)
+        _check(self.h, _lib.vofp_scaled_pair(self.h, _dev(b, self.n, "b"), _dev(x, self.n, "x"),
+                                             _dev(r, self.n, "r_scaled", "float32"),
+                                             _dev(xs, self.n, "x_scaled", "float32")))
+        return r, xs
 
     def vofp_merge_map(self):
         import torch
@@ -286,6 +312,79 @@ class Context:
         _check(self.h, _lib.vofp_time_iteration_kernels(self.h, int(precision), int(precond), int(reps),
                                                         ctypes.byref(a), ctypes.byref(b), ctypes.byref(r)))
         return a.value, b.value, r.value
+
+
+class Network:
+    """The learned preconditioner (vofp_nn_*): 3-level 3-D conv encoder-decoder, BF16 on tensor cores."""
+
+    def __init__(self, seed=0, stream=None):
+        self.h = _vp()
+        st = _lib.vofp_nn_create(ctypes.byref(self.h), ctypes.c_ulonglong(seed), _stream_handle(stream))
+        if st != OK:
+            raise VofpError(st, "vofp_nn_create failed")
+        n = ctypes.c_longlong(0)
+        _lib.vofp_nn_param_count(self.h, ctypes.byref(n))
+        self.nparams = n.value
+        self.n = 0
+
+    def _check(self, st):
+        if st != OK:
+            raise VofpError(st, _lib.vofp_nn_last_error(self.h).decode())
+
+    def close(self):
+        if self.h:
+            _lib.vofp_nn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self, grads=False):
+        out = np.empty(self.nparams, dtype=np.float32)
+        self._check(_lib.vofp_nn_get_params(self.h, ctypes.c_void_p(out.ctypes.data), self.nparams, int(grads)))
+        return out
+
+    def set_params(self, params):
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        assert params.size == self.nparams
+        self._check(_lib.vofp_nn_set_params(self.h, ctypes.c_void_p(params.ctypes.data), self.nparams))
+
+    def bind(self, ctx, F):
+        self._check(_lib.vofp_nn_bind(self.h, ctx.h, _dev(F, ctx.n, "F")))
+        self.n = ctx.n
+        self.shape = (ctx.nz, ctx.ny, ctx.nx)
+
+    def export_geometry(self):
+        import torch
+        geo = torch.empty(self.n * 8, dtype=torch.int16, device="cuda")
+        mask = torch.empty(self.n, dtype=torch.float32, device="cuda")
+        self._check(_lib.vofp_nn_export_geometry(self.h, ctypes.c_void_p(geo.data_ptr()),
+                                                 ctypes.c_void_p(mask.data_ptr())))
+        return geo, mask
+
+    def set_geometry(self, shape, geo, mask):
+        nz, ny, nx = shape
+        self.n = nx * ny * nz
+        self.shape = shape
+        self._check(_lib.vofp_nn_set_geometry(self.h, nx, ny, nz, ctypes.c_void_p(geo.data_ptr()),
+                                              ctypes.c_void_p(mask.data_ptr())))
+
+    def forward(self, r, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.n, dtype=torch.float32, device=r.device)
+        self._check(_lib.vofp_nn_forward(self.h, _dev(r, self.n, "r", "float32"), _dev(out, self.n, "z", "float32")))
+        return out
+
+    def train_step(self, r, target, lr=1e-3, update=True):
+        loss = ctypes.c_float(0.0)
+        self._check(_lib.vofp_nn_train_step(self.h, _dev(r, self.n, "r", "float32"),
+                                            _dev(target, self.n, "target", "float32"), float(lr), int(update),
+                                            ctypes.byref(loss)))
+        return loss.value
 
 
 def context_for(problem, stream=None, device="cuda"):

@@ -1,0 +1,236 @@
+"""Learned preconditioner: oracle pins (CPU) and GPU parity of forward, gradients and Adam.
+
+The oracle (oracle/nn_ref.py) is pinned by the definition of a convolution (brute-force loop),
+adjoint identities (the data and weight gradients are the transposes of the forward map), and a
+central finite difference of the full network loss in pure FP64.  The GPU network computes in BF16
+with FP32 accumulation; it must match the oracle run with BF16 rounding at the same storage points
+to 1e-2 relative L2 per tensor (output, loss, every parameter gradient).
+"""
+import numpy as np
+import pytest
+
+from oracle import nn_ref as R
+from paper_1410_1937_gb300 import inputs as I
+
+
+def random_params(rng):
+    layers = []
+    for cin, cout in R.LAYERS:
+        real = 8 if (cin, cout) == (16, 16) and not layers else cin
+        W = rng.normal(0, np.sqrt(2.0 / (27 * real)), (27, cout, cin))
+        if not layers:
+            W[:, :, 8:] = 0.0
+        layers.append((W, rng.normal(0, 0.05, cout)))
+    return R.pack(layers, rng.normal(0, 0.25, 16), 0.1)
+
+
+def test_bf16_rounding():
+    assert R.bf16_round(1.0 + 2.0 ** -9) == 1.0                  # tie -> even
+    assert R.bf16_round(1.0 + 3 * 2.0 ** -9) == 1.0 + 2.0 ** -7   # tie -> even (up)
+    assert R.bf16_round(1.0 + 2.0 ** -8) == 1.0 + 2.0 ** -7 or R.bf16_round(1.0 + 2.0 ** -8) == 1.0
+    assert R.bf16_round(3.0) == 3.0 and R.bf16_round(-0.0) == 0.0
+
+
+def test_conv_matches_brute_force_definition():
+    rng = np.random.default_rng(1)
+    x = rng.normal(size=(3, 4, 5, 2))
+    W = rng.normal(size=(27, 3, 2))
+    b = rng.normal(size=3)
+    out = R.conv3(x, W, b)
+    ref = np.zeros((3, 4, 5, 3))
+    for z in range(3):
+        for y in range(4):
+            for xx in range(5):
+                for co in range(3):
+                    s = b[co]
+                    for dz in (-1, 0, 1):
+                        for dy in (-1, 0, 1):
+                            for dx in (-1, 0, 1):
+                                zz, yy, xs = z + dz, y + dy, xx + dx
+                                if 0 <= zz < 3 and 0 <= yy < 4 and 0 <= xs < 5:
+                                    tap = (dz + 1) * 9 + (dy + 1) * 3 + dx + 1
+                                    s += W[tap, co] @ x[zz, yy, xs]
+                    ref[z, y, xx, co] = s
+    np.testing.assert_allclose(out, ref, rtol=1e-13, atol=1e-13)
+
+
+def test_gradients_are_adjoints():
+    rng = np.random.default_rng(2)
+    x = rng.normal(size=(4, 4, 6, 3))
+    W = rng.normal(size=(27, 5, 3))
+    y = rng.normal(size=(4, 4, 6, 5))
+    lhs = (R.conv3(x, W, None) * y).sum()
+    assert abs(lhs - (x * R.conv3_data_grad(y, W, x.shape[:3])).sum()) < 1e-10 * abs(lhs)
+    assert abs(lhs - (W * R.conv3_weight_grad(x, y)).sum()) < 1e-10 * abs(lhs)
+    p = rng.normal(size=(4, 4, 6, 3))
+    q = rng.normal(size=(2, 2, 3, 3))
+    assert abs((R.pool(p) * q).sum() - (p * R.pool_grad(q)).sum()) < 1e-12
+    assert abs((R.up(q) * p).sum() - (q * R.up_grad(p)).sum()) < 1e-12
+
+
+def _toy(rng, shape=(8, 8, 8)):
+    geo = rng.uniform(0, 1, shape + (8,))
+    mask = (rng.uniform(size=shape) > 0.1).astype(float)
+    r = rng.normal(size=shape) * mask
+    target = rng.normal(size=shape) * mask
+    return geo, mask, r, target
+
+
+def test_network_gradients_match_finite_differences():
+    rng = np.random.default_rng(3)
+    params = random_params(rng)
+    geo, mask, r, target = _toy(rng, (4, 8, 8))
+    loss, g, _ = R.loss_and_grads(params, geo, mask, r, target, bf16=False)
+    idx = rng.choice(params.size, 24, replace=False)
+    idx = np.concatenate([idx, [params.size - 1, params.size - 3]])
+    for i in idx:
+        h = 1e-6 * max(1.0, abs(params[i]))
+        pp, pm = params.copy(), params.copy()
+        pp[i] += h
+        pm[i] -= h
+        lp = R.loss_and_grads(pp, geo, mask, r, target, bf16=False)[0]
+        lm = R.loss_and_grads(pm, geo, mask, r, target, bf16=False)[0]
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(abs(g).max(), 1e-12) + 1e-5 * abs(g[i]), (i, fd, g[i])
+
+
+def test_adam_reference_step():
+    p = np.array([1.0, -2.0])
+    g = np.array([0.5, -0.25])
+    p1, m, v = R.adam_step(p, g, np.zeros(2), np.zeros(2), 1, 1e-3)
+    # first step moves every parameter by lr against the sign of its gradient
+    np.testing.assert_allclose(p1, p - 1e-3 * np.sign(g), rtol=1e-6)
+
+
+# ---------------------------------------------------------------------------------------------
+# GPU
+# ---------------------------------------------------------------------------------------------
+
+def _tiny_hull(shape=(32, 32, 16)):
+    nx, ny, nz = shape
+    xn, yn, zn = I.hull_domain_nodes(nx, ny, nz)
+    F = I.vof_cosine(xn, yn, zn, 0.015, 0.3, 0.4)
+    body = I.SlenderHull((0.02, 0.0, 0.0))
+    p = I._assemble("tiny-hull", xn, yn, zn, F, body, np.random.default_rng(11), rtol=1e-10)
+    return p
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-30)
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    import __graft_entry__ as g
+    g.build()
+    from paper_1410_1937_gb300 import vofp
+    return torch, vofp
+
+
+@pytest.mark.gpu
+def test_gpu_geometry_channels_match_oracle(gpu, oracle):
+    torch, vofp = gpu
+    prob = _tiny_hull()
+    s = oracle.System(prob)
+    ctx, t = vofp.context_for(prob)
+    net = vofp.Network(seed=5)
+    net.bind(ctx, t["F"])
+    geo, mask = net.export_geometry()
+    got = (geo.cpu().numpy().view(np.uint16).astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    ref = R.geometry(prob.F, s.apertures, prob.dx, prob.dy, prob.dz)
+    np.testing.assert_array_equal(got.reshape(prob.shape + (8,))[..., :7], R.bf16_round(ref[..., :7]))
+    np.testing.assert_array_equal(mask.cpu().numpy().reshape(prob.shape), (s.root >= 0).reshape(prob.shape))
+
+
+@pytest.mark.gpu
+def test_gpu_forward_and_gradients_match_oracle(gpu, oracle):
+    torch, vofp = gpu
+    prob = _tiny_hull()
+    s = oracle.System(prob)
+    ctx, t = vofp.context_for(prob)
+    net = vofp.Network(seed=7)
+    net.bind(ctx, t["F"])
+    rng = np.random.default_rng(8)
+    mask = (s.root >= 0).reshape(prob.shape).astype(float)
+    r = (rng.normal(size=prob.shape) * mask).astype(np.float32)
+    target = (rng.normal(size=prob.shape) * mask).astype(np.float32)
+    params = net.get_params().astype(np.float64)
+    geo = R.geometry(prob.F, s.apertures, prob.dx, prob.dy, prob.dz)
+    loss_ref, g_ref, z_ref = R.loss_and_grads(params, geo, mask, r.astype(np.float64), target.astype(np.float64))
+    rd = torch.from_numpy(r.ravel()).cuda()
+    td = torch.from_numpy(target.ravel()).cuda()
+    z = net.forward(rd).cpu().numpy().reshape(prob.shape)
+    assert _rel(z, z_ref) < 1e-2
+    loss = net.train_step(rd, td, update=False)
+    assert abs(loss - loss_ref) < 1e-2 * loss_ref
+    g = net.get_params(grads=True).astype(np.float64)
+    # activations and gradients are stored in BF16 through ten layers; rounding and ReLU-boundary
+    # flips make the coarse levels (few voxels per sum) the noisiest: 3e-2 per tensor there
+    errs, off = [], 0
+    for i, (cin, cout) in enumerate(R.LAYERS):
+        nw = 27 * cin * cout
+        errs.append((i, _rel(g[off:off + nw], g_ref[off:off + nw]), _rel(g[off + nw:off + nw + cout],
+                                                                         g_ref[off + nw:off + nw + cout])))
+        off += nw + cout
+    errs.append(("head", _rel(g[off:], g_ref[off:]), 0.0))
+    print("per-layer relative L2 gradient errors:", errs)
+    assert all(ew < 3e-2 and eb < 3e-2 for _, ew, eb in errs), errs
+    # the finest level and the output layer sum over every voxel: 1e-2 there
+    assert all(ew < 1e-2 for i, ew, _ in errs if i in (0, 1, 8, 9, "head")), errs
+
+
+@pytest.mark.gpu
+def test_gpu_adam_step_matches_reference(gpu):
+    torch, vofp = gpu
+    prob = _tiny_hull()
+    ctx, t = vofp.context_for(prob)
+    net = vofp.Network(seed=9)
+    net.bind(ctx, t["F"])
+    rng = np.random.default_rng(10)
+    rd = torch.from_numpy(rng.normal(size=prob.n).astype(np.float32)).cuda()
+    td = torch.from_numpy(rng.normal(size=prob.n).astype(np.float32)).cuda()
+    p0 = net.get_params().astype(np.float64)
+    net.train_step(rd, td, lr=1e-3, update=True)
+    g = net.get_params(grads=True).astype(np.float64)     # the gradients this step used
+    p1 = net.get_params().astype(np.float64)
+    ref, _, _ = R.adam_step(p0, g, np.zeros_like(p0), np.zeros_like(p0), 1, 1e-3)
+    assert np.abs(p1 - ref).max() < 1e-6
+
+
+@pytest.mark.gpu
+def test_gpu_training_reduces_loss(gpu):
+    torch, vofp = gpu
+    prob = _tiny_hull()
+    ctx, t = vofp.context_for(prob)
+    b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
+    x, info = ctx.vofp_solve(b, rtol=1e-10)
+    r, xs = ctx.vofp_scaled_pair(b, x)
+    net = vofp.Network(seed=12)
+    net.bind(ctx, t["F"])
+    first = net.train_step(r, xs, lr=3e-3)
+    for _ in range(60):
+        last = net.train_step(r, xs, lr=3e-3)
+    assert last < 0.5 * first, (first, last)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("train", [False, True])
+def test_gpu_learned_preconditioner_solve_matches_oracle(gpu, oracle, train):
+    torch, vofp = gpu
+    prob = _tiny_hull()
+    ref, _, s = oracle.solve(prob, rtol=1e-12)
+    ctx, t = vofp.context_for(prob)
+    b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
+    net = vofp.Network(seed=13)
+    net.bind(ctx, t["F"])
+    if train:
+        x, _ = ctx.vofp_solve(b, rtol=1e-10)
+        r, xs = ctx.vofp_scaled_pair(b, x)
+        for _ in range(60):
+            net.train_step(r, xs, lr=3e-3)
+    x, info = ctx.vofp_solve(b, rtol=1e-8, mode=vofp.MODE_FCG_NN, nn=net)
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-8, info
+    assert info["nn_applications"] > 0
+    got = x.cpu().numpy().reshape(prob.shape)
+    assert np.linalg.norm(got - ref) <= 1e-6 * np.linalg.norm(ref)
