@@ -35,16 +35,16 @@ RTOL = 1e-8
 FALLBACK_HBM_GBS = 6800.0
 # algorithmic bytes per cell of one launch / one iteration ("Roofline"), in units of
 # one vector element (8 B for FP64, 4 B for FP32)
-#   stencil: reads r, p_old, x, Tx, Ty, Tz; writes p, x, q (red-black: writes on the black half only)
+#   stencil, Jacobi: reads r, p_old, x, Tx, Ty, Tz; writes p, x, q
+#   stencil, red-black (fused red elimination): reads r, p_old, Tx, Ty, Tz everywhere and x on the
+#            black half; writes p, x, q on the black half
 #   update:  reads r, q; writes r
-#   red half-stencil (red-black): reads r, p_old, Tx, Ty, Tz; writes r on the red half
-STENCIL_ELEMS = {"jacobi": 9.0, "rbsgs": 7.5}
+STENCIL_ELEMS = {"jacobi": 9.0, "rbsgs": 7.0}
 UPDATE_ELEMS = 3.0
-RED_ELEMS = 5.5
 
 
 def iter_elems(precond):
-    return STENCIL_ELEMS[precond] + UPDATE_ELEMS + (RED_ELEMS if precond == "rbsgs" else 0.0)
+    return STENCIL_ELEMS[precond] + UPDATE_ELEMS
 # dram read+write bytes per cell of one stencil launch from the committed ncu capture, valid only
 # while the kernel sources hash to KERNEL_HASH (else reported as null)
 TRAFFIC_PER_CELL = {}

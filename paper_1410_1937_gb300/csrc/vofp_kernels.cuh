@@ -120,13 +120,12 @@ struct StCoef {
     V txp, txm, typ, tym, tzp, xo, dg;
 };
 
-template <typename V, int MODE, int PF, bool RB = false>
+template <typename V, int MODE, int PF>
 __global__ void __launch_bounds__(kBX* kBY, 4)
 k_stencil(const Dims d, const int per_block, const V* __restrict__ Tx, const V* __restrict__ Ty,
           const V* __restrict__ Tz, const double* __restrict__ diag, const V* __restrict__ src,
           const V* __restrict__ pold, V* __restrict__ pnew, V* __restrict__ xv, V* __restrict__ out,
-          CgScalars* __restrict__ sc, double* __restrict__ partials, unsigned int* __restrict__ counter,
-          const uint32_t* __restrict__ red) {
+          CgScalars* __restrict__ sc, double* __restrict__ partials, unsigned int* __restrict__ counter) {
     using Acc = typename AccFor<V>::type;
     constexpr bool CG = MODE == ST_CG;
     __shared__ V tile[4][kBY + 2][kBX + 2];
@@ -237,10 +236,7 @@ k_stencil(const Dims d, const int per_block, const V* __restrict__ Tx, const V* 
             StCoef<V> cn;
             loadc(k + 1, cn);
             __syncthreads();
-            // red-black mode: red cells hold E p (written by k_red) and are not rows of the system
-            const bool row = inside && !(RB && ((red[((long long)k * d.plane + own) >> 5] >>
-                                                  (((long long)k * d.plane + own) & 31)) & 1u));
-            if (row) {
+            if (inside) {
                 const long long c = (long long)k * d.plane + own;
                 const V v = tile[b0][ty + 1][tx + 1];
                 V t = (MODE == ST_APPLY_UNSCALED) ? cc.dg * v : v;
@@ -271,37 +267,187 @@ k_stencil(const Dims d, const int per_block, const V* __restrict__ Tx, const V* 
 // Red-black elimination (Eisenstat's form of red-black symmetric Gauss-Seidel).  On the scaled
 // operator I - E the red block is the identity, so red unknowns are eliminated exactly:
 // x_R = b_R + E_RS x_S, and CG runs on the Schur complement S = I_SS - E_SS - E_SR E_RS of the
-// remaining (black and merge-group) unknowns.  Each iteration first writes w_R = E_RS p into the
-// red entries of r (red cells have no other use for them), then the unchanged stencil applies
-// I - E to that vector on the black rows.
-// k_red: for every red cell, r_c = sum over its six faces of T_f * (r_nb + beta p_old,nb), the
-// direction of the black neighbour formed with the same fused multiply-add as the stencil.
-template <typename V>
-__global__ void __launch_bounds__(kRedThreads)
-k_red(const Dims d, const V* __restrict__ Tx, const V* __restrict__ Ty, const V* __restrict__ Tz,
-      const uint32_t* __restrict__ red, V* __restrict__ r, const V* __restrict__ pold,
-      const CgScalars* __restrict__ sc) {
-    const V beta = (V)sc->beta;
-    const long long rows = (long long)d.ny * d.nz;
-    const int half = (d.nx + 1) / 2;
-    for (long long row = blockIdx.y; row < rows; row += gridDim.y) {
-        const int j = int(row % d.ny), k = int(row / d.ny);
-        const int par = (j + k) & 1;
-        for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < half; m += gridDim.x * blockDim.x) {
-            const int i = 2 * m + par;
-            if (i >= d.nx) continue;
-            const long long c = i + (long long)d.nx * row;
-            if (!((red[c >> 5] >> (c & 31)) & 1u)) continue;
-            V acc = V(0);
-            if (i > 0) acc = fmav(Tx[c - 1], fmav(beta, pold[c - 1], r[c - 1]), acc);
-            if (i < d.nx - 1) acc = fmav(Tx[c], fmav(beta, pold[c + 1], r[c + 1]), acc);
-            if (j > 0) acc = fmav(Ty[c - d.nx], fmav(beta, pold[c - d.nx], r[c - d.nx]), acc);
-            if (j < d.ny - 1) acc = fmav(Ty[c], fmav(beta, pold[c + d.nx], r[c + d.nx]), acc);
-            if (k > 0) acc = fmav(Tz[c - d.plane], fmav(beta, pold[c - d.plane], r[c - d.plane]), acc);
-            if (k < d.nz - 1) acc = fmav(Tz[c], fmav(beta, pold[c + d.plane], r[c + d.plane]), acc);
-            r[c] = acc;
+// remaining (black and merge-group) unknowns.  An iteration forms w = E_RS p on the red cells
+// and w = p on the others, and applies I - E to w on the black rows.
+// Fused red-black iteration: one pass per CG iteration.
+// Per plane k a block (32 x 8 columns) keeps three planes of the direction p = r + beta p_old with
+// a 2-cell halo and three planes of w (w = p on black cells, w = E_RS p on red cells, 1-cell halo)
+// in shared memory.  Step k: store p of plane k+2 (prefetched into registers one step earlier);
+// barrier; form w of plane k+1 (red cells sum T_f p over their six neighbours, using their own
+// coefficients); barrier; apply I - E to w on the black rows of plane k.
+constexpr int kPX = kBX + 4, kPY = kBY + 4, kPN = kPX * kPY;
+
+template <typename V, int PF>
+__global__ void __launch_bounds__(kBX* kBY, 3)
+k_cg_rb(const Dims d, const int per_block, const V* __restrict__ Tx, const V* __restrict__ Ty,
+        const V* __restrict__ Tz, const uint32_t* __restrict__ red, const V* __restrict__ src,
+        const V* __restrict__ pold, V* __restrict__ pnew, V* __restrict__ xv, V* __restrict__ out,
+        CgScalars* __restrict__ sc, double* __restrict__ partials, unsigned int* __restrict__ counter) {
+    using Acc = typename AccFor<V>::type;
+    __shared__ V pt[3][kPN];                       // p, planes mod 3, (kBX+4) x (kBY+4)
+    __shared__ V wt[3][kBY + 2][kBX + 2];          // w, planes mod 3, one-cell halo (no corners)
+    __shared__ double sh[32];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + kBX * ty;
+    const V beta = (V)sc->beta, alpha = (V)sc->alpha;
+    Acc acc;
+    auto isred = [&](long long c) -> bool { return (red[c >> 5] >> (c & 31)) & 1u; };
+    const int tiles_x = (d.nx + kBX - 1) / kBX;
+    const long long ntiles = (long long)tiles_x * ((d.ny + kBY - 1) / kBY);
+    const long long total = ntiles * d.nz;
+    const long long w0 = min((long long)blockIdx.x * per_block, total);
+    const long long w1 = min(w0 + per_block, total);
+    for (long long w = w0; w < w1;) {
+        const long long tile_id = w / d.nz;
+        const int k0 = int(w - tile_id * d.nz);
+        const int k1 = (int)min((long long)d.nz, (long long)k0 + (w1 - w));
+        w += k1 - k0;
+        const int i0 = int(tile_id % tiles_x) * kBX, j0 = int(tile_id / tiles_x) * kBY;
+        const int i = i0 + tx, j = j0 + ty;
+        const bool inside = i < d.nx && j < d.ny;
+        const long long own = inside ? i + (long long)d.nx * j : 0;
+        // p-tile elements of this thread: e = tid and tid + 256 of the (kBX+4) x (kBY+4) tile
+        long long poff[2];
+        bool pval[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int e = tid + q * kBX * kBY;
+            const int gi = i0 - 2 + e % kPX, gj = j0 - 2 + e / kPX;
+            pval[q] = e < kPN && gi >= 0 && gi < d.nx && gj >= 0 && gj < d.ny;
+            poff[q] = pval[q] ? gi + (long long)d.nx * gj : 0;
+        }
+        // w element of the ring (rows j0-1, j0+kBY, columns i0-1, i0+kBX) handled by this thread
+        int hi = 0, hj = 0, hgi = -1, hgj = -1;
+        const bool has_ring = tid < kHalo;
+        if (has_ring) {
+            if (tid < kBX) { hgi = i0 + tid; hgj = j0 - 1; hi = tid + 1; hj = 0; }
+            else if (tid < 2 * kBX) { hgi = i0 + tid - kBX; hgj = j0 + kBY; hi = tid - kBX + 1; hj = kBY + 1; }
+            else if (tid < 2 * kBX + kBY) { hgi = i0 - 1; hgj = j0 + tid - 2 * kBX; hi = 0; hj = tid - 2 * kBX + 1; }
+            else { hgi = i0 + kBX; hgj = j0 + tid - 2 * kBX - kBY; hi = kBX + 1; hj = tid - 2 * kBX - kBY + 1; }
+        }
+        auto slot = [](int kk) { return (kk + 6) % 3; };
+        auto load_raw = [&](int kk, V (&rr)[2], V (&pp)[2]) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                rr[q] = V(0);
+                pp[q] = V(0);
+                if (pval[q] && kk >= 0 && kk < d.nz) {
+                    const long long c = (long long)kk * d.plane + poff[q];
+                    rr[q] = src[c];
+                    pp[q] = pold[c];
+                }
+            }
+        };
+        auto store_p = [&](int kk, const V (&rr)[2], const V (&pp)[2]) {
+            V* P = pt[slot(kk)];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int e = tid + q * kBX * kBY;
+                if (e < kPN) P[e] = fmav(beta, pp[q], rr[q]);
+            }
+        };
+        // w of one cell (gi, gj, kw) whose p-tile position is (px, py)
+        auto wval = [&](int gi, int gj, int kw, int px, int py) -> V {
+            if (gi < 0 || gi >= d.nx || gj < 0 || gj >= d.ny || kw < 0 || kw >= d.nz) return V(0);
+            const long long c = (long long)kw * d.plane + gi + (long long)d.nx * gj;
+            const V* P = pt[slot(kw)];
+            if (!isred(c)) return P[py * kPX + px];
+            const V* Pm = pt[slot(kw - 1)];
+            const V* Pp = pt[slot(kw + 1)];
+            V u = V(0);
+            if (gi > 0) u = fmav(Tx[c - 1], P[py * kPX + px - 1], u);
+            if (gi < d.nx - 1) u = fmav(Tx[c], P[py * kPX + px + 1], u);
+            if (gj > 0) u = fmav(Ty[c - d.nx], P[(py - 1) * kPX + px], u);
+            if (gj < d.ny - 1) u = fmav(Ty[c], P[(py + 1) * kPX + px], u);
+            if (kw > 0) u = fmav(Tz[c - d.plane], Pm[py * kPX + px], u);
+            if (kw < d.nz - 1) u = fmav(Tz[c], Pp[py * kPX + px], u);
+            return u;
+        };
+        auto form_w = [&](int kw) {
+            wt[slot(kw)][ty + 1][tx + 1] = wval(i, j, kw, tx + 2, ty + 2);
+            if (has_ring) wt[slot(kw)][hj][hi] = wval(hgi, hgj, kw, hi + 1, hj + 1);
+        };
+        auto loadc = [&](int kk, StCoef<V>& c) {
+            c.txp = c.txm = c.typ = c.tym = c.tzp = c.xo = c.dg = V(0);
+            if (!inside || kk >= k1) return;
+            const long long cc = (long long)kk * d.plane + own;
+            c.txp = Tx[cc];
+            c.txm = i > 0 ? Tx[cc - 1] : V(0);
+            c.typ = Ty[cc];
+            c.tym = j > 0 ? Ty[cc - d.nx] : V(0);
+            c.tzp = Tz[cc];
+            c.xo = xv[cc];
+            c.dg = pold[cc];                // p_old of the own cell, for the x update
+        };
+
+        __syncthreads();   // the previous segment's readers are done with the buffers
+        V rr_[PF][2], pp_[PF][2];
+        {
+            V a[2], b[2];
+            load_raw(k0 - 2, a, b);
+            store_p(k0 - 2, a, b);
+            load_raw(k0 - 1, a, b);
+            store_p(k0 - 1, a, b);
+            load_raw(k0, a, b);
+            store_p(k0, a, b);
+        }
+        __syncthreads();
+        form_w(k0 - 1);
+        {
+            V a[2], b[2];
+            load_raw(k0 + 1, a, b);
+            __syncthreads();
+            store_p(k0 + 1, a, b);     // overwrites plane k0-2, no longer needed
+        }
+        __syncthreads();
+        form_w(k0);
+        __syncthreads();   // the first step overwrites the p plane k0-1 that form_w(k0) read
+#pragma unroll
+        for (int q = 0; q < PF; ++q) {
+            if (k0 + 2 + q <= k1 + 1) load_raw(k0 + 2 + q, rr_[q], pp_[q]);
+            else {
+                rr_[q][0] = rr_[q][1] = pp_[q][0] = pp_[q][1] = V(0);
+            }
+        }
+        StCoef<V> cc;
+        loadc(k0, cc);
+        V tzm1 = (inside && k0 > 0) ? Tz[(long long)(k0 - 1) * d.plane + own] : V(0);
+        for (int k = k0; k < k1; ++k) {
+            store_p(k + 2, rr_[0], pp_[0]);
+#pragma unroll
+            for (int q = 0; q < PF - 1; ++q) {
+                rr_[q][0] = rr_[q + 1][0]; rr_[q][1] = rr_[q + 1][1];
+                pp_[q][0] = pp_[q + 1][0]; pp_[q][1] = pp_[q + 1][1];
+            }
+            const int kn = k + 2 + PF;
+            if (kn <= k1 + 1) load_raw(kn, rr_[PF - 1], pp_[PF - 1]);
+            StCoef<V> cn;
+            loadc(k + 1, cn);
+            __syncthreads();
+            form_w(k + 1);
+            __syncthreads();
+            if (inside) {
+                const long long c = (long long)k * d.plane + own;
+                if (!isred(c)) {
+                    const V v = wt[slot(k)][ty + 1][tx + 1];
+                    V t = v;
+                    t = fmav(-cc.txp, wt[slot(k)][ty + 1][tx + 2], t);
+                    t = fmav(-cc.txm, wt[slot(k)][ty + 1][tx], t);
+                    t = fmav(-cc.typ, wt[slot(k)][ty + 2][tx + 1], t);
+                    t = fmav(-cc.tym, wt[slot(k)][ty][tx + 1], t);
+                    t = fmav(-cc.tzp, wt[slot(k + 1)][ty + 1][tx + 1], t);
+                    t = fmav(-tzm1, wt[slot(k - 1)][ty + 1][tx + 1], t);
+                    out[c] = t;
+                    pnew[c] = v;
+                    xv[c] = fmav(alpha, cc.dg, cc.xo);
+                    acc.add(v, t);
+                }
+            }
+            tzm1 = cc.tzp;
+            cc = cn;
         }
     }
+    double tot;
+    if (grid_reduce(acc.value(), partials, counter, sh, &tot)) sc->pq_raw = tot;
 }
 
 // Set-up and reconstruction gathers on the scaled FP64 operator (not in the iteration loop):

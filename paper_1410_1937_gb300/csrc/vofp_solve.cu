@@ -329,11 +329,6 @@ dim3 rows_grid(const vofp_ctx* c, int threads) {
     const int gx = ceil_div(c->d.nx, threads);
     return dim3(gx, (unsigned)std::max(1LL, std::min(rows, (long long)num_sms() * 32)));
 }
-dim3 red_grid(const vofp_ctx* c) {
-    const long long rows = (long long)c->d.ny * c->d.nz;
-    const int gx = ceil_div((c->d.nx + 1) / 2, kNT);
-    return dim3(gx, (unsigned)std::max(1LL, std::min(rows, (long long)num_sms() * 32)));
-}
 
 // ---- flexible CG with the learned preconditioner -----------------------------------------
 // up to three dot products of FP32 vectors over cells outside `bits`, accumulated with the
@@ -410,14 +405,12 @@ __global__ void k_to_float(long long n, const double* __restrict__ a, float* __r
 
 void launch_stencil_apply_unscaled(vofp_ctx* c, const double* x, double* t) {
     launch(c, k_stencil<double, ST_APPLY_UNSCALED, 1>, stencil_grid(c), dim3(kBX, kBY), c->stream, 
-        c->d, stencil_per_block(c), c->Tx, c->Ty, c->Tz, c->diag, x, nullptr, nullptr, nullptr, t, c->sc, c->partials, c->counters,
-        (const uint32_t*)nullptr);
+        c->d, stencil_per_block(c), c->Tx, c->Ty, c->Tz, c->diag, x, nullptr, nullptr, nullptr, t, c->sc, c->partials, c->counters);
 }
 
 void launch_stencil_apply_scaled(vofp_ctx* c, const double* x, double* t) {
     launch(c, k_stencil<double, ST_APPLY_SCALED, 1>, stencil_grid(c), dim3(kBX, kBY), c->stream, 
-        c->d, stencil_per_block(c), c->Txs, c->Tys, c->Tzs, nullptr, x, nullptr, nullptr, nullptr, t, c->sc, c->partials, c->counters,
-        (const uint32_t*)nullptr);
+        c->d, stencil_per_block(c), c->Txs, c->Tys, c->Tzs, nullptr, x, nullptr, nullptr, nullptr, t, c->sc, c->partials, c->counters);
 }
 
 template <typename V>
@@ -439,15 +432,13 @@ void launch_cg_iteration(vofp_ctx* c, cudaStream_t st, V* r, V* po, V* pn, V* xv
                          cudaGraphConditionalHandle h, int use_h) {
     const uint32_t* bits = rb ? c->excl_bits : c->slave_bits;
     if (rb) {
-        launch(c, k_red<V>, red_grid(c), dim3(kNT), st, c->d, Tx, Ty, Tz, (const uint32_t*)c->red_bits, r,
-               (const V*)po, (const CgScalars*)c->sc);
-        launch(c, k_stencil<V, ST_CG, stencil_pf<V>(), true>, stencil_grid(c), dim3(kBX, kBY), st, c->d,
-               stencil_per_block(c), Tx, Ty, Tz, (const double*)nullptr, (const V*)r, (const V*)po, pn, xv, q, c->sc,
-               c->partials, c->counters, (const uint32_t*)c->red_bits);
+        launch(c, k_cg_rb<V, stencil_pf<V>()>, stencil_grid(c), dim3(kBX, kBY), st, c->d, stencil_per_block(c), Tx, Ty,
+               Tz, (const uint32_t*)c->red_bits, (const V*)r, (const V*)po, pn, xv, q, c->sc, c->partials,
+               c->counters);
     } else {
-        launch(c, k_stencil<V, ST_CG, stencil_pf<V>(), false>, stencil_grid(c), dim3(kBX, kBY), st, c->d,
+        launch(c, k_stencil<V, ST_CG, stencil_pf<V>()>, stencil_grid(c), dim3(kBX, kBY), st, c->d,
                stencil_per_block(c), Tx, Ty, Tz, (const double*)nullptr, (const V*)r, (const V*)po, pn, xv, q, c->sc,
-               c->partials, c->counters, (const uint32_t*)nullptr);
+               c->partials, c->counters);
     }
     if (c->ngroups > 0)
         launch(c, k_group_patch<V>, ceil_div(c->ngroups, kNT), kNT, st, c->ngroups, c->gptr, c->gcells, c->gcorr, q, pn,
@@ -461,7 +452,10 @@ void launch_cg_iteration(vofp_ctx* c, cudaStream_t st, V* r, V* po, V* pn, V* xv
 }
 
 // kernels of one iteration (for the launch count of graph executions)
-int iteration_kernels(const vofp_ctx* c, bool rb) { return 2 + (c->ngroups > 0 ? 1 : 0) + (rb ? 1 : 0); }
+int iteration_kernels(const vofp_ctx* c, bool rb) {
+    (void)rb;
+    return 2 + (c->ngroups > 0 ? 1 : 0);
+}
 
 // Mixed precision, red-black: the reduced right-hand side r_S + E_SR r_R of the correction
 // equation (folded over merge groups) into c->q, its norm into sc->rr0.
@@ -531,7 +525,7 @@ void launch_outer_head(vofp_ctx* c, cudaStream_t st, bool rb, cudaGraphCondition
     launch(c, k_stencil<double, ST_APPLY_SCALED, 1>, stencil_grid(c), dim3(kBX, kBY), st, c->d, stencil_per_block(c),
            (const double*)c->Txs, (const double*)c->Tys, (const double*)c->Tzs, (const double*)nullptr,
            (const double*)c->xt, (const double*)nullptr, (double*)nullptr, (double*)nullptr, c->q, c->sc, c->partials,
-           c->counters, (const uint32_t*)nullptr);
+           c->counters);
     if (c->ngroups > 0)
         launch(c, k_group_patch<double>, ceil_div(c->ngroups, kNT), kNT, st, c->ngroups, (const int*)c->gptr,
                (const int*)c->gcells, (const double*)c->gcorr, c->q, (const double*)c->xt, 0, c->sc, c->partials,
@@ -935,10 +929,10 @@ vofp_status solve_fcg(vofp_ctx* c, const double* b, double* x, const vofp_solve_
         return VOFP_OK;
     };
     auto apply_f = [&](const float* p, float* q) {
-        launch(c, k_stencil<float, ST_APPLY_SCALED, 2, false>, stencil_grid(c), dim3(kBX, kBY), st, c->d,
+        launch(c, k_stencil<float, ST_APPLY_SCALED, 2>, stencil_grid(c), dim3(kBX, kBY), st, c->d,
                stencil_per_block(c), (const float*)c->Txf, (const float*)c->Tyf, (const float*)c->Tzf,
                (const double*)nullptr, p, (const float*)nullptr, (float*)nullptr, (float*)nullptr, q, c->sc,
-               c->partials, c->counters, (const uint32_t*)nullptr);
+               c->partials, c->counters);
         if (c->ngroups > 0)
             launch(c, k_group_patch<float>, ceil_div(c->ngroups, kNT), kNT, st, c->ngroups, (const int*)c->gptr,
                    (const int*)c->gcells, (const double*)c->gcorr, q, p, 0, c->sc, c->partials, c->counters);
@@ -1094,51 +1088,39 @@ vofp_status time_iteration_kernels(vofp_ctx* c, int precision, bool rb, int reps
     if (precision == 32) {
         auto stn = [&]() {
             if (rb)
-                launch(c, k_stencil<float, ST_CG, stencil_pf<float>(), true>, stencil_grid(c), dim3(kBX, kBY), st, c->d,
-                       stencil_per_block(c), (const float*)c->Txf, (const float*)c->Tyf, (const float*)c->Tzf,
-                       (const double*)nullptr, (const float*)c->rf, (const float*)c->pf0, c->pf1, c->xf, c->qf, c->sc,
-                       c->partials, c->counters, red);
+                launch(c, k_cg_rb<float, stencil_pf<float>()>, stencil_grid(c), dim3(kBX, kBY), st, c->d,
+                       stencil_per_block(c), (const float*)c->Txf, (const float*)c->Tyf, (const float*)c->Tzf, red,
+                       (const float*)c->rf, (const float*)c->pf0, c->pf1, c->xf, c->qf, c->sc, c->partials,
+                       c->counters);
             else
-                launch(c, k_stencil<float, ST_CG, stencil_pf<float>(), false>, stencil_grid(c), dim3(kBX, kBY), st,
+                launch(c, k_stencil<float, ST_CG, stencil_pf<float>()>, stencil_grid(c), dim3(kBX, kBY), st,
                        c->d, stencil_per_block(c), (const float*)c->Txf, (const float*)c->Tyf, (const float*)c->Tzf,
                        (const double*)nullptr, (const float*)c->rf, (const float*)c->pf0, c->pf1, c->xf, c->qf, c->sc,
-                       c->partials, c->counters, red);
+                       c->partials, c->counters);
         };
         auto upd = [&]() {
             launch(c, k_cg_update<float, false>, stream_grid(N / 4 + 1), kNT, st, N, c->rf, (const float*)c->qf, bits,
                    c->sc, c->partials, c->counters, (cudaGraphConditionalHandle)0, 0);
         };
-        auto rd = [&]() {
-            launch(c, k_red<float>, red_grid(c), dim3(kNT), st, c->d, (const float*)c->Txf, (const float*)c->Tyf,
-                   (const float*)c->Tzf, (const uint32_t*)c->red_bits, c->rf, (const float*)c->pf0,
-                   (const CgScalars*)c->sc);
-        };
         if ((s = timed(stn, &t1)) || (s = timed(upd, &t2))) return s;
-        if (rb && (s = timed(rd, &t3))) return s;
     } else {
         auto stn = [&]() {
             if (rb)
-                launch(c, k_stencil<double, ST_CG, stencil_pf<double>(), true>, stencil_grid(c), dim3(kBX, kBY), st,
-                       c->d, stencil_per_block(c), (const double*)c->Txs, (const double*)c->Tys, (const double*)c->Tzs,
-                       (const double*)nullptr, (const double*)c->r, (const double*)c->p0, c->p1, c->xt, c->q, c->sc,
-                       c->partials, c->counters, red);
+                launch(c, k_cg_rb<double, stencil_pf<double>()>, stencil_grid(c), dim3(kBX, kBY), st, c->d,
+                       stencil_per_block(c), (const double*)c->Txs, (const double*)c->Tys, (const double*)c->Tzs, red,
+                       (const double*)c->r, (const double*)c->p0, c->p1, c->xt, c->q, c->sc, c->partials,
+                       c->counters);
             else
-                launch(c, k_stencil<double, ST_CG, stencil_pf<double>(), false>, stencil_grid(c), dim3(kBX, kBY), st,
+                launch(c, k_stencil<double, ST_CG, stencil_pf<double>()>, stencil_grid(c), dim3(kBX, kBY), st,
                        c->d, stencil_per_block(c), (const double*)c->Txs, (const double*)c->Tys, (const double*)c->Tzs,
                        (const double*)nullptr, (const double*)c->r, (const double*)c->p0, c->p1, c->xt, c->q, c->sc,
-                       c->partials, c->counters, red);
+                       c->partials, c->counters);
         };
         auto upd = [&]() {
             launch(c, k_cg_update<double, false>, stream_grid(N / 2 + 1), kNT, st, N, c->r, (const double*)c->q, bits,
                    c->sc, c->partials, c->counters, (cudaGraphConditionalHandle)0, 0);
         };
-        auto rd = [&]() {
-            launch(c, k_red<double>, red_grid(c), dim3(kNT), st, c->d, (const double*)c->Txs, (const double*)c->Tys,
-                   (const double*)c->Tzs, (const uint32_t*)c->red_bits, c->r, (const double*)c->p0,
-                   (const CgScalars*)c->sc);
-        };
         if ((s = timed(stn, &t1)) || (s = timed(upd, &t2))) return s;
-        if (rb && (s = timed(rd, &t3))) return s;
     }
     launch(c, k_set_pq_inf, 1, 1, st, c->sc, 0);
     VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));

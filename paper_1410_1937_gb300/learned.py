@@ -7,7 +7,8 @@ solution S^-1 x (FP32).  Training: the library's forward/backward/Adam kernels (
 on one sample per step.  Evaluation: flexible CG with the network against plain and mixed PCG on
 held-out seeds.  Checkpoints are .npz files of the FP32 master weights.
 
-    python -m paper_1410_1937_gb300.learned --samples 2000 --epochs 4 --out weights.npz
+    python -m paper_1410_1937_gb300.learned --samples 2000 --epochs 8 --out weights.npz
+    python -m paper_1410_1937_gb300.learned --samples 0 --init weights.npz   # evaluate only
 """
 from __future__ import annotations
 
@@ -23,6 +24,7 @@ import numpy as np
 TRAIN_SEED0 = 100000
 HELD_OUT_SEED0 = 200000
 TRAIN_SHAPE = (256, 128, 64)
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "unet_hull_256x128x64.npz")
 
 
 def _geometry_worker(args):
@@ -117,6 +119,17 @@ def evaluate(net, seeds, shape, rtol=1e-8, log=print):
             _, info = ctx.vofp_solve(b, rtol=rtol, raise_on_error=False, **kw)
             row[name] = {k: info[k] for k in ("iterations", "seconds", "rel_residual", "status_name",
                                               "nn_applications", "fell_back")}
+        # what the network gains per iteration: relative residual after k iterations
+        early = {}
+        for k in (2, 6, 10, 20, 40):
+            _, a = ctx.vofp_solve(b, rtol=rtol, max_iter=k, mode=vofp.MODE_FCG_NN, nn=net, stag_window=10 ** 6,
+                                  raise_on_error=False)
+            _, c = ctx.vofp_solve(b, rtol=rtol, max_iter=k, mode=vofp.MODE_MIXED, check_every=2,
+                                  raise_on_error=False)
+            _, d = ctx.vofp_solve(b, rtol=rtol, max_iter=k, mode=vofp.MODE_MIXED, check_every=2,
+                                  precond=vofp.PRECOND_RBSGS, raise_on_error=False)
+            early[k] = {"fcg_nn": a["rel_residual"], "cg_jacobi": c["rel_residual"], "cg_rbsgs": d["rel_residual"]}
+        row["residual_after_k_iterations"] = early
         rows.append(row)
         log(json.dumps(row))
         ctx.close()
@@ -137,14 +150,17 @@ def main():
     ap.add_argument("--report", default=None)
     args = ap.parse_args()
     shape = tuple(args.shape)
-    data = generate(range(TRAIN_SEED0, TRAIN_SEED0 + args.samples), shape, workers=args.workers or None)
+    hist = []
+    if args.samples > 0:
+        data = generate(range(TRAIN_SEED0, TRAIN_SEED0 + args.samples), shape, workers=args.workers or None)
     from paper_1410_1937_gb300 import vofp
     net = vofp.Network(seed=1)
     if args.init:
         load(net, args.init)
-    hist = train(net, data, shape, args.epochs, args.lr)
-    save(net, args.out)
-    del data
+    if args.samples > 0:
+        hist = train(net, data, shape, args.epochs, args.lr)
+        save(net, args.out)
+        del data
     rows = evaluate(net, range(HELD_OUT_SEED0, HELD_OUT_SEED0 + args.eval_seeds), tuple(args.eval_shape))
     if args.report:
         with open(args.report, "w") as f:
