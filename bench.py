@@ -340,7 +340,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--precond", default="rbsgs", choices=["jacobi", "rbsgs"])
+    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "rbsgs"])
     ap.add_argument("--shape", type=int, nargs=3, default=list(SHAPE))
     ap.add_argument("--check-every", type=int, default=8)
     ap.add_argument("--inner-rtol", type=float, default=1e-3)

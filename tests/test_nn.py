@@ -209,7 +209,7 @@ def test_gpu_training_reduces_loss(gpu):
     net = vofp.Network(seed=12)
     net.bind(ctx, t["F"])
     first = net.train_step(r, xs, lr=3e-3)
-    for _ in range(60):
+    for _ in range(150):
         last = net.train_step(r, xs, lr=3e-3)
     assert last < 0.5 * first, (first, last)
 
@@ -234,3 +234,32 @@ def test_gpu_learned_preconditioner_solve_matches_oracle(gpu, oracle, train):
     assert info["nn_applications"] > 0
     got = x.cpu().numpy().reshape(prob.shape)
     assert np.linalg.norm(got - ref) <= 1e-6 * np.linalg.norm(ref)
+
+
+@pytest.mark.gpu
+def test_trained_network_gain_is_measured(gpu):
+    """What the trained network gains: relative residual after 10 flexible-CG iterations with the
+    committed trained weights, against an untrained network and against plain Jacobi-PCG, on a
+    held-out sample.  Training must help the network; against plain PCG the measured gain is
+    reported (on this workload the network does not beat plain PCG, and the solve's stagnation
+    fallback keeps it convergent)."""
+    torch, vofp = gpu
+    from paper_1410_1937_gb300 import learned
+    p = I.config3_sample(200001, (128, 64, 32))
+    ctx, t = vofp.context_for(p)
+    b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
+    res = {}
+    for name in ("trained", "untrained"):
+        net = vofp.Network(seed=3)
+        if name == "trained":
+            learned.load(net, learned.WEIGHTS)
+        net.bind(ctx, t["F"])
+        _, info = ctx.vofp_solve(b, rtol=1e-8, max_iter=10, mode=vofp.MODE_FCG_NN, nn=net, stag_window=10 ** 6,
+                                 raise_on_error=False)
+        res[name] = info["rel_residual"]
+        _, full = ctx.vofp_solve(b, rtol=1e-8, mode=vofp.MODE_FCG_NN, nn=net, raise_on_error=False)
+        assert full["status"] == 0 and full["rel_residual"] <= 1e-8
+    _, cg = ctx.vofp_solve(b, rtol=1e-8, max_iter=10, mode=vofp.MODE_MIXED, check_every=2, raise_on_error=False)
+    res["plain_cg"] = cg["rel_residual"]
+    print("relative residual after 10 iterations:", res)
+    assert res["trained"] < res["untrained"], res
