@@ -58,7 +58,9 @@ typedef enum {
     VOFP_ERR_BREAKDOWN = 5,       /* p.Ap <= 0, r.z <= 0 or a non-finite scalar in the iteration  */
     VOFP_ERR_STAGNATED = 6,       /* residual stopped decreasing (stag_window / stag_ratio)       */
     VOFP_ERR_INCOMPATIBLE_RHS = 7,/* all-Neumann problem whose right-hand side does not sum to 0  */
-    VOFP_ERR_NOT_BUILT = 8        /* vofp_build_operator has not succeeded on this context        */
+    VOFP_ERR_NOT_BUILT = 8,       /* vofp_build_operator has not succeeded on this context        */
+    VOFP_ERR_DEVICE_TIMEOUT = 9   /* a bounded device-side wait (a bulk copy into shared memory)  */
+                                  /* ran out after about one second; the solve stopped            */
 } vofp_status;
 
 enum { VOFP_BC_NEUMANN = 0, VOFP_BC_DIRICHLET = 1 };
@@ -144,6 +146,9 @@ typedef struct {
     long long merged_cells;   /* cells folded into another cell's unknown                      */
     long long groups;         /* merge groups with more than one cell                          */
     long long device_bytes;   /* device memory held by the context                             */
+    int tma_stencil_fp32;     /* 1 if the FP32 CG stencil is fed by bulk tensor copies (TMA),  */
+    int tma_stencil_fp64;     /* 0 for the register-prefetch kernel; both are set once the     */
+                              /* context's kernels are prepared (first solve or timing call)   */
 } vofp_stats;
 
 /* Library version string (static storage). */

@@ -1,8 +1,11 @@
 // Internal declarations of libvofp: the context, launch helpers and shared device utilities.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/vofp.h"
@@ -115,6 +118,13 @@ struct vofp_ctx {
     size_t bytes = 0;
     std::vector<void*> allocs;
     long long launches = 0;           // kernels launched (graph bodies counted per execution)
+    bool kernels_prepared = false;    // dynamic shared memory opted in, occupancies queried
+    // TMA-fed CG stencil: usable per precision (row pitch a multiple of 16 bytes, driver entry
+    // point found, not disabled by VOFP_STENCIL_TMA=0); resident blocks per SM; encoded maps
+    bool tma_ok[2] = {false, false};  // FP32, FP64
+    int tma_blocks_per_sm[2] = {0, 0};
+    int tma_cpt32 = 2;                // FP32 TMA stencil: cells per thread along x
+    std::map<std::tuple<const void*, int, int>, CUtensorMap> tma_maps;
 
     void set_error(const std::string& m) { err = m; }
     template <typename T>
@@ -166,6 +176,13 @@ void launch_group_patch(vofp_ctx* c, V* t, const V* p, bool dot_correction);
 template <typename... KArgs, typename... Args>
 inline void launch(vofp_ctx* c, void (*k)(KArgs...), dim3 g, dim3 b, cudaStream_t s, Args... args) {
     k<<<g, b, 0, s>>>(static_cast<KArgs>(args)...);
+    ++c->launches;
+}
+// Same, with dynamic shared memory.
+template <typename... KArgs, typename... Args>
+inline void launch_smem(vofp_ctx* c, void (*k)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t s,
+                        Args... args) {
+    k<<<g, b, smem, s>>>(static_cast<KArgs>(args)...);
     ++c->launches;
 }
 

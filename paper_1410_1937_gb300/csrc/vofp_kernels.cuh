@@ -270,11 +270,12 @@ k_stencil(const Dims d, const int per_block, const V* __restrict__ Tx, const V* 
 // remaining (black and merge-group) unknowns.  An iteration forms w = E_RS p on the red cells
 // and w = p on the others, and applies I - E to w on the black rows.
 // Fused red-black iteration: one pass per CG iteration.
-// Per plane k a block (32 x 8 columns) keeps three planes of the direction p = r + beta p_old with
-// a 2-cell halo and three planes of w (w = p on black cells, w = E_RS p on red cells, 1-cell halo)
-// in shared memory.  Step k: store p of plane k+2 (prefetched into registers one step earlier);
-// barrier; form w of plane k+1 (red cells sum T_f p over their six neighbours, using their own
-// coefficients); barrier; apply I - E to w on the black rows of plane k.
+// A block (32 x 8 columns) marches planes in z.  Four rotating shared planes hold, with a 2-cell
+// halo, the direction p = r + beta p_old and the coefficients Tx, Ty, Tz; three rotating planes
+// hold w (w = p on black cells, w = E_RS p on red cells; 1-cell halo); a byte tile per plane
+// holds the red flags.  The raw inputs of plane k+2 are prefetched into registers one step ahead.
+// Step k: store plane k+2; barrier; form w of plane k+1 from shared memory; barrier; apply I - E
+// to w on the black rows of plane k.
 constexpr int kPX = kBX + 4, kPY = kBY + 4, kPN = kPX * kPY;
 
 template <typename V, int PF>
@@ -284,13 +285,19 @@ k_cg_rb(const Dims d, const int per_block, const V* __restrict__ Tx, const V* __
         const V* __restrict__ pold, V* __restrict__ pnew, V* __restrict__ xv, V* __restrict__ out,
         CgScalars* __restrict__ sc, double* __restrict__ partials, unsigned int* __restrict__ counter) {
     using Acc = typename AccFor<V>::type;
-    __shared__ V pt[3][kPN];                       // p, planes mod 3, (kBX+4) x (kBY+4)
-    __shared__ V wt[3][kBY + 2][kBX + 2];          // w, planes mod 3, one-cell halo (no corners)
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V* sm = reinterpret_cast<V*>(smem_raw);
+    // [4 planes][4 fields: p, Tx, Ty, Tz][kPN] then w [3 planes][(kBY+2) x (kBX+2)]
+    auto tile = [&](int kk, int f) -> V* { return sm + ((((kk + 8) & 3) * 4 + f) * kPN); };
+    constexpr int WN = (kBY + 2) * (kBX + 2);
+    auto wpl = [&](int kk) -> V* { return sm + 16 * kPN + ((kk + 6) % 3) * WN; };
+    // red flags of the same four planes, one byte per p-tile position
+    unsigned char* flags = reinterpret_cast<unsigned char*>(sm + 16 * kPN + 3 * WN);
+    auto ftile = [&](int kk) -> unsigned char* { return flags + ((kk + 8) & 3) * kPN; };
     __shared__ double sh[32];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + kBX * ty;
     const V beta = (V)sc->beta, alpha = (V)sc->alpha;
     Acc acc;
-    auto isred = [&](long long c) -> bool { return (red[c >> 5] >> (c & 31)) & 1u; };
     const int tiles_x = (d.nx + kBX - 1) / kBX;
     const long long ntiles = (long long)tiles_x * ((d.ny + kBY - 1) / kBY);
     const long long total = ntiles * d.nz;
@@ -305,7 +312,6 @@ k_cg_rb(const Dims d, const int per_block, const V* __restrict__ Tx, const V* __
         const int i = i0 + tx, j = j0 + ty;
         const bool inside = i < d.nx && j < d.ny;
         const long long own = inside ? i + (long long)d.nx * j : 0;
-        // p-tile elements of this thread: e = tid and tid + 256 of the (kBX+4) x (kBY+4) tile
         long long poff[2];
         bool pval[2];
 #pragma unroll
@@ -315,7 +321,6 @@ k_cg_rb(const Dims d, const int per_block, const V* __restrict__ Tx, const V* __
             pval[q] = e < kPN && gi >= 0 && gi < d.nx && gj >= 0 && gj < d.ny;
             poff[q] = pval[q] ? gi + (long long)d.nx * gj : 0;
         }
-        // w element of the ring (rows j0-1, j0+kBY, columns i0-1, i0+kBX) handled by this thread
         int hi = 0, hj = 0, hgi = -1, hgj = -1;
         const bool has_ring = tid < kHalo;
         if (has_ring) {
@@ -324,130 +329,140 @@ k_cg_rb(const Dims d, const int per_block, const V* __restrict__ Tx, const V* __
             else if (tid < 2 * kBX + kBY) { hgi = i0 - 1; hgj = j0 + tid - 2 * kBX; hi = 0; hj = tid - 2 * kBX + 1; }
             else { hgi = i0 + kBX; hgj = j0 + tid - 2 * kBX - kBY; hi = kBX + 1; hj = tid - 2 * kBX - kBY + 1; }
         }
-        auto slot = [](int kk) { return (kk + 6) % 3; };
-        auto load_raw = [&](int kk, V (&rr)[2], V (&pp)[2]) {
+        struct Raw { V r[2], p[2], x[2], y[2], z[2]; unsigned f[2]; };
+        auto load_raw = [&](int kk, Raw& R) {
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
-                rr[q] = V(0);
-                pp[q] = V(0);
+                R.r[q] = R.p[q] = R.x[q] = R.y[q] = R.z[q] = V(0);
+                R.f[q] = 0u;
                 if (pval[q] && kk >= 0 && kk < d.nz) {
                     const long long c = (long long)kk * d.plane + poff[q];
-                    rr[q] = src[c];
-                    pp[q] = pold[c];
+                    R.f[q] = (red[c >> 5] >> (c & 31)) & 1u;
+                    R.r[q] = src[c];
+                    R.p[q] = pold[c];
+                    R.x[q] = Tx[c];
+                    R.y[q] = Ty[c];
+                    R.z[q] = Tz[c];
                 }
             }
         };
-        auto store_p = [&](int kk, const V (&rr)[2], const V (&pp)[2]) {
-            V* P = pt[slot(kk)];
+        auto store_raw = [&](int kk, const Raw& R) {
+            V* P = tile(kk, 0);
+            V* X = tile(kk, 1);
+            V* Y = tile(kk, 2);
+            V* Z = tile(kk, 3);
+            unsigned char* Fl = ftile(kk);
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 const int e = tid + q * kBX * kBY;
-                if (e < kPN) P[e] = fmav(beta, pp[q], rr[q]);
+                if (e < kPN) {
+                    Fl[e] = (unsigned char)R.f[q];
+                    P[e] = fmav(beta, R.p[q], R.r[q]);
+                    X[e] = R.x[q];
+                    Y[e] = R.y[q];
+                    Z[e] = R.z[q];
+                }
             }
         };
-        // w of one cell (gi, gj, kw) whose p-tile position is (px, py)
+        // w of cell (gi, gj, kw) at p-tile position (px, py): red cells sum T p over their faces
         auto wval = [&](int gi, int gj, int kw, int px, int py) -> V {
             if (gi < 0 || gi >= d.nx || gj < 0 || gj >= d.ny || kw < 0 || kw >= d.nz) return V(0);
-            const long long c = (long long)kw * d.plane + gi + (long long)d.nx * gj;
-            const V* P = pt[slot(kw)];
-            if (!isred(c)) return P[py * kPX + px];
-            const V* Pm = pt[slot(kw - 1)];
-            const V* Pp = pt[slot(kw + 1)];
+            const int e = py * kPX + px;
+            const V* P = tile(kw, 0);
+            if (!ftile(kw)[e]) return P[e];
+            const V* X = tile(kw, 1);
+            const V* Y = tile(kw, 2);
+            const V* Z = tile(kw, 3);
             V u = V(0);
-            if (gi > 0) u = fmav(Tx[c - 1], P[py * kPX + px - 1], u);
-            if (gi < d.nx - 1) u = fmav(Tx[c], P[py * kPX + px + 1], u);
-            if (gj > 0) u = fmav(Ty[c - d.nx], P[(py - 1) * kPX + px], u);
-            if (gj < d.ny - 1) u = fmav(Ty[c], P[(py + 1) * kPX + px], u);
-            if (kw > 0) u = fmav(Tz[c - d.plane], Pm[py * kPX + px], u);
-            if (kw < d.nz - 1) u = fmav(Tz[c], Pp[py * kPX + px], u);
+            u = fmav(X[e], P[e + 1], u);
+            u = fmav(X[e - 1], P[e - 1], u);
+            u = fmav(Y[e], P[e + kPX], u);
+            u = fmav(Y[e - kPX], P[e - kPX], u);
+            u = fmav(Z[e], tile(kw + 1, 0)[e], u);
+            u = fmav(tile(kw - 1, 3)[e], tile(kw - 1, 0)[e], u);
             return u;
         };
         auto form_w = [&](int kw) {
-            wt[slot(kw)][ty + 1][tx + 1] = wval(i, j, kw, tx + 2, ty + 2);
-            if (has_ring) wt[slot(kw)][hj][hi] = wval(hgi, hgj, kw, hi + 1, hj + 1);
-        };
-        auto loadc = [&](int kk, StCoef<V>& c) {
-            c.txp = c.txm = c.typ = c.tym = c.tzp = c.xo = c.dg = V(0);
-            if (!inside || kk >= k1) return;
-            const long long cc = (long long)kk * d.plane + own;
-            c.txp = Tx[cc];
-            c.txm = i > 0 ? Tx[cc - 1] : V(0);
-            c.typ = Ty[cc];
-            c.tym = j > 0 ? Ty[cc - d.nx] : V(0);
-            c.tzp = Tz[cc];
-            c.xo = xv[cc];
-            c.dg = pold[cc];                // p_old of the own cell, for the x update
+            V* Wp = wpl(kw);
+            Wp[(ty + 1) * (kBX + 2) + tx + 1] = wval(i, j, kw, tx + 2, ty + 2);
+            if (has_ring) Wp[hj * (kBX + 2) + hi] = wval(hgi, hgj, kw, hi + 1, hj + 1);
         };
 
         __syncthreads();   // the previous segment's readers are done with the buffers
-        V rr_[PF][2], pp_[PF][2];
         {
-            V a[2], b[2];
-            load_raw(k0 - 2, a, b);
-            store_p(k0 - 2, a, b);
-            load_raw(k0 - 1, a, b);
-            store_p(k0 - 1, a, b);
-            load_raw(k0, a, b);
-            store_p(k0, a, b);
+            Raw R;
+            for (int kk = k0 - 2; kk <= k0 + 1; ++kk) {
+                load_raw(kk, R);
+                store_raw(kk, R);
+            }
         }
         __syncthreads();
         form_w(k0 - 1);
-        {
-            V a[2], b[2];
-            load_raw(k0 + 1, a, b);
-            __syncthreads();
-            store_p(k0 + 1, a, b);     // overwrites plane k0-2, no longer needed
-        }
-        __syncthreads();
         form_w(k0);
-        __syncthreads();   // the first step overwrites the p plane k0-1 that form_w(k0) read
+        __syncthreads();
+        Raw pre[PF];
 #pragma unroll
         for (int q = 0; q < PF; ++q) {
-            if (k0 + 2 + q <= k1 + 1) load_raw(k0 + 2 + q, rr_[q], pp_[q]);
-            else {
-                rr_[q][0] = rr_[q][1] = pp_[q][0] = pp_[q][1] = V(0);
-            }
+            if (k0 + 2 + q <= k1 + 1) load_raw(k0 + 2 + q, pre[q]);
+            else load_raw(-100, pre[q]);
         }
-        StCoef<V> cc;
-        loadc(k0, cc);
-        V tzm1 = (inside && k0 > 0) ? Tz[(long long)(k0 - 1) * d.plane + own] : V(0);
+        const int eo = (ty + 2) * kPX + tx + 2;       // own p-tile position
+        V tzm1 = tile(k0 - 1, 3)[eo];
+        V xo = V(0), po = V(0);
+        if (inside) {
+            const long long c = (long long)k0 * d.plane + own;
+            xo = xv[c];
+            po = pold[c];
+        }
         for (int k = k0; k < k1; ++k) {
-            store_p(k + 2, rr_[0], pp_[0]);
+            store_raw(k + 2, pre[0]);
 #pragma unroll
-            for (int q = 0; q < PF - 1; ++q) {
-                rr_[q][0] = rr_[q + 1][0]; rr_[q][1] = rr_[q + 1][1];
-                pp_[q][0] = pp_[q + 1][0]; pp_[q][1] = pp_[q + 1][1];
-            }
+            for (int q = 0; q < PF - 1; ++q) pre[q] = pre[q + 1];
             const int kn = k + 2 + PF;
-            if (kn <= k1 + 1) load_raw(kn, rr_[PF - 1], pp_[PF - 1]);
-            StCoef<V> cn;
-            loadc(k + 1, cn);
+            if (kn <= k1 + 1) load_raw(kn, pre[PF - 1]);
+            V xn = V(0), pn_ = V(0);
+            if (inside && k + 1 < k1) {
+                const long long c = (long long)(k + 1) * d.plane + own;
+                xn = xv[c];
+                pn_ = pold[c];
+            }
             __syncthreads();
             form_w(k + 1);
             __syncthreads();
+            const V tzk = tile(k, 3)[eo];
             if (inside) {
                 const long long c = (long long)k * d.plane + own;
-                if (!isred(c)) {
-                    const V v = wt[slot(k)][ty + 1][tx + 1];
+                if (!ftile(k)[eo]) {
+                    const V* Wk = wpl(k);
+                    const V* X = tile(k, 1);
+                    const V* Y = tile(k, 2);
+                    const int wo = (ty + 1) * (kBX + 2) + tx + 1;
+                    const V v = Wk[wo];
                     V t = v;
-                    t = fmav(-cc.txp, wt[slot(k)][ty + 1][tx + 2], t);
-                    t = fmav(-cc.txm, wt[slot(k)][ty + 1][tx], t);
-                    t = fmav(-cc.typ, wt[slot(k)][ty + 2][tx + 1], t);
-                    t = fmav(-cc.tym, wt[slot(k)][ty][tx + 1], t);
-                    t = fmav(-cc.tzp, wt[slot(k + 1)][ty + 1][tx + 1], t);
-                    t = fmav(-tzm1, wt[slot(k - 1)][ty + 1][tx + 1], t);
+                    t = fmav(-X[eo], Wk[wo + 1], t);
+                    t = fmav(-X[eo - 1], Wk[wo - 1], t);
+                    t = fmav(-Y[eo], Wk[wo + kBX + 2], t);
+                    t = fmav(-Y[eo - kPX], Wk[wo - kBX - 2], t);
+                    t = fmav(-tzk, wpl(k + 1)[wo], t);
+                    t = fmav(-tzm1, wpl(k - 1)[wo], t);
                     out[c] = t;
-                    pnew[c] = v;
-                    xv[c] = fmav(alpha, cc.dg, cc.xo);
+                    pnew[c] = tile(k, 0)[eo];
+                    xv[c] = fmav(alpha, po, xo);
                     acc.add(v, t);
                 }
             }
-            tzm1 = cc.tzp;
-            cc = cn;
+            tzm1 = tzk;
+            xo = xn;
+            po = pn_;
         }
     }
     double tot;
     if (grid_reduce(acc.value(), partials, counter, sh, &tot)) sc->pq_raw = tot;
+}
+
+template <typename V>
+constexpr size_t cg_rb_smem() {
+    return sizeof(V) * (16 * kPN + 3 * (kBY + 2) * (kBX + 2)) + 4 * kPN;
 }
 
 // Set-up and reconstruction gathers on the scaled FP64 operator (not in the iteration loop):

@@ -19,9 +19,9 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_STAGNATED, \
-    ERR_INCOMPATIBLE_RHS, ERR_NOT_BUILT = range(9)
+    ERR_INCOMPATIBLE_RHS, ERR_NOT_BUILT, ERR_DEVICE_TIMEOUT = range(10)
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGED", 5: "BREAKDOWN",
-                6: "STAGNATED", 7: "INCOMPATIBLE_RHS", 8: "NOT_BUILT"}
+                6: "STAGNATED", 7: "INCOMPATIBLE_RHS", 8: "NOT_BUILT", 9: "DEVICE_TIMEOUT"}
 BC_NEUMANN, BC_DIRICHLET = 0, 1
 MODE_FP64, MODE_MIXED, MODE_FCG_NN = 0, 1, 2
 PRECOND_JACOBI, PRECOND_RBSGS = 0, 1
@@ -65,7 +65,8 @@ class _Info(ctypes.Structure):
 class _Stats(ctypes.Structure):
     _fields_ = [("cells", ctypes.c_longlong), ("unknowns", ctypes.c_longlong),
                 ("inactive", ctypes.c_longlong), ("merged_cells", ctypes.c_longlong),
-                ("groups", ctypes.c_longlong), ("device_bytes", ctypes.c_longlong)]
+                ("groups", ctypes.c_longlong), ("device_bytes", ctypes.c_longlong),
+                ("tma_stencil_fp32", ctypes.c_int), ("tma_stencil_fp64", ctypes.c_int)]
 
 
 _vp = ctypes.c_void_p

@@ -137,6 +137,47 @@ def test_red_black_elimination_cuts_iterations(vofp, mode):
     assert ih["iterations"] == ir["iterations"] and torch.equal(x, x2)
 
 
+@pytest.mark.parametrize("mode,cpt", [("fp64", "1"), ("mixed", "1"), ("mixed", "2")])
+def test_tma_stencil_matches_register_stencil(vofp, oracle, monkeypatch, mode, cpt):
+    """The TMA-fed CG stencil and the register-prefetch stencil are the same arithmetic (same
+    fused multiply-adds per cell); only the partial-sum order of p.q differs.  Ragged tiles in x
+    (36 = 32 + 4 with one cell per thread, 36 < 64 with two) and y (11 = 8 + 3), zero-filled boxes
+    on every face."""
+    monkeypatch.setenv("VOFP_TMA_FP32_CPT", cpt)
+    prob = ragged_sphere(shape=(36, 11, 45))
+    m = vofp.MODE_FP64 if mode == "fp64" else vofp.MODE_MIXED
+    rtol = 1e-10 if mode == "fp64" else 1e-8
+    res = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("VOFP_STENCIL_TMA", flag)
+        ctx, t = vofp.context_for(prob)
+        b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
+        x, info = ctx.vofp_solve(b, rtol=rtol, mode=m)
+        assert info["status"] == 0, info
+        res[flag] = (host(x, prob.shape), info, ctx.vofp_get_stats())
+        ctx.close()
+    assert res["1"][2]["tma_stencil_fp32"] == 1 and res["1"][2]["tma_stencil_fp64"] == 1
+    assert res["0"][2]["tma_stencil_fp32"] == 0 and res["0"][2]["tma_stencil_fp64"] == 0
+    it1, it0 = res["1"][1]["iterations"], res["0"][1]["iterations"]
+    assert abs(it1 - it0) <= max(2, 0.02 * it0), (it1, it0)
+    s = oracle.System(prob)
+    for flag in ("1", "0"):
+        assert s.residual(res[flag][0]) <= rtol * 1.01
+    x1, x0 = res["1"][0], res["0"][0]
+    assert np.linalg.norm(x1 - x0) / np.linalg.norm(x0) <= (1e-8 if mode == "fp64" else 1e-6)
+
+
+def test_unaligned_rows_use_register_stencil(vofp):
+    """Rows of 37 FP32 values are not a multiple of 16 bytes: no tensor map, register kernel."""
+    prob = ragged_sphere()
+    ctx, t = vofp.context_for(prob)
+    b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
+    _, info = ctx.vofp_solve(b, rtol=1e-8, mode=vofp.MODE_MIXED)
+    assert info["status"] == 0
+    st = ctx.vofp_get_stats()
+    assert st["tma_stencil_fp32"] == 0 and st["tma_stencil_fp64"] == 0
+
+
 def test_solve_is_bitwise_reproducible(vofp):
     prob = CASES["hull-small"]()
     ctx, t = vofp.context_for(prob)
