@@ -350,7 +350,8 @@ def main():
     ap.add_argument("--precond", default="jacobi", choices=["jacobi", "rbsgs"])
     ap.add_argument("--shape", type=int, nargs=3, default=list(SHAPE))
     ap.add_argument("--check-every", type=int, default=8)
-    ap.add_argument("--inner-rtol", type=float, default=1e-3)
+    ap.add_argument("--inner-rtol", type=float, default=0.0,
+                    help="mixed precision: residual reduction per refinement step (0: library default)")
     ap.add_argument("--kernel-reps", type=int, default=20)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--host-loop", action="store_true",

@@ -103,7 +103,11 @@ typedef struct {
  *               Gauss-Seidel; FP64 mode only).
  *   rtol        stop when ||b_hat - A_hat x|| <= rtol ||b_hat|| (2-norm over the unknowns).
  *   max_iter    cap on PCG iterations (inner iterations summed in mixed mode).
- *   inner_rtol  mixed mode: relative residual reduction of each inner solve (e.g. 1e-3).
+ *   inner_rtol  mixed mode: relative residual reduction of each inner solve; 0 selects the
+ *               default, 0.2 with inner_restart = 0 and 1e-3 with inner_restart = 1.
+ *   inner_restart  mixed mode: 0 (default) keeps the FP32 search direction across refinement
+ *               steps (the FP64 residual replaces the FP32 one, a "reliable update"); 1 restarts
+ *               the inner PCG from p = r at every refinement step.
  *   check_every convergence is tested every check_every iterations (even, >= 2; 0 = default 8).
  *   x0_zero     1: ignore the contents of x and start from 0.
  *   host_loop   0: the loop runs as a CUDA graph with a device-side WHILE condition (no host round
@@ -127,6 +131,7 @@ typedef struct {
     int host_loop;
     vofp_nn* nn;
     int stag_window;
+    int inner_restart;
 } vofp_solve_opts;
 
 typedef struct {

@@ -153,6 +153,7 @@ vofp_status vofp_solve(vofp_ctx* c, const double* b, double* x, const vofp_solve
         return invalid(c, "check_every must be 0 or an even number <= 64");
     if (o->mode == VOFP_MODE_MIXED && (o->inner_rtol < 0.0 || o->inner_rtol >= 1.0))
         return invalid(c, "inner_rtol must be in [0, 1)");
+    if (o->inner_restart != 0 && o->inner_restart != 1) return invalid(c, "inner_restart must be 0 or 1");
     if (info) std::memset(info, 0, sizeof(*info));
     return vofp::solve(c, b, x, o, info);
 }

@@ -49,6 +49,9 @@ struct CgScalars {
     int inner_done;     // 1 when the current inner loop has finished
     int outer;          // refinement steps
     int timing;         // 1 while the measurement hook runs: breakdowns are not recorded
+    double rr_prev;     // r.r of the residual the last alpha was computed from
+    int keep_dir;       // mixed precision: refinement keeps the inner search direction
+    int dir_valid;      // the inner direction buffer holds a direction of this solve
 };
 
 struct Dims {

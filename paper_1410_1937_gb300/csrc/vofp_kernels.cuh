@@ -615,6 +615,7 @@ k_cg_update(long long n, V* __restrict__ r, const V* __restrict__ q, const uint3
     double tot;
     if (grid_reduce(acc.value(), partials, counter, sh, &tot)) {
         const double rr = sc->rr;
+        sc->rr_prev = rr;
         sc->rr = tot;
         sc->beta = (rr > 0.0) ? tot / rr : 0.0;
         sc->alpha = alpha_d;

@@ -370,34 +370,47 @@ __global__ void k_outer_residual(long long n, const double* __restrict__ bt, con
     }
 }
 
-// inner start: rf = r / ||r||, x_f = 0, p_f(old) = 0, rr = rf.rf (Dot2-accumulated)
+// Inner start: rf = r / ||r||, x_f = 0, rr = rf.rf (Dot2-accumulated).  Restarted refinement:
+// p_f(old) = 0, so the inner CG starts from p = rf.  Refinement that keeps the direction (a
+// "reliable update" of the residual, Sleijpen and van der Vorst 1996): the FP64 residual replaces
+// the recursively updated FP32 one, and the next direction is p = r_new + beta p_old with
+// beta = ||r_new||^2 / r_k.r_k (r_k: the residual of the last step length), the old direction
+// being rescaled from the old to the new inner units (factor scale_old / scale_new) inside beta.
 __global__ void k_inner_prep(long long n, const double* __restrict__ r, const uint32_t* __restrict__ bits,
                              float* __restrict__ rf, float* __restrict__ xf, float* __restrict__ pf0,
                              CgScalars* sc, double* __restrict__ partials, unsigned int* __restrict__ counter) {
     __shared__ double sh[32];
     const double rr = sc->rr0;
     const double inv = (rr > 0.0 && !sc->done) ? 1.0 / sqrt(rr) : 0.0;
+    const bool keep = sc->keep_dir && sc->dir_valid;
     AccF2 acc;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const float v = (float)(r[c] * inv);
         rf[c] = v;
         xf[c] = 0.0f;
-        pf0[c] = 0.0f;
+        if (!keep) pf0[c] = 0.0f;
         if (!is_slave(bits, c)) acc.add(v, v);
     }
     double t;
     if (grid_reduce(acc.value(), partials, counter, sh, &t)) {
-        sc->scale = (rr > 0.0 && !sc->done) ? sqrt(rr) : 0.0;
+        const double scale_old = sc->scale;
+        const double scale_new = (rr > 0.0 && !sc->done) ? sqrt(rr) : 0.0;
+        sc->scale = scale_new;
         // the last refinement step only needs the reduction that reaches rtol (with margin)
         const double need = sc->rnorm2 > 0.0 ? 0.3 * sc->rtol * sqrt(sc->ref2 / sc->rnorm2) : 1.0;
         sc->inner_target = fmax(sc->inner_rtol, fmin(need, 0.5));
+        double beta = 0.0;
+        if (keep && scale_old > 0.0 && sc->rr_prev > 0.0) {
+            beta = scale_new / (scale_old * sc->rr_prev);
+            if (!isfinite(beta)) beta = 0.0;
+        }
         sc->rr = t;
         sc->alpha = 0.0;
-        sc->beta = 0.0;
+        sc->beta = beta;
         sc->iter = 0;
         sc->inner_done = 0;
-        const double rr0 = t;
-        sc->rr0 = rr0;
+        sc->rr0 = t;
+        sc->dir_valid = sc->keep_dir;
     }
 }
 
@@ -939,10 +952,14 @@ vofp_status solve(vofp_ctx* c, const double* b, double* x, const vofp_solve_opts
     CgScalars h{};
     h.status = VOFP_OK;
     h.rtol = o->rtol;
-    h.inner_rtol = o->inner_rtol > 0 ? o->inner_rtol : 1e-3;
+    // default reduction per refinement step: 0.2 when the direction is kept (a frequent FP64
+    // residual keeps the FP32 recurrence close to it), 1e-3 for restarted inner solves
+    h.inner_rtol = o->inner_rtol > 0 ? o->inner_rtol : (o->inner_restart ? 1e-3 : 0.2);
     h.max_iter = o->max_iter > 0 ? o->max_iter : 100000;
     h.bnorm2 = sums[2];
     h.ref2 = sums[2];
+    h.keep_dir = o->inner_restart ? 0 : 1;
+    h.dir_valid = 0;
     VOFP_CUDA_TRY(c, cudaMemcpyAsync(c->sc, &h, sizeof(h), cudaMemcpyHostToDevice, st));
     launch(c, k_init_residual, stream_grid(N), kNT, st, N, rhs_loop, (const double*)c->q, (const double*)c->sq,
            (const uint32_t*)((rb && !mixed) ? c->excl_bits : c->slave_bits), c->r, c->sc, c->partials, c->counters);

@@ -53,7 +53,7 @@ class _Opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("precond", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("inner_rtol", ctypes.c_double),
                 ("check_every", ctypes.c_int), ("x0_zero", ctypes.c_int), ("host_loop", ctypes.c_int),
-                ("nn", ctypes.c_void_p), ("stag_window", ctypes.c_int)]
+                ("nn", ctypes.c_void_p), ("stag_window", ctypes.c_int), ("inner_restart", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -232,15 +232,15 @@ class Context:
                                                   ctypes.byref(r)))
         return r.value
 
-    def vofp_solve(self, b, x=None, mode=MODE_FP64, rtol=1e-10, max_iter=100000, inner_rtol=1e-3,
+    def vofp_solve(self, b, x=None, mode=MODE_FP64, rtol=1e-10, max_iter=100000, inner_rtol=0.0,
                    check_every=8, precond=PRECOND_JACOBI, raise_on_error=True, x0_zero=0, host_loop=0,
-                   nn=None, stag_window=20):
+                   nn=None, stag_window=20, inner_restart=0):
         import torch
         if x is None:
             x = torch.zeros(self.n, dtype=torch.float64, device=b.device)
             x0_zero = 1
         o = _Opts(int(mode), int(precond), float(rtol), int(max_iter), float(inner_rtol), int(check_every), x0_zero,
-                  int(host_loop), nn.h if nn is not None else None, int(stag_window))
+                  int(host_loop), nn.h if nn is not None else None, int(stag_window), int(inner_restart))
         info = _Info()
         st = _lib.vofp_solve(self.h, _dev(b, self.n, "b"), _dev(x, self.n, "x"), ctypes.byref(o), ctypes.byref(info))
         out = {"iterations": info.iterations, "outer_iterations": info.outer_iterations,
@@ -253,8 +253,8 @@ class Context:
         return x, out
 
     def vofp_solve_host(self, F, ax, ay, az, vol_frac, u, v, w, bc, x_out, mode=MODE_FP64, rtol=1e-10,
-                        max_iter=100000, inner_rtol=1e-3, check_every=8, rho_liquid=1000.0, rho_gas=1.2,
-                        merge_threshold=0.1, density_smoothing=0, dt=1.0, precond=PRECOND_JACOBI):
+                        max_iter=100000, inner_rtol=0.0, check_every=8, rho_liquid=1000.0, rho_gas=1.2,
+                        merge_threshold=0.1, density_smoothing=0, dt=1.0, precond=PRECOND_JACOBI, inner_restart=0):
         """Host-buffer end-to-end call: numpy (or pinned torch CPU) float64 arrays in, x_out out."""
         def hp(a, n, name):
             if a is None:
@@ -270,7 +270,7 @@ class Context:
         b = self._bc(bc, None)
         ph = _Phys(rho_liquid, rho_gas, merge_threshold, int(density_smoothing), dt)
         o = _Opts(int(mode), int(precond), float(rtol), int(max_iter), float(inner_rtol), int(check_every), 1, 0,
-                  None, 20)
+                  None, 20, int(inner_restart))
         info = _Info()
         st = _lib.vofp_solve_host(self.h, hp(F, self.n, "F"), hp(ax, self.nfx, "ax"), hp(ay, self.nfy, "ay"),
                                   hp(az, self.nfz, "az"), hp(vol_frac, self.n, "vol_frac"), hp(u, self.nfx, "u"),

@@ -167,6 +167,25 @@ def test_tma_stencil_matches_register_stencil(vofp, oracle, monkeypatch, mode, c
     assert np.linalg.norm(x1 - x0) / np.linalg.norm(x0) <= (1e-8 if mode == "fp64" else 1e-6)
 
 
+@pytest.mark.parametrize("precond", ["jacobi", "rbsgs"])
+def test_reliable_update_refinement(vofp, oracle, precond):
+    """Mixed precision keeping the FP32 direction across refinement steps (the FP64 residual
+    replaces the FP32 one) against restarted inner solves: both reach rtol by the oracle's own
+    residual, with more refinement steps and fewer CG iterations when the direction is kept."""
+    prob = CASES["hull-small"]()
+    s = oracle.System(prob)
+    ctx, t = vofp.context_for(prob)
+    b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
+    pc = vofp.PRECOND_JACOBI if precond == "jacobi" else vofp.PRECOND_RBSGS
+    x0, i0 = ctx.vofp_solve(b, rtol=1e-8, mode=vofp.MODE_MIXED, precond=pc, inner_restart=1)
+    x1, i1 = ctx.vofp_solve(b, rtol=1e-8, mode=vofp.MODE_MIXED, precond=pc)
+    assert i0["status"] == 0 and i1["status"] == 0
+    for x in (x0, x1):
+        assert s.residual(host(x, prob.shape)) <= 1e-8 * 1.01
+    assert i1["outer_iterations"] > i0["outer_iterations"]
+    assert i1["iterations"] < i0["iterations"], (i0, i1)
+
+
 def test_unaligned_rows_use_register_stencil(vofp):
     """Rows of 37 FP32 values are not a multiple of 16 bytes: no tensor map, register kernel."""
     prob = ragged_sphere()
