@@ -45,15 +45,16 @@ UPDATE_ELEMS = 3.0
 
 def iter_elems(precond):
     return STENCIL_ELEMS[precond] + UPDATE_ELEMS
-# dram read+write bytes per cell of one stencil launch from the committed ncu capture, valid only
-# while the kernel sources hash to KERNEL_HASH (else reported as null)
-TRAFFIC_PER_CELL = {}
-KERNEL_HASH = None
+# dram read+write bytes per cell of one stencil launch from the committed ncu capture (FP32 TMA
+# stencil at 512x256x64: 317.4 MB over 8388608 cells), valid only while the sources of that kernel
+# and its launch hash to KERNEL_HASH (else reported as null)
+TRAFFIC_PER_CELL = {(32, "jacobi"): 37.84}
+KERNEL_HASH = "ac1fd2a33e0e3446"
 
 
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("vofp_kernels.cuh", "vofp_solve.cu"):
+    for f in ("vofp_kernels.cuh", "vofp_tma.cuh", "vofp_tma.cu"):
         with open(os.path.join(ROOT, "paper_1410_1937_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -236,7 +237,8 @@ def run_ours(args, rank, world, local_rank):
         hbm, hbm_kind = peaks()
         achieved = STENCIL_ELEMS[args.precond] * vb * n / (st_ms * 1e-3) / 1e9
         traffic = None
-        if KERNEL_HASH is not None and KERNEL_HASH == kernel_hash() and (prec, args.precond) in TRAFFIC_PER_CELL:
+        if (KERNEL_HASH is not None and KERNEL_HASH == kernel_hash() and (prec, args.precond) in TRAFFIC_PER_CELL
+                and kernel_name.startswith("k_cg_tma")):
             traffic = TRAFFIC_PER_CELL[(prec, args.precond)] * n
         iter_s = info["seconds"] / max(info["iterations"], 1)
         # every solver variant once on the same input (plain FP64 Jacobi-PCG is the reference)

@@ -148,6 +148,13 @@ struct vofp_ctx {
 namespace vofp {
 
 // ---- launches implemented in the .cu files -------------------------------------------------
+// TMA-fed CG stencil (vofp_tma.cu): per-context preparation, and one launch when the context's
+// tensor maps can be built (returns false otherwise; the caller then uses the register kernel)
+void prepare_tma(vofp_ctx* c);
+template <typename V>
+bool launch_cg_tma(vofp_ctx* c, cudaStream_t st, const V* Tx, const V* Ty, const V* Tz, const V* r, const V* po,
+                   V* pn, V* xv, V* q);
+
 vofp_status build_operator(vofp_ctx* c, const double* F, const double* ax, const double* ay,
                            const double* az, const double* vf, const vofp_bc* bc,
                            const vofp_phys* phys);

@@ -4,13 +4,8 @@
 #include <algorithm>
 #include <cmath>
 
-#include <cstdlib>
-#include <cstring>
-#include <cudaTypedefs.h>
-#include <mutex>
-
 #include "vofp_kernels.cuh"
-#include "vofp_tma.cuh"
+#include "vofp_rb.cuh"
 
 namespace vofp {
 namespace {
@@ -57,106 +52,16 @@ constexpr int stencil_pf() {
     return sizeof(V) == 8 ? 1 : 2;
 }
 
-// TMA stencil configurations: FP32 two cells per thread (64 x 8 tiles), FP64 one (32 x 8); both
-// four stages, three resident blocks per SM.  VOFP_TMA_FP32_CPT=1 selects the 32 x 8 FP32 kernel
-// with six stages (four blocks per SM).
-constexpr int kTmaStages64 = 4;
-
-// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q{};
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    });
-    return fn;
-}
-
-// Opt the shared-memory-heavy kernels into their dynamic shared memory and size their persistent
-// grids, on the context's device, before any graph capture.
+// Opt the red-black kernel into its dynamic shared memory and prepare the TMA-fed stencil, on the
+// context's device, before any graph capture.
 void prepare_kernels(vofp_ctx* c) {
     if (c->kernels_prepared) return;
     cudaFuncSetAttribute(k_cg_rb<float, stencil_pf<float>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)cg_rb_smem<float>());
     cudaFuncSetAttribute(k_cg_rb<double, stencil_pf<double>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)cg_rb_smem<double>());
-    const char* env = std::getenv("VOFP_STENCIL_TMA");
-    const bool tma_allowed = !(env && std::strcmp(env, "0") == 0) && tensor_map_encoder() != nullptr;
-    const char* cpt = std::getenv("VOFP_TMA_FP32_CPT");
-    c->tma_cpt32 = (cpt && std::strcmp(cpt, "1") == 0) ? 1 : 2;
-    constexpr size_t sa = cg_tma_smem<float, 4, 2>(), sb = cg_tma_smem<float, 6, 1>(),
-                     sd = cg_tma_smem<double, kTmaStages64, 1>();
-    cudaFuncSetAttribute(k_cg_tma<float, 4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa);
-    cudaFuncSetAttribute(k_cg_tma<float, 6, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
-    cudaFuncSetAttribute(k_cg_tma<double, kTmaStages64, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sd);
-    int b32 = 0, b64 = 0;
-    cudaError_t e32 = c->tma_cpt32 == 2
-                          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_cg_tma<float, 4, 2>, kBX * kBY, sa)
-                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_cg_tma<float, 6, 1>, kBX * kBY, sb);
-    if (e32 != cudaSuccess) b32 = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_cg_tma<double, kTmaStages64, 1>, kBX * kBY, sd) !=
-        cudaSuccess)
-        b64 = 0;
-    cudaGetLastError();
-    c->tma_blocks_per_sm[0] = b32;
-    c->tma_blocks_per_sm[1] = b64;
-    // the tensor maps need row and plane pitches that are multiples of 16 bytes
-    c->tma_ok[0] = tma_allowed && b32 > 0 && (c->d.nx * sizeof(float)) % 16 == 0;
-    c->tma_ok[1] = tma_allowed && b64 > 0 && (c->d.nx * sizeof(double)) % 16 == 0;
+    prepare_tma(c);
     c->kernels_prepared = true;
-}
-
-// 3-D tensor map of one nx x ny x nz array with a box of bw x bh cells of one plane (cached).
-// L2 promotion 64 B: the boxes' rows are 128-160 B, and wider promotion pulls neighbouring tiles'
-// bytes from DRAM that are evicted before those tiles run (measured: 256 B promotion read 1.9x
-// the algorithmic bytes and ran 25% slower on the FP32 stencil).
-template <typename V>
-const CUtensorMap* tensor_map(vofp_ctx* c, const V* ptr, int bw, int bh) {
-    const auto key = std::make_tuple((const void*)ptr, bw, bh);
-    auto it = c->tma_maps.find(key);
-    if (it != c->tma_maps.end()) return &it->second;
-    CUtensorMap m;
-    std::memset(&m, 0, sizeof(m));
-    const cuuint64_t dims[3] = {(cuuint64_t)c->d.nx, (cuuint64_t)c->d.ny, (cuuint64_t)c->d.nz};
-    const cuuint64_t strides[2] = {(cuuint64_t)c->d.nx * sizeof(V), (cuuint64_t)c->d.plane * sizeof(V)};
-    const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1u};
-    const cuuint32_t estr[3] = {1u, 1u, 1u};
-    const CUresult r = tensor_map_encoder()(
-        &m, sizeof(V) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
-        const_cast<V*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-        CU_TENSOR_MAP_L2_PROMOTION_L2_64B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return nullptr;
-    return &(c->tma_maps[key] = m);
-}
-
-template <typename V, int NS, int CPT>
-bool launch_cg_tma(vofp_ctx* c, cudaStream_t st, const V* Tx, const V* Ty, const V* Tz, const V* r, const V* po,
-                   V* pn, V* xv, V* q) {
-    using G = TmaGeom<V, CPT>;
-    const CUtensorMap *mr = tensor_map(c, r, G::kHW, kBY + 2), *mp = tensor_map(c, po, G::kHW, kBY + 2),
-                      *mx = tensor_map(c, Tx, G::kHW, kBY), *my = tensor_map(c, Ty, G::TW, kBY + 1),
-                      *mz = tensor_map(c, Tz, G::TW, kBY), *mv = tensor_map(c, (const V*)xv, G::TW, kBY);
-    if (!(mr && mp && mx && my && mz && mv)) return false;
-    CgMaps maps;
-    maps.r = *mr;
-    maps.p = *mp;
-    maps.tx = *mx;
-    maps.ty = *my;
-    maps.tz = *mz;
-    maps.x = *mv;
-    const long long tiles = (long long)ceil_div(c->d.nx, G::TW) * ceil_div(c->d.ny, kBY);
-    const long long total = tiles * c->d.nz;
-    const int f64 = sizeof(V) == 8 ? 1 : 0;
-    const int nb = (int)std::max(1LL, std::min((long long)num_sms() * c->tma_blocks_per_sm[f64], total));
-    const int per = (int)((total + nb - 1) / nb);
-    launch_smem(c, k_cg_tma<V, NS, CPT>, dim3(nb), dim3(kBX, kBY), cg_tma_smem<V, NS, CPT>(), st, maps, c->d, per,
-                pn, xv, q, c->sc, c->partials, c->counters);
-    return true;
 }
 
 // One fused CG stencil (p = r + beta p_old, x += alpha p_old, q = S A S p, p.q): the TMA-fed
@@ -164,15 +69,7 @@ bool launch_cg_tma(vofp_ctx* c, cudaStream_t st, const V* Tx, const V* Ty, const
 template <typename V>
 void launch_cg_stencil(vofp_ctx* c, cudaStream_t st, const V* Tx, const V* Ty, const V* Tz, const V* r,
                        const V* po, V* pn, V* xv, V* q) {
-    bool done = false;
-    if constexpr (sizeof(V) == 8) {
-        if (c->tma_ok[1]) done = launch_cg_tma<double, kTmaStages64, 1>(c, st, Tx, Ty, Tz, r, po, pn, xv, q);
-    } else {
-        if (c->tma_ok[0])
-            done = c->tma_cpt32 == 2 ? launch_cg_tma<float, 4, 2>(c, st, Tx, Ty, Tz, r, po, pn, xv, q)
-                                     : launch_cg_tma<float, 6, 1>(c, st, Tx, Ty, Tz, r, po, pn, xv, q);
-    }
-    if (done) return;
+    if (launch_cg_tma(c, st, Tx, Ty, Tz, r, po, pn, xv, q)) return;
     launch(c, k_stencil<V, ST_CG, stencil_pf<V>()>, stencil_grid(c), dim3(kBX, kBY), st, c->d, stencil_per_block(c),
            Tx, Ty, Tz, (const double*)nullptr, r, po, pn, xv, q, c->sc, c->partials, c->counters);
 }
