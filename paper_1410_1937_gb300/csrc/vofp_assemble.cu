@@ -331,6 +331,14 @@ __global__ void k_slave_bits(Dims d, const int32_t* __restrict__ root, uint32_t*
 
 // red cells: (i+j+k) even, own root, and not the master of a multi-cell group (a master always
 // touches one of its members, so a neighbour whose root is c marks c as a master)
+// Tzr = Tzf with the sign bit set on red cells (coefficients are >= 0, so the sign carries the red
+// flag through the same tensor copy as the coefficient; -0.0 marks a red cell with a closed face)
+__global__ void k_signed_tz(long long n, const float* __restrict__ tz, const uint32_t* __restrict__ red,
+                            float* __restrict__ tzr) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+        tzr[c] = ((red[c >> 5] >> (c & 31)) & 1u) ? -fabsf(tz[c]) : tz[c];
+}
+
 __global__ void k_red_bits(Dims d, const int32_t* __restrict__ root, const uint32_t* __restrict__ slave,
                            uint32_t* __restrict__ red, uint32_t* __restrict__ excl, unsigned int* count) {
     const long long nw = (d.n + 31) / 32;
@@ -509,6 +517,7 @@ vofp_status build_operator(vofp_ctx* c, const double* F, const double* ax, const
             (s = c->alloc(&c->aze, nfz)) || (s = c->alloc(&c->s, N)) || (s = c->alloc(&c->sq, N)) ||
             (s = c->alloc(&c->Txs, N)) || (s = c->alloc(&c->Tys, N)) || (s = c->alloc(&c->Tzs, N)) ||
             (s = c->alloc(&c->Txf, N)) || (s = c->alloc(&c->Tyf, N)) || (s = c->alloc(&c->Tzf, N)) ||
+            (s = c->alloc(&c->Tzr, N)) ||
             (s = c->alloc(&c->slave_bits, (N + 31) / 32)) || (s = c->alloc(&c->root, N)) ||
             (s = c->alloc(&c->red_bits, (N + 31) / 32)) || (s = c->alloc(&c->excl_bits, (N + 31) / 32)) ||
             (s = c->alloc(&c->inactive, N)) || (s = c->alloc(&c->work, N)) ||
@@ -680,6 +689,7 @@ vofp_status build_operator(vofp_ctx* c, const double* F, const double* ax, const
         VOFP_CUDA_TRY(c, cudaMemsetAsync(nred, 0, sizeof(unsigned int), st));
         launch(c, k_red_bits, grid_for((N + 31) / 32), kNT, st, d, (const int32_t*)c->root,
                (const uint32_t*)c->slave_bits, c->red_bits, c->excl_bits, nred);
+        launch(c, k_signed_tz, gN, kNT, st, d.n, (const float*)c->Tzf, (const uint32_t*)c->red_bits, c->Tzr);
         unsigned int h = 0;
         VOFP_CUDA_TRY(c, cudaMemcpyAsync(&h, nred, sizeof(h), cudaMemcpyDeviceToHost, st));
         VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));

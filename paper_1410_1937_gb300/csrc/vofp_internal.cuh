@@ -89,6 +89,7 @@ struct vofp_ctx {
     // is set for "red" cells -- (i+j+k) even, with an unknown, in no merge group -- whose unknowns
     // are eliminated; excl_bits = slave_bits | red_bits marks cells left out of the reduced dots
     uint32_t* red_bits = nullptr;
+    float* Tzr = nullptr;             // Tzf with the sign bit set on red cells (red flag)
     uint32_t* excl_bits = nullptr;
     long long n_red = 0;
     int32_t* root = nullptr;          // group root per cell, -1 without unknown
@@ -127,6 +128,8 @@ struct vofp_ctx {
     bool tma_ok[2] = {false, false};  // FP32, FP64
     int tma_blocks_per_sm[2] = {0, 0};
     int tma_cpt32 = 2;                // FP32 TMA stencil: cells per thread along x
+    bool rb_tma_ok = false;           // FP32 red-black iteration fed by bulk tensor copies
+    int rb_tma_blocks_per_sm = 0;
     std::map<std::tuple<const void*, int, int>, CUtensorMap> tma_maps;
 
     void set_error(const std::string& m) { err = m; }
@@ -151,6 +154,12 @@ namespace vofp {
 // TMA-fed CG stencil (vofp_tma.cu): per-context preparation, and one launch when the context's
 // tensor maps can be built (returns false otherwise; the caller then uses the register kernel)
 void prepare_tma(vofp_ctx* c);
+// cached 3-D tensor map of an FP32 nx x ny x nz array with a bw x bh x 1 box (null if it cannot be built)
+const CUtensorMap* tensor_map_f32(vofp_ctx* c, const float* ptr, int bw, int bh);
+// TMA-fed fused red-black iteration, FP32 (vofp_rb_tma.cu): preparation and one launch (false
+// when it cannot run on this context; the caller then uses the register-prefetch kernel)
+void prepare_rb_tma(vofp_ctx* c);
+bool launch_cg_rb_tma(vofp_ctx* c, cudaStream_t st, const float* r, const float* po, float* pn, float* xv, float* q);
 template <typename V>
 bool launch_cg_tma(vofp_ctx* c, cudaStream_t st, const V* Tx, const V* Ty, const V* Tz, const V* r, const V* po,
                    V* pn, V* xv, V* q);

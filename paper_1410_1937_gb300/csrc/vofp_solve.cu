@@ -61,6 +61,7 @@ void prepare_kernels(vofp_ctx* c) {
     cudaFuncSetAttribute(k_cg_rb<double, stencil_pf<double>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)cg_rb_smem<double>());
     prepare_tma(c);
+    prepare_rb_tma(c);
     c->kernels_prepared = true;
 }
 
@@ -78,6 +79,9 @@ void launch_cg_stencil(vofp_ctx* c, cudaStream_t st, const V* Tx, const V* Ty, c
 template <typename V>
 void launch_cg_rb(vofp_ctx* c, cudaStream_t st, const V* Tx, const V* Ty, const V* Tz, const V* r,
                   const V* po, V* pn, V* xv, V* q) {
+    if constexpr (sizeof(V) == 4) {
+        if (launch_cg_rb_tma(c, st, r, po, pn, xv, q)) return;
+    }
     constexpr size_t smem = cg_rb_smem<V>();
     launch_smem(c, k_cg_rb<V, stencil_pf<V>()>, dim3(rb_blocks(c)), dim3(kBX, kBY), smem, st, c->d,
                 rb_per_block(c), Tx, Ty, Tz, (const uint32_t*)c->red_bits, r, po, pn, xv, q, c->sc, c->partials,

@@ -81,6 +81,10 @@ bool launch_tma(vofp_ctx* c, cudaStream_t st, const V* Tx, const V* Ty, const V*
 
 }  // namespace
 
+const CUtensorMap* tensor_map_f32(vofp_ctx* c, const float* ptr, int bw, int bh) {
+    return tensor_map_encoder() ? tensor_map(c, ptr, bw, bh) : nullptr;
+}
+
 template <typename V>
 bool launch_cg_tma(vofp_ctx* c, cudaStream_t st, const V* Tx, const V* Ty, const V* Tz, const V* r, const V* po,
                    V* pn, V* xv, V* q) {

@@ -186,6 +186,31 @@ def test_reliable_update_refinement(vofp, oracle, precond):
     assert i1["iterations"] < i0["iterations"], (i0, i1)
 
 
+@pytest.mark.parametrize("shape", [(36, 11, 45), (128, 24, 20)])
+def test_tma_red_black_matches_register_red_black(vofp, oracle, monkeypatch, shape):
+    """The TMA-fed FP32 red-black iteration (64 x 8 tiles, red flags in the sign of Tz) against
+    the register-prefetch red-black kernel: same Schur-complement CG, mixed precision.  (36, 11, 45)
+    is one ragged tile in x and y; (128, 24, 20) two full tiles in x, three in y."""
+    prob = ragged_sphere(shape=shape)
+    res = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("VOFP_STENCIL_TMA", flag)
+        ctx, t = vofp.context_for(prob)
+        b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
+        x, info = ctx.vofp_solve(b, rtol=1e-8, mode=vofp.MODE_MIXED, precond=vofp.PRECOND_RBSGS)
+        assert info["status"] == 0, info
+        res[flag] = (host(x, prob.shape), info, ctx.vofp_get_stats())
+        ctx.close()
+    assert res["1"][2]["tma_stencil_fp32"] == 1 and res["0"][2]["tma_stencil_fp32"] == 0
+    it1, it0 = res["1"][1]["iterations"], res["0"][1]["iterations"]
+    assert abs(it1 - it0) <= max(4, 0.03 * it0), (it1, it0)
+    s = oracle.System(prob)
+    for flag in ("1", "0"):
+        assert s.residual(res[flag][0]) <= 1e-8 * 1.01
+    x1, x0 = res["1"][0], res["0"][0]
+    assert np.linalg.norm(x1 - x0) / np.linalg.norm(x0) <= 1e-6
+
+
 def test_unaligned_rows_use_register_stencil(vofp):
     """Rows of 37 FP32 values are not a multiple of 16 bytes: no tensor map, register kernel."""
     prob = ragged_sphere()
