@@ -33,28 +33,33 @@ METRIC = "Poisson time-to-1e-8 residual & solves/s at 512×256×128; HBM GB/s pe
 SHAPE = (512, 256, 128)
 RTOL = 1e-8
 FALLBACK_HBM_GBS = 6800.0
-# algorithmic bytes per cell of one launch / one iteration ("Roofline"), in units of
-# one vector element (8 B for FP64, 4 B for FP32)
-#   stencil, Jacobi: reads r, p_old, x, Tx, Ty, Tz; writes p, x, q
-#   stencil, red-black (fused red elimination): reads r, p_old, Tx, Ty, Tz everywhere and x on the
-#            black half; writes p, x, q on the black half
+# algorithmic bytes per cell of one launch / one iteration, in units of one vector element (8 B for
+# FP64, 4 B for FP32); every array interleaves the two colours, so a red-black iteration streams
+# the same nine arrays as a Jacobi one
+#   stencil (Jacobi, or red-black with the red unknowns eliminated in the same pass): reads r,
+#            p_old, x, Tx, Ty, Tz; writes p, x, q
 #   update:  reads r, q; writes r
-STENCIL_ELEMS = {"jacobi": 9.0, "rbsgs": 7.0}
+STENCIL_ELEMS = {"jacobi": 9.0, "rbsgs": 9.0}
 UPDATE_ELEMS = 3.0
 
 
 def iter_elems(precond):
     return STENCIL_ELEMS[precond] + UPDATE_ELEMS
-# dram read+write bytes per cell of one stencil launch from the committed ncu capture (FP32 TMA
-# stencil at 512x256x64: 317.4 MB over 8388608 cells), valid only while the sources of that kernel
-# and its launch hash to KERNEL_HASH (else reported as null)
-TRAFFIC_PER_CELL = {(32, "jacobi"): 37.84}
-KERNEL_HASH = "ac1fd2a33e0e3446"
 
 
-def kernel_hash():
+# DRAM read+write bytes per cell of one launch of the dominant kernel, from committed ncu captures
+# of the 512x256x128 workload (dram__bytes_read.sum + dram__bytes_write.sum, one pass), each valid
+# only while the sources of that kernel and its launch hash to the value stored with it (else null):
+#   (32, "jacobi"): k_cg_tma<float, 6, 2> (column split), 561.8 MB over 16777216 cells
+#   (32, "rbsgs"):  k_cg_rb_tma<3>, 885.4 MB over 16777216 cells
+TRAFFIC_PER_CELL = {(32, "jacobi"): (33.49, "1c61b294ac00d54c"), (32, "rbsgs"): (52.77, "13e88b4a727581d4")}
+KERNEL_FILES = {(32, "jacobi"): ('vofp_internal.cuh', 'vofp_kernels.cuh', 'vofp_tma.cuh', 'vofp_tma.cu'),
+                (32, "rbsgs"): ('vofp_internal.cuh', 'vofp_kernels.cuh', 'vofp_tma.cuh', 'vofp_rb_tma.cuh', 'vofp_rb_tma.cu')}
+
+
+def kernel_hash(key):
     h = hashlib.sha256()
-    for f in ("vofp_kernels.cuh", "vofp_tma.cuh", "vofp_tma.cu"):
+    for f in KERNEL_FILES[key]:
         with open(os.path.join(ROOT, "paper_1410_1937_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -228,7 +233,9 @@ def run_ours(args, rank, world, local_rank):
         stats = ctx.vofp_get_stats()
         vname = "float" if prec == 32 else "double"
         if args.precond == "rbsgs":
-            kernel_name = f"k_cg_rb<{vname}> (fused red-black iteration)"
+            kernel_name = (f"k_cg_rb_tma<3> (TMA-fed fused red-black iteration)"
+                           if prec == 32 and stats["tma_stencil_fp32"] else
+                           f"k_cg_rb<{vname}> (register-prefetch fused red-black iteration)")
         elif stats["tma_stencil_fp32" if prec == 32 else "tma_stencil_fp64"]:
             kernel_name = f"k_cg_tma<{vname}> (TMA-fed CG stencil)"
         else:
@@ -237,9 +244,9 @@ def run_ours(args, rank, world, local_rank):
         hbm, hbm_kind = peaks()
         achieved = STENCIL_ELEMS[args.precond] * vb * n / (st_ms * 1e-3) / 1e9
         traffic = None
-        if (KERNEL_HASH is not None and KERNEL_HASH == kernel_hash() and (prec, args.precond) in TRAFFIC_PER_CELL
-                and kernel_name.startswith("k_cg_tma")):
-            traffic = TRAFFIC_PER_CELL[(prec, args.precond)] * n
+        key = (prec, args.precond)
+        if key in TRAFFIC_PER_CELL and TRAFFIC_PER_CELL[key][1] == kernel_hash(key) and "TMA" in kernel_name:
+            traffic = TRAFFIC_PER_CELL[key][0] * n
         iter_s = info["seconds"] / max(info["iterations"], 1)
         # every solver variant once on the same input (plain FP64 Jacobi-PCG is the reference)
         variants = {}

@@ -58,7 +58,7 @@ struct RbCo {
 };
 
 template <int NS>
-__global__ void __launch_bounds__(kBX* kBY, 3)
+__global__ void __launch_bounds__(kBX* kBY, NS <= 2 ? 4 : 3)
 k_cg_rb_tma(const __grid_constant__ RbMaps maps, const Dims d, const int per_block, const float* __restrict__ pold,
             float* __restrict__ pnew, float* __restrict__ xv, float* __restrict__ out, CgScalars* __restrict__ sc,
             double* __restrict__ partials, unsigned int* __restrict__ counter) {
