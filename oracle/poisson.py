@@ -431,6 +431,78 @@ class System:
         return self.expand(x), info
 
 
+# ----------------------------------------------------------------------------------------------
+# Projection (Sec. 2.1, Eq. runge1: u = u* - dt (1/rho) grad p) and its divergence check
+# ----------------------------------------------------------------------------------------------
+
+def project(prob, s, p_full, neumann_flux=None):
+    """Face velocities after the projection u = u* - dt (1/rho) dp/dn on every face, with the
+    face's 1/rho and distance those of the operator (half-cell harmonic average, Sec. 2.3):
+
+    * interior face with an open effective aperture: u - dt (p_R - p_L) / ((d_L rho_L + d_R rho_R)/2);
+    * p = 0 domain face (open): the outside value is 0 at half a cell, u - dt (p_out - p_in) with
+      the distance d_c rho_c / 2, signs following the axis;
+    * free-slip domain face: the wall velocity is not used by the right-hand side (it is taken as
+      0); with a prescribed outward flux g = (1/rho) dp/dn the projected velocity is -dt g on a +
+      face and +dt g on a - face, else 0;
+    * a face whose effective aperture is 0 keeps u (no flux passes it).
+
+    ``p_full`` is the full-grid pressure (every cell of a merge group holds the group's value,
+    0 where there is no unknown).  Returns (u, v, w) with the shapes of prob.u, prob.v, prob.w.
+    """
+    ex, ey, ez = s.apertures
+    rho = density(prob.F, prob.rho_liquid, prob.rho_gas, bool(prob.density_smoothing))
+    dx, dy, dz = prob.dx, prob.dy, prob.dz
+    dt = prob.dt
+    p = np.asarray(p_full, dtype=np.float64).reshape(prob.shape)
+    bc = prob.bc
+    g = neumann_flux if neumann_flux is not None else [None] * 6
+    u = np.array(prob.u, dtype=np.float64)
+    v = np.array(prob.v, dtype=np.float64)
+    w = np.array(prob.w, dtype=np.float64)
+    # interior faces
+    gx = (p[:, :, 1:] - p[:, :, :-1]) / (0.5 * (dx[:-1] * rho[:, :, :-1] + dx[1:] * rho[:, :, 1:]))
+    u[:, :, 1:-1] = np.where(ex[:, :, 1:-1] > 0, u[:, :, 1:-1] - dt * gx, u[:, :, 1:-1])
+    gy = (p[:, 1:, :] - p[:, :-1, :]) / (0.5 * (dy[:-1, None] * rho[:, :-1, :] + dy[1:, None] * rho[:, 1:, :]))
+    v[:, 1:-1, :] = np.where(ey[:, 1:-1, :] > 0, v[:, 1:-1, :] - dt * gy, v[:, 1:-1, :])
+    gz = (p[1:] - p[:-1]) / (0.5 * (dz[:-1, None, None] * rho[:-1] + dz[1:, None, None] * rho[1:]))
+    w[1:-1] = np.where(ez[1:-1] > 0, w[1:-1] - dt * gz, w[1:-1])
+
+    # domain faces: (array, aperture, face slice, adjacent cell slice, cell width, sign of outward normal)
+    def wall(arr, ap, fsl, csl, width, sign, kind, flux):
+        if kind == DIRICHLET:
+            pin = p[csl]
+            grad = sign * (0.0 - pin) / (0.5 * width * rho[csl])   # (p_out - p_in) along +axis
+            arr[fsl] = np.where(ap[fsl] > 0, arr[fsl] - dt * grad, arr[fsl])
+        else:
+            arr[fsl] = 0.0 if flux is None else -sign * dt * flux
+
+    wall(u, ex, np.s_[:, :, 0], np.s_[:, :, 0], dx[0], -1, bc[0], g[0])
+    wall(u, ex, np.s_[:, :, -1], np.s_[:, :, -1], dx[-1], +1, bc[1], g[1])
+    wall(v, ey, np.s_[:, 0, :], np.s_[:, 0, :], dy[0], -1, bc[2], g[2])
+    wall(v, ey, np.s_[:, -1, :], np.s_[:, -1, :], dy[-1], +1, bc[3], g[3])
+    wall(w, ez, np.s_[0], np.s_[0], dz[0], -1, bc[4], g[4])
+    wall(w, ez, np.s_[-1], np.s_[-1], dz[-1], +1, bc[5], g[5])
+    return u, v, w
+
+
+def divergence(prob, s, u, v, w, body_flux=None):
+    """Net outward flux of the face velocities through each cell's open faces, sum_f sigma_f A_f
+    S_f u_f (+ the body-surface flux), folded over merge groups: the group's total at its master,
+    0 at its other cells and where there is no unknown (full-grid shape)."""
+    ex, ey, ez = s.apertures
+    dx, dy, dz = prob.dx, prob.dy, prob.dz
+    fx = ex * (dz[:, None] * dy[None, :])[:, :, None] * u
+    fy = ey * (dz[:, None] * dx[None, :])[:, None, :] * v
+    fz = ez * (dy[:, None] * dx[None, :])[None, :, :] * w
+    div = (fx[:, :, 1:] - fx[:, :, :-1]) + (fy[:, 1:, :] - fy[:, :-1, :]) + (fz[1:] - fz[:-1])
+    if body_flux is not None:
+        div = div + np.asarray(body_flux).reshape(prob.shape)
+    out = np.zeros(prob.n)
+    out[s.masters] = s.fold(div)
+    return out.reshape(prob.shape)
+
+
 def lanczos_extremes(alpha, beta):
     """Extreme eigenvalues of the Jacobi-preconditioned operator estimated from the CG
     coefficients (the Lanczos tridiagonal matrix that CG builds implicitly)."""

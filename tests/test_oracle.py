@@ -233,6 +233,66 @@ def test_projection_makes_velocity_divergence_free(oracle):
     assert np.abs(div_groups).max() <= 1e-12 * scale
 
 
+def test_projection_functions_give_divergence_free_groups(oracle):
+    # oracle.project / oracle.divergence (Sec. 2.1 Eq. runge1) with the dense solution: every
+    # merge group's net outward flux vanishes (Dirichlet exit, free-slip walls)
+    p = I.tiny_sphere(n=8)
+    p.dt = 0.3
+    s = oracle.System(p)
+    ph = s.solve_dense()
+    u, v, w = oracle.project(p, s, ph)
+    div = oracle.divergence(p, s, u, v, w)
+    ex = s.apertures[0]
+    scale = np.abs(s.fold((ex * np.abs(p.u))[:, :, 1:])).max() * p.dx.max() ** 2
+    assert np.abs(div).max() <= 1e-12 * scale
+    # the unprojected field is far from divergence-free (the check has teeth)
+    assert np.abs(oracle.divergence(p, s, p.u, p.v, p.w)).max() > 1e-3 * scale
+
+
+def test_projection_all_neumann_with_prescribed_wall_flux(oracle):
+    # free-slip everywhere, outward (1/rho) dp/dn = g0 on the -x wall and -g0 on the +x wall
+    # (compatible: the prescribed fluxes sum to zero); the projected wall velocities are +dt g0
+    # and +dt g0 (sign of the outward normal) and every group is divergence-free
+    p = I.tiny_sphere(n=8)
+    p.dt = 0.7
+    p.bc = (0, 0, 0, 0, 0, 0)
+    nz, ny, nx = p.shape
+    g0 = np.random.default_rng(11).uniform(-1, 1, (nz, ny))
+    flux = [g0, -g0, None, None, None, None]
+    s = oracle.System(p, neumann_flux=flux)
+    assert abs(s.bhat.sum()) <= 1e-12 * np.abs(s.bhat).sum()
+    ph = s.solve_dense()
+    u, v, w = oracle.project(p, s, ph, neumann_flux=flux)
+    np.testing.assert_allclose(u[:, :, 0], p.dt * g0, rtol=1e-15)
+    np.testing.assert_allclose(u[:, :, -1], p.dt * g0, rtol=1e-15)
+    assert np.all(v[:, 0, :] == 0) and np.all(w[-1] == 0)
+    div = oracle.divergence(p, s, u, v, w)
+    scale = np.abs(s.fold((s.apertures[0] * np.abs(p.u))[:, :, 1:])).max() * p.dx.max() ** 2
+    # the singular all-Neumann system is solved by least squares: about 1e-12 relative accuracy
+    assert np.abs(div).max() <= 1e-11 * scale
+    assert np.abs(oracle.divergence(p, s, p.u, p.v, p.w)).max() > 1e-3 * scale
+
+
+def test_projection_of_a_linear_pressure_closed_form(oracle):
+    # uniform grid, rho = 1, p = a x at the cell centres: every open interior x face loses dt*a,
+    # y and z faces keep their velocity, and the p = 0 face at x = 1 (half a cell from the last
+    # centre) loses dt * (0 - a x_last) / (dx/2)
+    n, a, dt = 5, 0.37, 0.6
+    p = I.manufactured(n)
+    p.dt = dt
+    rng = np.random.default_rng(5)
+    p.u, p.v, p.w = rng.uniform(-1, 1, p.u.shape), rng.uniform(-1, 1, p.v.shape), rng.uniform(-1, 1, p.w.shape)
+    s = oracle.System(p)
+    xc = 0.5 * (p.meta["nodes"][0][:-1] + p.meta["nodes"][0][1:])
+    pres = np.broadcast_to(a * xc, p.shape)
+    u, v, w = oracle.project(p, s, pres)
+    np.testing.assert_allclose(u[:, :, 1:-1], p.u[:, :, 1:-1] - dt * a, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(u[:, :, -1], p.u[:, :, -1] + dt * a * xc[-1] / (0.5 * p.dx[-1]), rtol=1e-14)
+    assert np.all(u[:, :, 0] == 0)                           # free-slip wall, no prescribed flux
+    np.testing.assert_array_equal(v[:, 1:-1, :], p.v[:, 1:-1, :])
+    np.testing.assert_array_equal(w[1:-1], p.w[1:-1])
+
+
 def test_lanczos_estimates_inside_spectrum(oracle):
     p = I.tiny_sphere()
     s = oracle.System(p)
