@@ -186,6 +186,28 @@ vofp_status vofp_build_operator(vofp_ctx* ctx, const double* F, const double* ax
 vofp_status vofp_rhs_from_face_velocity(vofp_ctx* ctx, const double* u, const double* v,
                                         const double* w, const double* body_flux, double* b);
 
+/* Projection of the face velocities (Sec. 2.1, Eq. runge1: u = u* - dt (1/rho) grad p) with the
+ * operator's face reading (Sec. 2.3): on an interior face whose effective aperture is open,
+ * u_out = u - dt (p_R - p_L) / ((d_L rho_L + d_R rho_R) / 2); on an open p = 0 domain face the
+ * outside pressure 0 sits half a cell from the centre; on a free-slip domain face u_out = 0, or
+ * -dt g on a + face and +dt g on a - face where an outward flux g = (1/rho) dp/dn was prescribed;
+ * a closed face keeps u.  dt and rho are those of vofp_build_operator.
+ *   p             device, cells: the pressure as vofp_solve returns it (every cell of a merge
+ *                 group holds the group's value, 0 where there is no unknown).
+ *   u, v, w       device, the x-, y- and z-face velocities u* (same layout as for the rhs).
+ *   body_flux     device, cells, or NULL: as for vofp_rhs_from_face_velocity; enters div only.
+ *   u_out, v_out, w_out  device, face arrays; may be u, v, w themselves (each face is read and
+ *                 written by one thread).
+ *   div           device, cells, or NULL: net outward flux of the projected field through each
+ *                 cell's open faces plus body_flux, summed over each merge group at its master
+ *                 (0 at the group's other cells and where there is no unknown).  With the exact
+ *                 solution this vanishes: it is the residual of the pressure equation times -dt.
+ *   max_div       host, or NULL: max |div| over cells (synchronises the stream).
+ * Errors: NOT_BUILT before vofp_build_operator, INVALID_ARG for a null required pointer. */
+vofp_status vofp_project(vofp_ctx* ctx, const double* p, const double* u, const double* v, const double* w,
+                         const double* body_flux, double* u_out, double* v_out, double* w_out, double* div,
+                         double* max_div);
+
 /* y = A_hat x: x is read at each group's master cell; y receives the group's value at the master
  * and 0 at every other cell and at cells without an unknown. */
 vofp_status vofp_apply(vofp_ctx* ctx, const double* x, double* y);

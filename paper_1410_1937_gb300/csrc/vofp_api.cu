@@ -125,6 +125,15 @@ vofp_status vofp_rhs_from_face_velocity(vofp_ctx* c, const double* u, const doub
     return fail_cuda(c);
 }
 
+vofp_status vofp_project(vofp_ctx* c, const double* p, const double* u, const double* v, const double* w,
+                         const double* body, double* uo, double* vo, double* wo, double* div, double* max_div) {
+    vofp_status s = check_ctx(c, true);
+    if (s) return s;
+    if (!p || !u || !v || !w || !uo || !vo || !wo) return invalid(c, "null input");
+    if ((s = vofp::project(c, p, u, v, w, body, uo, vo, wo, div, max_div))) return s;
+    return fail_cuda(c);
+}
+
 vofp_status vofp_apply(vofp_ctx* c, const double* x, double* y) {
     vofp_status s = check_ctx(c, true);
     if (s) return s;

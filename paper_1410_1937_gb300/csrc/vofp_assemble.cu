@@ -15,24 +15,6 @@ namespace {
 
 constexpr int kNT = 256;
 
-__device__ __forceinline__ long long fx_idx(const Dims& d, int i, int j, int k) {
-    return i + (long long)(d.nx + 1) * (j + (long long)d.ny * k);
-}
-__device__ __forceinline__ long long fy_idx(const Dims& d, int i, int j, int k) {
-    return i + (long long)d.nx * (j + (long long)(d.ny + 1) * k);
-}
-__device__ __forceinline__ long long fz_idx(const Dims& d, int i, int j, int k) {
-    return i + (long long)d.nx * (j + (long long)d.ny * k);
-}
-// cell counts stay below 2^31 (checked by vofp_create): 32-bit division is enough
-__device__ __forceinline__ void cell_ijk(const Dims& d, long long c, int& i, int& j, int& k) {
-    const unsigned int uc = (unsigned int)c, nx = (unsigned int)d.nx, ny = (unsigned int)d.ny;
-    const unsigned int t = uc / nx;
-    i = int(uc - t * nx);
-    const unsigned int kk = t / ny;
-    j = int(t - kk * ny);
-    k = int(kk);
-}
 
 // rho = rho_g + (rho_l - rho_g) F   (Eq. density with H(phi) = phi)
 __global__ void k_density(Dims d, const double* __restrict__ F, double rl, double rg,
@@ -517,7 +499,7 @@ vofp_status build_operator(vofp_ctx* c, const double* F, const double* ax, const
             (s = c->alloc(&c->aze, nfz)) || (s = c->alloc(&c->s, N)) || (s = c->alloc(&c->sq, N)) ||
             (s = c->alloc(&c->Txs, N)) || (s = c->alloc(&c->Tys, N)) || (s = c->alloc(&c->Tzs, N)) ||
             (s = c->alloc(&c->Txf, N)) || (s = c->alloc(&c->Tyf, N)) || (s = c->alloc(&c->Tzf, N)) ||
-            (s = c->alloc(&c->Tzr, N)) ||
+            (s = c->alloc(&c->Tzr, N)) || (s = c->alloc(&c->rho, N)) ||
             (s = c->alloc(&c->slave_bits, (N + 31) / 32)) || (s = c->alloc(&c->root, N)) ||
             (s = c->alloc(&c->red_bits, (N + 31) / 32)) || (s = c->alloc(&c->excl_bits, (N + 31) / 32)) ||
             (s = c->alloc(&c->inactive, N)) || (s = c->alloc(&c->work, N)) ||
@@ -547,6 +529,7 @@ vofp_status build_operator(vofp_ctx* c, const double* F, const double* ax, const
             std::swap(rho, tmp);
         }
     }
+    VOFP_CUDA_TRY(c, cudaMemcpyAsync(c->rho, rho, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
     // activity, iterated to a fixed point
     uint8_t* ina_a = c->inactive;
     uint8_t* ina_b = reinterpret_cast<uint8_t*>(c->work);

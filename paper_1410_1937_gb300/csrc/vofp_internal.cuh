@@ -88,6 +88,7 @@ struct vofp_ctx {
     // red-black elimination (Eisenstat form of red-black symmetric Gauss-Seidel): bit c of red_bits
     // is set for "red" cells -- (i+j+k) even, with an unknown, in no merge group -- whose unknowns
     // are eliminated; excl_bits = slave_bits | red_bits marks cells left out of the reduced dots
+    double* rho = nullptr;            // cell density (after the optional smoothing)
     uint32_t* red_bits = nullptr;
     float* Tzr = nullptr;             // Tzf with the sign bit set on red cells (red flag)
     uint32_t* excl_bits = nullptr;
@@ -180,6 +181,30 @@ vofp_status time_iteration_kernels(vofp_ctx* c, int precision, bool rb, int reps
                                    float* red);
 
 // group helpers (vofp_assemble.cu)
+// face and cell indexing: x faces (nx+1) x ny x nz, y faces nx x (ny+1) x nz, z faces nx x ny x (nz+1)
+__device__ __forceinline__ long long fx_idx(const Dims& d, int i, int j, int k) {
+    return i + (long long)(d.nx + 1) * (j + (long long)d.ny * k);
+}
+__device__ __forceinline__ long long fy_idx(const Dims& d, int i, int j, int k) {
+    return i + (long long)d.nx * (j + (long long)(d.ny + 1) * k);
+}
+__device__ __forceinline__ long long fz_idx(const Dims& d, int i, int j, int k) {
+    return i + (long long)d.nx * (j + (long long)d.ny * k);
+}
+// cell counts stay below 2^31 (checked by vofp_create): 32-bit division is enough
+__device__ __forceinline__ void cell_ijk(const Dims& d, long long c, int& i, int& j, int& k) {
+    const unsigned int uc = (unsigned int)c, nx = (unsigned int)d.nx, ny = (unsigned int)d.ny;
+    const unsigned int t = uc / nx;
+    i = int(uc - t * nx);
+    const unsigned int kk = t / ny;
+    j = int(t - kk * ny);
+    k = int(kk);
+}
+
+// projection of the face velocities and its divergence check (vofp_project.cu)
+vofp_status project(vofp_ctx* c, const double* p, const double* u, const double* v, const double* w,
+                    const double* body, double* uo, double* vo, double* wo, double* div, double* max_div);
+
 void launch_group_expand(vofp_ctx* c, double* v);
 void launch_group_fold(vofp_ctx* c, double* v, bool zero_slaves);
 

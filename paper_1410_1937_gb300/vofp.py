@@ -78,6 +78,7 @@ _sig = {
     "vofp_last_error": (ctypes.c_char_p, [_vp]),
     "vofp_build_operator": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _P(_Bc), _P(_Phys)]),
     "vofp_rhs_from_face_velocity": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "vofp_project": (ctypes.c_int, [_vp] * 10 + [_P(ctypes.c_double)]),
     "vofp_apply": (ctypes.c_int, [_vp, _vp, _vp]),
     "vofp_residual": (ctypes.c_int, [_vp, _vp, _vp, _P(ctypes.c_double)]),
     "vofp_solve": (ctypes.c_int, [_vp, _vp, _vp, _P(_Opts), _P(_Info)]),
@@ -212,6 +213,24 @@ class Context:
         _check(self.h, _lib.vofp_rhs_from_face_velocity(self.h, _dev(u, self.nfx, "u"), _dev(v, self.nfy, "v"),
                                                         _dev(w, self.nfz, "w"), bf, _dev(out, self.n, "b")))
         return out
+
+    def vofp_project(self, p, u, v, w, body_flux=None, out=None, want_div=True, want_max=True):
+        """Projected face velocities (u, v, w), the group-folded divergence per cell (or None) and
+        its max |.| (or None).  out = (u_out, v_out, w_out) may be the inputs themselves."""
+        import torch
+        if out is None:
+            out = (torch.empty_like(u), torch.empty_like(v), torch.empty_like(w))
+        uo, vo, wo = out
+        div = torch.empty(self.n, dtype=torch.float64, device=p.device) if want_div else None
+        m = ctypes.c_double(0.0)
+        bf = None if body_flux is None else _dev(body_flux, self.n, "body_flux")
+        _check(self.h, _lib.vofp_project(self.h, _dev(p, self.n, "p"), _dev(u, self.nfx, "u"),
+                                         _dev(v, self.nfy, "v"), _dev(w, self.nfz, "w"), bf,
+                                         _dev(uo, self.nfx, "u_out"), _dev(vo, self.nfy, "v_out"),
+                                         _dev(wo, self.nfz, "w_out"),
+                                         None if div is None else _dev(div, self.n, "div"),
+                                         ctypes.byref(m) if want_max else None))
+        return uo, vo, wo, div, (m.value if want_max else None)
 
     def vofp_apply(self, x, out=None):
         import torch

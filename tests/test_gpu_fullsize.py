@@ -52,3 +52,22 @@ def test_fullsize_solution_residual_by_oracle(setup, mode, precond, rtol):
     res = s.residual(x.cpu().numpy())
     assert res <= rtol * 1.01, (res, info)
     assert abs(res - info["rel_residual"]) <= 1e-3 * res + 1e-16
+
+
+def test_fullsize_projection(setup, oracle):
+    """Projection of the face velocities with the mixed-precision pressure (Sec. 2.1 Eq. runge1),
+    face by face against the oracle on the same pressure; the projected field's group divergence
+    is the pressure equation's residual times dt (rtol 1e-8 of b_hat)."""
+    vofp, prob, s, ctx, b = setup
+    u, v, w = (torch.from_numpy(np.ascontiguousarray(a).ravel()).cuda() for a in (prob.u, prob.v, prob.w))
+    x, info = ctx.vofp_solve(b, rtol=1e-8, mode=vofp.MODE_MIXED)
+    assert info["status"] == 0
+    uo, vo, wo, div, mx = ctx.vofp_project(x, u, v, w)
+    ru, rv, rw = oracle.project(prob, s, x.cpu().numpy().reshape(prob.shape))
+    for got, ref in ((uo, ru), (vo, rv), (wo, rw)):
+        g = got.cpu().numpy().reshape(ref.shape)
+        assert np.abs(g - ref).max() <= 1e-13 * np.abs(ref).max()
+    # sum over groups of div^2 = dt^2 ||b_hat - A_hat x||^2 (the residual identity of the projection)
+    gdiv = div.cpu().numpy()
+    assert abs(np.linalg.norm(gdiv) - prob.dt * np.linalg.norm(s.bhat) * info["rel_residual"]) <= \
+        1e-3 * prob.dt * np.linalg.norm(s.bhat) * info["rel_residual"]

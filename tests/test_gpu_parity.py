@@ -211,6 +211,68 @@ def test_tma_red_black_matches_register_red_black(vofp, oracle, monkeypatch, sha
     assert np.linalg.norm(x1 - x0) / np.linalg.norm(x0) <= 1e-6
 
 
+@pytest.mark.parametrize("case", ["tiny", "ragged", "hull-small"])
+def test_projection_matches_oracle(vofp, oracle, case):
+    """vofp_project (Sec. 2.1 Eq. runge1) against oracle.project on the GPU's own pressure, face by
+    face; the group-folded divergence against oracle.divergence of those faces; and the projected
+    field is divergence-free to the solver's residual while the input is not."""
+    prob = CASES[case]()
+    prob.dt = 0.4
+    s = oracle.System(prob)
+    ctx, t = vofp.context_for(prob)
+    b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
+    x, info = ctx.vofp_solve(b, rtol=1e-12, mode=vofp.MODE_FP64)
+    assert info["status"] == 0
+    uo, vo, wo, div, mx = ctx.vofp_project(x, t["u"], t["v"], t["w"])
+    ph = host(x, prob.shape)
+    ru, rv, rw = oracle.project(prob, s, ph)
+    for got, ref, shp in ((uo, ru, prob.u.shape), (vo, rv, prob.v.shape), (wo, rw, prob.w.shape)):
+        g = got.cpu().numpy().reshape(shp)
+        assert np.abs(g - ref).max() <= 1e-13 * max(np.abs(ref).max(), 1e-300)
+    rdiv = oracle.divergence(prob, s, uo.cpu().numpy().reshape(prob.u.shape), vo.cpu().numpy().reshape(prob.v.shape),
+                             wo.cpu().numpy().reshape(prob.w.shape))
+    gdiv = host(div, prob.shape)
+    flux = np.abs(oracle.divergence(prob, s, np.abs(prob.u), np.abs(prob.v), np.abs(prob.w))).max()
+    assert np.abs(gdiv - rdiv).max() <= 1e-13 * flux
+    assert mx == np.abs(gdiv).max()
+    assert mx <= 1e-9 * flux          # residual 1e-12 of b_hat = -(1/dt) div u*
+    _, _, _, div0, mx0 = ctx.vofp_project(torch.zeros_like(x), t["u"], t["v"], t["w"])
+    assert mx0 > 1e-3 * flux
+
+
+def test_projection_in_place_and_prescribed_wall_flux(vofp, oracle):
+    """All-Neumann box with prescribed outward fluxes +-g0 on the x walls (compatible): in-place
+    projection (outputs aliasing the inputs) equals the out-of-place one bitwise, the wall
+    velocities are +dt g0, and every group is divergence-free."""
+    prob = I.tiny_sphere(n=12)
+    prob.dt = 0.7
+    prob.bc = (0, 0, 0, 0, 0, 0)
+    nz, ny, nx = prob.shape
+    g0 = np.random.default_rng(11).uniform(-1, 1, (nz, ny))
+    flux = [g0, -g0, None, None, None, None]
+    s = oracle.System(prob, neumann_flux=flux)
+    from paper_1410_1937_gb300 import vofp as V
+    ctx = V.Context(prob.dx, prob.dy, prob.dz)
+    t = {k: dev(getattr(prob, k)) for k in ("F", "ax", "ay", "az", "vf", "u", "v", "w")}
+    ctx.vofp_build_operator(t["F"], t["ax"], t["ay"], t["az"], t["vf"], prob.bc, prob.rho_liquid, prob.rho_gas,
+                            prob.merge_threshold, 0, prob.dt,
+                            neumann_flux=[dev(g0), dev(-g0), None, None, None, None])
+    b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
+    x, info = ctx.vofp_solve(b, rtol=1e-12, mode=vofp.MODE_FP64)
+    assert info["status"] == 0
+    uo, vo, wo, div, mx = ctx.vofp_project(x, t["u"], t["v"], t["w"])
+    u2, v2, w2 = t["u"].clone(), t["v"].clone(), t["w"].clone()
+    ctx.vofp_project(x, u2, v2, w2, out=(u2, v2, w2), want_div=False, want_max=False)
+    assert torch.equal(uo, u2) and torch.equal(vo, v2) and torch.equal(wo, w2)
+    ug = uo.cpu().numpy().reshape(prob.u.shape)
+    np.testing.assert_allclose(ug[:, :, 0], prob.dt * g0, rtol=1e-15)
+    np.testing.assert_allclose(ug[:, :, -1], prob.dt * g0, rtol=1e-15)
+    ru, rv, rw = oracle.project(prob, s, host(x, prob.shape), neumann_flux=flux)
+    assert np.abs(ug - ru).max() <= 1e-13 * np.abs(ru).max()
+    fl = np.abs(oracle.divergence(prob, s, np.abs(prob.u), np.abs(prob.v), np.abs(prob.w))).max()
+    assert mx <= 1e-9 * fl
+
+
 def test_unaligned_rows_use_register_stencil(vofp):
     """Rows of 37 FP32 values are not a multiple of 16 bytes: no tensor map, register kernel."""
     prob = ragged_sphere()
