@@ -43,6 +43,12 @@ STENCIL_ELEMS = {"jacobi": 9.0, "rbsgs": 9.0}
 UPDATE_ELEMS = 3.0
 
 
+# projection + divergence check, FP64: reads p, rho, three apertures and three velocities and
+# writes three velocities (88 B per cell), then reads the apertures and the new velocities, the
+# activity byte and writes the divergence (57 B per cell)
+PROJECTION_BYTES = 145.0
+
+
 def iter_elems(precond):
     return STENCIL_ELEMS[precond] + UPDATE_ELEMS
 
@@ -228,6 +234,20 @@ def run_ours(args, rank, world, local_rank):
         ms_max = float(tm.item())
         info = infos[-1]
         assert all(i["status"] == 0 for i in infos), infos
+        # the projection that consumes the pressure (u = u* - dt grad p / rho, with the group
+        # divergence check): not part of the step, reported beside it
+        uo, vo, wo = torch.empty_like(t["u"]), torch.empty_like(t["v"]), torch.empty_like(t["w"])
+        for _ in range(3):
+            ctx.vofp_project(x, t["u"], t["v"], t["w"], out=(uo, vo, wo), want_max=False)
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 20
+        p0.record(stream)
+        for _ in range(reps):
+            ctx.vofp_project(x, t["u"], t["v"], t["w"], out=(uo, vo, wo), want_max=False)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        proj_ms = p0.elapsed_time(p1) / reps
+        max_div = ctx.vofp_project(x, t["u"], t["v"], t["w"], out=(uo, vo, wo))[4]
         # dominant kernel: the fused CG stencil of the solve's precision, timed live
         st_ms, up_ms, red_ms = ctx.vofp_time_iteration_kernels(prec, args.kernel_reps, precond=pc)
         stats = ctx.vofp_get_stats()
@@ -322,6 +342,8 @@ def run_ours(args, rank, world, local_rank):
                      "achieved": achieved, "peak": hbm, "peak_kind": hbm_kind, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "stencil_ms": st_ms, "update_ms": up_ms,
                      "red_ms": red_ms, "update_gbs": UPDATE_ELEMS * vb * n / (up_ms * 1e-3) / 1e9},
+        "projection": {"ms": proj_ms, "bytes_per_cell": PROJECTION_BYTES,
+                       "gbs": PROJECTION_BYTES * n / (proj_ms * 1e-3) / 1e9, "max_group_divergence": max_div},
         "clocks": clk.summary(),
         "gpu_launches": launches[0],
         "e2e": e2e,

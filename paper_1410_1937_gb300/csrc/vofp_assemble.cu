@@ -116,26 +116,42 @@ __global__ void k_eff_apertures(Dims d, const double* __restrict__ ax, const dou
 }
 
 // T of each cell's +x, +y, +z face: A_f S_f / ((d_L rho_L + d_R rho_R) / 2); 0 on domain faces
+// T of each cell's +x, +y, +z interior face, and the face's inverse resistance
+// kappa = 1 / ((d_L rho_L + d_R rho_R) / 2) where the face is open (0 where it is closed or on the
+// domain boundary), which the projection of the face velocities uses
 __global__ void k_face_coeffs(Dims d, const double* __restrict__ dx, const double* __restrict__ dy,
                               const double* __restrict__ dz, const double* __restrict__ rho,
                               const double* __restrict__ axe, const double* __restrict__ aye,
                               const double* __restrict__ aze, double* __restrict__ Tx,
-                              double* __restrict__ Ty, double* __restrict__ Tz) {
+                              double* __restrict__ Ty, double* __restrict__ Tz, double* __restrict__ kx,
+                              double* __restrict__ ky, double* __restrict__ kz) {
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < d.n;
          c += (long long)gridDim.x * blockDim.x) {
         int i, j, k;
         cell_ijk(d, c, i, j, k);
         const double rc = rho[c];
-        double tx = 0.0, ty = 0.0, tz = 0.0;
-        if (i < d.nx - 1)
-            tx = (axe[fx_idx(d, i + 1, j, k)] * (dz[k] * dy[j])) / (0.5 * (dx[i] * rc + dx[i + 1] * rho[c + 1]));
-        if (j < d.ny - 1)
-            ty = (aye[fy_idx(d, i, j + 1, k)] * (dz[k] * dx[i])) / (0.5 * (dy[j] * rc + dy[j + 1] * rho[c + d.nx]));
-        if (k < d.nz - 1)
-            tz = (aze[fz_idx(d, i, j, k + 1)] * (dy[j] * dx[i])) / (0.5 * (dz[k] * rc + dz[k + 1] * rho[c + d.plane]));
+        double tx = 0.0, ty = 0.0, tz = 0.0, qx = 0.0, qy = 0.0, qz = 0.0;
+        if (i < d.nx - 1) {
+            const double a = axe[fx_idx(d, i + 1, j, k)], den = 0.5 * (dx[i] * rc + dx[i + 1] * rho[c + 1]);
+            tx = (a * (dz[k] * dy[j])) / den;
+            qx = a > 0.0 ? 1.0 / den : 0.0;
+        }
+        if (j < d.ny - 1) {
+            const double a = aye[fy_idx(d, i, j + 1, k)], den = 0.5 * (dy[j] * rc + dy[j + 1] * rho[c + d.nx]);
+            ty = (a * (dz[k] * dx[i])) / den;
+            qy = a > 0.0 ? 1.0 / den : 0.0;
+        }
+        if (k < d.nz - 1) {
+            const double a = aze[fz_idx(d, i, j, k + 1)], den = 0.5 * (dz[k] * rc + dz[k + 1] * rho[c + d.plane]);
+            tz = (a * (dy[j] * dx[i])) / den;
+            qz = a > 0.0 ? 1.0 / den : 0.0;
+        }
         Tx[c] = tx;
         Ty[c] = ty;
         Tz[c] = tz;
+        kx[c] = qx;
+        ky[c] = qy;
+        kz[c] = qz;
     }
 }
 
@@ -499,7 +515,8 @@ vofp_status build_operator(vofp_ctx* c, const double* F, const double* ax, const
             (s = c->alloc(&c->aze, nfz)) || (s = c->alloc(&c->s, N)) || (s = c->alloc(&c->sq, N)) ||
             (s = c->alloc(&c->Txs, N)) || (s = c->alloc(&c->Tys, N)) || (s = c->alloc(&c->Tzs, N)) ||
             (s = c->alloc(&c->Txf, N)) || (s = c->alloc(&c->Tyf, N)) || (s = c->alloc(&c->Tzf, N)) ||
-            (s = c->alloc(&c->Tzr, N)) || (s = c->alloc(&c->rho, N)) ||
+            (s = c->alloc(&c->Tzr, N)) || (s = c->alloc(&c->rho, N)) || (s = c->alloc(&c->kx, N)) ||
+            (s = c->alloc(&c->ky, N)) || (s = c->alloc(&c->kz, N)) ||
             (s = c->alloc(&c->slave_bits, (N + 31) / 32)) || (s = c->alloc(&c->root, N)) ||
             (s = c->alloc(&c->red_bits, (N + 31) / 32)) || (s = c->alloc(&c->excl_bits, (N + 31) / 32)) ||
             (s = c->alloc(&c->inactive, N)) || (s = c->alloc(&c->work, N)) ||
@@ -568,7 +585,8 @@ vofp_status build_operator(vofp_ctx* c, const double* F, const double* ax, const
         }
     }
     launch(c, k_eff_apertures, grid_for(nfx + nfy + nfz), kNT, st, d, ax, ay, az, c->inactive, c->axe, c->aye, c->aze);
-    launch(c, k_face_coeffs, gN, kNT, st, d, c->dx, c->dy, c->dz, rho, c->axe, c->aye, c->aze, c->Tx, c->Ty, c->Tz);
+    launch(c, k_face_coeffs, gN, kNT, st, d, c->dx, c->dy, c->dz, rho, c->axe, c->aye, c->aze, c->Tx, c->Ty, c->Tz,
+           c->kx, c->ky, c->kz);
     launch(c, k_diag, gN, kNT, st, d, b6, c->dx, c->dy, c->dz, rho, c->axe, c->aye, c->aze, c->Tx, c->Ty, c->Tz, c->diag);
 
     // merge map (Sec. 2.3): small cells on the device, chains resolved on the host

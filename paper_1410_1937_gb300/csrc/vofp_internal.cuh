@@ -89,6 +89,8 @@ struct vofp_ctx {
     // is set for "red" cells -- (i+j+k) even, with an unknown, in no merge group -- whose unknowns
     // are eliminated; excl_bits = slave_bits | red_bits marks cells left out of the reduced dots
     double* rho = nullptr;            // cell density (after the optional smoothing)
+    // inverse face resistance 1/((d_L rho_L + d_R rho_R)/2) of each cell's open +x, +y, +z face
+    double *kx = nullptr, *ky = nullptr, *kz = nullptr;
     uint32_t* red_bits = nullptr;
     float* Tzr = nullptr;             // Tzf with the sign bit set on red cells (red flag)
     uint32_t* excl_bits = nullptr;

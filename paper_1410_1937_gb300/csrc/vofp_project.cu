@@ -3,8 +3,9 @@
 // group (Sec. 2.3, the integral form over open faces) of the projected field.
 //
 // The face gradient uses the operator's own face coefficient reading: (p_R - p_L) over the
-// half-cell resistance sum (d_L rho_L + d_R rho_R) / 2, so the projected fluxes satisfy the
-// discrete pressure equation row by row and every group's net flux is the solver's residual.
+// half-cell resistance sum (d_L rho_L + d_R rho_R) / 2 (its inverse kept per face from the
+// assembly, so the projection needs no division), so the projected fluxes satisfy the discrete
+// pressure equation row by row and every group's net flux is the solver's residual.
 #include <algorithm>
 #include <cstring>
 
@@ -25,11 +26,10 @@ int grid_cells(long long n) {
     return int(std::max(1LL, std::min(b, (long long)num_sms() * 16)));
 }
 
-// u_new on an interior face between cells L and R; a closed face keeps its velocity (the pressure
-// gradient drives no flux through it)
-__device__ __forceinline__ double interior(double u, double a, double dt, double pL, double pR, double dL,
-                                           double dR, double rL, double rR) {
-    return a > 0.0 ? u - dt * ((pR - pL) / (0.5 * (dL * rL + dR * rR))) : u;
+// u_new on an interior face between cells L and R with inverse resistance kap (0 on a closed face,
+// which keeps its velocity: the pressure gradient drives no flux through it)
+__device__ __forceinline__ double interior(double u, double kap, double dt, double pL, double pR) {
+    return u - dt * ((pR - pL) * kap);
 }
 // u_new on a domain face next to cell c; `sgn` = +1 on a + face, -1 on a - face
 __device__ __forceinline__ double wall(double u, double a, double dt, int kind, const double* g, long long gi,
@@ -43,33 +43,34 @@ __device__ __forceinline__ double wall(double u, double a, double dt, int kind, 
 __global__ void k_project(Dims d, Walls wl, double dt, const double* __restrict__ dx, const double* __restrict__ dy,
                           const double* __restrict__ dz, const double* __restrict__ rho,
                           const double* __restrict__ axe, const double* __restrict__ aye,
-                          const double* __restrict__ aze, const double* __restrict__ p,
+                          const double* __restrict__ aze, const double* __restrict__ kx,
+                          const double* __restrict__ ky, const double* __restrict__ kz, const double* __restrict__ p,
                           const double* u, const double* v, const double* w, double* uo, double* vo, double* wo) {
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < d.n;
          c += (long long)gridDim.x * blockDim.x) {
         int i, j, k;
         cell_ijk(d, c, i, j, k);
-        const double pc = p[c], rc = rho[c];
+        const double pc = p[c];
         long long f = fx_idx(d, i, j, k);
-        uo[f] = i > 0 ? interior(u[f], axe[f], dt, p[c - 1], pc, dx[i - 1], dx[i], rho[c - 1], rc)
-                      : wall(u[f], axe[f], dt, wl.kind[0], wl.g[0], j + (long long)d.ny * k, -1, pc, dx[i], rc);
+        uo[f] = i > 0 ? interior(u[f], kx[c - 1], dt, p[c - 1], pc)
+                      : wall(u[f], axe[f], dt, wl.kind[0], wl.g[0], j + (long long)d.ny * k, -1, pc, dx[i], rho[c]);
         if (i == d.nx - 1) {
             f = fx_idx(d, i + 1, j, k);
-            uo[f] = wall(u[f], axe[f], dt, wl.kind[1], wl.g[1], j + (long long)d.ny * k, +1, pc, dx[i], rc);
+            uo[f] = wall(u[f], axe[f], dt, wl.kind[1], wl.g[1], j + (long long)d.ny * k, +1, pc, dx[i], rho[c]);
         }
         f = fy_idx(d, i, j, k);
-        vo[f] = j > 0 ? interior(v[f], aye[f], dt, p[c - d.nx], pc, dy[j - 1], dy[j], rho[c - d.nx], rc)
-                      : wall(v[f], aye[f], dt, wl.kind[2], wl.g[2], i + (long long)d.nx * k, -1, pc, dy[j], rc);
+        vo[f] = j > 0 ? interior(v[f], ky[c - d.nx], dt, p[c - d.nx], pc)
+                      : wall(v[f], aye[f], dt, wl.kind[2], wl.g[2], i + (long long)d.nx * k, -1, pc, dy[j], rho[c]);
         if (j == d.ny - 1) {
             f = fy_idx(d, i, j + 1, k);
-            vo[f] = wall(v[f], aye[f], dt, wl.kind[3], wl.g[3], i + (long long)d.nx * k, +1, pc, dy[j], rc);
+            vo[f] = wall(v[f], aye[f], dt, wl.kind[3], wl.g[3], i + (long long)d.nx * k, +1, pc, dy[j], rho[c]);
         }
         f = fz_idx(d, i, j, k);
-        wo[f] = k > 0 ? interior(w[f], aze[f], dt, p[c - d.plane], pc, dz[k - 1], dz[k], rho[c - d.plane], rc)
-                      : wall(w[f], aze[f], dt, wl.kind[4], wl.g[4], i + (long long)d.nx * j, -1, pc, dz[k], rc);
+        wo[f] = k > 0 ? interior(w[f], kz[c - d.plane], dt, p[c - d.plane], pc)
+                      : wall(w[f], aze[f], dt, wl.kind[4], wl.g[4], i + (long long)d.nx * j, -1, pc, dz[k], rho[c]);
         if (k == d.nz - 1) {
             f = fz_idx(d, i, j, k + 1);
-            wo[f] = wall(w[f], aze[f], dt, wl.kind[5], wl.g[5], i + (long long)d.nx * j, +1, pc, dz[k], rc);
+            wo[f] = wall(w[f], aze[f], dt, wl.kind[5], wl.g[5], i + (long long)d.nx * j, +1, pc, dz[k], rho[c]);
         }
     }
 }
@@ -125,7 +126,8 @@ vofp_status project(vofp_ctx* c, const double* p, const double* u, const double*
     const int g = grid_cells(d.n);
     launch(c, k_project, g, kNT, st, d, wl, c->phys.dt, (const double*)c->dx, (const double*)c->dy,
            (const double*)c->dz, (const double*)c->rho, (const double*)c->axe, (const double*)c->aye,
-           (const double*)c->aze, p, u, v, w, uo, vo, wo);
+           (const double*)c->aze, (const double*)c->kx, (const double*)c->ky, (const double*)c->kz, p, u, v, w, uo, vo,
+           wo);
     if (div || max_div) {
         double* dv = div ? div : c->work;
         launch(c, k_divergence, g, kNT, st, d, (const double*)c->dx, (const double*)c->dy, (const double*)c->dz,
