@@ -21,14 +21,16 @@ struct RbMaps {
 
 constexpr size_t rb_al(size_t b) { return (b + 127) / 128 * 128; }
 
+template <int TH>
 struct RbGeom {
-    static constexpr int TW = 2 * kBX;                // 64 cells of a tile row
+    static constexpr int TW = 2 * kBX;                // 64 cells of a tile row; TH rows
+    static constexpr int NT = kBX * TH;               // threads of a block
     static constexpr int HX = 4;                      // box x origin i0 - 4 (16-byte aligned)
     static constexpr int BW = TW + 2 * HX;            // 72: every box spans x = i0-4 .. i0+67
-    static constexpr int RN = BW * (kBY + 4);         // r, p_old: rows j0-2 .. j0+9
-    static constexpr int XN = BW * (kBY + 2);         // Tx: rows j0-1 .. j0+8
-    static constexpr int YN = BW * (kBY + 3);         // Ty: rows j0-2 .. j0+8
-    static constexpr int ZN = BW * (kBY + 2);         // Tz (signed): rows j0-1 .. j0+8
+    static constexpr int RN = BW * (TH + 4);          // r, p_old: rows j0-2 .. j0+TH+1
+    static constexpr int XN = BW * (TH + 2);          // Tx: rows j0-1 .. j0+TH
+    static constexpr int YN = BW * (TH + 3);          // Ty: rows j0-2 .. j0+TH
+    static constexpr int ZN = BW * (TH + 2);          // Tz (signed): rows j0-1 .. j0+TH
     static constexpr size_t oR = 0;
     static constexpr size_t oP = oR + rb_al(RN * 4);
     static constexpr size_t oX = oP + rb_al(RN * 4);
@@ -36,17 +38,19 @@ struct RbGeom {
     static constexpr size_t oZ = oY + rb_al(YN * 4);
     static constexpr size_t kStage = oZ + rb_al(ZN * 4);
     static constexpr uint32_t kTx = (uint32_t)((2 * RN + XN + YN + ZN) * 4);
-    // p ring plane: x index xr <-> cell i0 + xr - 2, row yr <-> j0 + yr - 2 (68 x 12)
+    // p ring plane: x index xr <-> cell i0 + xr - 2, row yr <-> j0 + yr - 2 (68 x (TH+4))
     static constexpr int PW = TW + 4;
-    static constexpr int PN = PW * (kBY + 4);
-    // w ring plane: same x index, row yw <-> j0 + yw - 1 (68 x 10)
-    static constexpr int WN = PW * (kBY + 2);
-    static constexpr int kPItems = (PW / 2) * (kBY + 4);   // p pairs formed per plane: 408
+    static constexpr int PN = PW * (TH + 4);
+    // w ring plane: same x index, row yw <-> j0 + yw - 1 (68 x (TH+2))
+    static constexpr int WN = PW * (TH + 2);
+    static constexpr int kPItems = (PW / 2) * (TH + 4);   // p pairs formed per plane
+    static constexpr int kPPer = (kPItems + NT - 1) / NT; // p pairs per thread
 };
 
-template <int NS>
+template <int NS, int TH>
 constexpr size_t cg_rb_tma_smem() {
-    return 128 + NS * RbGeom::kStage + 3 * RbGeom::PN * 4 + 3 * RbGeom::WN * 4 + NS * sizeof(uint64_t);
+    using G = RbGeom<TH>;
+    return 128 + NS * G::kStage + 3 * G::PN * 4 + 3 * G::WN * 4 + NS * sizeof(uint64_t);
 }
 
 // coefficients of a thread's own pair kept from its w to its t (plane m): Tx of both cells and of
@@ -57,13 +61,13 @@ struct RbCo {
     float txl;
 };
 
-template <int NS>
-__global__ void __launch_bounds__(kBX* kBY, NS <= 2 ? 4 : 3)
+template <int NS, int TH>
+__global__ void __launch_bounds__(kBX* TH, TH == 8 ? 3 : 6)
 k_cg_rb_tma(const __grid_constant__ RbMaps maps, const Dims d, const int per_block, const float* __restrict__ pold,
             float* __restrict__ pnew, float* __restrict__ xv, float* __restrict__ out, CgScalars* __restrict__ sc,
             double* __restrict__ partials, unsigned int* __restrict__ counter) {
-    using G = RbGeom;
-    constexpr int PW = G::PW, BW = G::BW;
+    using G = RbGeom<TH>;
+    constexpr int PW = G::PW, BW = G::BW, NT = G::NT, PP = G::kPPer;
     extern __shared__ __align__(128) unsigned char rb_smem[];
     unsigned char* base = rb_smem + ((128u - (smem_addr(rb_smem) & 127u)) & 127u);
     float* pring = reinterpret_cast<float*>(base + NS * G::kStage);
@@ -85,28 +89,28 @@ k_cg_rb_tma(const __grid_constant__ RbMaps maps, const Dims d, const int per_blo
     auto wl = [&](int kk) -> float* { return wring + ((kk + 6) % 3) * G::WN; };
 
     // this thread's p items (pairs of the 68 x 12 plane)
-    int pi_dst[2], pi_src[2];
-    bool pi_on[2];
+    int pi_dst[PP], pi_src[PP];
+    bool pi_on[PP];
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const int it = tid + q * kBX * kBY;
+    for (int q = 0; q < PP; ++q) {
+        const int it = tid + q * NT;
         pi_on[q] = it < G::kPItems;
         const int xr = pi_on[q] ? 2 * (it % (PW / 2)) : 0, yr = pi_on[q] ? it / (PW / 2) : 0;
         pi_dst[q] = yr * PW + xr;
         pi_src[q] = yr * BW + xr + 2;
     }
-    // own pair: w/p ring x index xo, w row ty + 1; ring item of threads 0..79: a pair in the rows
-    // j0-1 / j0+8 (threads 0..63) or a single cell in the columns i0-1 / i0+64 (threads 64..79)
+    // own pair: w/p ring x index xo, w row ty + 1; ring item of threads 0..63+2TH: a pair in the
+    // rows j0-1 / j0+TH (threads 0..63) or a single cell in the columns i0-1 / i0+64
     const int xo = 2 + 2 * tx, yo = ty + 1;
     int rx = 0, ry = 0;
-    const bool ring_pair = tid < 64, ring_single = tid >= 64 && tid < 80;
+    const bool ring_pair = tid < 64, ring_single = tid >= 64 && tid < 64 + 2 * TH;
     if (tid < 32) { rx = 2 + 2 * tid; ry = 0; }
-    else if (tid < 64) { rx = 2 + 2 * (tid - 32); ry = kBY + 1; }
-    else if (tid < 72) { rx = 1; ry = 1 + (tid - 64); }
-    else if (tid < 80) { rx = PW - 2; ry = 1 + (tid - 72); }
+    else if (tid < 64) { rx = 2 + 2 * (tid - 32); ry = TH + 1; }
+    else if (tid < 64 + TH) { rx = 1; ry = 1 + (tid - 64); }
+    else if (tid < 64 + 2 * TH) { rx = PW - 2; ry = 1 + (tid - 64 - TH); }
 
     const int tiles_x = (d.nx + G::TW - 1) / G::TW;
-    const long long ntiles = (long long)tiles_x * ((d.ny + kBY - 1) / kBY);
+    const long long ntiles = (long long)tiles_x * ((d.ny + TH - 1) / TH);
     const long long total = ntiles * d.nz;
     const long long w0 = min((long long)blockIdx.x * per_block, total);
     const long long w1 = min(w0 + per_block, total);
@@ -115,7 +119,7 @@ k_cg_rb_tma(const __grid_constant__ RbMaps maps, const Dims d, const int per_blo
         const int k0 = int(w - tile_id * d.nz);
         const int k1 = (int)min((long long)d.nz, (long long)k0 + (w1 - w));
         w += k1 - k0;
-        const int i0 = int(tile_id % tiles_x) * G::TW, j0 = int(tile_id / tiles_x) * kBY;
+        const int i0 = int(tile_id % tiles_x) * G::TW, j0 = int(tile_id / tiles_x) * TH;
         const int i = i0 + 2 * tx, j = j0 + ty;
         const bool inside = i < d.nx && j < d.ny;     // nx is even: both cells of the pair
         const int s_first = k0 - 4, s_last = k1 - 1;  // steps that consume a stage
@@ -216,7 +220,7 @@ k_cg_rb_tma(const __grid_constant__ RbMaps maps, const Dims d, const int per_blo
                 const float* P = reinterpret_cast<const float*>(b + G::oP);
                 float* op = pl(s + 2);
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
+                for (int q = 0; q < PP; ++q) {
                     if (!pi_on[q]) continue;
                     const float2 pv = *reinterpret_cast<const float2*>(P + pi_src[q]);
                     const float2 rv = *reinterpret_cast<const float2*>(R + pi_src[q]);
