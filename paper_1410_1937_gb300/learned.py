@@ -36,15 +36,20 @@ def _geometry_worker(args):
     return seed, (p.dx, p.dy, p.dz), {k: f32(getattr(p, k)) for k in ("F", "vf", "ax", "ay", "az", "u", "v", "w")}
 
 
-def generate(seeds, shape=TRAIN_SHAPE, workers=None, rtol=1e-9, log=print):
+def generate(seeds, shape=TRAIN_SHAPE, workers=None, rtol=1e-9, stages=(0,), log=print):
     """Solve every seed's sample with the mixed-precision PCG and keep the training tensors on the GPU.
-    Geometry is built by a spawned process pool (started before this process touches CUDA)."""
+    Geometry is built by a spawned process pool (started before this process touches CUDA).
+
+    A preconditioner is applied to residuals, so each sample gives one input/target pair per CG
+    stage k in `stages`: the scaled residual S (b_hat - A_hat x_k) of the FP64 Jacobi-PCG iterate
+    after k iterations and the scaled error S^-1 (x - x_k) (k = 0: the right-hand side and the
+    solution).  Pairs share their sample's geometry channels."""
     ctxmp = mp.get_context("spawn")
     workers = workers or max(1, min(16, (os.cpu_count() or 2) - 1))
     pool = ctxmp.Pool(workers)
     import torch
     from paper_1410_1937_gb300 import vofp
-    data = []
+    data = {"geo": [], "pairs": []}
     t0 = time.perf_counter()
     net = vofp.Network(seed=0)
     try:
@@ -56,13 +61,22 @@ def generate(seeds, shape=TRAIN_SHAPE, workers=None, rtol=1e-9, log=print):
                                     (0, 1, 0, 0, 0, 0), 1000.0, 1.2, 0.1, 0, 1.0)
             b = ctx.vofp_rhs_from_face_velocity(d["u"], d["v"], d["w"])
             x, info = ctx.vofp_solve(b, rtol=rtol, mode=vofp.MODE_MIXED, precond=vofp.PRECOND_RBSGS)
-            r, xs = ctx.vofp_scaled_pair(b, x)
             net.bind(ctx, d["F"])
             geo, mask = net.export_geometry()
-            data.append({"seed": seed, "geo": geo, "mask": mask, "r": r, "x": xs, "iters": info["iterations"]})
+            g = len(data["geo"])
+            data["geo"].append((geo, mask))
+            for k in stages:
+                if k == 0:
+                    r, e = ctx.vofp_scaled_pair(b, x)
+                else:
+                    xk, _ = ctx.vofp_solve(b, rtol=1e-30, max_iter=k, mode=vofp.MODE_FP64, check_every=2,
+                                           raise_on_error=False)
+                    r, e = ctx.vofp_scaled_pair(b - ctx.vofp_apply(xk), x - xk)
+                data["pairs"].append({"seed": seed, "geo": g, "stage": k, "r": r, "x": e})
             ctx.close()
             if (i + 1) % 100 == 0 or i + 1 == len(seeds):
-                log(f"generated {i + 1}/{len(seeds)} samples in {time.perf_counter() - t0:.1f} s")
+                log(f"generated {i + 1}/{len(seeds)} samples ({len(data['pairs'])} pairs) in "
+                    f"{time.perf_counter() - t0:.1f} s")
     finally:
         pool.close()
         pool.join()
@@ -70,18 +84,20 @@ def generate(seeds, shape=TRAIN_SHAPE, workers=None, rtol=1e-9, log=print):
 
 
 def train(net, data, shape=TRAIN_SHAPE, epochs=4, lr=1e-3, seed=0, log=print):
-    """One sample per Adam step, samples shuffled every epoch, cosine learning-rate decay."""
+    """One input/target pair per Adam step, pairs shuffled every epoch, cosine learning-rate decay."""
     rng = np.random.default_rng(seed)
     nz_ny_nx = (shape[2], shape[1], shape[0])
-    total = epochs * len(data)
+    pairs = data["pairs"]
+    total = epochs * len(pairs)
     step = 0
     hist = []
     t0 = time.perf_counter()
     for ep in range(epochs):
         losses = []
-        for i in rng.permutation(len(data)):
-            s = data[i]
-            net.set_geometry(nz_ny_nx, s["geo"], s["mask"])
+        for i in rng.permutation(len(pairs)):
+            s = pairs[i]
+            geo, mask = data["geo"][s["geo"]]
+            net.set_geometry(nz_ny_nx, geo, mask)
             lr_t = lr * 0.5 * (1 + math.cos(math.pi * step / max(total, 1)))
             losses.append(net.train_step(s["r"], s["x"], lr=lr_t))
             step += 1
@@ -148,11 +164,14 @@ def main():
     ap.add_argument("--init", default=None)
     ap.add_argument("--workers", type=int, default=0)
     ap.add_argument("--report", default=None)
+    ap.add_argument("--stages", default="0", help="CG stages of the training pairs, e.g. 0,16,64,256")
     args = ap.parse_args()
     shape = tuple(args.shape)
+    stages = tuple(int(v) for v in args.stages.split(","))
     hist = []
     if args.samples > 0:
-        data = generate(range(TRAIN_SEED0, TRAIN_SEED0 + args.samples), shape, workers=args.workers or None)
+        data = generate(range(TRAIN_SEED0, TRAIN_SEED0 + args.samples), shape, workers=args.workers or None,
+                        stages=stages)
     from paper_1410_1937_gb300 import vofp
     net = vofp.Network(seed=1)
     if args.init:
@@ -164,7 +183,8 @@ def main():
     rows = evaluate(net, range(HELD_OUT_SEED0, HELD_OUT_SEED0 + args.eval_seeds), tuple(args.eval_shape))
     if args.report:
         with open(args.report, "w") as f:
-            json.dump({"samples": args.samples, "epochs": args.epochs, "loss": hist, "eval": rows}, f, indent=1)
+            json.dump({"samples": args.samples, "stages": stages, "epochs": args.epochs, "loss": hist, "eval": rows},
+                  f, indent=1)
 
 
 if __name__ == "__main__":
