@@ -143,11 +143,36 @@ def cpu_baseline(prob, gpu_fp64_iterations, iters=40):
     _, info = s.solve_pcg(rtol=RTOL, maxit=iters)
     t_it = info["seconds"] / max(info["iterations"], 1)
     t_solve = t_asm + t_it * gpu_fp64_iterations
+    # the same PCG on one thread (a shorter sample), for the single-core figure
+    poisson.set_threads(1)
+    _, info1 = s.solve_pcg(rtol=RTOL, maxit=max(iters // 4, 4))
+    poisson.set_threads(threads)
+    t_it1 = info1["seconds"] / max(info1["iterations"], 1)
     return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": threads, "kind": "oracle",
             "sample": (f"oracle assembly of the {prob.shape[2]}x{prob.shape[1]}x{prob.shape[0]} workload "
                        f"({t_asm:.1f} s) + {info['iterations']} Jacobi-PCG iterations "
                        f"({t_it * 1e3:.1f} ms each), extrapolated to {gpu_fp64_iterations} iterations"),
-            "iterations_per_s": 1.0 / t_it, "assembly_s": t_asm}
+            "iterations_per_s": 1.0 / t_it, "assembly_s": t_asm, "cpu_model": cpu_model(),
+            "single_thread": {"value": 1.0 / (t_asm + t_it1 * gpu_fp64_iterations), "unit": "solves/s",
+                              "iterations_per_s": 1.0 / t_it1,
+                              "sample": f"{info1['iterations']} iterations on 1 thread, extrapolated the same way"}}
+
+
+def cpu_model():
+    """CPU model name of this host (/proc/cpuinfo or lscpu), or the machine type."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
 
 
 def max_over_ranks(value, world, device):
@@ -354,6 +379,7 @@ def run_ours(args, rank, world, local_rank):
                      "red_ms": red_ms, "update_gbs": UPDATE_ELEMS * vb * n / (up_ms * 1e-3) / 1e9},
         "projection": {"ms": proj_ms, "bytes_per_cell": PROJECTION_BYTES,
                        "gbs": PROJECTION_BYTES * n / (proj_ms * 1e-3) / 1e9, "max_group_divergence": max_div},
+        "device_bytes": ctx.vofp_get_stats()["device_bytes"],
         "clocks": clk.summary(),
         "gpu_launches": launches[0],
         "e2e": e2e,
