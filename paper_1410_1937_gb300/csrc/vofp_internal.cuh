@@ -240,21 +240,6 @@ cudaStream_t stream_of(const vofp_nn* n);
 
 inline int ceil_div(long long a, long long b) { return int((a + b - 1) / b); }
 
-// Work split of the plane-marching persistent kernels over `tiles` column tiles of nz planes and
-// `resident` co-resident blocks.  column: one block per tile column (tiles <= resident), so all
-// blocks march z in step and the halo rows a block reads from its neighbours' tiles were brought
-// into L2 by those neighbours moments earlier.  Otherwise equal shares of tile-planes (in
-// tile-major order) over all resident blocks.
-inline void plane_split(long long tiles, int nz, long long resident, bool column, int* nb, int* per) {
-    const long long total = tiles * nz;
-    if (column && tiles <= resident) {
-        *nb = (int)tiles;
-        *per = nz;
-        return;
-    }
-    *nb = (int)(resident < 1 ? 1 : (resident < total ? resident : total));
-    *per = (int)((total + *nb - 1) / *nb);
-}
 inline int num_sms() {
     static int n = 0;
     if (!n) {

@@ -18,6 +18,22 @@
 
 namespace vofp {
 
+// Work split of the plane-marching persistent kernels over `tiles` column tiles of nz planes and
+// `resident` co-resident blocks.  column: one block per tile column (tiles <= resident), so all
+// blocks march z in step and the halo rows a block reads from its neighbours' tiles were brought
+// into L2 by those neighbours moments earlier.  Otherwise equal shares of tile-planes (in
+// tile-major order) over all resident blocks.
+inline void plane_split(long long tiles, int nz, long long resident, bool column, int* nb, int* per) {
+    const long long total = tiles * nz;
+    if (column && tiles <= resident) {
+        *nb = (int)tiles;
+        *per = nz;
+        return;
+    }
+    *nb = (int)(resident < 1 ? 1 : (resident < total ? resident : total));
+    *per = (int)((total + *nb - 1) / *nb);
+}
+
 // The six tensor maps of one CG stencil launch: r and p_old with a one-cell halo in x and y, Tx
 // with a halo on the low-x side, Ty with a halo on the low-y side, Tz and x on the tile itself.
 struct CgMaps {
