@@ -526,6 +526,8 @@ vofp_status build_operator(vofp_ctx* c, const double* F, const double* ax, const
         VOFP_CUDA_TRY(c, cudaMemsetAsync(c->counters, 0, 64 * sizeof(unsigned int), st));
     }
     c->built = false;
+    c->rbc_built = false;
+    c->rbc_ok = false;
     for (int f = 0; f < 6; ++f) c->bc[f] = bc->kind[f];
     c->phys = *phys;
     c->dirichlet = false;

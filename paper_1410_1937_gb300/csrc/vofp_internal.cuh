@@ -132,6 +132,19 @@ struct vofp_ctx {
     int tma_blocks_per_sm[2] = {0, 0};
     int tma_cpt32 = 2;                // FP32 TMA stencil: cells per thread along x
     bool rb_tma_ok = false;           // FP32 red-black iteration fed by bulk tensor copies
+    // colour-compact FP32 vectors of the red-black inner solve (vofp_rbc.cu): black cell of each x
+    // pair (N/2), then the even-parity merge-group cells ("exceptions"); built per operator
+    bool rbc_ok = false;              // usable for the current operator
+    bool rbc_built = false;           // structures built for the current operator
+    long long rbc_nh = 0;             // N/2
+    int rbc_ne = 0, rbc_nf = 0;       // exceptions, rows next to an exception
+    float *rbc_r = nullptr, *rbc_p0 = nullptr, *rbc_p1 = nullptr, *rbc_x = nullptr, *rbc_q = nullptr;
+    uint32_t* rbc_bits = nullptr;     // compact entries excluded from the dots (copies of a group value)
+    int* rbc_exc = nullptr;           // exception cells
+    int *rbc_fcell = nullptr, *rbc_fexc = nullptr;   // rows next to exceptions, exception per face
+    int* rbc_gref = nullptr;          // compact index of every gcells entry
+    long long rbc_cap = 0;            // allocated compact length
+    int rbc_blocks_per_sm = 0;
     int tma_blocks_deep32 = 0;        // resident blocks per SM of the six-stage FP32 stencil
     int rb_tma_blocks_per_sm = 0;
     std::map<std::tuple<const void*, int, int>, CUtensorMap> tma_maps;
@@ -160,10 +173,19 @@ namespace vofp {
 void prepare_tma(vofp_ctx* c);
 // cached 3-D tensor map of an FP32 nx x ny x nz array with a bw x bh x 1 box (null if it cannot be built)
 const CUtensorMap* tensor_map_f32(vofp_ctx* c, const float* ptr, int bw, int bh);
+// the same for an nxe x ny x nz array (the colour-compact vectors: nxe = nx/2)
+const CUtensorMap* tensor_map_f32_x(vofp_ctx* c, const float* ptr, int nxe, int bw, int bh);
 // TMA-fed fused red-black iteration, FP32 (vofp_rb_tma.cu): preparation and one launch (false
 // when it cannot run on this context; the caller then uses the register-prefetch kernel)
 void prepare_rb_tma(vofp_ctx* c);
 bool launch_cg_rb_tma(vofp_ctx* c, cudaStream_t st, const float* r, const float* po, float* pn, float* xv, float* q);
+// colour-compact red-black inner solve (vofp_rbc.cu)
+vofp_status rbc_ensure(vofp_ctx* c);   // build the compact structures if eligible; sets c->rbc_ok
+void rbc_prep(vofp_ctx* c, cudaStream_t st, const double* rhs);   // inner start from the FP64 reduced rhs
+void rbc_iteration(vofp_ctx* c, cudaStream_t st, const float* po, float* pn, cudaGraphConditionalHandle h,
+                   int use_h);
+void rbc_finish_xf(vofp_ctx* c, cudaStream_t st);                 // xf (full grid) = x_c + alpha p0_c
+void rbc_time_kernel(vofp_ctx* c, cudaStream_t st);               // one iteration kernel launch
 template <typename V>
 bool launch_cg_tma(vofp_ctx* c, cudaStream_t st, const V* Tx, const V* Ty, const V* Tz, const V* r, const V* po,
                    V* pn, V* xv, V* q);
@@ -183,6 +205,30 @@ vofp_status time_iteration_kernels(vofp_ctx* c, int precision, bool rb, int reps
                                    float* red);
 
 // group helpers (vofp_assemble.cu)
+// Scalars at the start of an inner (FP32) solve, set by the block that completes the reduction of
+// the new inner residual: t = r_f . r_f of the normalised residual, rr = ||r||^2 before
+// normalisation.  With the direction kept (reliable update), beta rescales the old direction.
+__device__ inline void inner_start_scalars(CgScalars* sc, double t, double rr, bool keep) {
+    const double scale_old = sc->scale;
+    const double scale_new = (rr > 0.0 && !sc->done) ? sqrt(rr) : 0.0;
+    sc->scale = scale_new;
+    // the last refinement step only needs the reduction that reaches rtol (with margin)
+    const double need = sc->rnorm2 > 0.0 ? 0.3 * sc->rtol * sqrt(sc->ref2 / sc->rnorm2) : 1.0;
+    sc->inner_target = fmax(sc->inner_rtol, fmin(need, 0.5));
+    double beta = 0.0;
+    if (keep && scale_old > 0.0 && sc->rr_prev > 0.0) {
+        beta = scale_new / (scale_old * sc->rr_prev);
+        if (!isfinite(beta)) beta = 0.0;
+    }
+    sc->rr = t;
+    sc->alpha = 0.0;
+    sc->beta = beta;
+    sc->iter = 0;
+    sc->inner_done = 0;
+    sc->rr0 = t;
+    sc->dir_valid = sc->keep_dir;
+}
+
 // face and cell indexing: x faces (nx+1) x ny x nz, y faces nx x (ny+1) x nz, z faces nx x ny x (nz+1)
 __device__ __forceinline__ long long fx_idx(const Dims& d, int i, int j, int k) {
     return i + (long long)(d.nx + 1) * (j + (long long)d.ny * k);

@@ -1,0 +1,461 @@
+// Host side and small kernels of the colour-compact red-black inner solve (see vofp_rbc.cuh).
+//
+// Per operator (on the device, deterministic order):
+//   exceptions  even-parity cells with an unknown that are not red (members of merge groups),
+//               sorted by cell index; their compact index is N/2 + e;
+//   fix rows    black cells next to an exception, sorted, with the exception index behind each of
+//               their six faces (-1 where there is none);
+//   bits        compact entries that hold a copy of a group value (excluded from the dots);
+//   gref        the compact index of every entry of the merge-group cell lists.
+// Per iteration: the TMA iteration kernel (every even cell takes the red formula), the exception
+// kernel (exception rows; black rows next to an exception get the exception's p in place of the
+// red formula), the merge-group patch and the vector update on the compact vectors.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+
+#include "vofp_rbc.cuh"
+
+namespace vofp {
+namespace {
+
+constexpr int kNT = 256;
+constexpr int kRbcStages = 3;
+constexpr int kChunk = 2048;            // cells per block of the compaction passes (8 per thread)
+
+int grid_n(long long n) {
+    long long b = (n + kNT - 1) / kNT;
+    return int(std::max(1LL, std::min(b, (long long)num_sms() * 8)));
+}
+
+__device__ __forceinline__ bool bit_of(const uint32_t* __restrict__ bits, long long c) {
+    return (bits[c >> 5] >> (c & 31)) & 1u;
+}
+__device__ __forceinline__ int parity(const Dims& d, long long c) {
+    int i, j, k;
+    cell_ijk(d, c, i, j, k);
+    return (i + j + k) & 1;
+}
+// black (odd-parity) cell of pair h (nx even: the pair's cells are 2h and 2h+1)
+__device__ __forceinline__ long long black_of(const Dims& d, long long h) {
+    const long long row = h / (d.nx >> 1);
+    const int j = int(row % d.ny), k = int(row / d.ny);
+    return 2 * h + 1 - ((j + k) & 1);
+}
+// exception: even parity, an unknown, not red
+__device__ __forceinline__ bool is_exception(const Dims& d, long long c, const int32_t* root, const uint32_t* red) {
+    return root[c] >= 0 && parity(d, c) == 0 && !bit_of(red, c);
+}
+// fix row: black cell with an exception behind one of its faces
+__device__ __forceinline__ bool is_fix_row(const Dims& d, long long c, const uint8_t* isexc) {
+    if (parity(d, c) == 0) return false;
+    int i, j, k;
+    cell_ijk(d, c, i, j, k);
+    return (i > 0 && isexc[c - 1]) || (i < d.nx - 1 && isexc[c + 1]) || (j > 0 && isexc[c - d.nx]) ||
+           (j < d.ny - 1 && isexc[c + d.nx]) || (k > 0 && isexc[c - d.plane]) || (k < d.nz - 1 && isexc[c + d.plane]);
+}
+
+template <int MODE>
+__device__ __forceinline__ bool pred(const Dims& d, long long c, const int32_t* root, const uint32_t* red,
+                                     const uint8_t* isexc) {
+    if (MODE == 0) return is_exception(d, c, root, red);
+    return is_fix_row(d, c, isexc);
+}
+
+// stable compaction, pass 1: count per chunk of kChunk cells
+template <int MODE>
+__global__ void __launch_bounds__(kNT) k_cmp_count(Dims d, const int32_t* __restrict__ root,
+                                                   const uint32_t* __restrict__ red, const uint8_t* __restrict__ isexc,
+                                                   unsigned int* __restrict__ counts) {
+    __shared__ unsigned int sh[kNT / 32];
+    const long long c0 = (long long)blockIdx.x * kChunk + (long long)threadIdx.x * (kChunk / kNT);
+    unsigned int n = 0;
+    for (int u = 0; u < kChunk / kNT; ++u) {
+        const long long c = c0 + u;
+        if (c < d.n && pred<MODE>(d, c, root, red, isexc)) ++n;
+    }
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = n;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int s = 0;
+        for (int w = 0; w < kNT / 32; ++w) s += sh[w];
+        counts[blockIdx.x] = s;
+    }
+}
+
+// pass 2: exclusive scan of the chunk counts (one block), total into counts[nchunks]
+__global__ void k_cmp_scan(int nchunks, unsigned int* __restrict__ counts, unsigned int* __restrict__ offsets) {
+    __shared__ unsigned int part[1024];
+    const int t = threadIdx.x, per = (nchunks + 1023) / 1024;
+    unsigned int s = 0;
+    for (int u = 0; u < per; ++u) {
+        const int i = t * per + u;
+        if (i < nchunks) s += counts[i];
+    }
+    part[t] = s;
+    __syncthreads();
+    if (t == 0) {
+        unsigned int run = 0;
+        for (int i = 0; i < 1024; ++i) {
+            const unsigned int v = part[i];
+            part[i] = run;
+            run += v;
+        }
+        counts[nchunks] = run;
+    }
+    __syncthreads();
+    unsigned int run = part[t];
+    for (int u = 0; u < per; ++u) {
+        const int i = t * per + u;
+        if (i < nchunks) {
+            offsets[i] = run;
+            run += counts[i];
+        }
+    }
+}
+
+// pass 3: write the selected cells of each chunk in index order
+template <int MODE>
+__global__ void __launch_bounds__(kNT) k_cmp_write(Dims d, const int32_t* __restrict__ root,
+                                                   const uint32_t* __restrict__ red, const uint8_t* __restrict__ isexc,
+                                                   const unsigned int* __restrict__ offsets, int* __restrict__ out) {
+    __shared__ unsigned int sh[kNT / 32];
+    const long long c0 = (long long)blockIdx.x * kChunk + (long long)threadIdx.x * (kChunk / kNT);
+    unsigned int n = 0;
+    for (int u = 0; u < kChunk / kNT; ++u) {
+        const long long c = c0 + u;
+        if (c < d.n && pred<MODE>(d, c, root, red, isexc)) ++n;
+    }
+    // exclusive scan of n over the block's threads (in thread order = cell order)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned int x = n;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[wid] = x;
+    __syncthreads();
+    unsigned int wbase = 0;
+    for (int w = 0; w < wid; ++w) wbase += sh[w];
+    unsigned int pos = offsets[blockIdx.x] + wbase + x - n;
+    for (int u = 0; u < kChunk / kNT; ++u) {
+        const long long c = c0 + u;
+        if (c < d.n && pred<MODE>(d, c, root, red, isexc)) out[pos++] = (int)c;
+    }
+}
+
+__global__ void k_mark(int n, const int* __restrict__ cells, uint8_t* __restrict__ flag, uint8_t v) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) flag[cells[t]] = v;
+}
+
+// index of cell c in the sorted exception list (or -1)
+__device__ __forceinline__ int find_exc(const int* __restrict__ exc, int ne, long long c) {
+    int lo = 0, hi = ne - 1;
+    while (lo <= hi) {
+        const int mid = (lo + hi) >> 1;
+        const long long v = exc[mid];
+        if (v == c) return mid;
+        if (v < c) lo = mid + 1;
+        else hi = mid - 1;
+    }
+    return -1;
+}
+
+// exception index behind each face of each fix row (order +x, -x, +y, -y, +z, -z)
+__global__ void k_fix_faces(Dims d, int nf, const int* __restrict__ fcell, const int* __restrict__ exc, int ne,
+                            const uint8_t* __restrict__ isexc, int* __restrict__ fexc) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nf) return;
+    const long long b = fcell[r];
+    int i, j, k;
+    cell_ijk(d, b, i, j, k);
+    const long long nb[6] = {i < d.nx - 1 ? b + 1 : -1, i > 0 ? b - 1 : -1,
+                             j < d.ny - 1 ? b + d.nx : -1, j > 0 ? b - d.nx : -1,
+                             k < d.nz - 1 ? b + d.plane : -1, k > 0 ? b - d.plane : -1};
+    for (int f = 0; f < 6; ++f) fexc[6 * r + f] = (nb[f] >= 0 && isexc[nb[f]]) ? find_exc(exc, ne, nb[f]) : -1;
+}
+
+// compact index of every merge-group cell entry
+__global__ void k_gref(Dims d, int n, const int* __restrict__ gcells, const int* __restrict__ exc, int ne,
+                       long long nh, int* __restrict__ gref) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const long long c = gcells[t];
+    gref[t] = parity(d, c) ? (int)(c >> 1) : (int)(nh + find_exc(exc, ne, c));
+}
+
+// compact dot-exclusion bits: the entry's cell belongs to another cell's group (or has no unknown)
+__global__ void k_cbits(Dims d, long long nh, int ne, const int* __restrict__ exc, const int32_t* __restrict__ root,
+                        uint32_t* __restrict__ bits) {
+    const long long nc = nh + ne, nw = (nc + 31) / 32;
+    for (long long wd = blockIdx.x * (long long)blockDim.x + threadIdx.x; wd < nw; wd += (long long)gridDim.x * blockDim.x) {
+        uint32_t v = 0;
+        for (int u = 0; u < 32; ++u) {
+            const long long t = wd * 32 + u;
+            if (t >= nc) break;
+            const long long c = t < nh ? black_of(d, t) : (long long)exc[t - nh];
+            if (root[c] != (int32_t)c) v |= 1u << u;
+        }
+        bits[wd] = v;
+    }
+}
+
+// inner start: gather the FP64 reduced right-hand side (full grid) onto the compact vectors,
+// normalised; x = 0; p_old = 0 unless the direction is kept; r.r over the entries that count
+__global__ void k_rbc_prep(Dims d, long long nh, int ne, const int* __restrict__ exc, const double* __restrict__ src,
+                           const uint32_t* __restrict__ bits, float* __restrict__ r, float* __restrict__ x,
+                           float* __restrict__ p0, CgScalars* sc, double* __restrict__ partials,
+                           unsigned int* __restrict__ counter) {
+    __shared__ double sh[32];
+    const double rr = sc->rr0;
+    const double inv = (rr > 0.0 && !sc->done) ? 1.0 / sqrt(rr) : 0.0;
+    const bool keep = sc->keep_dir && sc->dir_valid;
+    AccF2 acc;
+    const long long nc = nh + ne;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nc; t += (long long)gridDim.x * blockDim.x) {
+        const long long c = t < nh ? black_of(d, t) : (long long)exc[t - nh];
+        const float v = (float)(src[c] * inv);
+        r[t] = v;
+        x[t] = 0.0f;
+        if (!keep) p0[t] = 0.0f;
+        if (!bit_of(bits, t)) acc.add(v, v);
+    }
+    double tot;
+    if (grid_reduce(acc.value(), partials, counter, sh, &tot)) inner_start_scalars(sc, tot, rr, keep);
+}
+
+// the red formula at an even cell ce with the new black p (same order of operations as k_rbc_tma)
+__device__ __forceinline__ float red_formula(const Dims& d, long long ce, const float* __restrict__ Tx,
+                                             const float* __restrict__ Ty, const float* __restrict__ Tz,
+                                             const float* __restrict__ pn) {
+    int i, j, k;
+    cell_ijk(d, ce, i, j, k);
+    float u = 0.0f;
+    u = fmav(i < d.nx - 1 ? Tx[ce] : 0.0f, i < d.nx - 1 ? pn[(ce + 1) >> 1] : 0.0f, u);
+    u = fmav(i > 0 ? Tx[ce - 1] : 0.0f, i > 0 ? pn[(ce - 1) >> 1] : 0.0f, u);
+    u = fmav(j < d.ny - 1 ? Ty[ce] : 0.0f, j < d.ny - 1 ? pn[(ce + d.nx) >> 1] : 0.0f, u);
+    u = fmav(j > 0 ? Ty[ce - d.nx] : 0.0f, j > 0 ? pn[(ce - d.nx) >> 1] : 0.0f, u);
+    u = fmav(k < d.nz - 1 ? Tz[ce] : 0.0f, k < d.nz - 1 ? pn[(ce + d.plane) >> 1] : 0.0f, u);
+    u = fmav(k > 0 ? Tz[ce - d.plane] : 0.0f, k > 0 ? pn[(ce - d.plane) >> 1] : 0.0f, u);
+    return u;
+}
+
+// Exception rows (threads 0..ne-1): p, x updates and t_e = p_e - sum_f T_f p_nb.  Fix rows
+// (threads ne..ne+nf-1): the black row took the red formula at each neighbouring exception; add
+// T_f (w_red - p_e) back.  p.t of both into pq_raw (after the iteration kernel's sum).
+__global__ void __launch_bounds__(kNT)
+k_rbc_exc(Dims d, long long nh, int ne, const int* __restrict__ exc, int nf, const int* __restrict__ fcell,
+          const int* __restrict__ fexc, const float* __restrict__ Tx, const float* __restrict__ Ty,
+          const float* __restrict__ Tz, const float* __restrict__ r, const float* __restrict__ po,
+          float* __restrict__ pn, float* __restrict__ xv, float* __restrict__ q, CgScalars* sc,
+          double* __restrict__ partials, unsigned int* __restrict__ counter) {
+    __shared__ double sh[32];
+    const float beta = (float)sc->beta, alpha = (float)sc->alpha;
+    AccF2 acc;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ne + nf; t += gridDim.x * blockDim.x) {
+        if (t < ne) {
+            const long long ce = exc[t], ie = nh + t;
+            const float pe = fmav(beta, po[ie], r[ie]);
+            xv[ie] = fmav(alpha, po[ie], xv[ie]);
+            pn[ie] = pe;
+            int i, j, k;
+            cell_ijk(d, ce, i, j, k);
+            float tt = pe;
+            if (i < d.nx - 1) tt = fmav(-Tx[ce], pn[(ce + 1) >> 1], tt);
+            if (i > 0) tt = fmav(-Tx[ce - 1], pn[(ce - 1) >> 1], tt);
+            if (j < d.ny - 1) tt = fmav(-Ty[ce], pn[(ce + d.nx) >> 1], tt);
+            if (j > 0) tt = fmav(-Ty[ce - d.nx], pn[(ce - d.nx) >> 1], tt);
+            if (k < d.nz - 1) tt = fmav(-Tz[ce], pn[(ce + d.plane) >> 1], tt);
+            if (k > 0) tt = fmav(-Tz[ce - d.plane], pn[(ce - d.plane) >> 1], tt);
+            q[ie] = tt;
+            acc.add(pe, tt);
+        } else {
+            const int rr = t - ne;
+            const long long b = fcell[rr];
+            float delta = 0.0f;
+            for (int f = 0; f < 6; ++f) {
+                const int e = fexc[6 * rr + f];
+                if (e < 0) continue;
+                const long long ce = exc[e], ie = nh + e;
+                // coefficient of the face between b and ce: the + face of the lower cell
+                const float T = f == 0 ? Tx[b] : f == 1 ? Tx[ce] : f == 2 ? Ty[b] : f == 3 ? Ty[ce] : f == 4 ? Tz[b] : Tz[ce];
+                const float pe = fmav(beta, po[ie], r[ie]);
+                delta = fmav(T, red_formula(d, ce, Tx, Ty, Tz, pn) - pe, delta);
+            }
+            const long long hb = b >> 1;
+            q[hb] += delta;
+            acc.add(pn[hb], delta);
+        }
+    }
+    double tot;
+    if (grid_reduce(acc.value(), partials, counter, sh, &tot)) sc->pq_raw += tot;
+}
+
+// end of an inner solve: x_f (full grid) = x + alpha p_old of the compact vectors (black cells),
+// 0 on even cells; then the exceptions
+__global__ void k_rbc_expand(Dims d, const float* __restrict__ x, const float* __restrict__ p0,
+                             float* __restrict__ xf, const CgScalars* sc) {
+    const float alpha = (float)sc->alpha;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < d.n; c += (long long)gridDim.x * blockDim.x)
+        xf[c] = parity(d, c) ? __fmaf_rn(alpha, p0[c >> 1], x[c >> 1]) : 0.0f;
+}
+__global__ void k_rbc_expand_exc(long long nh, int ne, const int* __restrict__ exc, const float* __restrict__ x,
+                                 const float* __restrict__ p0, float* __restrict__ xf, const CgScalars* sc) {
+    const float alpha = (float)sc->alpha;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < ne) xf[exc[e]] = __fmaf_rn(alpha, p0[nh + e], x[nh + e]);
+}
+
+}  // namespace
+
+vofp_status rbc_ensure(vofp_ctx* c) {
+    if (c->rbc_built) return VOFP_OK;
+    c->rbc_built = true;
+    c->rbc_ok = false;
+    const Dims d = c->d;
+    // compact tensor maps: N/2 pairs per row, rows of 16-byte multiples (nx multiple of 8);
+    // VOFP_RB_COMPACT=0 keeps the interleaved red-black kernel
+    const char* env = std::getenv("VOFP_RB_COMPACT");
+    if (env && std::strcmp(env, "0") == 0) return VOFP_OK;
+    if (!c->tma_ok[0] || d.nx % 8 != 0 || !c->Txf) return VOFP_OK;
+    cudaStream_t st = c->stream;
+    vofp_status s;
+    const long long nh = d.n / 2;
+    // scratch: exception flags per cell and chunk counts
+    const int nchunks = (int)((d.n + kChunk - 1) / kChunk);
+    uint8_t* isexc = reinterpret_cast<uint8_t*>(c->work);            // N doubles of scratch: N bytes used
+    unsigned int* counts = reinterpret_cast<unsigned int*>(c->partials);
+    unsigned int* offsets = counts + nchunks + 1;
+    if (2 * (nchunks + 1) > 2 * kMaxPartials) return VOFP_OK;
+    // exceptions
+    launch(c, k_cmp_count<0>, nchunks, kNT, st, d, (const int32_t*)c->root, (const uint32_t*)c->red_bits,
+           (const uint8_t*)nullptr, counts);
+    launch(c, k_cmp_scan, 1, 1024, st, nchunks, counts, offsets);
+    unsigned int ne = 0;
+    VOFP_CUDA_TRY(c, cudaMemcpyAsync(&ne, counts + nchunks, sizeof(ne), cudaMemcpyDeviceToHost, st));
+    VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
+    const long long need = nh + ne;
+    if (need > c->rbc_cap) {
+        // grow (once per operator size class): the compact vectors and per-entry bits
+        const long long cap = need + need / 8 + 1024;
+        if ((s = c->alloc(&c->rbc_r, cap)) || (s = c->alloc(&c->rbc_p0, cap)) || (s = c->alloc(&c->rbc_p1, cap)) ||
+            (s = c->alloc(&c->rbc_x, cap)) || (s = c->alloc(&c->rbc_q, cap)) ||
+            (s = c->alloc(&c->rbc_bits, (cap + 31) / 32)) || (s = c->alloc(&c->rbc_exc, cap - nh)) ||
+            (s = c->alloc(&c->rbc_fcell, 6 * (cap - nh))) ||
+            (s = c->alloc(&c->rbc_fexc, 36 * (cap - nh))))
+            return s;
+        c->rbc_cap = cap;
+        for (float* v : {c->rbc_r, c->rbc_p0, c->rbc_p1, c->rbc_x, c->rbc_q})
+            VOFP_CUDA_TRY(c, cudaMemsetAsync(v, 0, sizeof(float) * cap, st));
+    }
+    if (c->ngroups > 0 && !c->rbc_gref) {
+        if ((s = c->alloc(&c->rbc_gref, (long long)d.n / 4 + 1))) return s;
+    }
+    launch(c, k_cmp_write<0>, nchunks, kNT, st, d, (const int32_t*)c->root, (const uint32_t*)c->red_bits,
+           (const uint8_t*)nullptr, (const unsigned int*)offsets, c->rbc_exc);
+    // rows next to exceptions
+    VOFP_CUDA_TRY(c, cudaMemsetAsync(isexc, 0, d.n, st));
+    if (ne > 0) launch(c, k_mark, ceil_div(ne, kNT), kNT, st, (int)ne, (const int*)c->rbc_exc, isexc, (uint8_t)1);
+    launch(c, k_cmp_count<1>, nchunks, kNT, st, d, (const int32_t*)nullptr, (const uint32_t*)nullptr,
+           (const uint8_t*)isexc, counts);
+    launch(c, k_cmp_scan, 1, 1024, st, nchunks, counts, offsets);
+    unsigned int nf = 0;
+    VOFP_CUDA_TRY(c, cudaMemcpyAsync(&nf, counts + nchunks, sizeof(nf), cudaMemcpyDeviceToHost, st));
+    VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
+    if ((long long)nf > 6 * (c->rbc_cap - nh)) return VOFP_OK;    // cannot happen: 6 faces per exception
+    launch(c, k_cmp_write<1>, nchunks, kNT, st, d, (const int32_t*)nullptr, (const uint32_t*)nullptr,
+           (const uint8_t*)isexc, (const unsigned int*)offsets, c->rbc_fcell);
+    if (nf > 0)
+        launch(c, k_fix_faces, ceil_div(nf, kNT), kNT, st, d, (int)nf, (const int*)c->rbc_fcell,
+               (const int*)c->rbc_exc, (int)ne, (const uint8_t*)isexc, c->rbc_fexc);
+    launch(c, k_cbits, grid_n((need + 31) / 32), kNT, st, d, nh, (int)ne, (const int*)c->rbc_exc,
+           (const int32_t*)c->root, c->rbc_bits);
+    if (c->ngroups > 0) {
+        int ncells = 0;
+        VOFP_CUDA_TRY(c, cudaMemcpyAsync(&ncells, c->gptr + c->ngroups, sizeof(int), cudaMemcpyDeviceToHost, st));
+        VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
+        if (ncells > d.n / 4) return VOFP_OK;
+        launch(c, k_gref, ceil_div(ncells, kNT), kNT, st, d, ncells, (const int*)c->gcells, (const int*)c->rbc_exc,
+               (int)ne, nh, c->rbc_gref);
+    }
+    // the iteration kernel's dynamic shared memory and resident blocks
+    constexpr size_t smem = cg_rbc_smem<kRbcStages>();
+    cudaFuncSetAttribute(k_rbc_tma<kRbcStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_rbc_tma<kRbcStages>, kBX * kBY, smem) != cudaSuccess)
+        nb = 0;
+    cudaGetLastError();
+    VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
+    if (nb <= 0) return VOFP_OK;
+    c->rbc_blocks_per_sm = nb;
+    c->rbc_nh = nh;
+    c->rbc_ne = (int)ne;
+    c->rbc_nf = (int)nf;
+    c->rbc_ok = true;
+    return VOFP_OK;
+}
+
+void rbc_prep(vofp_ctx* c, cudaStream_t st, const double* rhs) {
+    const long long nc = c->rbc_nh + c->rbc_ne;
+    launch(c, k_rbc_prep, grid_n(nc), kNT, st, c->d, c->rbc_nh, c->rbc_ne, (const int*)c->rbc_exc, rhs,
+           (const uint32_t*)c->rbc_bits, c->rbc_r, c->rbc_x, c->rbc_p0, c->sc, c->partials, c->counters);
+}
+
+namespace {
+void launch_main(vofp_ctx* c, cudaStream_t st, const float* po, float* pn) {
+    using G = RbcGeom;
+    const Dims d = c->d;
+    const int nh = d.nx / 2;
+    const CUtensorMap *mr = tensor_map_f32_x(c, c->rbc_r, nh, G::BWC, kBY + 4),
+                      *mp = tensor_map_f32_x(c, po, nh, G::BWC, kBY + 4),
+                      *mx = tensor_map_f32(c, c->Txf, G::BWF, kBY + 2), *my = tensor_map_f32(c, c->Tyf, G::BWF, kBY + 3),
+                      *mz = tensor_map_f32(c, c->Tzf, G::BWF, kBY + 2);
+    if (!(mr && mp && mx && my && mz)) {
+        c->set_error("tensor map of the compact red-black vectors could not be built");
+        return;
+    }
+    RbcMaps maps;
+    maps.r = *mr;
+    maps.p = *mp;
+    maps.tx = *mx;
+    maps.ty = *my;
+    maps.tz = *mz;
+    const long long tiles = (long long)ceil_div(nh, G::NP) * ceil_div(d.ny, kBY);
+    int nb = 1, per = 1;
+    plane_split(tiles, d.nz, (long long)num_sms() * c->rbc_blocks_per_sm, false, &nb, &per);
+    launch_smem(c, k_rbc_tma<kRbcStages>, dim3(nb), dim3(kBX, kBY), cg_rbc_smem<kRbcStages>(), st, maps, d, per, po,
+                pn, c->rbc_x, c->rbc_q, c->sc, c->partials, c->counters);
+}
+}  // namespace
+
+void rbc_iteration(vofp_ctx* c, cudaStream_t st, const float* po, float* pn, cudaGraphConditionalHandle h,
+                   int use_h) {
+    launch_main(c, st, po, pn);
+    const int nx = c->rbc_ne + c->rbc_nf;
+    if (nx > 0)
+        launch(c, k_rbc_exc, ceil_div(nx, kNT), kNT, st, c->d, c->rbc_nh, c->rbc_ne, (const int*)c->rbc_exc,
+               c->rbc_nf, (const int*)c->rbc_fcell, (const int*)c->rbc_fexc, (const float*)c->Txf,
+               (const float*)c->Tyf, (const float*)c->Tzf, (const float*)c->rbc_r, po, pn, c->rbc_x, c->rbc_q, c->sc,
+               c->partials, c->counters);
+    if (c->ngroups > 0)
+        launch(c, k_group_patch<float>, ceil_div(c->ngroups, kNT), kNT, st, c->ngroups, (const int*)c->gptr,
+               (const int*)c->rbc_gref, (const double*)c->gcorr, c->rbc_q, (const float*)pn, 1, c->sc, c->partials,
+               c->counters);
+    const long long nc = c->rbc_nh + c->rbc_ne;
+    launch(c, k_cg_update<float, true>, grid_n(nc / 4 + 1), kNT, st, nc, c->rbc_r, (const float*)c->rbc_q,
+           (const uint32_t*)c->rbc_bits, c->sc, c->partials, c->counters, h, use_h);
+}
+
+void rbc_finish_xf(vofp_ctx* c, cudaStream_t st) {
+    launch(c, k_rbc_expand, grid_n(c->d.n), kNT, st, c->d, (const float*)c->rbc_x, (const float*)c->rbc_p0, c->xf,
+           (const CgScalars*)c->sc);
+    if (c->rbc_ne > 0)
+        launch(c, k_rbc_expand_exc, ceil_div(c->rbc_ne, kNT), kNT, st, c->rbc_nh, c->rbc_ne, (const int*)c->rbc_exc,
+               (const float*)c->rbc_x, (const float*)c->rbc_p0, c->xf, (const CgScalars*)c->sc);
+}
+
+void rbc_time_kernel(vofp_ctx* c, cudaStream_t st) { launch_main(c, st, c->rbc_p0, c->rbc_p1); }
+
+}  // namespace vofp

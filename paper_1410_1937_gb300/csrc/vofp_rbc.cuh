@@ -1,0 +1,281 @@
+// Red-black CG iteration on colour-compact vectors (FP32, TMA-fed).
+//
+// CG on the red Schur complement (Eisenstat's form of red-black symmetric Gauss-Seidel) needs the
+// vectors r, p, x, q only on the black unknowns.  With nx even, the cells c = 2h and 2h+1 of a row
+// form pair h = c >> 1, and each pair holds exactly one odd-parity (black) cell: the compact
+// vectors store that cell's value at index h (N/2 entries), followed by the few even-parity cells
+// that belong to merge groups (the "exceptions", unknowns of the black set too).  A red-black
+// iteration then streams half of each vector instead of all of it: about 24 B per cell for the
+// iteration kernel instead of 36.
+//
+// Per plane m, for a tile of 32 pairs (64 cells) x 8 rows:
+//   p = r + beta p_old on the pairs of the tile with a two-pair / two-row halo (compact);
+//   w on the even cell of each pair of the tile with a one-cell halo: the red formula
+//     w = sum_f T_f p_nb for every even cell (all its neighbours are black); an exception's w must
+//     be its own p instead, which the exception kernel corrects afterwards;
+//   t = p - sum_f T_f w_nb on the black cell of each own pair, p.t, x += alpha p_old.
+// The even cell of pair h in row j, plane m sits at x = 2h + rho with rho = (j + m) & 1, the black
+// one at 2h + 1 - rho; x-neighbours of the even cell are the black cells of pairs h - 1 + rho and
+// h + rho, those of the black cell the even cells of pairs h - rho and h + 1 - rho; y- and
+// z-neighbours keep x and so belong to the same pair.  Coefficients stay full-grid arrays.
+#pragma once
+#include "vofp_tma.cuh"
+
+namespace vofp {
+
+struct RbcMaps {
+    CUtensorMap r, p, tx, ty, tz;
+};
+
+constexpr size_t rbc_al(size_t b) { return (b + 127) / 128 * 128; }
+
+struct RbcGeom {
+    static constexpr int NP = kBX;                    // pairs of a tile row (64 cells)
+    static constexpr int HXC = 4;                     // compact box x origin h0 - 4 (16-byte aligned)
+    static constexpr int BWC = NP + 2 * HXC;          // 40 pairs: h0-4 .. h0+35
+    static constexpr int HXF = 4;                     // full-grid box x origin i0 - 4
+    static constexpr int BWF = 2 * NP + 2 * HXF;      // 72 cells: i0-4 .. i0+67
+    static constexpr int RN = BWC * (kBY + 4);        // compact r, p_old: rows j0-2 .. j0+9
+    static constexpr int XN = BWF * (kBY + 2);        // Tx: rows j0-1 .. j0+8
+    static constexpr int YN = BWF * (kBY + 3);        // Ty: rows j0-2 .. j0+8
+    static constexpr int ZN = BWF * (kBY + 2);        // Tz: rows j0-1 .. j0+8
+    static constexpr size_t oR = 0;
+    static constexpr size_t oP = oR + rbc_al(RN * 4);
+    static constexpr size_t oX = oP + rbc_al(RN * 4);
+    static constexpr size_t oY = oX + rbc_al(XN * 4);
+    static constexpr size_t oZ = oY + rbc_al(YN * 4);
+    static constexpr size_t kStage = oZ + rbc_al(ZN * 4);
+    static constexpr uint32_t kTx = (uint32_t)((2 * RN + XN + YN + ZN) * 4);
+    // p ring plane (black cells): index xr <-> pair h0 + xr - 2 (36), row yr <-> j0 + yr - 2 (12)
+    static constexpr int PW = NP + 4;
+    static constexpr int PN = PW * (kBY + 4);
+    // w ring plane (even cells): same pair index, row yw <-> j0 + yw - 1 (10)
+    static constexpr int WN = PW * (kBY + 2);
+    static constexpr int kPItems = PN;                // p values formed per plane
+};
+
+template <int NS>
+constexpr size_t cg_rbc_smem() {
+    using G = RbcGeom;
+    return 128 + NS * G::kStage + 3 * G::PN * 4 + 3 * G::WN * 4 + NS * sizeof(uint64_t);
+}
+
+// A stage of step s carries compact r and p_old of plane s+2 and Tx, Ty, Tz of plane s+1; a step
+// forms p of plane s+2, w of plane s+1 and t of plane s-1 (two barriers per step).
+template <int NS>
+__global__ void __launch_bounds__(kBX* kBY, 3)
+k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_block, const float* __restrict__ pold,
+          float* __restrict__ pnew, float* __restrict__ xv, float* __restrict__ out, CgScalars* __restrict__ sc,
+          double* __restrict__ partials, unsigned int* __restrict__ counter) {
+    using G = RbcGeom;
+    constexpr int PW = G::PW, BWF = G::BWF, BWC = G::BWC;
+    extern __shared__ __align__(128) unsigned char rbc_smem[];
+    unsigned char* base = rbc_smem + ((128u - (smem_addr(rbc_smem) & 127u)) & 127u);
+    float* pring = reinterpret_cast<float*>(base + NS * G::kStage);
+    float* wring = pring + 3 * G::PN;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(wring + 3 * G::WN);
+    __shared__ double sh[32];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + kBX * ty;
+    const float beta = (float)sc->beta, alpha = (float)sc->alpha;
+    AccF2 acc;
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0u, pending = 0u;
+    bool bad = false;
+    auto stage = [&](int s) -> unsigned char* { return base + s * G::kStage; };
+    auto pl = [&](int kk) -> float* { return pring + ((kk + 6) % 3) * G::PN; };
+    auto wl = [&](int kk) -> float* { return wring + ((kk + 6) % 3) * G::WN; };
+
+    // p items: ring index e = tid, tid + 256 of the 36 x 12 plane; box index of the same pair
+    int pi_dst[2], pi_src[2];
+    bool pi_on[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int it = tid + q * kBX * kBY;
+        pi_on[q] = it < G::kPItems;
+        const int xr = pi_on[q] ? it % PW : 0, yr = pi_on[q] ? it / PW : 0;
+        pi_dst[q] = yr * PW + xr;
+        pi_src[q] = yr * BWC + xr + 2;
+    }
+    // own pair xr = tx + 2 in w row ty + 1; ring items (threads 0..79): the pairs of rows j0-1 and
+    // j0+8 (threads 0..63) and the pairs h0-1 and h0+32 of rows j0 .. j0+7 (threads 64..79)
+    const int xo = tx + 2, yo = ty + 1;
+    int rx = 0, ry = 0;
+    const bool has_ring = tid < 80;
+    if (tid < 32) { rx = tid + 2; ry = 0; }
+    else if (tid < 64) { rx = tid - 32 + 2; ry = kBY + 1; }
+    else if (tid < 72) { rx = 1; ry = 1 + (tid - 64); }
+    else if (tid < 80) { rx = PW - 2; ry = 1 + (tid - 72); }
+
+    const int nh = d.nx >> 1;
+    const int tiles_x = (nh + G::NP - 1) / G::NP;
+    const long long ntiles = (long long)tiles_x * ((d.ny + kBY - 1) / kBY);
+    const long long total = ntiles * d.nz;
+    const long long w0 = min((long long)blockIdx.x * per_block, total);
+    const long long w1 = min(w0 + per_block, total);
+    for (long long w = w0; w < w1 && !bad;) {
+        const long long tile_id = w / d.nz;
+        const int k0 = int(w - tile_id * d.nz);
+        const int k1 = (int)min((long long)d.nz, (long long)k0 + (w1 - w));
+        w += k1 - k0;
+        const int h0 = int(tile_id % tiles_x) * G::NP, j0 = int(tile_id / tiles_x) * kBY;
+        const int i0 = 2 * h0;
+        const int h = h0 + tx, j = j0 + ty;
+        const bool inside = h < nh && j < d.ny;
+        const long long own = inside ? h + (long long)nh * j : 0;   // compact index within a plane
+        const long long cplane = (long long)nh * d.ny;
+        const int s_first = k0 - 4, s_last = k1 - 1;
+        auto slot = [&](int s) { return (s - s_first) % NS; };
+        auto issue = [&](int s) {
+            const int q = slot(s);
+            pending |= 1u << q;
+            if (tid == 0) {
+                unsigned char* b = stage(q);
+                mbar_expect_tx(&bars[q], G::kTx);
+                tma_load_3d(b + G::oR, &maps.r, &bars[q], h0 - G::HXC, j0 - 2, s + 2);
+                tma_load_3d(b + G::oP, &maps.p, &bars[q], h0 - G::HXC, j0 - 2, s + 2);
+                tma_load_3d(b + G::oX, &maps.tx, &bars[q], i0 - G::HXF, j0 - 1, s + 1);
+                tma_load_3d(b + G::oY, &maps.ty, &bars[q], i0 - G::HXF, j0 - 2, s + 1);
+                tma_load_3d(b + G::oZ, &maps.tz, &bars[q], i0 - G::HXF, j0 - 1, s + 1);
+            }
+        };
+        auto wait = [&](int s) -> bool {
+            const int q = slot(s);
+            const bool ok = mbar_wait_bounded(&bars[q], (phase >> q) & 1u);
+            phase ^= 1u << q;
+            pending &= ~(1u << q);
+            return ok;
+        };
+        // w of the even cell of pair index xr in w row yw, plane m; tzm: the pair's Tz of plane
+        // m-1 (both cells); tzp returns the pair's Tz of plane m
+        auto w_even = [&](const unsigned char* b, int m, int xr, int yw, float2 tzm, float2& tzp) -> float {
+            const float* X = reinterpret_cast<const float*>(b + G::oX);
+            const float* Y = reinterpret_cast<const float*>(b + G::oY);
+            const float* Z = reinterpret_cast<const float*>(b + G::oZ);
+            const float* P0 = pl(m);
+            const int rho = (j0 + yw - 1 + m) & 1;
+            const int yr = yw + 1, e = yr * PW + xr;
+            const int xb = 2 * xr + rho;                  // full-grid box index of the even cell
+            tzp = *reinterpret_cast<const float2*>(Z + yw * BWF + 2 * xr);
+            float u = 0.0f;
+            u = fmav(X[yw * BWF + xb], P0[e + rho], u);
+            u = fmav(X[yw * BWF + xb - 1], P0[e - 1 + rho], u);
+            u = fmav(Y[yr * BWF + xb], P0[e + PW], u);
+            u = fmav(Y[(yr - 1) * BWF + xb], P0[e - PW], u);
+            u = fmav(rho ? tzp.y : tzp.x, pl(m + 1)[e], u);
+            u = fmav(rho ? tzm.y : tzm.x, pl(m - 1)[e], u);
+            return u;
+        };
+
+        // coefficients of the own black cell kept from plane m's w step to its t step
+        struct Co {
+            float tx, txl, ty, tyd, tz, tzm, p;
+        };
+        Co sa{}, sb{};
+        float2 own_tzm = make_float2(0.f, 0.f), ring_tzm = own_tzm;
+        float xa = 0.f, pa = 0.f, xb2 = 0.f, pb = 0.f;
+
+        __syncthreads();
+        if (tid == 0) fence_proxy_async_smem();
+        for (int s = s_first; s <= min(s_first + NS - 1, s_last); ++s) issue(s);
+        for (int s = s_first; s <= k1; ++s) {
+            if (s - 1 >= s_first && s - 1 + NS <= s_last) {
+                if (tid == 0) fence_proxy_async_smem();
+                issue(s - 1 + NS);
+            }
+            bool ok = true;
+            if (s <= s_last) ok = wait(s);
+            const unsigned char* b = stage(slot(s));
+            // P1: p of plane s+2
+            if (s <= s_last) {
+                const float* R = reinterpret_cast<const float*>(b + G::oR);
+                const float* P = reinterpret_cast<const float*>(b + G::oP);
+                float* op = pl(s + 2);
+#pragma unroll
+                for (int q = 0; q < 2; ++q)
+                    if (pi_on[q]) op[pi_dst[q]] = fmav(beta, P[pi_src[q]], R[pi_src[q]]);
+            }
+            // P1: t of plane s-1 on the black cell of the own pair
+            const int m = s - 1;
+            if (m >= k0 && m < k1 && inside) {
+                const int rho = (j + m) & 1;
+                const float* W0 = wl(m);
+                const int e = yo * PW + xo;
+                float t = sa.p;
+                t = fmav(-sa.tx, W0[e + 1 - rho], t);
+                t = fmav(-sa.txl, W0[e - rho], t);
+                t = fmav(-sa.ty, W0[e + PW], t);
+                t = fmav(-sa.tyd, W0[e - PW], t);
+                t = fmav(-sa.tz, wl(m + 1)[e], t);
+                t = fmav(-sa.tzm, wl(m - 1)[e], t);
+                const long long c = (long long)m * cplane + own;
+                out[c] = t;
+                pnew[c] = sa.p;
+                xv[c] = fmav(alpha, pa, xa);
+                acc.add(sa.p, t);
+            }
+            xa = xb2;
+            pa = pb;
+            xb2 = 0.f;
+            pb = 0.f;
+            if (s + 1 >= k0 && s + 1 < k1 && inside) {
+                const long long c = (long long)(s + 1) * cplane + own;
+                xb2 = xv[c];
+                pb = pold[c];
+            }
+            if (__syncthreads_or(!ok)) {
+                bad = true;
+                break;
+            }
+            // P2: w of plane s+1 (even cells of the own pair and the ring); before plane k0-1 only
+            // the pair's Tz is carried
+            if (s <= s_last && s + 1 >= k0 - 2) {
+                const int mw = s + 1;
+                const float* Z = reinterpret_cast<const float*>(b + G::oZ);
+                if (mw >= k0 - 1) {
+                    float2 tzp;
+                    wl(mw)[yo * PW + xo] = w_even(b, mw, xo, yo, own_tzm, tzp);
+                    // the own black cell's coefficients and p for its t two steps later
+                    const int rho = (j + mw) & 1;
+                    const float* X = reinterpret_cast<const float*>(b + G::oX);
+                    const float* Y = reinterpret_cast<const float*>(b + G::oY);
+                    const int xbb = 2 * xo + 1 - rho;      // full-grid box index of the black cell
+                    Co co;
+                    co.tx = X[yo * BWF + xbb];
+                    co.txl = X[yo * BWF + xbb - 1];
+                    co.ty = Y[(yo + 1) * BWF + xbb];
+                    co.tyd = Y[yo * BWF + xbb];
+                    co.tz = rho ? tzp.x : tzp.y;
+                    co.tzm = rho ? own_tzm.x : own_tzm.y;
+                    co.p = pl(mw)[(yo + 1) * PW + xo];
+                    own_tzm = tzp;
+                    sa = sb;
+                    sb = co;
+                    if (has_ring) {
+                        float2 tzr;
+                        wl(mw)[ry * PW + rx] = w_even(b, mw, rx, ry, ring_tzm, tzr);
+                        ring_tzm = tzr;
+                    }
+                } else {
+                    own_tzm = *reinterpret_cast<const float2*>(Z + yo * BWF + 2 * xo);
+                    if (has_ring) ring_tzm = *reinterpret_cast<const float2*>(Z + ry * BWF + 2 * rx);
+                }
+            } else {
+                sa = sb;
+            }
+            __syncthreads();
+        }
+    }
+    if (bad) {
+        for (int s = 0; s < NS; ++s)
+            if (pending & (1u << s)) mbar_wait_bounded(&bars[s], (phase >> s) & 1u);
+        if (tid == 0) atomicCAS(&sc->status, (int)VOFP_OK, (int)VOFP_ERR_DEVICE_TIMEOUT);
+    }
+    double tot;
+    if (grid_reduce(acc.value(), partials, counter, sh, &tot)) sc->pq_raw = tot;
+}
+
+}  // namespace vofp

@@ -293,26 +293,7 @@ __global__ void k_inner_prep(long long n, const double* __restrict__ r, const ui
         if (!is_slave(bits, c)) acc.add(v, v);
     }
     double t;
-    if (grid_reduce(acc.value(), partials, counter, sh, &t)) {
-        const double scale_old = sc->scale;
-        const double scale_new = (rr > 0.0 && !sc->done) ? sqrt(rr) : 0.0;
-        sc->scale = scale_new;
-        // the last refinement step only needs the reduction that reaches rtol (with margin)
-        const double need = sc->rnorm2 > 0.0 ? 0.3 * sc->rtol * sqrt(sc->ref2 / sc->rnorm2) : 1.0;
-        sc->inner_target = fmax(sc->inner_rtol, fmin(need, 0.5));
-        double beta = 0.0;
-        if (keep && scale_old > 0.0 && sc->rr_prev > 0.0) {
-            beta = scale_new / (scale_old * sc->rr_prev);
-            if (!isfinite(beta)) beta = 0.0;
-        }
-        sc->rr = t;
-        sc->alpha = 0.0;
-        sc->beta = beta;
-        sc->iter = 0;
-        sc->inner_done = 0;
-        sc->rr0 = t;
-        sc->dir_valid = sc->keep_dir;
-    }
+    if (grid_reduce(acc.value(), partials, counter, sh, &t)) inner_start_scalars(sc, t, rr, keep);
 }
 
 // end of an inner solve: x_f += alpha p_f (pending), x_t += ||r|| * x_f in FP64
@@ -593,8 +574,11 @@ void launch_outer_head(vofp_ctx* c, cudaStream_t st, bool rb, cudaGraphCondition
            (const double*)c->sq, (const uint32_t*)c->slave_bits, c->r, c->sc, c->partials, c->counters, ho, hi, use_h);
     if (rb) {
         launch_reduced_rhs(c, st);
-        launch(c, k_inner_prep, stream_grid(c->d.n), kNT, st, c->d.n, (const double*)c->q,
-               (const uint32_t*)c->excl_bits, c->rf, c->xf, c->pf0, c->sc, c->partials, c->counters);
+        if (c->rbc_ok)
+            rbc_prep(c, st, c->q);
+        else
+            launch(c, k_inner_prep, stream_grid(c->d.n), kNT, st, c->d.n, (const double*)c->q,
+                   (const uint32_t*)c->excl_bits, c->rf, c->xf, c->pf0, c->sc, c->partials, c->counters);
     } else {
         launch(c, k_inner_prep, stream_grid(c->d.n), kNT, st, c->d.n, (const double*)c->r,
                (const uint32_t*)c->slave_bits, c->rf, c->xf, c->pf0, c->sc, c->partials, c->counters);
@@ -605,6 +589,11 @@ int outer_head_kernels(const vofp_ctx* c, bool rb) {
     return 1 + g + 1 + (rb ? 2 + g : 0) + 1;
 }
 void launch_inner_body(vofp_ctx* c, cudaStream_t st, int U, bool rb, cudaGraphConditionalHandle hi, int use_h) {
+    if (rb && c->rbc_ok) {
+        for (int u = 0; u < U; ++u)
+            rbc_iteration(c, st, (u % 2 == 0) ? c->rbc_p0 : c->rbc_p1, (u % 2 == 0) ? c->rbc_p1 : c->rbc_p0, hi, use_h);
+        return;
+    }
     for (int u = 0; u < U; ++u) {
         float* po = (u % 2 == 0) ? c->pf0 : c->pf1;
         float* pn = (u % 2 == 0) ? c->pf1 : c->pf0;
@@ -614,7 +603,11 @@ void launch_inner_body(vofp_ctx* c, cudaStream_t st, int U, bool rb, cudaGraphCo
 // Mixed outer step, last part: fold the inner solution into x_t (FP64).
 void launch_outer_tail(vofp_ctx* c, cudaStream_t st, bool rb) {
     if (rb) {
-        launch(c, k_inner_xf, stream_grid(c->d.n), kNT, st, c->d.n, c->xf, (const float*)c->pf0, (const CgScalars*)c->sc);
+        if (c->rbc_ok)
+            rbc_finish_xf(c, st);
+        else
+            launch(c, k_inner_xf, stream_grid(c->d.n), kNT, st, c->d.n, c->xf, (const float*)c->pf0,
+                   (const CgScalars*)c->sc);
         launch(c, k_inner_finish_rb, rows_grid(c, kNT), dim3(kNT), st, c->d, (const double*)c->Txs,
                (const double*)c->Tys, (const double*)c->Tzs, (const uint32_t*)c->red_bits, (const float*)c->xf,
                (const double*)c->r, c->xt, (const CgScalars*)c->sc);
@@ -623,7 +616,15 @@ void launch_outer_tail(vofp_ctx* c, cudaStream_t st, bool rb) {
                (const CgScalars*)c->sc);
     }
 }
-int outer_tail_kernels(bool rb) { return rb ? 2 : 1; }
+int outer_tail_kernels(const vofp_ctx* c, bool rb) {
+    return rb ? (c->rbc_ok ? 2 + (c->rbc_ne > 0 ? 1 : 0) : 2) : 1;
+}
+// kernels of one mixed inner iteration
+int inner_iteration_kernels(const vofp_ctx* c, bool rb) {
+    if (rb && c->rbc_ok)
+        return 2 + (c->rbc_ne + c->rbc_nf > 0 ? 1 : 0) + (c->ngroups > 0 ? 1 : 0);
+    return iteration_kernels(c, rb);
+}
 
 int graph_key(int U, bool rb) { return U * 2 + (rb ? 1 : 0); }
 
@@ -811,6 +812,8 @@ vofp_status solve(vofp_ctx* c, const double* b, double* x, const vofp_solve_opts
     if (o->mode == VOFP_MODE_FCG_NN) return solve_fcg(c, b, x, o, info);
     vofp_status s = ensure_workspace(c);
     if (s) return s;
+    // colour-compact vectors of the red-black inner solve (built once per operator)
+    if (o->mode == VOFP_MODE_MIXED && o->precond == VOFP_PRECOND_RBSGS && (s = rbc_ensure(c))) return s;
     const long long N = c->d.n;
     cudaStream_t st = c->stream;
     const int U = o->check_every > 0 ? o->check_every : 8;
@@ -923,7 +926,7 @@ vofp_status solve(vofp_ctx* c, const double* b, double* x, const vofp_solve_opts
         // kernels executed by the graph: whole bodies of U iterations
         if (mixed)
             c->launches += (long long)(h.outer + 1) * outer_head_kernels(c, rb) +
-                           (long long)h.outer * outer_tail_kernels(rb) + h.iter_total * iteration_kernels(c, rb);
+                           (long long)h.outer * outer_tail_kernels(c, rb) + h.iter_total * inner_iteration_kernels(c, rb);
         else
             c->launches += (h.iter_total / U) * fp64_body_kernels(c, U, rb);
     }
@@ -1149,7 +1152,18 @@ vofp_status time_iteration_kernels(vofp_ctx* c, int precision, bool rb, int reps
         return VOFP_OK;
     };
     const uint32_t* bits = rb ? c->excl_bits : c->slave_bits;
-    if (precision == 32) {
+    if (precision == 32 && rb && (s = rbc_ensure(c))) return s;
+    if (precision == 32 && rb && c->rbc_ok) {
+        // the colour-compact red-black iteration kernel and the update on the compact vectors
+        const long long nc = c->rbc_nh + c->rbc_ne;
+        auto stn = [&]() { rbc_time_kernel(c, st); };
+        auto upd = [&]() {
+            launch(c, k_cg_update<float, false>, stream_grid(nc / 4 + 1), kNT, st, nc, c->rbc_r,
+                   (const float*)c->rbc_q, (const uint32_t*)c->rbc_bits, c->sc, c->partials, c->counters,
+                   (cudaGraphConditionalHandle)0, 0);
+        };
+        if ((s = timed(stn, &t1)) || (s = timed(upd, &t2))) return s;
+    } else if (precision == 32) {
         auto stn = [&]() {
             if (rb)
                 launch_cg_rb<float>(c, st, c->Txf, c->Tyf, c->Tzf, c->rf, c->pf0, c->pf1, c->xf, c->qf);

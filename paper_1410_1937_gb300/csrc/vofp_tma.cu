@@ -36,14 +36,15 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // bytes from DRAM that are evicted before those tiles run (measured: 256 B promotion read 1.9x
 // the algorithmic bytes and ran 25% slower on the FP32 stencil).
 template <typename V>
-const CUtensorMap* tensor_map(vofp_ctx* c, const V* ptr, int bw, int bh) {
-    const auto key = std::make_tuple((const void*)ptr, bw, bh);
+const CUtensorMap* tensor_map(vofp_ctx* c, const V* ptr, int bw, int bh, int nxe = 0) {
+    if (nxe <= 0) nxe = c->d.nx;
+    const auto key = std::make_tuple((const void*)ptr, bw, bh * 65536 + (nxe == c->d.nx ? 0 : 1));
     auto it = c->tma_maps.find(key);
     if (it != c->tma_maps.end()) return &it->second;
     CUtensorMap m;
     std::memset(&m, 0, sizeof(m));
-    const cuuint64_t dims[3] = {(cuuint64_t)c->d.nx, (cuuint64_t)c->d.ny, (cuuint64_t)c->d.nz};
-    const cuuint64_t strides[2] = {(cuuint64_t)c->d.nx * sizeof(V), (cuuint64_t)c->d.plane * sizeof(V)};
+    const cuuint64_t dims[3] = {(cuuint64_t)nxe, (cuuint64_t)c->d.ny, (cuuint64_t)c->d.nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)nxe * sizeof(V), (cuuint64_t)nxe * c->d.ny * sizeof(V)};
     const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1u};
     const cuuint32_t estr[3] = {1u, 1u, 1u};
     const CUresult r = tensor_map_encoder()(
@@ -83,6 +84,10 @@ bool launch_tma(vofp_ctx* c, cudaStream_t st, const V* Tx, const V* Ty, const V*
 
 const CUtensorMap* tensor_map_f32(vofp_ctx* c, const float* ptr, int bw, int bh) {
     return tensor_map_encoder() ? tensor_map(c, ptr, bw, bh) : nullptr;
+}
+const CUtensorMap* tensor_map_f32_x(vofp_ctx* c, const float* ptr, int nxe, int bw, int bh) {
+    if (!tensor_map_encoder() || (nxe * sizeof(float)) % 16 != 0) return nullptr;
+    return tensor_map(c, ptr, bw, bh, nxe);
 }
 
 template <typename V>

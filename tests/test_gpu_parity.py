@@ -273,6 +273,30 @@ def test_projection_in_place_and_prescribed_wall_flux(vofp, oracle):
     assert mx <= 1e-9 * fl
 
 
+@pytest.mark.parametrize("case", ["c1-small", "hull-small"])
+def test_compact_red_black_matches_interleaved(vofp, oracle, monkeypatch, case):
+    """Mixed red-black solve on colour-compact vectors (black cell of each x pair, then the
+    even-parity merge-group cells) against the interleaved red-black kernel: the same Schur-
+    complement CG, both to rtol by the oracle's own residual."""
+    prob = CASES[case]()
+    res = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("VOFP_RB_COMPACT", flag)
+        ctx, t = vofp.context_for(prob)
+        b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
+        x, info = ctx.vofp_solve(b, rtol=1e-8, mode=vofp.MODE_MIXED, precond=vofp.PRECOND_RBSGS)
+        assert info["status"] == 0, info
+        res[flag] = (host(x, prob.shape), info)
+        ctx.close()
+    it1, it0 = res["1"][1]["iterations"], res["0"][1]["iterations"]
+    assert abs(it1 - it0) <= max(8, 0.05 * it0), (it1, it0)
+    s = oracle.System(prob)
+    for flag in ("1", "0"):
+        assert s.residual(res[flag][0]) <= 1e-8 * 1.01
+    x1, x0 = res["1"][0], res["0"][0]
+    assert np.linalg.norm(x1 - x0) / np.linalg.norm(x0) <= 1e-6
+
+
 def test_unaligned_rows_use_register_stencil(vofp):
     """Rows of 37 FP32 values are not a multiple of 16 bytes: no tensor map, register kernel."""
     prob = ragged_sphere()
