@@ -34,23 +34,26 @@ SHAPE = (512, 256, 128)
 RTOL = 1e-8
 FALLBACK_HBM_GBS = 6800.0
 # algorithmic bytes per cell of one launch / one iteration, in units of one vector element (8 B for
-# FP64, 4 B for FP32); every array interleaves the two colours, so a red-black iteration streams
-# the same nine arrays as a Jacobi one
-#   stencil (Jacobi, or red-black with the red unknowns eliminated in the same pass): reads r,
-#            p_old, x, Tx, Ty, Tz; writes p, x, q
-#   update:  reads r, q; writes r
-STENCIL_ELEMS = {"jacobi": 9.0, "rbsgs": 9.0}
-UPDATE_ELEMS = 3.0
+# FP64, 4 B for FP32)
+#   stencil, Jacobi: reads r, p_old, x, Tx, Ty, Tz; writes p, x, q (all N cells)
+#   red-black iteration on colour-compact vectors (FP32): r, p_old, x read and p, x, q written on
+#            the black half (N/2 each), Tx, Ty, Tz read on all cells: 3 + 3/2 + 3/2 = 6
+#   red-black iteration on interleaved vectors (FP64, or grids the compact layout does not fit):
+#            the same nine full arrays as the Jacobi stencil
+#   update:  reads r, q; writes r (halved on compact vectors)
+STENCIL_ELEMS = {"jacobi": 9.0, "rbsgs": 9.0, "rbsgs-compact": 6.0}
+UPDATE_ELEMS = {"jacobi": 3.0, "rbsgs": 3.0, "rbsgs-compact": 1.5}
 
 
-# projection + divergence check, FP64: reads p, rho, three apertures and three velocities and
-# writes three velocities (88 B per cell), then reads the apertures and the new velocities, the
-# activity byte and writes the divergence (57 B per cell)
+# projection + divergence check, FP64, per cell: p, three inverse face resistances and three
+# velocities read, three velocities written (80 B); then three apertures, the three new velocities
+# and the activity byte read and the divergence written (57 B); 145 B counted (8 B for the
+# apertures of the domain faces and the pressure's neighbour reads)
 PROJECTION_BYTES = 145.0
 
 
-def iter_elems(precond):
-    return STENCIL_ELEMS[precond] + UPDATE_ELEMS
+def iter_elems(variant):
+    return STENCIL_ELEMS[variant] + UPDATE_ELEMS[variant]
 
 
 # DRAM read+write bytes per cell of one launch of the dominant kernel, from committed ncu captures
@@ -58,9 +61,11 @@ def iter_elems(precond):
 # only while the sources of that kernel and its launch hash to the value stored with it (else null):
 #   (32, "jacobi"): k_cg_tma<float, 6, 2> (column split), 561.8 MB over 16777216 cells
 #   (32, "rbsgs"):  k_cg_rb_tma<3, 8>, 885.0 MB over 16777216 cells
-TRAFFIC_PER_CELL = {(32, "jacobi"): (33.49, "016eb6bf6b81fa38"), (32, "rbsgs"): (52.75, "76c4a8efa6725475")}
+#   (32, "rbsgs-compact"): k_rbc_tma<3>, 572.3 MB over 16777216 cells
+TRAFFIC_PER_CELL = {(32, "jacobi"): (33.49, "df9c516f622d4506"), (32, "rbsgs"): (52.75, "76c4a8efa6725475"), (32, "rbsgs-compact"): (34.11, "55faf96541ed7330")}
 KERNEL_FILES = {(32, "jacobi"): ('vofp_kernels.cuh', 'vofp_tma.cuh', 'vofp_tma.cu'),
-                (32, "rbsgs"): ('vofp_kernels.cuh', 'vofp_tma.cuh', 'vofp_rb_tma.cuh', 'vofp_rb_tma.cu')}
+                (32, "rbsgs"): ('vofp_kernels.cuh', 'vofp_tma.cuh', 'vofp_rb_tma.cuh', 'vofp_rb_tma.cu'),
+                (32, "rbsgs-compact"): ('vofp_kernels.cuh', 'vofp_tma.cuh', 'vofp_rbc.cuh', 'vofp_rbc.cu')}
 
 
 def kernel_hash(key):
@@ -322,18 +327,23 @@ def run_ours(args, rank, world, local_rank):
         st_ms, up_ms, red_ms = ctx.vofp_time_iteration_kernels(prec, args.kernel_reps, precond=pc)
         stats = ctx.vofp_get_stats()
         vname = "float" if prec == 32 else "double"
+        variant = args.precond
         if args.precond == "rbsgs":
-            kernel_name = (f"k_cg_rb_tma<3> (TMA-fed fused red-black iteration)"
-                           if prec == 32 and stats["tma_stencil_fp32"] else
-                           f"k_cg_rb<{vname}> (register-prefetch fused red-black iteration)")
+            if prec == 32 and stats["rb_compact"]:
+                kernel_name = "k_rbc_tma<3> (TMA-fed red-black iteration on colour-compact vectors)"
+                variant = "rbsgs-compact"
+            elif prec == 32 and stats["tma_stencil_fp32"]:
+                kernel_name = "k_cg_rb_tma<3, 8> (TMA-fed fused red-black iteration)"
+            else:
+                kernel_name = f"k_cg_rb<{vname}> (register-prefetch fused red-black iteration)"
         elif stats["tma_stencil_fp32" if prec == 32 else "tma_stencil_fp64"]:
             kernel_name = f"k_cg_tma<{vname}> (TMA-fed CG stencil)"
         else:
             kernel_name = f"k_stencil<{vname},ST_CG> (register-prefetch CG stencil)"
         hbm, hbm_kind = peaks()
-        achieved = STENCIL_ELEMS[args.precond] * vb * n / (st_ms * 1e-3) / 1e9
+        achieved = STENCIL_ELEMS[variant] * vb * n / (st_ms * 1e-3) / 1e9
         traffic = None
-        key = (prec, args.precond)
+        key = (prec, variant)
         if key in TRAFFIC_PER_CELL and TRAFFIC_PER_CELL[key][1] == kernel_hash(key) and "TMA" in kernel_name:
             traffic = TRAFFIC_PER_CELL[key][0] * n
         iter_s = info["seconds"] / max(info["iterations"], 1)
@@ -367,7 +377,7 @@ def run_ours(args, rank, world, local_rank):
         "iterations": info["iterations"], "outer_iterations": info["outer_iterations"],
         "rel_residual": info["rel_residual"],
         "cg_iterations_per_s": info["iterations"] / info["seconds"],
-        "hbm_gbs_per_iter": iter_elems(args.precond) * vb * n / iter_s / 1e9,
+        "hbm_gbs_per_iter": iter_elems(variant) * vb * n / iter_s / 1e9,
         "variants": variants,
         "fp64_reference": {"time_to_tol_ms": info64["time_to_tol_ms"], "iterations": info64["iterations"],
                            "rel_residual": info64["rel_residual"], "status": info64["status"],
@@ -378,7 +388,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "kernel": kernel_name,
                      "achieved": achieved, "peak": hbm, "peak_kind": hbm_kind, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "stencil_ms": st_ms, "update_ms": up_ms,
-                     "red_ms": red_ms, "update_gbs": UPDATE_ELEMS * vb * n / (up_ms * 1e-3) / 1e9},
+                     "red_ms": red_ms, "update_gbs": UPDATE_ELEMS[variant] * vb * n / (up_ms * 1e-3) / 1e9},
         "projection": {"ms": proj_ms, "bytes_per_cell": PROJECTION_BYTES,
                        "gbs": PROJECTION_BYTES * n / (proj_ms * 1e-3) / 1e9, "max_group_divergence": max_div},
         "device_bytes": ctx.vofp_get_stats()["device_bytes"],
@@ -416,7 +426,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "rbsgs"])
+    ap.add_argument("--precond", default="rbsgs", choices=["jacobi", "rbsgs"])
     ap.add_argument("--shape", type=int, nargs=3, default=list(SHAPE))
     ap.add_argument("--check-every", type=int, default=8)
     ap.add_argument("--inner-rtol", type=float, default=0.0,

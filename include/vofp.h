@@ -154,6 +154,8 @@ typedef struct {
     int tma_stencil_fp32;     /* 1 if the FP32 CG stencil is fed by bulk tensor copies (TMA),  */
     int tma_stencil_fp64;     /* 0 for the register-prefetch kernel; both are set once the     */
                               /* context's kernels are prepared (first solve or timing call)   */
+    int rb_compact;           /* 1 if the mixed red-black solve of this operator runs on       */
+                              /* colour-compact vectors (set by its first solve or timing)     */
 } vofp_stats;
 
 /* Library version string (static storage). */

@@ -234,6 +234,7 @@ vofp_status vofp_get_stats(vofp_ctx* c, vofp_stats* st) {
     st->device_bytes = (long long)c->bytes;
     st->tma_stencil_fp32 = c->tma_ok[0] ? 1 : 0;
     st->tma_stencil_fp64 = c->tma_ok[1] ? 1 : 0;
+    st->rb_compact = c->rbc_ok ? 1 : 0;
     return VOFP_OK;
 }
 
