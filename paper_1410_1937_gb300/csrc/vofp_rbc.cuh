@@ -149,13 +149,13 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_bloc
             pending &= ~(1u << q);
             return ok;
         };
-        // w of the even cell of pair index xr in w row yw, plane m; tzm: the pair's Tz of plane
-        // m-1 (both cells); tzp returns the pair's Tz of plane m
-        auto w_even = [&](const unsigned char* b, int m, int xr, int yw, float2 tzm, float2& tzp) -> float {
+        // w of the even cell of pair index xr in w row yw, plane m (p ring planes P0 = m, Pu = m+1,
+        // Pd = m-1); tzm: the pair's Tz of plane m-1 (both cells); tzp returns the pair's Tz of plane m
+        auto w_even = [&](const unsigned char* b, int m, int xr, int yw, float2 tzm, float2& tzp, const float* P0,
+                          const float* Pu, const float* Pd) -> float {
             const float* X = reinterpret_cast<const float*>(b + G::oX);
             const float* Y = reinterpret_cast<const float*>(b + G::oY);
             const float* Z = reinterpret_cast<const float*>(b + G::oZ);
-            const float* P0 = pl(m);
             const int rho = (j0 + yw - 1 + m) & 1;
             const int yr = yw + 1, e = yr * PW + xr;
             const int xb = 2 * xr + rho;                  // full-grid box index of the even cell
@@ -165,8 +165,8 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_bloc
             u = fmav(X[yw * BWF + xb - 1], P0[e - 1 + rho], u);
             u = fmav(Y[yr * BWF + xb], P0[e + PW], u);
             u = fmav(Y[(yr - 1) * BWF + xb], P0[e - PW], u);
-            u = fmav(rho ? tzp.y : tzp.x, pl(m + 1)[e], u);
-            u = fmav(rho ? tzm.y : tzm.x, pl(m - 1)[e], u);
+            u = fmav(rho ? tzp.y : tzp.x, Pu[e], u);
+            u = fmav(rho ? tzm.y : tzm.x, Pd[e], u);
             return u;
         };
 
@@ -181,6 +181,10 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_bloc
         __syncthreads();
         if (tid == 0) fence_proxy_async_smem();
         for (int s = s_first; s <= min(s_first + NS - 1, s_last); ++s) issue(s);
+        // ring slots of planes s, s+1, s+2 (slot s+2 of w still holds plane s-1 until P2), rotated
+        // once per step
+        float *Pa = pl(s_first), *Pb = pl(s_first + 1), *Pc = pl(s_first + 2);
+        float *Wa = wl(s_first), *Wb = wl(s_first + 1), *Wc = wl(s_first + 2);
         for (int s = s_first; s <= k1; ++s) {
             if (s - 1 >= s_first && s - 1 + NS <= s_last) {
                 if (tid == 0) fence_proxy_async_smem();
@@ -193,7 +197,7 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_bloc
             if (s <= s_last) {
                 const float* R = reinterpret_cast<const float*>(b + G::oR);
                 const float* P = reinterpret_cast<const float*>(b + G::oP);
-                float* op = pl(s + 2);
+                float* op = Pc;
 #pragma unroll
                 for (int q = 0; q < 2; ++q)
                     if (pi_on[q]) op[pi_dst[q]] = fmav(beta, P[pi_src[q]], R[pi_src[q]]);
@@ -202,15 +206,15 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_bloc
             const int m = s - 1;
             if (m >= k0 && m < k1 && inside) {
                 const int rho = (j + m) & 1;
-                const float* W0 = wl(m);
+                const float* W0 = Wc;
                 const int e = yo * PW + xo;
                 float t = sa.p;
                 t = fmav(-sa.tx, W0[e + 1 - rho], t);
                 t = fmav(-sa.txl, W0[e - rho], t);
                 t = fmav(-sa.ty, W0[e + PW], t);
                 t = fmav(-sa.tyd, W0[e - PW], t);
-                t = fmav(-sa.tz, wl(m + 1)[e], t);
-                t = fmav(-sa.tzm, wl(m - 1)[e], t);
+                t = fmav(-sa.tz, Wa[e], t);
+                t = fmav(-sa.tzm, Wb[e], t);
                 const long long c = (long long)m * cplane + own;
                 out[c] = t;
                 pnew[c] = sa.p;
@@ -237,7 +241,7 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_bloc
                 const float* Z = reinterpret_cast<const float*>(b + G::oZ);
                 if (mw >= k0 - 1) {
                     float2 tzp;
-                    wl(mw)[yo * PW + xo] = w_even(b, mw, xo, yo, own_tzm, tzp);
+                    Wb[yo * PW + xo] = w_even(b, mw, xo, yo, own_tzm, tzp, Pb, Pc, Pa);
                     // the own black cell's coefficients and p for its t two steps later
                     const int rho = (j + mw) & 1;
                     const float* X = reinterpret_cast<const float*>(b + G::oX);
@@ -250,13 +254,13 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_bloc
                     co.tyd = Y[yo * BWF + xbb];
                     co.tz = rho ? tzp.x : tzp.y;
                     co.tzm = rho ? own_tzm.x : own_tzm.y;
-                    co.p = pl(mw)[(yo + 1) * PW + xo];
+                    co.p = Pb[(yo + 1) * PW + xo];
                     own_tzm = tzp;
                     sa = sb;
                     sb = co;
                     if (has_ring) {
                         float2 tzr;
-                        wl(mw)[ry * PW + rx] = w_even(b, mw, rx, ry, ring_tzm, tzr);
+                        Wb[ry * PW + rx] = w_even(b, mw, rx, ry, ring_tzm, tzr, Pb, Pc, Pa);
                         ring_tzm = tzr;
                     }
                 } else {
@@ -265,6 +269,16 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_bloc
                 }
             } else {
                 sa = sb;
+            }
+            {
+                float* const tp = Pa;
+                Pa = Pb;
+                Pb = Pc;
+                Pc = tp;
+                float* const tw = Wa;
+                Wa = Wb;
+                Wb = Wc;
+                Wc = tw;
             }
             __syncthreads();
         }

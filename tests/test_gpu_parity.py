@@ -297,6 +297,42 @@ def test_compact_red_black_matches_interleaved(vofp, oracle, monkeypatch, case):
     assert np.linalg.norm(x1 - x0) / np.linalg.norm(x0) <= 1e-6
 
 
+def test_compact_red_black_ragged_tiles_and_all_neumann(vofp, oracle):
+    """Colour-compact red-black on a grid whose pair rows (20 pairs) and rows (11) leave ragged
+    tiles, and on an all-Neumann box with prescribed wall fluxes (zero-mean solution)."""
+    prob = ragged_sphere(shape=(40, 11, 45))
+    ref, info_ref, s = oracle.solve(prob, rtol=1e-12)
+    ctx, t = vofp.context_for(prob)
+    b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
+    x, info = ctx.vofp_solve(b, rtol=1e-8, mode=vofp.MODE_MIXED, precond=vofp.PRECOND_RBSGS)
+    assert info["status"] == 0 and ctx.vofp_get_stats()["rb_compact"] == 1
+    got = host(x, prob.shape)
+    assert s.residual(got) <= 1e-8 * 1.01
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-6
+    ctx.close()
+
+    prob = I.tiny_sphere(n=16)
+    prob.bc = (0, 0, 0, 0, 0, 0)
+    nz, ny, nx = prob.shape
+    g0 = np.random.default_rng(3).uniform(-1, 1, (nz, ny))
+    flux = [g0, -g0, None, None, None, None]
+    s = oracle.System(prob, neumann_flux=flux)
+    ref = s.solve_dense()
+    from paper_1410_1937_gb300 import vofp as V
+    ctx = V.Context(prob.dx, prob.dy, prob.dz)
+    tt = {k: dev(getattr(prob, k)) for k in ("F", "ax", "ay", "az", "vf", "u", "v", "w")}
+    ctx.vofp_build_operator(tt["F"], tt["ax"], tt["ay"], tt["az"], tt["vf"], prob.bc, prob.rho_liquid,
+                            prob.rho_gas, prob.merge_threshold, 0, prob.dt,
+                            neumann_flux=[dev(g0), dev(-g0), None, None, None, None])
+    b = ctx.vofp_rhs_from_face_velocity(tt["u"], tt["v"], tt["w"])
+    x, info = ctx.vofp_solve(b, rtol=1e-8, mode=vofp.MODE_MIXED, precond=vofp.PRECOND_RBSGS)
+    assert info["status"] == 0 and ctx.vofp_get_stats()["rb_compact"] == 1
+    got = host(x, prob.shape)
+    assert s.residual(got) <= 1e-8 * 1.01
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-6
+    ctx.close()
+
+
 def test_unaligned_rows_use_register_stencil(vofp):
     """Rows of 37 FP32 values are not a multiple of 16 bytes: no tensor map, register kernel."""
     prob = ragged_sphere()
