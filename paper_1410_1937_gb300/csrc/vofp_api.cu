@@ -245,15 +245,15 @@ vofp_status vofp_launch_count(vofp_ctx* c, long long* count) {
 }
 
 vofp_status vofp_time_iteration_kernels(vofp_ctx* c, int precision, int precond, int reps, float* stencil_ms,
-                                        float* update_ms, float* red_ms) {
+                                        float* update_ms, float* aux_ms) {
     vofp_status s = check_ctx(c, true);
     if (s) return s;
     if ((precision != 64 && precision != 32) || (precond != VOFP_PRECOND_JACOBI && precond != VOFP_PRECOND_RBSGS) ||
         reps <= 0 || !stencil_ms || !update_ms)
         return invalid(c, "bad arguments");
-    float red = 0.0f;
-    s = vofp::time_iteration_kernels(c, precision, precond == VOFP_PRECOND_RBSGS, reps, stencil_ms, update_ms, &red);
-    if (red_ms) *red_ms = red;
+    float aux = 0.0f;
+    s = vofp::time_iteration_kernels(c, precision, precond == VOFP_PRECOND_RBSGS, reps, stencil_ms, update_ms, &aux);
+    if (aux_ms) *aux_ms = aux;
     return s;
 }
 

@@ -142,7 +142,14 @@ struct vofp_ctx {
     uint32_t* rbc_bits = nullptr;     // compact entries excluded from the dots (copies of a group value)
     int* rbc_exc = nullptr;           // exception cells
     int *rbc_fcell = nullptr, *rbc_fexc = nullptr;   // rows next to exceptions, exception per face
-    int* rbc_gref = nullptr;          // compact index of every gcells entry
+    int* rbc_fh = nullptr;            // compact index per fix row (-1: a merge-group member)
+    float* rbc_fT = nullptr;          // face coefficient per fix row and face (0: no exception)
+    int* rbc_enb = nullptr;           // per exception and face: the compact index of the black pair
+    float* rbc_eT = nullptr;          // per exception and face: the coefficient (0 at the boundary)
+    float* rbc_dE = nullptr;          // per exception: red formula - p (entry ne: 0)
+    int *rbc_gref = nullptr, *rbc_gfx = nullptr;     // compact / fix-row index of every gcells entry
+    int *rbc_gm = nullptr, *rbc_gf = nullptr;        // per group: four members' compact / fix-row index
+    int* rbc_gn = nullptr;            // per group: member count
     long long rbc_cap = 0;            // allocated compact length
     int rbc_blocks_per_sm = 0;
     int tma_blocks_deep32 = 0;        // resident blocks per SM of the six-stage FP32 stencil
@@ -186,6 +193,7 @@ void rbc_iteration(vofp_ctx* c, cudaStream_t st, const float* po, float* pn, cud
                    int use_h);
 void rbc_finish_xf(vofp_ctx* c, cudaStream_t st);                 // xf (full grid) = x_c + alpha p0_c
 void rbc_time_kernel(vofp_ctx* c, cudaStream_t st);               // one iteration kernel launch
+void rbc_time_aux(vofp_ctx* c, cudaStream_t st);                  // the exception and group kernels of one iteration
 template <typename V>
 bool launch_cg_tma(vofp_ctx* c, cudaStream_t st, const V* Tx, const V* Ty, const V* Tz, const V* r, const V* po,
                    V* pn, V* xv, V* q);

@@ -3,13 +3,16 @@
 // Per operator (on the device, deterministic order):
 //   exceptions  even-parity cells with an unknown that are not red (members of merge groups),
 //               sorted by cell index; their compact index is N/2 + e;
-//   fix rows    black cells next to an exception, sorted, with the exception index behind each of
-//               their six faces (-1 where there is none);
+//   exception tables  per exception the black pair behind each face and the face coefficient;
+//   fix rows    black cells next to an exception, sorted, with the exception index and the face
+//               coefficient behind each of their six faces (-1 / 0 where there is none);
 //   bits        compact entries that hold a copy of a group value (excluded from the dots);
-//   gref        the compact index of every entry of the merge-group cell lists.
-// Per iteration: the TMA iteration kernel (every even cell takes the red formula), the exception
-// kernel (exception rows; black rows next to an exception get the exception's p in place of the
-// red formula), the merge-group patch and the vector update on the compact vectors.
+//   gref, gfx   the compact index and the fix-row index (-1 if none) of every entry of the
+//               merge-group cell lists.
+// Per iteration: the TMA iteration kernel (every even cell takes the red formula), the fix kernel
+// (exception entries; black rows next to an exception get the exception's p in place of the red
+// formula; merge groups summed and their value written to every member) and the vector update on
+// the compact vectors.
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
@@ -150,40 +153,111 @@ __global__ void k_mark(int n, const int* __restrict__ cells, uint8_t* __restrict
     if (t < n) flag[cells[t]] = v;
 }
 
-// index of cell c in the sorted exception list (or -1)
-__device__ __forceinline__ int find_exc(const int* __restrict__ exc, int ne, long long c) {
-    int lo = 0, hi = ne - 1;
+// index of cell c in a sorted cell list (or -1)
+__device__ __forceinline__ int find_sorted(const int* __restrict__ list, int n, long long c) {
+    int lo = 0, hi = n - 1;
     while (lo <= hi) {
         const int mid = (lo + hi) >> 1;
-        const long long v = exc[mid];
+        const long long v = list[mid];
         if (v == c) return mid;
         if (v < c) lo = mid + 1;
         else hi = mid - 1;
     }
     return -1;
 }
+__device__ __forceinline__ int find_exc(const int* __restrict__ exc, int ne, long long c) {
+    return find_sorted(exc, ne, c);
+}
 
-// exception index behind each face of each fix row (order +x, -x, +y, -y, +z, -z)
+// coefficient of face f (order +x, -x, +y, -y, +z, -z) of cell c: the + face of the lower cell
+__device__ __forceinline__ float face_T(const Dims& d, long long c, int f, const float* __restrict__ Tx,
+                                        const float* __restrict__ Ty, const float* __restrict__ Tz) {
+    switch (f) {
+        case 0: return Tx[c];
+        case 1: return Tx[c - 1];
+        case 2: return Ty[c];
+        case 3: return Ty[c - d.nx];
+        case 4: return Tz[c];
+        default: return Tz[c - d.plane];
+    }
+}
+
+// per exception: the compact index of the black pair behind each face and the face coefficient
+// (the own pair and 0 at the domain boundary), in the order of the red formula
+__global__ void k_exc_tables(Dims d, int ne, const int* __restrict__ exc, const float* __restrict__ Tx,
+                             const float* __restrict__ Ty, const float* __restrict__ Tz, int* __restrict__ enb,
+                             float* __restrict__ eT) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    const long long ce = exc[e];
+    int i, j, k;
+    cell_ijk(d, ce, i, j, k);
+    const bool has[6] = {i < d.nx - 1, i > 0, j < d.ny - 1, j > 0, k < d.nz - 1, k > 0};
+    const long long nb[6] = {ce + 1, ce - 1, ce + d.nx, ce - d.nx, ce + d.plane, ce - d.plane};
+    for (int f = 0; f < 6; ++f) {
+        enb[6 * e + f] = (int)((has[f] ? nb[f] : ce) >> 1);
+        eT[6 * e + f] = has[f] ? face_T(d, ce, f, Tx, Ty, Tz) : 0.0f;
+    }
+}
+
+// per fix row: the exception index and the face coefficient behind each face (ne, whose
+// difference entry is 0, and 0 where there is none), and its compact index (-1 for a merge-group
+// member: its group handles it).  Row nf is a dummy with no exception.
 __global__ void k_fix_faces(Dims d, int nf, const int* __restrict__ fcell, const int* __restrict__ exc, int ne,
-                            const uint8_t* __restrict__ isexc, int* __restrict__ fexc) {
+                            const uint8_t* __restrict__ isexc, const uint8_t* __restrict__ isgrp,
+                            const float* __restrict__ Tx, const float* __restrict__ Ty, const float* __restrict__ Tz,
+                            int* __restrict__ fexc, float* __restrict__ fT, int* __restrict__ fh) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nf) return;
+    if (r > nf) return;
+    if (r == nf) {
+        for (int f = 0; f < 6; ++f) {
+            fexc[6 * r + f] = ne;
+            fT[6 * r + f] = 0.0f;
+        }
+        return;
+    }
     const long long b = fcell[r];
     int i, j, k;
     cell_ijk(d, b, i, j, k);
     const long long nb[6] = {i < d.nx - 1 ? b + 1 : -1, i > 0 ? b - 1 : -1,
                              j < d.ny - 1 ? b + d.nx : -1, j > 0 ? b - d.nx : -1,
                              k < d.nz - 1 ? b + d.plane : -1, k > 0 ? b - d.plane : -1};
-    for (int f = 0; f < 6; ++f) fexc[6 * r + f] = (nb[f] >= 0 && isexc[nb[f]]) ? find_exc(exc, ne, nb[f]) : -1;
+    for (int f = 0; f < 6; ++f) {
+        const int e = (nb[f] >= 0 && isexc[nb[f]]) ? find_exc(exc, ne, nb[f]) : -1;
+        fexc[6 * r + f] = e >= 0 ? e : ne;
+        fT[6 * r + f] = e >= 0 ? face_T(d, b, f, Tx, Ty, Tz) : 0.0f;
+    }
+    fh[r] = isgrp[b] ? -1 : (int)(b >> 1);
 }
 
-// compact index of every merge-group cell entry
+// compact index and fix-row index (-1 if none) of every merge-group cell entry
 __global__ void k_gref(Dims d, int n, const int* __restrict__ gcells, const int* __restrict__ exc, int ne,
-                       long long nh, int* __restrict__ gref) {
+                       const int* __restrict__ fcell, int nf, long long nh, int* __restrict__ gref,
+                       int* __restrict__ gfx) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     const long long c = gcells[t];
-    gref[t] = parity(d, c) ? (int)(c >> 1) : (int)(nh + find_exc(exc, ne, c));
+    const bool black = parity(d, c) != 0;
+    gref[t] = black ? (int)(c >> 1) : (int)(nh + find_exc(exc, ne, c));
+    gfx[t] = black ? find_sorted(fcell, nf, c) : -1;
+}
+
+// per merge group: the compact and fix-row indices of up to four members (padding: the master
+// and the dummy fix row nf; a member that is no fix row also gets nf) and the member count
+__global__ void k_gflat(int ng, const int* __restrict__ gptr, const int* __restrict__ gref,
+                        const int* __restrict__ gfx, int nf, int4* __restrict__ gm, int4* __restrict__ gf,
+                        int* __restrict__ gn) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    const int u0 = gptr[g], n = gptr[g + 1] - u0;
+    int m[4], f[4];
+    for (int u = 0; u < 4; ++u) {
+        m[u] = gref[u0 + (u < n ? u : 0)];
+        f[u] = (u < n && gfx[u0 + u] >= 0) ? gfx[u0 + u] : nf;
+    }
+    gm[g] = make_int4(m[0], m[1], m[2], m[3]);
+    gf[g] = make_int4(f[0], f[1], f[2], f[3]);
+    gn[g] = n;
 }
 
 // compact dot-exclusion bits: the entry's cell belongs to another cell's group (or has no unknown)
@@ -226,71 +300,127 @@ __global__ void k_rbc_prep(Dims d, long long nh, int ne, const int* __restrict__
     if (grid_reduce(acc.value(), partials, counter, sh, &tot)) inner_start_scalars(sc, tot, rr, keep);
 }
 
-// the red formula at an even cell ce with the new black p (same order of operations as k_rbc_tma)
-__device__ __forceinline__ float red_formula(const Dims& d, long long ce, const float* __restrict__ Tx,
-                                             const float* __restrict__ Ty, const float* __restrict__ Tz,
-                                             const float* __restrict__ pn) {
-    int i, j, k;
-    cell_ijk(d, ce, i, j, k);
-    float u = 0.0f;
-    u = fmav(i < d.nx - 1 ? Tx[ce] : 0.0f, i < d.nx - 1 ? pn[(ce + 1) >> 1] : 0.0f, u);
-    u = fmav(i > 0 ? Tx[ce - 1] : 0.0f, i > 0 ? pn[(ce - 1) >> 1] : 0.0f, u);
-    u = fmav(j < d.ny - 1 ? Ty[ce] : 0.0f, j < d.ny - 1 ? pn[(ce + d.nx) >> 1] : 0.0f, u);
-    u = fmav(j > 0 ? Ty[ce - d.nx] : 0.0f, j > 0 ? pn[(ce - d.nx) >> 1] : 0.0f, u);
-    u = fmav(k < d.nz - 1 ? Tz[ce] : 0.0f, k < d.nz - 1 ? pn[(ce + d.plane) >> 1] : 0.0f, u);
-    u = fmav(k > 0 ? Tz[ce - d.plane] : 0.0f, k > 0 ? pn[(ce - d.plane) >> 1] : 0.0f, u);
-    return u;
-}
-
-// Exception rows (threads 0..ne-1): p, x updates and t_e = p_e - sum_f T_f p_nb.  Fix rows
-// (threads ne..ne+nf-1): the black row took the red formula at each neighbouring exception; add
-// T_f (w_red - p_e) back.  p.t of both into pq_raw (after the iteration kernel's sum).
+// After the TMA iteration kernel, per exception e (compact entry N/2 + e): p = r + beta p_old,
+// x += alpha p_old, the exception row t_e = p_e - sum_f T_f p_nb, and dE_e = w_red - p_e, the
+// difference between the red formula the black neighbours took in the TMA kernel (same order of
+// operations) and the exception's p.  p.t of the rows into pq_raw.
 __global__ void __launch_bounds__(kNT)
-k_rbc_exc(Dims d, long long nh, int ne, const int* __restrict__ exc, int nf, const int* __restrict__ fcell,
-          const int* __restrict__ fexc, const float* __restrict__ Tx, const float* __restrict__ Ty,
-          const float* __restrict__ Tz, const float* __restrict__ r, const float* __restrict__ po,
-          float* __restrict__ pn, float* __restrict__ xv, float* __restrict__ q, CgScalars* sc,
-          double* __restrict__ partials, unsigned int* __restrict__ counter) {
+k_rbc_exc_rows(long long nh, int ne, const int* __restrict__ enb, const float* __restrict__ eT,
+               const float* __restrict__ r, const float* __restrict__ po, float* __restrict__ pn,
+               float* __restrict__ xv, float* __restrict__ q, float* __restrict__ dE, CgScalars* sc,
+               double* __restrict__ partials, unsigned int* __restrict__ counter) {
     __shared__ double sh[32];
     const float beta = (float)sc->beta, alpha = (float)sc->alpha;
     AccF2 acc;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ne + nf; t += gridDim.x * blockDim.x) {
-        if (t < ne) {
-            const long long ce = exc[t], ie = nh + t;
-            const float pe = fmav(beta, po[ie], r[ie]);
-            xv[ie] = fmav(alpha, po[ie], xv[ie]);
-            pn[ie] = pe;
-            int i, j, k;
-            cell_ijk(d, ce, i, j, k);
-            float tt = pe;
-            if (i < d.nx - 1) tt = fmav(-Tx[ce], pn[(ce + 1) >> 1], tt);
-            if (i > 0) tt = fmav(-Tx[ce - 1], pn[(ce - 1) >> 1], tt);
-            if (j < d.ny - 1) tt = fmav(-Ty[ce], pn[(ce + d.nx) >> 1], tt);
-            if (j > 0) tt = fmav(-Ty[ce - d.nx], pn[(ce - d.nx) >> 1], tt);
-            if (k < d.nz - 1) tt = fmav(-Tz[ce], pn[(ce + d.plane) >> 1], tt);
-            if (k > 0) tt = fmav(-Tz[ce - d.plane], pn[(ce - d.plane) >> 1], tt);
-            q[ie] = tt;
-            acc.add(pe, tt);
-        } else {
-            const int rr = t - ne;
-            const long long b = fcell[rr];
-            float delta = 0.0f;
-            for (int f = 0; f < 6; ++f) {
-                const int e = fexc[6 * rr + f];
-                if (e < 0) continue;
-                const long long ce = exc[e], ie = nh + e;
-                // coefficient of the face between b and ce: the + face of the lower cell
-                const float T = f == 0 ? Tx[b] : f == 1 ? Tx[ce] : f == 2 ? Ty[b] : f == 3 ? Ty[ce] : f == 4 ? Tz[b] : Tz[ce];
-                const float pe = fmav(beta, po[ie], r[ie]);
-                delta = fmav(T, red_formula(d, ce, Tx, Ty, Tz, pn) - pe, delta);
-            }
-            const long long hb = b >> 1;
-            q[hb] += delta;
-            acc.add(pn[hb], delta);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
+        const long long ie = nh + e;
+        const float pold = po[ie];
+        const float pe = fmav(beta, pold, r[ie]);
+        pn[ie] = pe;
+        xv[ie] = fmav(alpha, pold, xv[ie]);
+        float T[6], p[6];
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            T[f] = eT[6 * e + f];
+            p[f] = pn[enb[6 * e + f]];
         }
+        float w = 0.0f, t = pe;
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            w = fmav(T[f], p[f], w);
+            t = fmav(-T[f], p[f], t);
+        }
+        dE[e] = w - pe;
+        q[ie] = t;
+        acc.add(pe, t);
     }
     double tot;
     if (grid_reduce(acc.value(), partials, counter, sh, &tot)) sc->pq_raw += tot;
+}
+
+// correction of fix row rr: the black row took the red formula at each neighbouring exception,
+// T_f (w_red - p_e) puts the exception's p back (faces without one point at a zero entry)
+__device__ __forceinline__ float fix_delta(int rr, const int* __restrict__ fexc, const float* __restrict__ fT,
+                                           const float* __restrict__ dE) {
+    int e[6];
+    float T[6];
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+        e[f] = fexc[6 * rr + f];
+        T[f] = fT[6 * rr + f];
+    }
+    float delta = 0.0f;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) delta = fmav(T[f], dE[e[f]], delta);
+    return delta;
+}
+
+// After k_rbc_exc_rows.  Fix rows that are not merge-group members (threads 0..nf-1): q += delta.
+// Merge groups (threads nf..nf+ng-1): every member's final row (the exception row, or the black
+// row plus its correction), then the group value sum + gcorr p_G written to every member.
+// p.delta of the corrections and gcorr p_G^2 into pq_raw.
+__global__ void __launch_bounds__(kNT)
+k_rbc_fix_rows(int nf, int ng, const int* __restrict__ fh, const int* __restrict__ fexc,
+               const float* __restrict__ fT, const float* __restrict__ dE, const int4* __restrict__ gm,
+               const int4* __restrict__ gf, const int* __restrict__ gn, const int* __restrict__ gptr,
+               const int* __restrict__ gref, const int* __restrict__ gfx, const double* __restrict__ gcorr,
+               const float* __restrict__ pn, float* __restrict__ q, CgScalars* sc, double* __restrict__ partials,
+               unsigned int* __restrict__ counter) {
+    __shared__ double sh[32];
+    AccF2 acc;
+    double corr = 0.0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf + ng; t += gridDim.x * blockDim.x) {
+        if (t < nf) {
+            const int h = fh[t];
+            if (h >= 0) {
+                const float delta = fix_delta(t, fexc, fT, dE);
+                q[h] += delta;
+                acc.add(pn[h], delta);
+            }
+            continue;
+        }
+        const int g = t - nf, n = gn[g];
+        const int4 m4 = gm[g], f4 = gf[g];
+        const double gc = gcorr[g];
+        const double pm = (double)pn[m4.x];
+        double s = 0.0;
+        if (n <= 4) {
+            const int mm[4] = {m4.x, m4.y, m4.z, m4.w}, ff[4] = {f4.x, f4.y, f4.z, f4.w};
+            float qv[4], pv[4], dv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                qv[u] = q[mm[u]];
+                pv[u] = pn[mm[u]];
+                dv[u] = fix_delta(ff[u], fexc, fT, dE);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (u < n) {
+                    s += (double)(qv[u] + dv[u]);
+                    acc.add(pv[u], dv[u]);
+                }
+            const float qm = (float)(s + gc * pm);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (u < n) q[mm[u]] = qm;
+        } else {
+            const int u0 = gptr[g], u1 = gptr[g + 1];
+            for (int u = u0; u < u1; ++u) {
+                const int ix = gref[u], fr = gfx[u] >= 0 ? gfx[u] : nf;
+                const float dv = fix_delta(fr, fexc, fT, dE);
+                s += (double)(q[ix] + dv);
+                acc.add(pn[ix], dv);
+            }
+            const float qm = (float)(s + gc * pm);
+            for (int u = u0; u < u1; ++u) q[gref[u]] = qm;
+        }
+        corr += gc * pm * pm;
+    }
+    double tot;
+    if (grid_reduce(acc.value() + corr, partials, counter, sh, &tot)) {
+        sc->pq_raw += tot;
+        sc->pq_corr = 0.0;
+    }
 }
 
 // end of an inner solve: x_f (full grid) = x + alpha p_old of the compact vectors (black cells),
@@ -325,7 +455,8 @@ vofp_status rbc_ensure(vofp_ctx* c) {
     const long long nh = d.n / 2;
     // scratch: exception flags per cell and chunk counts
     const int nchunks = (int)((d.n + kChunk - 1) / kChunk);
-    uint8_t* isexc = reinterpret_cast<uint8_t*>(c->work);            // N doubles of scratch: N bytes used
+    uint8_t* isexc = reinterpret_cast<uint8_t*>(c->work);            // N doubles of scratch: 2N bytes used
+    uint8_t* isgrp = isexc + d.n;
     unsigned int* counts = reinterpret_cast<unsigned int*>(c->partials);
     unsigned int* offsets = counts + nchunks + 1;
     if (2 * (nchunks + 1) > 2 * kMaxPartials) return VOFP_OK;
@@ -343,43 +474,58 @@ vofp_status rbc_ensure(vofp_ctx* c) {
         if ((s = c->alloc(&c->rbc_r, cap)) || (s = c->alloc(&c->rbc_p0, cap)) || (s = c->alloc(&c->rbc_p1, cap)) ||
             (s = c->alloc(&c->rbc_x, cap)) || (s = c->alloc(&c->rbc_q, cap)) ||
             (s = c->alloc(&c->rbc_bits, (cap + 31) / 32)) || (s = c->alloc(&c->rbc_exc, cap - nh)) ||
-            (s = c->alloc(&c->rbc_fcell, 6 * (cap - nh))) ||
-            (s = c->alloc(&c->rbc_fexc, 36 * (cap - nh))))
+            (s = c->alloc(&c->rbc_fcell, 6 * (cap - nh))) || (s = c->alloc(&c->rbc_fh, 6 * (cap - nh))) ||
+            (s = c->alloc(&c->rbc_fexc, 36 * (cap - nh))) || (s = c->alloc(&c->rbc_fT, 36 * (cap - nh))) ||
+            (s = c->alloc(&c->rbc_enb, 6 * (cap - nh))) || (s = c->alloc(&c->rbc_eT, 6 * (cap - nh))) ||
+            (s = c->alloc(&c->rbc_dE, cap - nh + 1)))
             return s;
         c->rbc_cap = cap;
         for (float* v : {c->rbc_r, c->rbc_p0, c->rbc_p1, c->rbc_x, c->rbc_q})
             VOFP_CUDA_TRY(c, cudaMemsetAsync(v, 0, sizeof(float) * cap, st));
     }
-    if (c->ngroups > 0 && !c->rbc_gref) {
-        if ((s = c->alloc(&c->rbc_gref, (long long)d.n / 4 + 1))) return s;
+    int ncells = 0;
+    if (c->ngroups > 0) {
+        VOFP_CUDA_TRY(c, cudaMemcpyAsync(&ncells, c->gptr + c->ngroups, sizeof(int), cudaMemcpyDeviceToHost, st));
+        VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
+        if (ncells > d.n / 4) return VOFP_OK;
+        if (!c->rbc_gref &&
+            ((s = c->alloc(&c->rbc_gref, (long long)d.n / 4 + 1)) || (s = c->alloc(&c->rbc_gfx, (long long)d.n / 4 + 1)) ||
+             (s = c->alloc(&c->rbc_gm, 4 * ((long long)d.n / 8 + 1))) ||
+             (s = c->alloc(&c->rbc_gf, 4 * ((long long)d.n / 8 + 1))) || (s = c->alloc(&c->rbc_gn, (long long)d.n / 8 + 1))))
+            return s;
     }
     launch(c, k_cmp_write<0>, nchunks, kNT, st, d, (const int32_t*)c->root, (const uint32_t*)c->red_bits,
            (const uint8_t*)nullptr, (const unsigned int*)offsets, c->rbc_exc);
+    if (ne > 0)
+        launch(c, k_exc_tables, ceil_div(ne, kNT), kNT, st, d, (int)ne, (const int*)c->rbc_exc, (const float*)c->Txf,
+               (const float*)c->Tyf, (const float*)c->Tzf, c->rbc_enb, c->rbc_eT);
     // rows next to exceptions
-    VOFP_CUDA_TRY(c, cudaMemsetAsync(isexc, 0, d.n, st));
+    VOFP_CUDA_TRY(c, cudaMemsetAsync(isexc, 0, 2 * d.n, st));
     if (ne > 0) launch(c, k_mark, ceil_div(ne, kNT), kNT, st, (int)ne, (const int*)c->rbc_exc, isexc, (uint8_t)1);
+    if (ncells > 0) launch(c, k_mark, ceil_div(ncells, kNT), kNT, st, ncells, (const int*)c->gcells, isgrp, (uint8_t)1);
     launch(c, k_cmp_count<1>, nchunks, kNT, st, d, (const int32_t*)nullptr, (const uint32_t*)nullptr,
            (const uint8_t*)isexc, counts);
     launch(c, k_cmp_scan, 1, 1024, st, nchunks, counts, offsets);
     unsigned int nf = 0;
     VOFP_CUDA_TRY(c, cudaMemcpyAsync(&nf, counts + nchunks, sizeof(nf), cudaMemcpyDeviceToHost, st));
     VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
-    if ((long long)nf > 6 * (c->rbc_cap - nh)) return VOFP_OK;    // cannot happen: 6 faces per exception
+    if ((long long)nf + 1 > 6 * (c->rbc_cap - nh)) return VOFP_OK;    // cannot happen: 6 faces per exception
     launch(c, k_cmp_write<1>, nchunks, kNT, st, d, (const int32_t*)nullptr, (const uint32_t*)nullptr,
            (const uint8_t*)isexc, (const unsigned int*)offsets, c->rbc_fcell);
-    if (nf > 0)
-        launch(c, k_fix_faces, ceil_div(nf, kNT), kNT, st, d, (int)nf, (const int*)c->rbc_fcell,
-               (const int*)c->rbc_exc, (int)ne, (const uint8_t*)isexc, c->rbc_fexc);
+    launch(c, k_fix_faces, ceil_div(nf + 1, kNT), kNT, st, d, (int)nf, (const int*)c->rbc_fcell,
+               (const int*)c->rbc_exc, (int)ne, (const uint8_t*)isexc, (const uint8_t*)isgrp, (const float*)c->Txf,
+               (const float*)c->Tyf, (const float*)c->Tzf, c->rbc_fexc, c->rbc_fT, c->rbc_fh);
     launch(c, k_cbits, grid_n((need + 31) / 32), kNT, st, d, nh, (int)ne, (const int*)c->rbc_exc,
            (const int32_t*)c->root, c->rbc_bits);
-    if (c->ngroups > 0) {
-        int ncells = 0;
-        VOFP_CUDA_TRY(c, cudaMemcpyAsync(&ncells, c->gptr + c->ngroups, sizeof(int), cudaMemcpyDeviceToHost, st));
-        VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
-        if (ncells > d.n / 4) return VOFP_OK;
+    if (ncells > 0) {
         launch(c, k_gref, ceil_div(ncells, kNT), kNT, st, d, ncells, (const int*)c->gcells, (const int*)c->rbc_exc,
-               (int)ne, nh, c->rbc_gref);
+               (int)ne, (const int*)c->rbc_fcell, (int)nf, nh, c->rbc_gref, c->rbc_gfx);
+        launch(c, k_gflat, ceil_div(c->ngroups, kNT), kNT, st, c->ngroups, (const int*)c->gptr,
+               (const int*)c->rbc_gref, (const int*)c->rbc_gfx, (int)nf, reinterpret_cast<int4*>(c->rbc_gm),
+               reinterpret_cast<int4*>(c->rbc_gf), c->rbc_gn);
     }
+    // the zero difference entry behind faces without an exception
+    VOFP_CUDA_TRY(c, cudaMemsetAsync(c->rbc_dE + ne, 0, sizeof(float), st));
     // the iteration kernel's dynamic shared memory and resident blocks
     constexpr size_t smem = cg_rbc_smem<kRbcStages>();
     cudaFuncSetAttribute(k_rbc_tma<kRbcStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -430,19 +576,25 @@ void launch_main(vofp_ctx* c, cudaStream_t st, const float* po, float* pn) {
 }
 }  // namespace
 
+// exception rows, then the rows next to exceptions and the merge groups
+void rbc_aux(vofp_ctx* c, cudaStream_t st, const float* po, float* pn) {
+    const int ng = c->rbc_gm ? c->ngroups : 0;
+    if (c->rbc_ne > 0)
+        launch(c, k_rbc_exc_rows, ceil_div(c->rbc_ne, kNT), kNT, st, c->rbc_nh, c->rbc_ne, (const int*)c->rbc_enb,
+               (const float*)c->rbc_eT, (const float*)c->rbc_r, po, pn, c->rbc_x, c->rbc_q, c->rbc_dE, c->sc,
+               c->partials, c->counters);
+    if (c->rbc_nf + ng > 0)
+        launch(c, k_rbc_fix_rows, ceil_div(c->rbc_nf + ng, kNT), kNT, st, c->rbc_nf, ng, (const int*)c->rbc_fh,
+               (const int*)c->rbc_fexc, (const float*)c->rbc_fT, (const float*)c->rbc_dE,
+               (const int4*)c->rbc_gm, (const int4*)c->rbc_gf, (const int*)c->rbc_gn, (const int*)c->gptr,
+               (const int*)c->rbc_gref, (const int*)c->rbc_gfx, (const double*)c->gcorr, (const float*)pn,
+               c->rbc_q, c->sc, c->partials, c->counters);
+}
+
 void rbc_iteration(vofp_ctx* c, cudaStream_t st, const float* po, float* pn, cudaGraphConditionalHandle h,
                    int use_h) {
     launch_main(c, st, po, pn);
-    const int nx = c->rbc_ne + c->rbc_nf;
-    if (nx > 0)
-        launch(c, k_rbc_exc, ceil_div(nx, kNT), kNT, st, c->d, c->rbc_nh, c->rbc_ne, (const int*)c->rbc_exc,
-               c->rbc_nf, (const int*)c->rbc_fcell, (const int*)c->rbc_fexc, (const float*)c->Txf,
-               (const float*)c->Tyf, (const float*)c->Tzf, (const float*)c->rbc_r, po, pn, c->rbc_x, c->rbc_q, c->sc,
-               c->partials, c->counters);
-    if (c->ngroups > 0)
-        launch(c, k_group_patch<float>, ceil_div(c->ngroups, kNT), kNT, st, c->ngroups, (const int*)c->gptr,
-               (const int*)c->rbc_gref, (const double*)c->gcorr, c->rbc_q, (const float*)pn, 1, c->sc, c->partials,
-               c->counters);
+    rbc_aux(c, st, po, pn);
     const long long nc = c->rbc_nh + c->rbc_ne;
     launch(c, k_cg_update<float, true>, grid_n(nc / 4 + 1), kNT, st, nc, c->rbc_r, (const float*)c->rbc_q,
            (const uint32_t*)c->rbc_bits, c->sc, c->partials, c->counters, h, use_h);
@@ -457,5 +609,6 @@ void rbc_finish_xf(vofp_ctx* c, cudaStream_t st) {
 }
 
 void rbc_time_kernel(vofp_ctx* c, cudaStream_t st) { launch_main(c, st, c->rbc_p0, c->rbc_p1); }
+void rbc_time_aux(vofp_ctx* c, cudaStream_t st) { rbc_aux(c, st, c->rbc_p0, c->rbc_p1); }
 
 }  // namespace vofp

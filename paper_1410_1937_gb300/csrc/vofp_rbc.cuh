@@ -12,7 +12,7 @@
 //   p = r + beta p_old on the pairs of the tile with a two-pair / two-row halo (compact);
 //   w on the even cell of each pair of the tile with a one-cell halo: the red formula
 //     w = sum_f T_f p_nb for every even cell (all its neighbours are black); an exception's w must
-//     be its own p instead, which the exception kernel corrects afterwards;
+//     be its own p instead, which the fix kernels of vofp_rbc.cu put back afterwards;
 //   t = p - sum_f T_f w_nb on the black cell of each own pair, p.t, x += alpha p_old.
 // The even cell of pair h in row j, plane m sits at x = 2h + rho with rho = (j + m) & 1, the black
 // one at 2h + 1 - rho; x-neighbours of the even cell are the black cells of pairs h - 1 + rho and
