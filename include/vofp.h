@@ -210,6 +210,33 @@ vofp_status vofp_project(vofp_ctx* ctx, const double* p, const double* u, const 
                          const double* body_flux, double* u_out, double* v_out, double* w_out, double* div,
                          double* max_div);
 
+/* Exit flux of the radiation condition (Sec. 2.6): from the x-momentum balance with the
+ * Orlanski-type condition du/dt + u_c du/dx = 0 (Eq. orlanski), the pressure datum on the +x
+ * domain face is (1/rho) dp/dx = u_c du/dx + R (Eq. exit).  Per exit face (row j, k; index
+ * j + ny k) the call forms
+ *     g = u_c (u[nx] - u[nx-1]) / dx[nx-1] + R - u[nx] / dt
+ * from the x-face velocities u of that row (du/dx one-sided across the last cell; dt of
+ * vofp_build_operator) and installs it as the prescribed flux of the +x face, which must be
+ * NEUMANN in the built operator (copied into the context; later vofp_rhs_from_face_velocity and
+ * vofp_project use it).  Free-slip faces take no normal velocity in the divergence and project to
+ * -dt g on a + face, so the -u[nx]/dt term makes the projected exit velocity
+ * u[nx] - dt (u_c du/dx + R): the discrete Orlanski update.
+ *   u, v, w     device, face velocities (layout of vofp_rhs_from_face_velocity); v and w are read
+ *               only when balance is set.
+ *   body_flux   device, cells, or NULL (balance only).
+ *   u_c         the ship's forward speed.
+ *   R           device, (nz, ny) exit faces, or NULL (= 0): the remaining x-momentum terms R_1.
+ *   balance     0: g as above.  1: g is then shifted by the same amount on every open exit face so
+ *               that the right-hand side of the all-Neumann problem sums to zero (the radiation
+ *               condition alone does not conserve mass); *shift receives the amount subtracted.
+ *   g           device, (nz, ny), or NULL: a copy of the installed flux.
+ *   shift       host, or NULL.
+ * Errors: VOFP_ERR_NOT_BUILT before vofp_build_operator; VOFP_ERR_INVALID_ARG for a null u (or v,
+ * w with balance) or a +x face that is not NEUMANN. */
+vofp_status vofp_exit_flux(vofp_ctx* ctx, const double* u, const double* v, const double* w,
+                           const double* body_flux, double u_c, const double* R, int balance, double* g,
+                           double* shift);
+
 /* y = A_hat x: x is read at each group's master cell; y receives the group's value at the master
  * and 0 at every other cell and at cells without an unknown. */
 vofp_status vofp_apply(vofp_ctx* ctx, const double* x, double* y);

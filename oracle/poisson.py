@@ -19,6 +19,8 @@ out from its definition:
 * the right-hand side -(1/dt) * sum of outward face fluxes A_f S_f u_f (Sec. 2.1 Eq. poisson1 and
   Sec. 2.4, F_i = A_i (u_i - v_i)), plus the body-surface term of Eq. integral2 and prescribed
   outward pressure fluxes on Neumann faces (Sec. 2.6, Eq. exit), both optional;
+* the exit flux of the radiation condition (Sec. 2.6, Eqs. orlanski and exit), optionally shifted
+  uniformly over the open exit faces so that the all-Neumann problem is compatible;
 * merging of cells whose open volume is below a threshold (Sec. 2.3) as the explicit triple
   product P^T A P, one unknown per merge group;
 * the solution of that system by textbook Jacobi-PCG (oracle/pcg.c) to a tight tolerance, or by
@@ -484,6 +486,37 @@ def project(prob, s, p_full, neumann_flux=None):
     wall(w, ez, np.s_[0], np.s_[0], dz[0], -1, bc[4], g[4])
     wall(w, ez, np.s_[-1], np.s_[-1], dz[-1], +1, bc[5], g[5])
     return u, v, w
+
+
+def exit_flux(prob, u_c, R=None, balance=False, body_flux=None, neumann_flux=None):
+    """Prescribed outward flux g = (1/rho) dp/dx on the +x domain face from the radiation condition
+    (Sec. 2.6): du/dt + u_c du/dx = 0 (Eq. orlanski) in the x-momentum balance gives
+    (1/rho) dp/dx = u_c du/dx + R (Eq. exit).  du/dx is the difference of the x-face velocities
+    at the exit face and one cell upstream over the last cell's width.  The free-slip reading of
+    the projection sets the projected velocity of a + face to -dt g, so the exit face's own
+    velocity enters as -u_exit/dt: the projected exit velocity is then u_exit - dt (u_c du/dx + R).
+
+    With ``balance`` the same amount is subtracted on every open exit face so that the cell
+    right-hand sides (rhs with this flux and the other prescribed ones) sum to zero, the condition
+    of the all-Neumann problem.  Returns (g with shape (nz, ny), the amount subtracted).
+    """
+    u = np.asarray(prob.u, dtype=np.float64)
+    ue, uu = u[:, :, -1], u[:, :, -2]
+    g = u_c * (ue - uu) / prob.dx[-1] - ue / prob.dt
+    if R is not None:
+        g = g + np.asarray(R, dtype=np.float64).reshape(g.shape)
+    shift = 0.0
+    if balance:
+        inactive, ex, ey, ez = activity(prob.vf, prob.ax, prob.ay, prob.az, prob.bc)
+        flux = list(neumann_flux) if neumann_flux is not None else [None] * 6
+        flux[1] = g
+        b = rhs(prob, (inactive, ex, ey, ez), body_flux, flux)
+        Sx = prob.dz[:, None] * prob.dy[None, :]
+        area = (ex[:, :, -1] * Sx).sum()
+        if area > 0:
+            shift = b.sum() / area
+            g = np.where(ex[:, :, -1] > 0, g - shift, g)
+    return g, shift
 
 
 def divergence(prob, s, u, v, w, body_flux=None):

@@ -134,6 +134,17 @@ vofp_status vofp_project(vofp_ctx* c, const double* p, const double* u, const do
     return fail_cuda(c);
 }
 
+vofp_status vofp_exit_flux(vofp_ctx* c, const double* u, const double* v, const double* w, const double* body,
+                           double u_c, const double* R, int balance, double* g, double* shift) {
+    vofp_status s = check_ctx(c, true);
+    if (s) return s;
+    if (!u || (balance && (!v || !w))) return invalid(c, "null input");
+    if (c->bc[1] != VOFP_BC_NEUMANN) return invalid(c, "the +x face is not NEUMANN");
+    if (!std::isfinite(u_c)) return invalid(c, "u_c must be finite");
+    if ((s = vofp::exit_flux(c, u, v, w, body, u_c, R, balance, g, shift))) return s;
+    return fail_cuda(c);
+}
+
 vofp_status vofp_apply(vofp_ctx* c, const double* x, double* y) {
     vofp_status s = check_ctx(c, true);
     if (s) return s;

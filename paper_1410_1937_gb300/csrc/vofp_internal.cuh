@@ -261,6 +261,10 @@ __device__ __forceinline__ void cell_ijk(const Dims& d, long long c, int& i, int
 vofp_status project(vofp_ctx* c, const double* p, const double* u, const double* v, const double* w,
                     const double* body, double* uo, double* vo, double* wo, double* div, double* max_div);
 
+// exit flux of the radiation condition, installed as the +x face's prescribed flux (vofp_exit.cu)
+vofp_status exit_flux(vofp_ctx* c, const double* u, const double* v, const double* w, const double* body, double uc,
+                      const double* r1, int balance, double* g_out, double* shift_out);
+
 void launch_group_expand(vofp_ctx* c, double* v);
 void launch_group_fold(vofp_ctx* c, double* v, bool zero_slaves);
 

@@ -79,6 +79,7 @@ _sig = {
     "vofp_build_operator": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _P(_Bc), _P(_Phys)]),
     "vofp_rhs_from_face_velocity": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "vofp_project": (ctypes.c_int, [_vp] * 10 + [_P(ctypes.c_double)]),
+    "vofp_exit_flux": (ctypes.c_int, [_vp] * 5 + [ctypes.c_double, _vp, ctypes.c_int, _vp, _P(ctypes.c_double)]),
     "vofp_apply": (ctypes.c_int, [_vp, _vp, _vp]),
     "vofp_residual": (ctypes.c_int, [_vp, _vp, _vp, _P(ctypes.c_double)]),
     "vofp_solve": (ctypes.c_int, [_vp, _vp, _vp, _P(_Opts), _P(_Info)]),
@@ -231,6 +232,24 @@ class Context:
                                          None if div is None else _dev(div, self.n, "div"),
                                          ctypes.byref(m) if want_max else None))
         return uo, vo, wo, div, (m.value if want_max else None)
+
+    def vofp_exit_flux(self, u, v=None, w=None, u_c=0.0, R=None, balance=False, body_flux=None, out=None):
+        """Exit flux of the radiation condition (Sec. 2.6, Eq. exit) from the x-face velocities u,
+        installed as the +x face's prescribed flux; with balance, shifted over the open exit area so
+        that the all-Neumann right-hand side sums to zero.  Returns (g on the (nz, ny) exit faces,
+        the shift subtracted)."""
+        import torch
+        rows = self.nz * self.ny
+        if out is None:
+            out = torch.empty(rows, dtype=torch.float64, device=u.device)
+        sh = ctypes.c_double(0.0)
+        _check(self.h, _lib.vofp_exit_flux(self.h, _dev(u, self.nfx, "u"),
+                                           None if v is None else _dev(v, self.nfy, "v"),
+                                           None if w is None else _dev(w, self.nfz, "w"),
+                                           None if body_flux is None else _dev(body_flux, self.n, "body_flux"),
+                                           float(u_c), None if R is None else _dev(R, rows, "R"), int(bool(balance)),
+                                           _dev(out, rows, "g"), ctypes.byref(sh)))
+        return out, sh.value
 
     def vofp_apply(self, x, out=None):
         import torch

@@ -333,6 +333,67 @@ def test_compact_red_black_ragged_tiles_and_all_neumann(vofp, oracle):
     ctx.close()
 
 
+@pytest.mark.parametrize("case", ["tiny16", "hull-small"])
+def test_exit_flux_matches_oracle(vofp, oracle, case):
+    """Radiation-condition exit flux (Sec. 2.6, Eq. exit) on an all-Neumann box: the raw flux and
+    the balanced one face by face against the oracle, and the balanced problem is compatible
+    (the solve accepts it)."""
+    prob = I.tiny_sphere(n=16) if case == "tiny16" else I.config2(shape=(96, 48, 40))
+    prob.bc = (0, 0, 0, 0, 0, 0)
+    nz, ny, nx = prob.shape
+    R = np.random.default_rng(8).uniform(-0.5, 0.5, (nz, ny))
+    uc = 1.1
+    ctx, t = vofp.context_for(prob)
+    g, sh = ctx.vofp_exit_flux(t["u"], u_c=uc, R=dev(R))
+    ref, _ = oracle.exit_flux(prob, uc, R=R)
+    gh = g.cpu().numpy().reshape(nz, ny)
+    assert sh == 0.0
+    assert np.abs(gh - ref).max() <= 1e-13 * np.abs(ref).max()
+    g, sh = ctx.vofp_exit_flux(t["u"], t["v"], t["w"], u_c=uc, R=dev(R), balance=True)
+    ref, shr = oracle.exit_flux(prob, uc, R=R, balance=True)
+    gh = g.cpu().numpy().reshape(nz, ny)
+    assert abs(sh - shr) <= 1e-12 * abs(shr)
+    assert np.abs(gh - ref).max() <= 1e-12 * np.abs(ref).max()
+    b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
+    x, info = ctx.vofp_solve(b, rtol=1e-10)
+    assert info["status"] == 0
+    ctx.close()
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_orlanski_exit_solve_and_projection_match_oracle(vofp, oracle, mode):
+    """All-Neumann hull case with the balanced radiation exit: the solution against the oracle's
+    (zero mean over the unknowns), and the projected exit velocities are the discrete Orlanski
+    update u_exit - dt (u_c du/dx + R) + dt shift."""
+    prob = I.config2(shape=(96, 48, 40))
+    prob.bc = (0, 0, 0, 0, 0, 0)
+    prob.dt = 0.8
+    nz, ny, nx = prob.shape
+    uc = 0.8
+    ctx, t = vofp.context_for(prob)
+    g, sh = ctx.vofp_exit_flux(t["u"], t["v"], t["w"], u_c=uc, balance=True)
+    gr, shr = oracle.exit_flux(prob, uc, balance=True)
+    flux = [None, gr, None, None, None, None]
+    s = oracle.System(prob, neumann_flux=flux)
+    ref, info_ref = s.solve_pcg(rtol=1e-12)
+    b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
+    kw = dict(mode=vofp.MODE_MIXED, precond=vofp.PRECOND_RBSGS, rtol=1e-8) if mode == "mixed" else dict(rtol=1e-10)
+    x, info = ctx.vofp_solve(b, **kw)
+    assert info["status"] == 0
+    got = host(x, prob.shape)
+    assert abs(s.restrict(got).mean()) <= 1e-10 * np.abs(ref).max()
+    assert np.linalg.norm(got - ref) <= 1e-6 * np.linalg.norm(ref)
+    uo, vo, wo, div, mx = ctx.vofp_project(x, t["u"], t["v"], t["w"])
+    ue, uu = prob.u[:, :, -1], prob.u[:, :, -2]
+    want = ue - prob.dt * (uc * (ue - uu) / prob.dx[-1]) + prob.dt * shr
+    ug = uo.cpu().numpy().reshape(prob.u.shape)
+    open_ = s.apertures[0][:, :, -1] > 0
+    np.testing.assert_allclose(ug[:, :, -1][open_], want[open_], rtol=1e-12, atol=1e-12 * np.abs(want).max())
+    fl = np.abs(oracle.divergence(prob, s, np.abs(prob.u), np.abs(prob.v), np.abs(prob.w))).max()
+    assert mx <= (1e-7 if mode == "fp64" else 1e-5) * fl
+    ctx.close()
+
+
 def test_unaligned_rows_use_register_stencil(vofp):
     """Rows of 37 FP32 values are not a multiple of 16 bytes: no tensor map, register kernel."""
     prob = ragged_sphere()

@@ -273,6 +273,65 @@ def test_projection_all_neumann_with_prescribed_wall_flux(oracle):
     assert np.abs(oracle.divergence(p, s, p.u, p.v, p.w)).max() > 1e-3 * scale
 
 
+def test_exit_flux_of_a_linear_profile_closed_form(oracle):
+    # Sec. 2.6 Eq. exit with u = a x + c on the x faces of a stretched grid: du/dx = a exactly, so
+    # g = u_c a + R - u_exit / dt on every exit face (the last cell's width, not the first's)
+    p = I.tiny_sphere(n=8)
+    p.bc = (0, 0, 0, 0, 0, 0)
+    p.dt = 0.4
+    p.dx = np.array([0.05, 0.07, 0.1, 0.12, 0.14, 0.16, 0.18, 0.18])
+    a, c0, uc = 0.73, -0.2, 1.7
+    xf = np.concatenate([[0.0], np.cumsum(p.dx)])
+    p.u = np.broadcast_to(a * xf + c0, p.u.shape).copy()
+    R = np.random.default_rng(2).uniform(-1, 1, p.u.shape[:2])
+    g, shift = oracle.exit_flux(p, uc, R=R)
+    assert shift == 0.0
+    np.testing.assert_allclose(g, uc * a + R - (a * xf[-1] + c0) / p.dt, rtol=1e-12, atol=1e-13)
+
+
+def test_exit_flux_balance_makes_the_all_neumann_problem_compatible(oracle):
+    # the radiation condition alone leaves sum(b_hat) != 0 (Sec. 2.6: it does not conserve mass);
+    # the uniform shift over the open exit faces makes the merged system compatible, and a closed
+    # exit face keeps its value
+    p = I.tiny_sphere(n=8)
+    p.bc = (0, 0, 0, 0, 0, 0)
+    p.dt = 0.5
+    p.ax = p.ax.copy()
+    p.ax[0, 0, -1] = 0.0                                        # one closed exit face
+    g0, _ = oracle.exit_flux(p, 1.3)
+    s0 = oracle.System(p, neumann_flux=[None, g0, None, None, None, None])
+    assert abs(s0.bhat.sum()) > 1e-6 * np.abs(s0.bhat).sum()
+    g, shift = oracle.exit_flux(p, 1.3, balance=True)
+    s = oracle.System(p, neumann_flux=[None, g, None, None, None, None])
+    assert abs(s.bhat.sum()) <= 1e-12 * np.abs(s.bhat).sum()
+    assert shift != 0.0 and g[0, 0] == g0[0, 0]
+    np.testing.assert_allclose((g0 - g)[s.apertures[0][:, :, -1] > 0], shift, rtol=1e-12)
+
+
+def test_exit_projection_is_the_discrete_orlanski_update(oracle):
+    # with the balanced exit flux the all-Neumann solve and the projection (Sec. 2.1 Eq. runge1)
+    # give every open exit face u_exit - dt (u_c du/dx + R) + dt * shift, i.e. Eq. orlanski
+    # advanced by dt with the momentum balance of Eq. exit, and every merge group is divergence-free
+    p = I.tiny_sphere(n=8)
+    p.bc = (0, 0, 0, 0, 0, 0)
+    p.dt = 0.5
+    uc = 0.9
+    R = np.random.default_rng(4).uniform(-1, 1, p.u.shape[:2])
+    g, shift = oracle.exit_flux(p, uc, R=R, balance=True)
+    flux = [None, g, None, None, None, None]
+    s = oracle.System(p, neumann_flux=flux)
+    ph = s.solve_dense()
+    u, v, w = oracle.project(p, s, ph, neumann_flux=flux)
+    ue, uu = p.u[:, :, -1], p.u[:, :, -2]
+    want = ue - p.dt * (uc * (ue - uu) / p.dx[-1] + R) + p.dt * shift
+    open_ = s.apertures[0][:, :, -1] > 0
+    np.testing.assert_allclose(u[:, :, -1][open_], want[open_], rtol=1e-12, atol=1e-12)
+    div = oracle.divergence(p, s, u, v, w)
+    scale = np.abs(s.fold((s.apertures[0] * np.abs(p.u))[:, :, 1:])).max() * p.dx.max() ** 2
+    assert np.abs(div).max() <= 1e-11 * scale
+    assert np.abs(oracle.divergence(p, s, p.u, p.v, p.w)).max() > 1e-3 * scale
+
+
 def test_projection_of_a_linear_pressure_closed_form(oracle):
     # uniform grid, rho = 1, p = a x at the cell centres: every open interior x face loses dt*a,
     # y and z faces keep their velocity, and the p = 0 face at x = 1 (half a cell from the last
