@@ -360,6 +360,7 @@ def run_ours(args, rank, world, local_rank):
         info64 = variants["fp64+jacobi"]
         st64, up64, _ = ctx.vofp_time_iteration_kernels(64, args.kernel_reps)
         paper_bc = paper_boundary_variants(vofp, prob, stream, mode, pc, args) if not args.no_paper_bc else None
+        vof_step = vof_advection_timing(vofp, ctx, prob, t, stream) if not args.no_paper_bc else None
 
 
     if rank != 0:
@@ -393,6 +394,7 @@ def run_ours(args, rank, world, local_rank):
         "projection": {"ms": proj_ms, "bytes_per_cell": PROJECTION_BYTES,
                        "gbs": PROJECTION_BYTES * n / (proj_ms * 1e-3) / 1e9, "max_group_divergence": max_div},
         "paper_bc": paper_bc,
+        "vof_advect": vof_step,
         "device_bytes": ctx.vofp_get_stats()["device_bytes"],
         "clocks": clk.summary(),
         "gpu_launches": launches[0],
@@ -401,6 +403,38 @@ def run_ours(args, rank, world, local_rank):
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(prob, info64["iterations"])
     print(json.dumps(out), flush=True)
+
+
+# VOF step (Sec. 2.4), FP64, per cell: the correction reads three apertures and three velocities
+# and writes four stage velocities (80 B); each of the three stages reads phi and the open volume
+# and writes the interface plane (48 B), then reads phi, the planes and two face velocities and
+# writes phi (56 B)
+VOF_BYTES = 80 + 3 * (48 + 56)
+
+
+def vof_advection_timing(vofp, ctx, prob, t, stream):
+    """One VOF step (flux-error correction and three split stages) on the workload's fraction and
+    face velocities, dt at Courant number 0.4 of the corrected velocities."""
+    import torch
+    ux, uy, wm, wp = ctx.vofp_vof_flux_correct(t["ax"], t["ay"], t["az"], t["u"], t["v"], t["w"])
+    rate = max((ux.abs().max() / float(prob.dx.min())).item(), (uy.abs().max() / float(prob.dy.min())).item(),
+               (torch.maximum(wm.abs(), wp.abs()).max() / float(prob.dz.min())).item())
+    dt = 0.4 / rate
+    out = torch.empty_like(t["F"])
+    args = (t["F"], t["ax"], t["ay"], t["az"], t["vf"], t["u"], t["v"], t["w"], dt)
+    for _ in range(2):
+        ctx.vofp_vof_advect(*args, out=out)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    a.record(stream)
+    for r in range(reps):
+        ctx.vofp_vof_advect(*args, order=r % 2, out=out)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    moved = (out - t["F"]).abs().max().item()
+    return {"ms": ms, "bytes_per_cell": VOF_BYTES, "gbs": VOF_BYTES * prob.n / (ms * 1e-3) / 1e9, "dt": dt,
+            "max_change": moved}
 
 
 def paper_boundary_variants(vofp, prob, stream, mode, pc, args):

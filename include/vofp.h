@@ -237,6 +237,40 @@ vofp_status vofp_exit_flux(vofp_ctx* ctx, const double* u, const double* v, cons
                            const double* body_flux, double u_c, const double* R, int balance, double* g,
                            double* shift);
 
+/* VOF operator of Sec. 2.4, part 1: flux-error correction.  Face fluxes F = A (u - v) with A the
+ * open face area (aperture x face area) and u, v, w the relative face velocities (u - v of the
+ * paper); each cell's conservation error E = sum_i (F+_i - F-_i) (Eq. diverge) is removed along
+ * z in proportion to the open areas of its two z faces (unchanged where both are closed); the
+ * stage velocities u^_i = dx_i F~_i / V on the uncut faces are written to
+ *   ux_hat   x faces (layout of u), uy_hat   y faces (layout of v),
+ *   wm_hat, wp_hat   cells: the cell's own -z and +z face values (a z face shared by two cells may
+ *                    carry two values after the correction).
+ * ax, ay, az, u, v, w, outputs: device FP64.  Needs a context (grid), not a built operator. */
+vofp_status vofp_vof_flux_correct(vofp_ctx* ctx, const double* ax, const double* ay, const double* az,
+                                  const double* u, const double* v, const double* w, double* ux_hat,
+                                  double* uy_hat, double* wm_hat, double* wp_hat);
+
+/* VOF operator of Sec. 2.4: phi_out = phi - VOF(u, phi, dt).  The flux-error correction above,
+ * then three operator-split stages along the axes (x, y, z) for order 0 or (z, y, x) for order 1
+ * (the paper alternates them between time steps).  A stage moves fluid through the uncut faces
+ * in slabs of thickness |u^| dt of the donor cell, cut by that cell's piecewise-linear interface
+ * (normal = minus the gradient of phi by central differences weighted (1, 2, 1) x (1, 2, 1) over
+ * the other two axes, skipping neighbours with vol_frac = 0 and outside the domain; plane position
+ * from phi), and adds the dilation term dt phi (u^+ - u^-) / dx with the stage's new phi in the
+ * first two stages and the stage's input phi in the third.  Inflow through a domain face takes the
+ * boundary cell as donor; phi is not clipped; the caller keeps |u^| dt within a cell (the Courant
+ * limit of Sec. 2.8).
+ *   F            device, cells: phi at the start of the step.
+ *   ax..w        device: apertures and relative face velocities (layouts of vofp_build_operator
+ *                and vofp_rhs_from_face_velocity); vol_frac device, cells.
+ *   dt > 0, order 0 or 1.
+ *   F_out        device, cells; may be F itself.
+ * Scratch (allocated on the first call, kept by the context): about 9 doubles per cell.
+ * Needs a context (grid), not a built operator. */
+vofp_status vofp_vof_advect(vofp_ctx* ctx, const double* F, const double* ax, const double* ay,
+                            const double* az, const double* vol_frac, const double* u, const double* v,
+                            const double* w, double dt, int order, double* F_out);
+
 /* y = A_hat x: x is read at each group's master cell; y receives the group's value at the master
  * and 0 at every other cell and at cells without an unknown. */
 vofp_status vofp_apply(vofp_ctx* ctx, const double* x, double* y);

@@ -145,6 +145,29 @@ vofp_status vofp_exit_flux(vofp_ctx* c, const double* u, const double* v, const 
     return fail_cuda(c);
 }
 
+vofp_status vofp_vof_flux_correct(vofp_ctx* c, const double* ax, const double* ay, const double* az,
+                                  const double* u, const double* v, const double* w, double* ux_hat, double* uy_hat,
+                                  double* wm_hat, double* wp_hat) {
+    vofp_status s = check_ctx(c, false);
+    if (s) return s;
+    if (!ax || !ay || !az || !u || !v || !w || !ux_hat || !uy_hat || !wm_hat || !wp_hat)
+        return invalid(c, "null input");
+    if ((s = vofp::vof_flux_correct(c, ax, ay, az, u, v, w, ux_hat, uy_hat, wm_hat, wp_hat))) return s;
+    return fail_cuda(c);
+}
+
+vofp_status vofp_vof_advect(vofp_ctx* c, const double* F, const double* ax, const double* ay, const double* az,
+                            const double* vol_frac, const double* u, const double* v, const double* w, double dt,
+                            int order, double* F_out) {
+    vofp_status s = check_ctx(c, false);
+    if (s) return s;
+    if (!F || !ax || !ay || !az || !vol_frac || !u || !v || !w || !F_out) return invalid(c, "null input");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return invalid(c, "dt must be positive");
+    if (order != 0 && order != 1) return invalid(c, "order must be 0 or 1");
+    if ((s = vofp::vof_advect(c, F, ax, ay, az, vol_frac, u, v, w, dt, order, F_out))) return s;
+    return fail_cuda(c);
+}
+
 vofp_status vofp_apply(vofp_ctx* c, const double* x, double* y) {
     vofp_status s = check_ctx(c, true);
     if (s) return s;

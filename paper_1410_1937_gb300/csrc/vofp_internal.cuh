@@ -150,6 +150,9 @@ struct vofp_ctx {
     int *rbc_gref = nullptr, *rbc_gfx = nullptr;     // compact / fix-row index of every gcells entry
     int *rbc_gm = nullptr, *rbc_gf = nullptr;        // per group: four members' compact / fix-row index
     int* rbc_gn = nullptr;            // per group: member count
+    // VOF operator (vofp_vof.cu): corrected stage velocities, two stage buffers, interface planes
+    double *vof_uxh = nullptr, *vof_uyh = nullptr, *vof_wmh = nullptr, *vof_wph = nullptr;
+    double *vof_phi = nullptr, *vof_plic = nullptr;
     long long rbc_cap = 0;            // allocated compact length
     int rbc_blocks_per_sm = 0;
     int tma_blocks_deep32 = 0;        // resident blocks per SM of the six-stage FP32 stencil
@@ -260,6 +263,13 @@ __device__ __forceinline__ void cell_ijk(const Dims& d, long long c, int& i, int
 // projection of the face velocities and its divergence check (vofp_project.cu)
 vofp_status project(vofp_ctx* c, const double* p, const double* u, const double* v, const double* w,
                     const double* body, double* uo, double* vo, double* wo, double* div, double* max_div);
+
+// VOF operator of Sec. 2.4 (vofp_vof.cu)
+vofp_status vof_flux_correct(vofp_ctx* c, const double* ax, const double* ay, const double* az, const double* u,
+                             const double* v, const double* w, double* uxh, double* uyh, double* wmh, double* wph);
+vofp_status vof_advect(vofp_ctx* c, const double* F, const double* ax, const double* ay, const double* az,
+                       const double* vf, const double* u, const double* v, const double* w, double dt, int order,
+                       double* F_out);
 
 // exit flux of the radiation condition, installed as the +x face's prescribed flux (vofp_exit.cu)
 vofp_status exit_flux(vofp_ctx* c, const double* u, const double* v, const double* w, const double* body, double uc,

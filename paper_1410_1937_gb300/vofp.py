@@ -80,6 +80,8 @@ _sig = {
     "vofp_rhs_from_face_velocity": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "vofp_project": (ctypes.c_int, [_vp] * 10 + [_P(ctypes.c_double)]),
     "vofp_exit_flux": (ctypes.c_int, [_vp] * 5 + [ctypes.c_double, _vp, ctypes.c_int, _vp, _P(ctypes.c_double)]),
+    "vofp_vof_flux_correct": (ctypes.c_int, [_vp] * 11),
+    "vofp_vof_advect": (ctypes.c_int, [_vp] * 9 + [ctypes.c_double, ctypes.c_int, _vp]),
     "vofp_apply": (ctypes.c_int, [_vp, _vp, _vp]),
     "vofp_residual": (ctypes.c_int, [_vp, _vp, _vp, _P(ctypes.c_double)]),
     "vofp_solve": (ctypes.c_int, [_vp, _vp, _vp, _P(_Opts), _P(_Info)]),
@@ -250,6 +252,30 @@ class Context:
                                            float(u_c), None if R is None else _dev(R, rows, "R"), int(bool(balance)),
                                            _dev(out, rows, "g"), ctypes.byref(sh)))
         return out, sh.value
+
+    def vofp_vof_flux_correct(self, ax, ay, az, u, v, w):
+        """Flux-error correction of Sec. 2.4: (ux^ on x faces, uy^ on y faces, wm^, wp^ per cell)."""
+        import torch
+        o = (torch.empty_like(u), torch.empty_like(v), torch.empty(self.n, dtype=torch.float64, device=u.device),
+             torch.empty(self.n, dtype=torch.float64, device=u.device))
+        _check(self.h, _lib.vofp_vof_flux_correct(self.h, _dev(ax, self.nfx, "ax"), _dev(ay, self.nfy, "ay"),
+                                                  _dev(az, self.nfz, "az"), _dev(u, self.nfx, "u"),
+                                                  _dev(v, self.nfy, "v"), _dev(w, self.nfz, "w"),
+                                                  _dev(o[0], self.nfx, "ux_hat"), _dev(o[1], self.nfy, "uy_hat"),
+                                                  _dev(o[2], self.n, "wm_hat"), _dev(o[3], self.n, "wp_hat")))
+        return o
+
+    def vofp_vof_advect(self, F, ax, ay, az, vol_frac, u, v, w, dt, order=0, out=None):
+        """phi - VOF(u, phi, dt) of Sec. 2.4 (flux-error correction, three split stages)."""
+        import torch
+        if out is None:
+            out = torch.empty_like(F)
+        _check(self.h, _lib.vofp_vof_advect(self.h, _dev(F, self.n, "F"), _dev(ax, self.nfx, "ax"),
+                                            _dev(ay, self.nfy, "ay"), _dev(az, self.nfz, "az"),
+                                            _dev(vol_frac, self.n, "vol_frac"), _dev(u, self.nfx, "u"),
+                                            _dev(v, self.nfy, "v"), _dev(w, self.nfz, "w"), float(dt), int(order),
+                                            _dev(out, self.n, "F_out")))
+        return out
 
     def vofp_apply(self, x, out=None):
         import torch

@@ -187,16 +187,12 @@ def test_dilation_keeps_full_and_empty_cells(vof):
     p.F = plane_fractions(xn, yn, zn, nrm, 0.52)
     stream_function_flow(p, xn, zn, 0.05)
     dt = 0.45 / (np.abs(p.u).max() / p.dx[0] + np.abs(p.w).max() / p.dz[0])
-    full = np.ones_like(p.F, dtype=bool)
-    empty = np.ones_like(p.F, dtype=bool)
-    P = np.pad(p.F, 1, mode="edge")
-    for dk in range(3):
-        for dj in range(3):
-            for di in range(3):
-                nb = P[dk:dk + n, dj:dj + n, di:di + n]
-                full &= nb == 1.0
-                empty &= nb == 0.0
-    assert full.sum() > 50 and empty.sum() > 50
+    # three stages move fluid at most three cells: cells whose 7x7x7 neighbourhood is all full
+    # (all empty) must come back exactly full (empty)
+    from scipy.ndimage import maximum_filter, minimum_filter
+    full = minimum_filter(p.F, size=7, mode="nearest") == 1.0
+    empty = maximum_filter(p.F, size=7, mode="nearest") == 0.0
+    assert full.sum() > 20 and empty.sum() > 20
     for order in (0, 1):
         got = vof.advect(p, dt=dt, order=order)
         assert np.abs(got[full] - 1.0).max() <= 1e-14
