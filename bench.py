@@ -361,6 +361,7 @@ def run_ours(args, rank, world, local_rank):
         st64, up64, _ = ctx.vofp_time_iteration_kernels(64, args.kernel_reps)
         paper_bc = paper_boundary_variants(vofp, prob, stream, mode, pc, args) if not args.no_paper_bc else None
         vof_step = vof_advection_timing(vofp, ctx, prob, t, stream) if not args.no_paper_bc else None
+        rk2 = rk2_timing(vofp, prob, stream, pc, args) if not args.no_paper_bc else None
 
 
     if rank != 0:
@@ -395,6 +396,7 @@ def run_ours(args, rank, world, local_rank):
                        "gbs": PROJECTION_BYTES * n / (proj_ms * 1e-3) / 1e9, "max_group_divergence": max_div},
         "paper_bc": paper_bc,
         "vof_advect": vof_step,
+        "rk2_step": rk2,
         "device_bytes": ctx.vofp_get_stats()["device_bytes"],
         "clocks": clk.summary(),
         "gpu_launches": launches[0],
@@ -435,6 +437,40 @@ def vof_advection_timing(vofp, ctx, prob, t, stream):
     moved = (out - t["F"]).abs().max().item()
     return {"ms": ms, "bytes_per_cell": VOF_BYTES, "gbs": VOF_BYTES * prob.n / (ms * 1e-3) / 1e9, "dt": dt,
             "max_change": moved}
+
+
+def rk2_timing(vofp, prob, stream, pc, args, steps=2):
+    """The paper's call pattern (Sec. 2.1): RK2 steps of two operator builds, two mixed solves (the
+    first from the previous step's pressure, the second from the first's), two projections and two
+    VOF steps each, on the workload with dt at Courant number 0.25 of its corrected VOF velocities and
+    seeded U[-1, 1] momentum terms R."""
+    import torch
+    from paper_1410_1937_gb300 import inputs as I
+    R = tuple(torch.from_numpy(a.ravel()).cuda() for a in I.momentum_terms(prob))
+    ctx = vofp.Context(prob.dx, prob.dy, prob.dz, stream)
+    t = {k: torch.from_numpy(np.ascontiguousarray(getattr(prob, k)).ravel()).cuda()
+         for k in ("F", "vf", "ax", "ay", "az", "u", "v", "w")}
+    # dt from the corrected VOF velocities of the initial field (the z correction can exceed u)
+    ux, uy, wm, wp = ctx.vofp_vof_flux_correct(t["ax"], t["ay"], t["az"], t["u"], t["v"], t["w"])
+    rate = max((ux.abs().max() / float(prob.dx.min())).item(), (uy.abs().max() / float(prob.dy.min())).item(),
+               (torch.maximum(wm.abs(), wp.abs()).max() / float(prob.dz.min())).item())
+    dt = 0.25 / rate
+    p = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    out = []
+    for k in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        i1, i2, mx = ctx.vofp_rk2_step(t["F"], t["ax"], t["ay"], t["az"], t["vf"], t["u"], t["v"], t["w"], prob.bc, p,
+                                       order=k % 2, R=R, rho_liquid=prob.rho_liquid, rho_gas=prob.rho_gas,
+                                       merge_threshold=prob.merge_threshold, dt=dt, precond=pc, rtol=RTOL,
+                                       inner_rtol=args.inner_rtol, raise_on_error=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out.append({"ms": a.elapsed_time(b), "solve1_iterations": i1["iterations"], "solve1_ms": i1["seconds"] * 1e3,
+                    "solve2_iterations": i2["iterations"], "solve2_ms": i2["seconds"] * 1e3,
+                    "status": [i1["status_name"], i2["status_name"]], "max_group_divergence": mx})
+    ctx.close()
+    return {"dt": dt, "steps": out}
 
 
 def paper_boundary_variants(vofp, prob, stream, mode, pc, args):

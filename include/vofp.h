@@ -271,6 +271,40 @@ vofp_status vofp_vof_advect(vofp_ctx* ctx, const double* F, const double* ax, co
                             const double* az, const double* vol_frac, const double* u, const double* v,
                             const double* w, double dt, int order, double* F_out);
 
+/* One second-order Runge-Kutta step of Sec. 2.1 around the pressure solve, from the library's own
+ * calls on the context stream:
+ *   stage 1: operator with rho(phi^k); P* from the face field u^k + dt R (Eq. poisson1), the solve
+ *            starting from p; u* = u^k + dt (R - grad P* / rho) (Eq. runge1);
+ *            phi* = phi^k - VOF(u^k, phi^k, dt);
+ *   stage 2: operator with rho(phi*); P^{k+1} from the face field u* + u^k + dt R (Eq. poisson2),
+ *            the solve starting from P*; u^{k+1} = (u* + u^k + dt (R - grad P^{k+1} / rho)) / 2
+ *            (Eq. runge2); phi^{k+1} = phi^k - VOF((u* + u^k) / 2, phi^k, dt).
+ * The right-hand side of each solve is -(1/dt) times the divergence of its face field and the
+ * projection subtracts dt grad P / rho on the operator's faces (vofp_rhs_from_face_velocity,
+ * vofp_project); VOF is vofp_vof_advect with the given axis order.
+ *   F            device, cells: phi^k in, phi^{k+1} out.
+ *   ax..vol_frac device: apertures and open volumes (as for vofp_build_operator).
+ *   u, v, w      device, face velocities: u^k in, u^{k+1} out.
+ *   Ru, Rv, Rw   device, face arrays of the momentum terms R, or all NULL (R = 0).
+ *   bc, phys     as for vofp_build_operator (phys->dt is the step).
+ *   opts         as for vofp_solve (x0_zero is ignored: both solves start from a pressure).
+ *   p            device, cells: the first solve's starting guess in (the previous step's P^{k+1},
+ *                or zeros), P^{k+1} out.
+ *   order        0 or 1, the VOF axis order (alternate between steps).
+ *   info         host, or NULL: both solves' vofp_solve_info and the largest group divergence of
+ *                u^{k+1}.
+ * Scratch: about 6 face arrays and 3 cell arrays, allocated on the first call.  Errors: those of
+ * the calls it is made of; the step stops at the first failure (its arrays are then partly
+ * updated). */
+typedef struct {
+    vofp_solve_info solve1, solve2;
+    double max_div;
+} vofp_rk2_info;
+vofp_status vofp_rk2_step(vofp_ctx* ctx, double* F, const double* ax, const double* ay, const double* az,
+                          const double* vol_frac, double* u, double* v, double* w, const double* Ru,
+                          const double* Rv, const double* Rw, const vofp_bc* bc, const vofp_phys* phys,
+                          const vofp_solve_opts* opts, double* p, int order, vofp_rk2_info* info);
+
 /* y = A_hat x: x is read at each group's master cell; y receives the group's value at the master
  * and 0 at every other cell and at cells without an unknown. */
 vofp_status vofp_apply(vofp_ctx* ctx, const double* x, double* y);

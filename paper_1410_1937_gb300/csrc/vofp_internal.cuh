@@ -153,6 +153,7 @@ struct vofp_ctx {
     // VOF operator (vofp_vof.cu): corrected stage velocities, two stage buffers, interface planes
     double *vof_uxh = nullptr, *vof_uyh = nullptr, *vof_wmh = nullptr, *vof_wph = nullptr;
     double *vof_phi = nullptr, *vof_plic = nullptr;
+    double* rk2_buf = nullptr;        // RK2 step (vofp_rk2.cu): face fields and cell arrays
     long long rbc_cap = 0;            // allocated compact length
     int rbc_blocks_per_sm = 0;
     int tma_blocks_deep32 = 0;        // resident blocks per SM of the six-stage FP32 stencil

@@ -485,6 +485,14 @@ def config(i: int, **kw) -> Problem:
     return (config0, config1, config2, lambda **k: config3_sample(200000, **k), config4)[i](**kw)
 
 
+def momentum_terms(prob: Problem, seed: int = 21):
+    """Seeded stand-in for the momentum terms R of Sec. 2.1 (convection, hydrostatics, viscosity,
+    sub-grid and body forces) on the x, y and z faces: independent U[-1, 1] values."""
+    rng = np.random.default_rng(seed)
+    return (rng.uniform(-1.0, 1.0, prob.u.shape), rng.uniform(-1.0, 1.0, prob.v.shape),
+            rng.uniform(-1.0, 1.0, prob.w.shape))
+
+
 def tiny_sphere(n: int = 8, seed: int = 7, radius: float = 0.3, threshold: float = 0.25,
                 center=(0.05, -0.02, 0.03)) -> Problem:
     """n^3 uniform cells on [-1/2,1/2]^3 cut by a sphere, with merging; small enough for dense

@@ -62,6 +62,10 @@ class _Info(ctypes.Structure):
                 ("status", ctypes.c_int), ("nn_applications", ctypes.c_int), ("fell_back", ctypes.c_int)]
 
 
+class _Rk2Info(ctypes.Structure):
+    _fields_ = [("solve1", _Info), ("solve2", _Info), ("max_div", ctypes.c_double)]
+
+
 class _Stats(ctypes.Structure):
     _fields_ = [("cells", ctypes.c_longlong), ("unknowns", ctypes.c_longlong),
                 ("inactive", ctypes.c_longlong), ("merged_cells", ctypes.c_longlong),
@@ -82,6 +86,7 @@ _sig = {
     "vofp_exit_flux": (ctypes.c_int, [_vp] * 5 + [ctypes.c_double, _vp, ctypes.c_int, _vp, _P(ctypes.c_double)]),
     "vofp_vof_flux_correct": (ctypes.c_int, [_vp] * 11),
     "vofp_vof_advect": (ctypes.c_int, [_vp] * 9 + [ctypes.c_double, ctypes.c_int, _vp]),
+    "vofp_rk2_step": (ctypes.c_int, [_vp] * 12 + [_P(_Bc), _P(_Phys), _P(_Opts), _vp, ctypes.c_int, _P(_Rk2Info)]),
     "vofp_apply": (ctypes.c_int, [_vp, _vp, _vp]),
     "vofp_residual": (ctypes.c_int, [_vp, _vp, _vp, _P(ctypes.c_double)]),
     "vofp_solve": (ctypes.c_int, [_vp, _vp, _vp, _P(_Opts), _P(_Info)]),
@@ -276,6 +281,33 @@ class Context:
                                             _dev(v, self.nfy, "v"), _dev(w, self.nfz, "w"), float(dt), int(order),
                                             _dev(out, self.n, "F_out")))
         return out
+
+    def vofp_rk2_step(self, F, ax, ay, az, vol_frac, u, v, w, bc, p, order=0, R=None, neumann_flux=None,
+                      rho_liquid=1000.0, rho_gas=1.2, merge_threshold=0.1, density_smoothing=0, dt=1.0,
+                      mode=MODE_MIXED, precond=PRECOND_RBSGS, rtol=1e-8, max_iter=100000, inner_rtol=0.0,
+                      check_every=8, raise_on_error=True):
+        """One RK2 step of Sec. 2.1 (two solves, two projections, two VOF steps); F, u, v, w and p
+        are updated in place.  Returns the two solves' info dicts and the largest group divergence."""
+        b = self._bc(bc, neumann_flux)
+        ph = _Phys(float(rho_liquid), float(rho_gas), float(merge_threshold), int(density_smoothing), float(dt))
+        o = _Opts(int(mode), int(precond), float(rtol), int(max_iter), float(inner_rtol), int(check_every), 0, 0,
+                  None, 20, 0)
+        info = _Rk2Info()
+        Rs = (None, None, None) if R is None else (_dev(R[0], self.nfx, "Ru"), _dev(R[1], self.nfy, "Rv"),
+                                                   _dev(R[2], self.nfz, "Rw"))
+        st = _lib.vofp_rk2_step(self.h, _dev(F, self.n, "F"), _dev(ax, self.nfx, "ax"), _dev(ay, self.nfy, "ay"),
+                                _dev(az, self.nfz, "az"), _dev(vol_frac, self.n, "vol_frac"), _dev(u, self.nfx, "u"),
+                                _dev(v, self.nfy, "v"), _dev(w, self.nfz, "w"), *Rs, ctypes.byref(b),
+                                ctypes.byref(ph), ctypes.byref(o), _dev(p, self.n, "p"), int(order),
+                                ctypes.byref(info))
+        if raise_on_error:
+            _check(self.h, st)
+
+        def d(i):
+            return {"iterations": i.iterations, "outer_iterations": i.outer_iterations,
+                    "rel_residual": i.rel_residual, "seconds": i.seconds, "status": i.status,
+                    "status_name": STATUS_NAMES.get(i.status, str(i.status))}
+        return d(info.solve1), d(info.solve2), info.max_div
 
     def vofp_apply(self, x, out=None):
         import torch
