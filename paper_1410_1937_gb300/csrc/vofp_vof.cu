@@ -10,7 +10,7 @@
 //
 // Stage along axis d (two passes): the piecewise-linear interface of every cell with 0 < phi < 1
 // (normal m = -grad phi by central differences weighted (1, 2, 1) x (1, 2, 1) across the other
-// axes; plane constant alpha with the fluid volume {m.x <= alpha} equal to phi V, by bisection),
+// axes; plane constant alpha with the fluid volume {m.x <= alpha} equal to phi V, by safeguarded Newton steps),
 // then per cell the fluid carried through its two d faces in slabs of thickness |u^| dt of the
 // donor cell (the cell itself on outflow, the neighbour on inflow; the boundary cell on inflow
 // through a domain face), and
@@ -109,6 +109,22 @@ struct CubeFrac {
         }
         return flip ? 1.0 - f : f;
     }
+    // d/db of the fraction: the area of the cut, region by region (the fraction is symmetric,
+    // f(b) = 1 - f(1 - b), so its derivative at b is the one at 1 - b)
+    __device__ double deriv(double b) const {
+        if (b > 0.5) b = 1.0 - b;
+        if (b <= 0.0) return 0.0;
+        const double c12 = c1 + c2;
+        if (b < c1) return b * (b * ic1) * (3.0 * k6);
+        if (b < c2) return (2.0 * b - c1) * k2;
+        const double e2 = b - c2;
+        if (b < fmin(c12, c3)) return (2.0 * b - c1 - e2 * (e2 * ic1)) * k2;
+        if (c3 < c12) {
+            const double e3 = b - c3;
+            return (2.0 * b - c1 - e2 * (e2 * ic1) - e3 * (e3 * ic1)) * k2;
+        }
+        return 2.0 * k5;
+    }
 };
 
 // volume of {x in [0,h] : m.x <= alpha}
@@ -122,11 +138,12 @@ __device__ double box_volume(double mx, double my, double mz, double alpha, doub
     const double vol = (hx * hy) * hz;
     if (alpha <= 0.0) return 0.0;
     if (alpha >= s) return vol;
-    a1 /= s;
-    a2 /= s;
-    a3 /= s;
+    const double is = 1.0 / s;
+    a1 *= is;
+    a2 *= is;
+    a3 *= is;
     sort3(a1, a2, a3);
-    return cube_fraction(a1, a2, a3, alpha / s) * vol;
+    return cube_fraction(a1, a2, a3, alpha * is) * vol;
 }
 
 // ---- correction --------------------------------------------------------------------------------
@@ -149,14 +166,15 @@ __global__ void k_vof_correct(Dims d, const double* __restrict__ dx, const doubl
         const double Fzm = Am * w[fzm], Fzp = Ap * w[fzp];
         const double E = ((Fxp - Fxm) + (Fyp - Fym)) + (Fzp - Fzm);
         const double tot = Ap + Am;
-        const double fp = tot > 0.0 ? Fzp - E * Ap / tot : Fzp;
-        const double fm = tot > 0.0 ? Fzm + E * Am / tot : Fzm;
-        wph[c] = fp / Sz;
-        wmh[c] = fm / Sz;
-        uxh[fxm] = Fxm / Sx;
-        if (i == d.nx - 1) uxh[fxp] = Fxp / Sx;
-        uyh[fym] = Fym / Sy;
-        if (j == d.ny - 1) uyh[fyp] = Fyp / Sy;
+        const double share = tot > 0.0 ? E / tot : 0.0;
+        const double iSz = 1.0 / Sz;
+        wph[c] = (Fzp - share * Ap) * iSz;
+        wmh[c] = (Fzm + share * Am) * iSz;
+        // u^ = F / S = aperture x velocity on the x and y faces
+        uxh[fxm] = ax[fxm] * u[fxm];
+        if (i == d.nx - 1) uxh[fxp] = ax[fxp] * u[fxp];
+        uyh[fym] = ay[fym] * v[fym];
+        if (j == d.ny - 1) uyh[fyp] = ay[fyp] * v[fyp];
     }
 }
 
@@ -203,21 +221,32 @@ __global__ void k_vof_plic(Dims d, const double* __restrict__ dx, const double* 
                      mz = -(gz / 16.0) / span(dz, k, d.nz);
         const double hx = dx[i], hy = dy[j], hz = dz[k];
         // with x_i -> h_i - x_i for negative components the fluid is {a.y <= beta} in the unit
-        // cube, a_i = |m_i| h_i / s, beta = (alpha - lo) / s, s = sum |m_i| h_i: bisect on beta
+        // cube, a_i = |m_i| h_i / s, beta = (alpha - lo) / s, s = sum |m_i| h_i: Newton steps on
+        // beta with the cut area as derivative, kept inside a bracket that bisects when a step
+        // leaves it
         const double lo0 = fmin(mx * hx, 0.0) + fmin(my * hy, 0.0) + fmin(mz * hz, 0.0);
         const double a1 = fabs(mx) * hx, a2 = fabs(my) * hy, a3 = fabs(mz) * hz;
         const double sum = (a1 + a2) + a3;
         double alpha = 0.0;
         if (sum > 0.0) {
-            const CubeFrac f(a1 / sum, a2 / sum, a3 / sum);
-            double lo = 0.0, hi = 1.0;
-            for (int it = 0; it < 200; ++it) {
-                const double mid = 0.5 * (lo + hi);
-                if (mid == lo || mid == hi) break;
-                if (f(mid) < pc) lo = mid;
-                else hi = mid;
+            const double is = 1.0 / sum;
+            const CubeFrac f(a1 * is, a2 * is, a3 * is);
+            double lo = 0.0, hi = 1.0, b = pc;
+            for (int it = 0; it < 100; ++it) {
+                const double r = f(b) - pc;
+                if (r == 0.0) break;
+                if (r < 0.0) lo = b;
+                else hi = b;
+                const double dv = f.deriv(b);
+                double nb = dv > 0.0 ? b - r / dv : 0.5 * (lo + hi);
+                if (!(nb > lo && nb < hi)) nb = 0.5 * (lo + hi);
+                if (nb == b || fabs(nb - b) <= 2.3e-16 * b) {
+                    b = nb;
+                    break;
+                }
+                b = nb;
             }
-            alpha = lo0 + 0.5 * (lo + hi) * sum;
+            alpha = lo0 + b * sum;
         }
         plic[c] = make_double4(mx, my, mz, alpha);
     }
@@ -290,10 +319,10 @@ __global__ void k_vof_stage(Dims d, int axis, int implicit, double dt, const dou
         } else {
             Fm = -slab(pc, lc, hx, hy, hz, axis, false, -um * dt);
         }
-        const double V = (hx * hy) * hz;
-        const double hd = axis == 0 ? hx : axis == 1 ? hy : hz;
-        const double adv = pc - (Fp - Fm) / V;
-        const double div = dt * (up - um) / hd;
+        const double iV = 1.0 / ((hx * hy) * hz);
+        const double other = axis == 0 ? hy * hz : axis == 1 ? hx * hz : hx * hy;   // V / dx_d
+        const double adv = pc - (Fp - Fm) * iV;
+        const double div = dt * (up - um) * (other * iV);
         out[c] = implicit ? adv / (1.0 - div) : adv + pc * div;
     }
 }
