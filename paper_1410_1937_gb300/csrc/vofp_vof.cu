@@ -10,7 +10,7 @@
 //
 // Stage along axis d (two passes): the piecewise-linear interface of every cell with 0 < phi < 1
 // (normal m = -grad phi by central differences weighted (1, 2, 1) x (1, 2, 1) across the other
-// axes; plane constant alpha with the fluid volume {m.x <= alpha} equal to phi V, by safeguarded Newton steps),
+// axes; plane constant alpha with the fluid volume {m.x <= alpha} equal to phi V, by Newton steps),
 // then per cell the fluid carried through its two d faces in slabs of thickness |u^| dt of the
 // donor cell (the cell itself on outflow, the neighbour on inflow; the boundary cell on inflow
 // through a domain face), and

@@ -1,8 +1,8 @@
 """GPU parity of the VOF operator (Sec. 2.4) against oracle/vof.py on the same seeded inputs.
 
 Tolerances: the correction is the same FP64 arithmetic in the same order (1e-13 relative); after
-the three stages the fractions agree to 1e-11 (the plane constants come from two bisections of the
-same monotone volume, bisection in the oracle and Newton steps on the GPU, which may stop a few
+the three stages the fractions agree to 1e-11 (the plane constants come from two root searches on
+the same monotone volume, bisection in the oracle and Newton steps on the GPU, which may stop a few
 units in the last place apart).
 """
 import numpy as np
