@@ -86,6 +86,11 @@ void vofp_destroy(vofp_ctx* c) {
     if (c->graph_mixed) cudaGraphExecDestroy(c->graph_mixed);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->copy_stream) {
+        cudaStreamSynchronize(c->copy_stream);
+        cudaStreamDestroy(c->copy_stream);
+    }
+    if (c->copy_done) cudaEventDestroy(c->copy_done);
     for (void* p : c->allocs) cudaFree(p);
     delete c;
 }
@@ -222,15 +227,28 @@ vofp_status vofp_solve_host(vofp_ctx* c, const double* F, const double* ax, cons
     double *dax = p + 4 * N, *day = dax + nfx, *daz = day + nfy;
     double *du = daz + nfz, *dv = du + nfx, *dw = dv + nfy;
     cudaStream_t st = c->stream;
+    if (!c->copy_stream) {
+        VOFP_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+        VOFP_CUDA_TRY(c, cudaEventCreateWithFlags(&c->copy_done, cudaEventDisableTiming));
+    }
+    // the operator's inputs on the context stream; the face velocities on the copy stream while
+    // the operator builds (the previous call ended with both streams idle)
     VOFP_CUDA_TRY(c, cudaMemcpyAsync(dF, F, sizeof(double) * N, cudaMemcpyHostToDevice, st));
     if (vf) VOFP_CUDA_TRY(c, cudaMemcpyAsync(dvf, vf, sizeof(double) * N, cudaMemcpyHostToDevice, st));
     VOFP_CUDA_TRY(c, cudaMemcpyAsync(dax, ax, sizeof(double) * nfx, cudaMemcpyHostToDevice, st));
     VOFP_CUDA_TRY(c, cudaMemcpyAsync(day, ay, sizeof(double) * nfy, cudaMemcpyHostToDevice, st));
     VOFP_CUDA_TRY(c, cudaMemcpyAsync(daz, az, sizeof(double) * nfz, cudaMemcpyHostToDevice, st));
-    VOFP_CUDA_TRY(c, cudaMemcpyAsync(du, u, sizeof(double) * nfx, cudaMemcpyHostToDevice, st));
-    VOFP_CUDA_TRY(c, cudaMemcpyAsync(dv, v, sizeof(double) * nfy, cudaMemcpyHostToDevice, st));
-    VOFP_CUDA_TRY(c, cudaMemcpyAsync(dw, w, sizeof(double) * nfz, cudaMemcpyHostToDevice, st));
-    if ((s = vofp_build_operator(c, dF, dax, day, daz, vf ? dvf : nullptr, bc, phys))) return s;
+    cudaStream_t cs = c->copy_stream;
+    VOFP_CUDA_TRY(c, cudaMemcpyAsync(du, u, sizeof(double) * nfx, cudaMemcpyHostToDevice, cs));
+    VOFP_CUDA_TRY(c, cudaMemcpyAsync(dv, v, sizeof(double) * nfy, cudaMemcpyHostToDevice, cs));
+    VOFP_CUDA_TRY(c, cudaMemcpyAsync(dw, w, sizeof(double) * nfz, cudaMemcpyHostToDevice, cs));
+    VOFP_CUDA_TRY(c, cudaEventRecord(c->copy_done, cs));
+    s = vofp_build_operator(c, dF, dax, day, daz, vf ? dvf : nullptr, bc, phys);
+    VOFP_CUDA_TRY(c, cudaStreamWaitEvent(st, c->copy_done, 0));
+    if (s) {
+        cudaStreamSynchronize(cs);
+        return s;
+    }
     if ((s = vofp_rhs_from_face_velocity(c, du, dv, dw, nullptr, db))) return s;
     vofp_solve_opts o2 = *o;
     o2.x0_zero = 1;

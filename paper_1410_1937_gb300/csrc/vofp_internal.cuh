@@ -121,6 +121,9 @@ struct vofp_ctx {
     cudaGraphExec_t graph_mixed = nullptr;
     int graph_mixed_key = -1;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // vofp_solve_host: a copy stream that brings the face velocities in while the operator builds
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t copy_done = nullptr;
 
     size_t bytes = 0;
     std::vector<void*> allocs;
