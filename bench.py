@@ -293,7 +293,7 @@ def run_ours(args, rank, world, local_rank):
                                          rho_liquid=prob.rho_liquid, rho_gas=prob.rho_gas,
                                          merge_threshold=prob.merge_threshold, dt=prob.dt, precond=pc)
                 assert r["status"] == 0, r
-            for _ in range(max(1, args.warmup // 2)):
+            for _ in range(max(1, args.warmup)):
                 host_step()
             if world > 1:
                 dist.barrier()
