@@ -51,3 +51,23 @@ def test_invalid_arguments_rejected_before_device_use(lib):
     assert vofp.vofp_version().startswith("vofp")
     lib.vofp_last_error.restype = ctypes.c_char_p
     assert lib.vofp_last_error(None) == b"null context"
+
+
+def test_null_context_is_rejected_by_every_entry_point():
+    # no device is touched: each call checks its context first
+    from paper_1410_1937_gb300 import vofp
+    L = vofp._lib
+    n = None
+    calls = {
+        "vofp_build_operator": lambda: L.vofp_build_operator(n, n, n, n, n, n, n, n),
+        "vofp_rhs_from_face_velocity": lambda: L.vofp_rhs_from_face_velocity(n, n, n, n, n, n),
+        "vofp_project": lambda: L.vofp_project(n, n, n, n, n, n, n, n, n, n, n),
+        "vofp_exit_flux": lambda: L.vofp_exit_flux(n, n, n, n, n, 1.0, n, 0, n, n),
+        "vofp_vof_flux_correct": lambda: L.vofp_vof_flux_correct(*([n] * 11)),
+        "vofp_vof_advect": lambda: L.vofp_vof_advect(*([n] * 9), 0.1, 0, n),
+        "vofp_rk2_step": lambda: L.vofp_rk2_step(*([n] * 15), n, 0, n),
+        "vofp_apply": lambda: L.vofp_apply(n, n, n),
+        "vofp_solve": lambda: L.vofp_solve(n, n, n, n, n),
+    }
+    for name, call in calls.items():
+        assert call() == vofp.ERR_INVALID_ARG, name
