@@ -103,3 +103,42 @@ def test_advection_full_size_properties(vofp, vof):
     assert np.abs(got[full] - 1.0).max() <= 1e-12
     assert np.abs(got[empty]).max() <= 1e-12
     ctx.close()
+
+
+def test_advection_small_and_degenerate_grids(vofp, vof):
+    """A row of five cells with closed z faces (the oracle's one-dimensional closed form), a 7x3x5
+    box of random fractions and velocities, and a single cell: GPU against the oracle."""
+    z = np.zeros
+    rng = np.random.default_rng(17)
+    cases = []
+    nx, h = 5, 0.2
+    row = I.Problem(name="vof-row", dx=np.full(nx, h), dy=np.array([0.3]), dz=np.array([0.4]),
+                    F=np.array([[[1.0, 1.0, 0.5, 0.0, 0.0]]]), vf=np.ones((1, 1, nx)), ax=np.ones((1, 1, nx + 1)),
+                    ay=np.ones((1, 2, nx)), az=np.zeros((2, 1, nx)), u=z((1, 1, nx + 1)), v=z((1, 2, nx)),
+                    w=z((2, 1, nx)))
+    row.u[0, 0, :] = 0.6 * np.arange(nx + 1) * h
+    cases.append((row, 0.4 * h / (0.6 * nx * h)))
+    shp = (5, 3, 7)
+    box = I.Problem(name="vof-box", dx=rng.uniform(0.5, 1.5, shp[2]), dy=rng.uniform(0.5, 1.5, shp[1]),
+                    dz=rng.uniform(0.5, 1.5, shp[0]), F=rng.uniform(0, 1, shp), vf=np.ones(shp),
+                    ax=rng.uniform(0, 1, (shp[0], shp[1], shp[2] + 1)), ay=rng.uniform(0, 1, (shp[0], shp[1] + 1, shp[2])),
+                    az=rng.uniform(0, 1, (shp[0] + 1, shp[1], shp[2])), u=rng.uniform(-1, 1, (shp[0], shp[1], shp[2] + 1)),
+                    v=rng.uniform(-1, 1, (shp[0], shp[1] + 1, shp[2])), w=rng.uniform(-1, 1, (shp[0] + 1, shp[1], shp[2])))
+    box.F[box.F < 0.2] = 0.0
+    box.F[box.F > 0.8] = 1.0
+    box.vf[0, 0, 0] = 0.0
+    cases.append((box, stable_dt(box, vof, 0.3)))
+    one = I.Problem(name="vof-one", dx=np.array([1.0]), dy=np.array([1.0]), dz=np.array([1.0]),
+                    F=np.array([[[0.3]]]), vf=np.ones((1, 1, 1)), ax=np.ones((1, 1, 2)), ay=np.ones((1, 2, 1)),
+                    az=np.ones((2, 1, 1)), u=np.array([[[0.2, 0.1]]]), v=np.array([[[0.0], [0.1]]]),
+                    w=np.array([[[0.1]], [[-0.2]]]))
+    cases.append((one, 0.5))
+    for prob, dt in cases:
+        ctx = vofp.Context(prob.dx, prob.dy, prob.dz)
+        t = {k: dev(getattr(prob, k)) for k in ("F", "vf", "ax", "ay", "az", "u", "v", "w")}
+        for order in (0, 1):
+            out = ctx.vofp_vof_advect(t["F"], t["ax"], t["ay"], t["az"], t["vf"], t["u"], t["v"], t["w"], dt,
+                                      order=order)
+            ref = vof.advect(prob, dt=dt, order=order)
+            assert np.abs(out.cpu().numpy().reshape(prob.shape) - ref).max() <= 1e-11, (prob.name, order)
+        ctx.close()
