@@ -71,3 +71,13 @@ def test_null_context_is_rejected_by_every_entry_point():
     }
     for name, call in calls.items():
         assert call() == vofp.ERR_INVALID_ARG, name
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    # no CPU fallback: the binding refuses to import when libvofp.so is absent
+    import shutil
+    import subprocess
+    import sys
+    shutil.copy(os.path.join(ROOT, "paper_1410_1937_gb300", "vofp.py"), tmp_path / "vofp.py")
+    r = subprocess.run([sys.executable, "-c", "import vofp"], cwd=tmp_path, capture_output=True, text=True)
+    assert r.returncode != 0 and "libvofp.so is not built" in r.stderr
