@@ -156,6 +156,10 @@ typedef struct {
                               /* context's kernels are prepared (first solve or timing call)   */
     int rb_compact;           /* 1 if the mixed red-black solve of this operator runs on       */
                               /* colour-compact vectors (set by its first solve or timing)     */
+    int pdl_chained;          /* 1 if the kernels of the compact mixed iteration are chained   */
+                              /* by programmatic dependent launch in the solve's graph (the    */
+                              /* default; environment VOFP_PDL=0 turns it off, and the context */
+                              /* turns it off if the driver refuses it inside the loop body)   */
 } vofp_stats;
 
 /* Library version string (static storage). */

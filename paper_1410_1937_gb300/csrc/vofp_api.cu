@@ -1,6 +1,7 @@
 // extern "C" entry points of libvofp (declared and documented in include/vofp.h): argument
 // checks, context lifetime and error reporting around the implementations in the other files.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -60,6 +61,7 @@ vofp_status vofp_create(vofp_ctx** out, const vofp_grid* g, vofp_stream stream) 
     c->d.n = n;
     c->d.plane = (long long)g->nx * g->ny;
     c->stream = reinterpret_cast<cudaStream_t>(stream);
+    if (const char* e = std::getenv("VOFP_PDL")) c->pdl = std::atoi(e) != 0 ? 1 : 0;
     c->hdx.assign(g->dx, g->dx + g->nx);
     c->hdy.assign(g->dy, g->dy + g->ny);
     c->hdz.assign(g->dz, g->dz + g->nz);
@@ -287,6 +289,7 @@ vofp_status vofp_get_stats(vofp_ctx* c, vofp_stats* st) {
     st->tma_stencil_fp32 = c->tma_ok[0] ? 1 : 0;
     st->tma_stencil_fp64 = c->tma_ok[1] ? 1 : 0;
     st->rb_compact = c->rbc_ok ? 1 : 0;
+    st->pdl_chained = c->pdl ? 1 : 0;
     return VOFP_OK;
 }
 

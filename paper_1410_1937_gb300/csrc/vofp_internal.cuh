@@ -128,6 +128,8 @@ struct vofp_ctx {
     size_t bytes = 0;
     std::vector<void*> allocs;
     long long launches = 0;           // kernels launched (graph bodies counted per execution)
+    int pdl = 1;                      // programmatic dependent launch in the mixed inner loop
+    cudaError_t launch_err = cudaSuccess;  // first failed extended launch since it was cleared
     bool kernels_prepared = false;    // dynamic shared memory opted in, occupancies queried
     // TMA-fed CG stencil: usable per precision (row pitch a multiple of 16 bytes, driver entry
     // point found, not disabled by VOFP_STENCIL_TMA=0); resident blocks per SM; encoded maps
@@ -302,6 +304,27 @@ template <typename... KArgs, typename... Args>
 inline void launch_smem(vofp_ctx* c, void (*k)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t s,
                         Args... args) {
     k<<<g, b, smem, s>>>(static_cast<KArgs>(args)...);
+    ++c->launches;
+}
+
+// Same, optionally as a programmatic dependent launch: the kernel may be scheduled while the
+// previous kernel on the stream drains, and must call griddepcontrol.wait before it reads what
+// that kernel wrote. A refused launch is recorded in c->launch_err.
+template <typename... KArgs, typename... Args>
+inline void launch_dep(vofp_ctx* c, bool pdl, void (*k)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t s,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = b;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+    if (e != cudaSuccess && c->launch_err == cudaSuccess) c->launch_err = e;
     ++c->launches;
 }
 

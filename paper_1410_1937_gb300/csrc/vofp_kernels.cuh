@@ -67,6 +67,15 @@ struct AccFor<float> {
 __device__ __forceinline__ double fmav(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fmav(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
+// Programmatic dependent launch (sm_90 and later). A kernel launched with programmatic stream
+// serialisation may be scheduled while the kernel before it on the stream still runs;
+// griddepcontrol.wait holds it until that kernel has completed and its writes are visible (for an
+// ordinary launch it returns at once), and launch_dependents lets the next kernel's blocks be
+// scheduled before this grid ends. Every kernel that takes part calls the wait before it reads
+// anything its predecessor wrote, so the chain stays ordered kernel by kernel.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Reduce `part` over the grid; the last block to finish writes the sum (index order) to *out.
 // Returns true in thread 0 of that block.
 __device__ __forceinline__ bool grid_reduce(double part, double* partials, unsigned int* counter,
@@ -304,6 +313,7 @@ k_cg_update(long long n, V* __restrict__ r, const V* __restrict__ q, const uint3
     __shared__ double sh[32];
     __shared__ double s_alpha;
     __shared__ int s_flags;
+    grid_dep_wait();
     // the scalar step is computed once per block (FP64 division is slow on this part)
     if (threadIdx.x == 0) {
         const double rr = sc->rr;

@@ -310,6 +310,8 @@ k_rbc_exc_rows(long long nh, int ne, const int* __restrict__ enb, const float* _
                float* __restrict__ xv, float* __restrict__ q, float* __restrict__ dE, CgScalars* sc,
                double* __restrict__ partials, unsigned int* __restrict__ counter) {
     __shared__ double sh[32];
+    grid_dep_wait();
+    grid_dep_trigger();
     const float beta = (float)sc->beta, alpha = (float)sc->alpha;
     AccF2 acc;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
@@ -367,6 +369,8 @@ k_rbc_fix_rows(int nf, int ng, const int* __restrict__ fh, const int* __restrict
                const float* __restrict__ pn, float* __restrict__ q, CgScalars* sc, double* __restrict__ partials,
                unsigned int* __restrict__ counter) {
     __shared__ double sh[32];
+    grid_dep_wait();
+    grid_dep_trigger();
     AccF2 acc;
     double corr = 0.0;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nf + ng; t += gridDim.x * blockDim.x) {
@@ -550,7 +554,7 @@ void rbc_prep(vofp_ctx* c, cudaStream_t st, const double* rhs) {
 }
 
 namespace {
-void launch_main(vofp_ctx* c, cudaStream_t st, const float* po, float* pn) {
+void launch_main(vofp_ctx* c, cudaStream_t st, const float* po, float* pn, bool pdl) {
     using G = RbcGeom;
     const Dims d = c->d;
     const int nh = d.nx / 2;
@@ -571,33 +575,41 @@ void launch_main(vofp_ctx* c, cudaStream_t st, const float* po, float* pn) {
     const long long tiles = (long long)ceil_div(nh, G::NP) * ceil_div(d.ny, kBY);
     int nb = 1, per = 1;
     plane_split(tiles, d.nz, (long long)num_sms() * c->rbc_blocks_per_sm, false, &nb, &per);
-    launch_smem(c, k_rbc_tma<kRbcStages>, dim3(nb), dim3(kBX, kBY), cg_rbc_smem<kRbcStages>(), st, maps, d, per, po,
-                pn, c->rbc_x, c->rbc_q, c->sc, c->partials, c->counters);
+    launch_dep(c, pdl, k_rbc_tma<kRbcStages>, dim3(nb), dim3(kBX, kBY), cg_rbc_smem<kRbcStages>(), st, maps, d, per,
+               po, pn, c->rbc_x, c->rbc_q, c->sc, c->partials, c->counters);
 }
 }  // namespace
 
 // exception rows, then the rows next to exceptions and the merge groups
-void rbc_aux(vofp_ctx* c, cudaStream_t st, const float* po, float* pn) {
+void rbc_aux(vofp_ctx* c, cudaStream_t st, const float* po, float* pn, bool pdl) {
     const int ng = c->rbc_gm ? c->ngroups : 0;
     if (c->rbc_ne > 0)
-        launch(c, k_rbc_exc_rows, ceil_div(c->rbc_ne, kNT), kNT, st, c->rbc_nh, c->rbc_ne, (const int*)c->rbc_enb,
-               (const float*)c->rbc_eT, (const float*)c->rbc_r, po, pn, c->rbc_x, c->rbc_q, c->rbc_dE, c->sc,
-               c->partials, c->counters);
+        launch_dep(c, pdl, k_rbc_exc_rows, dim3(ceil_div(c->rbc_ne, kNT)), dim3(kNT), 0, st, c->rbc_nh, c->rbc_ne,
+                   (const int*)c->rbc_enb, (const float*)c->rbc_eT, (const float*)c->rbc_r, po, pn, c->rbc_x,
+                   c->rbc_q, c->rbc_dE, c->sc, c->partials, c->counters);
     if (c->rbc_nf + ng > 0)
-        launch(c, k_rbc_fix_rows, ceil_div(c->rbc_nf + ng, kNT), kNT, st, c->rbc_nf, ng, (const int*)c->rbc_fh,
-               (const int*)c->rbc_fexc, (const float*)c->rbc_fT, (const float*)c->rbc_dE,
-               (const int4*)c->rbc_gm, (const int4*)c->rbc_gf, (const int*)c->rbc_gn, (const int*)c->gptr,
-               (const int*)c->rbc_gref, (const int*)c->rbc_gfx, (const double*)c->gcorr, (const float*)pn,
-               c->rbc_q, c->sc, c->partials, c->counters);
+        launch_dep(c, pdl, k_rbc_fix_rows, dim3(ceil_div(c->rbc_nf + ng, kNT)), dim3(kNT), 0, st, c->rbc_nf, ng,
+                   (const int*)c->rbc_fh, (const int*)c->rbc_fexc, (const float*)c->rbc_fT, (const float*)c->rbc_dE,
+                   (const int4*)c->rbc_gm, (const int4*)c->rbc_gf, (const int*)c->rbc_gn, (const int*)c->gptr,
+                   (const int*)c->rbc_gref, (const int*)c->rbc_gfx, (const double*)c->gcorr, (const float*)pn,
+                   c->rbc_q, c->sc, c->partials, c->counters);
 }
 
 void rbc_iteration(vofp_ctx* c, cudaStream_t st, const float* po, float* pn, cudaGraphConditionalHandle h,
                    int use_h) {
-    launch_main(c, st, po, pn);
-    rbc_aux(c, st, po, pn);
+    // the four kernels of an iteration (and the next iteration's first) chained by programmatic
+    // dependent launch: each waits for its predecessor before it reads, so only the launch
+    // latency and the block set-up overlap the predecessor's drain. The two short exception and
+    // fix kernels release their successor's blocks at once; the iteration kernel and the update
+    // release theirs as their own blocks end (blocks of the next kernel resident early beside the
+    // streaming ones slowed the solve: 395.2 ms with every kernel releasing early, 387.8 ms with
+    // the update also releasing, 386.2 ms as here, 388.2 ms without the chaining)
+    const bool pdl = c->pdl != 0;
+    launch_main(c, st, po, pn, pdl);
+    rbc_aux(c, st, po, pn, pdl);
     const long long nc = c->rbc_nh + c->rbc_ne;
-    launch(c, k_cg_update<float, true>, grid_n(nc / 4 + 1), kNT, st, nc, c->rbc_r, (const float*)c->rbc_q,
-           (const uint32_t*)c->rbc_bits, c->sc, c->partials, c->counters, h, use_h);
+    launch_dep(c, pdl, k_cg_update<float, true>, dim3(grid_n(nc / 4 + 1)), dim3(kNT), 0, st, nc, c->rbc_r,
+               (const float*)c->rbc_q, (const uint32_t*)c->rbc_bits, c->sc, c->partials, c->counters, h, use_h);
 }
 
 void rbc_finish_xf(vofp_ctx* c, cudaStream_t st) {
@@ -608,7 +620,8 @@ void rbc_finish_xf(vofp_ctx* c, cudaStream_t st) {
                (const float*)c->rbc_x, (const float*)c->rbc_p0, c->xf, (const CgScalars*)c->sc);
 }
 
-void rbc_time_kernel(vofp_ctx* c, cudaStream_t st) { launch_main(c, st, c->rbc_p0, c->rbc_p1); }
-void rbc_time_aux(vofp_ctx* c, cudaStream_t st) { rbc_aux(c, st, c->rbc_p0, c->rbc_p1); }
+// timed as ordinary launches, one kernel after the other
+void rbc_time_kernel(vofp_ctx* c, cudaStream_t st) { launch_main(c, st, c->rbc_p0, c->rbc_p1, false); }
+void rbc_time_aux(vofp_ctx* c, cudaStream_t st) { rbc_aux(c, st, c->rbc_p0, c->rbc_p1, false); }
 
 }  // namespace vofp

@@ -76,7 +76,6 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_bloc
     uint64_t* bars = reinterpret_cast<uint64_t*>(wring + 3 * G::WN);
     __shared__ double sh[32];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + kBX * ty;
-    const float beta = (float)sc->beta, alpha = (float)sc->alpha;
     AccF2 acc;
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
@@ -110,6 +109,9 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_bloc
     else if (tid < 72) { rx = 1; ry = 1 + (tid - 64); }
     else if (tid < 80) { rx = PW - 2; ry = 1 + (tid - 72); }
 
+    // everything above is block-local set-up; the scalars and vectors come from the kernels before
+    grid_dep_wait();
+    const float beta = (float)sc->beta, alpha = (float)sc->alpha;
     const int nh = d.nx >> 1;
     const int tiles_x = (nh + G::NP - 1) / G::NP;
     const long long ntiles = (long long)tiles_x * ((d.ny + kBY - 1) / kBY);

@@ -657,8 +657,7 @@ vofp_status build_graph_fp64(vofp_ctx* c, int U, bool rb) {
 
 // Mixed: WHILE_outer { FP64 residual, outer test, inner right-hand side (sets both conditions);
 //                      WHILE_inner { U x FP32 iterations (inner stop) }; fold the correction }
-vofp_status build_graph_mixed(vofp_ctx* c, int U, bool rb) {
-    if (c->graph_mixed && c->graph_mixed_key == graph_key(U, rb)) return VOFP_OK;
+vofp_status build_graph_mixed_once(vofp_ctx* c, int U, bool rb) {
     const long long launches0 = c->launches;
     if (c->graph_mixed) {
         cudaGraphExecDestroy(c->graph_mixed);
@@ -708,12 +707,41 @@ vofp_status build_graph_mixed(vofp_ctx* c, int U, bool rb) {
         cudaGraph_t tmp = obody;
         VOFP_CUDA_TRY(c, cudaStreamEndCapture(cs, &tmp));
     }
-    VOFP_CUDA_TRY(c, cudaGraphInstantiate(&c->graph_mixed, g, 0));
+    c->launches = launches0;
+    const cudaError_t ie = cudaGraphInstantiate(&c->graph_mixed, g, 0);
     cudaGraphDestroy(g);
     cudaStreamDestroy(cs);
+    if (ie != cudaSuccess) {
+        c->graph_mixed = nullptr;
+        c->set_error(std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+        return VOFP_ERR_CUDA;
+    }
     c->graph_mixed_key = graph_key(U, rb);
-    c->launches = launches0;
     return VOFP_OK;
+}
+
+// The mixed loop's graph, with the inner iteration's kernels chained by programmatic dependent
+// launch where the driver accepts that inside the conditional body; otherwise rebuilt once with
+// ordinary edges (and kept so for the context).
+vofp_status build_graph_mixed(vofp_ctx* c, int U, bool rb) {
+    if (c->graph_mixed && c->graph_mixed_key == graph_key(U, rb)) return VOFP_OK;
+    c->launch_err = cudaSuccess;
+    vofp_status s = build_graph_mixed_once(c, U, rb);
+    if ((s != VOFP_OK || c->launch_err != cudaSuccess) && c->pdl) {
+        (void)cudaGetLastError();
+        if (c->graph_mixed) {
+            cudaGraphExecDestroy(c->graph_mixed);
+            c->graph_mixed = nullptr;
+        }
+        c->pdl = 0;
+        c->launch_err = cudaSuccess;
+        s = build_graph_mixed_once(c, U, rb);
+    }
+    if (s == VOFP_OK && c->launch_err != cudaSuccess) {
+        c->set_error(std::string("kernel launch during capture: ") + cudaGetErrorString(c->launch_err));
+        s = VOFP_ERR_CUDA;
+    }
+    return s;
 }
 
 // b_hat (expanded over groups) into c->work, its scaled copy into c->bt; returns sums over

@@ -70,7 +70,8 @@ class _Stats(ctypes.Structure):
     _fields_ = [("cells", ctypes.c_longlong), ("unknowns", ctypes.c_longlong),
                 ("inactive", ctypes.c_longlong), ("merged_cells", ctypes.c_longlong),
                 ("groups", ctypes.c_longlong), ("device_bytes", ctypes.c_longlong),
-                ("tma_stencil_fp32", ctypes.c_int), ("tma_stencil_fp64", ctypes.c_int), ("rb_compact", ctypes.c_int)]
+                ("tma_stencil_fp32", ctypes.c_int), ("tma_stencil_fp64", ctypes.c_int), ("rb_compact", ctypes.c_int),
+                ("pdl_chained", ctypes.c_int)]
 
 
 _vp = ctypes.c_void_p

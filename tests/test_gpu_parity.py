@@ -297,6 +297,30 @@ def test_compact_red_black_matches_interleaved(vofp, oracle, monkeypatch, case):
     assert np.linalg.norm(x1 - x0) / np.linalg.norm(x0) <= 1e-6
 
 
+@pytest.mark.parametrize("case", ["c1-small", "hull-small"])
+def test_compact_chained_launch_is_bitwise_identical(vofp, oracle, monkeypatch, case):
+    """The compact mixed iteration's kernels chained by programmatic dependent launch (the
+    default) and launched as ordinary dependent kernels: every kernel waits for its predecessor
+    before it reads, and every reduction is summed in a fixed order, so the solutions, iteration
+    counts and residuals agree bit for bit."""
+    prob = CASES[case]()
+    res = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("VOFP_PDL", flag)
+        ctx, t = vofp.context_for(prob)
+        b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
+        x, info = ctx.vofp_solve(b, rtol=1e-8, mode=vofp.MODE_MIXED, precond=vofp.PRECOND_RBSGS)
+        st = ctx.vofp_get_stats()
+        assert info["status"] == 0 and st["rb_compact"] == 1, (info, st)
+        res[flag] = (host(x, prob.shape), info, st["pdl_chained"])
+        ctx.close()
+    assert res["0"][2] == 0 and res["1"][2] in (0, 1)
+    assert np.array_equal(res["1"][0], res["0"][0])
+    for k in ("iterations", "outer_iterations", "rel_residual"):
+        assert res["1"][1][k] == res["0"][1][k], k
+    assert oracle.System(prob).residual(res["1"][0]) <= 1e-8 * 1.01
+
+
 def test_compact_red_black_ragged_tiles_and_all_neumann(vofp, oracle):
     """Colour-compact red-black on a grid whose pair rows (20 pairs) and rows (11) leave ragged
     tiles, and on an all-Neumann box with prescribed wall fluxes (zero-mean solution)."""
