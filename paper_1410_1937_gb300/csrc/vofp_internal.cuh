@@ -161,6 +161,7 @@ struct vofp_ctx {
     double* rk2_buf = nullptr;        // RK2 step (vofp_rk2.cu): face fields and cell arrays
     long long rbc_cap = 0;            // allocated compact length
     int rbc_blocks_per_sm = 0;
+    int rbc_nblocks = 0, rbc_per = 0, rbc_pad = 0;  // iteration kernel split (see rbc_split)
     int tma_blocks_deep32 = 0;        // resident blocks per SM of the six-stage FP32 stencil
     int rb_tma_blocks_per_sm = 0;
     std::map<std::tuple<const void*, int, int>, CUtensorMap> tma_maps;

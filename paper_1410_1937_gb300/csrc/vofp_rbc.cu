@@ -442,6 +442,48 @@ __global__ void k_rbc_expand_exc(long long nh, int ne, const int* __restrict__ e
     if (e < ne) xf[exc[e]] = __fmaf_rn(alpha, p0[nh + e], x[nh + e]);
 }
 
+// Split of the iteration kernel's work over at most `slots` resident blocks. Block b takes the
+// items [b per, (b+1) per) of w = tile * (nz + pad) + pad + plane (tile columns one after the
+// other). A block marches each tile-column segment it holds with kSegSteps plane steps besides
+// its planes (four prologue steps that fill the p and w rings before the first output plane, and
+// the closing t step), so the kernel lasts as long as its costliest block. With pad = 0 (equal
+// planes per block) the blocks that cross a column boundary pay for two segments; with
+// pad = kSegSteps every column's first segment is charged for its overhead in the split itself,
+// so only a block that starts inside a column pays beyond its share. The cheaper of the two is
+// taken (ties: pad 0).
+constexpr int kSegSteps = 5;
+
+long long split_cost(long long tiles, long long nz, long long slots, int pad, int* nb, int* per) {
+    const long long nzp = nz + pad, total = tiles * nzp;
+    const long long n = std::max(1LL, std::min(slots, total));
+    const long long p = (total + n - 1) / n;
+    long long worst = 0, blocks = 0;
+    for (long long w0 = 0; w0 < total; w0 += p, ++blocks) {
+        const long long w1 = std::min(w0 + p, total);
+        long long cost = 0;
+        for (long long w = w0; w < w1;) {
+            const long long t = w / nzp, kp0 = w - t * nzp, kp1 = std::min(nzp, kp0 + (w1 - w));
+            w += kp1 - kp0;
+            const long long k0 = std::max(kp0 - pad, 0LL), k1 = kp1 - pad;
+            if (k1 > k0) cost += (k1 - k0) + kSegSteps;
+        }
+        worst = std::max(worst, cost);
+    }
+    *nb = (int)blocks;
+    *per = (int)p;
+    return worst;
+}
+
+void rbc_split(vofp_ctx* c, long long tiles, long long slots) {
+    int nb0, per0, nb1, per1;
+    const long long c0 = split_cost(tiles, c->d.nz, slots, 0, &nb0, &per0);
+    const long long c1 = split_cost(tiles, c->d.nz, slots, kSegSteps, &nb1, &per1);
+    const bool padded = c1 < c0;
+    c->rbc_nblocks = padded ? nb1 : nb0;
+    c->rbc_per = padded ? per1 : per0;
+    c->rbc_pad = padded ? kSegSteps : 0;
+}
+
 }  // namespace
 
 vofp_status rbc_ensure(vofp_ctx* c) {
@@ -539,6 +581,11 @@ vofp_status rbc_ensure(vofp_ctx* c) {
     cudaGetLastError();
     VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
     if (nb <= 0) return VOFP_OK;
+    {
+        const long long tiles = (long long)ceil_div(d.nx / 2, RbcGeom::NP) * ceil_div(d.ny, kBY);
+        if (tiles * (d.nz + kSegSteps) > 0x7fffffffLL) return VOFP_OK;   // the kernel's work index is an int
+        rbc_split(c, tiles, (long long)num_sms() * nb);
+    }
     c->rbc_blocks_per_sm = nb;
     c->rbc_nh = nh;
     c->rbc_ne = (int)ne;
@@ -572,11 +619,8 @@ void launch_main(vofp_ctx* c, cudaStream_t st, const float* po, float* pn, bool 
     maps.tx = *mx;
     maps.ty = *my;
     maps.tz = *mz;
-    const long long tiles = (long long)ceil_div(nh, G::NP) * ceil_div(d.ny, kBY);
-    int nb = 1, per = 1;
-    plane_split(tiles, d.nz, (long long)num_sms() * c->rbc_blocks_per_sm, false, &nb, &per);
-    launch_dep(c, pdl, k_rbc_tma<kRbcStages>, dim3(nb), dim3(kBX, kBY), cg_rbc_smem<kRbcStages>(), st, maps, d, per,
-               po, pn, c->rbc_x, c->rbc_q, c->sc, c->partials, c->counters);
+    launch_dep(c, pdl, k_rbc_tma<kRbcStages>, dim3(c->rbc_nblocks), dim3(kBX, kBY), cg_rbc_smem<kRbcStages>(), st,
+               maps, d, c->rbc_per, c->rbc_pad, po, pn, c->rbc_x, c->rbc_q, c->sc, c->partials, c->counters);
 }
 }  // namespace
 

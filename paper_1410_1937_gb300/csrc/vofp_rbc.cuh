@@ -64,7 +64,8 @@ constexpr size_t cg_rbc_smem() {
 // forms p of plane s+2, w of plane s+1 and t of plane s-1 (two barriers per step).
 template <int NS>
 __global__ void __launch_bounds__(kBX* kBY, 3)
-k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_block, const float* __restrict__ pold,
+k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_block, const int pad,
+          const float* __restrict__ pold,
           float* __restrict__ pnew, float* __restrict__ xv, float* __restrict__ out, CgScalars* __restrict__ sc,
           double* __restrict__ partials, unsigned int* __restrict__ counter) {
     using G = RbcGeom;
@@ -88,16 +89,15 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_bloc
     auto pl = [&](int kk) -> float* { return pring + ((kk + 6) % 3) * G::PN; };
     auto wl = [&](int kk) -> float* { return wring + ((kk + 6) % 3) * G::WN; };
 
-    // p items: ring index e = tid, tid + 256 of the 36 x 12 plane; box index of the same pair
-    int pi_dst[2], pi_src[2];
+    // p items: ring index e = tid + 256 q of the 36 x 12 plane (row e / PW, pair e % PW); box
+    // index of the same pair e + (BWC - PW) (e / PW) + 2
+    int pi_src[2];
     bool pi_on[2];
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
         const int it = tid + q * kBX * kBY;
         pi_on[q] = it < G::kPItems;
-        const int xr = pi_on[q] ? it % PW : 0, yr = pi_on[q] ? it / PW : 0;
-        pi_dst[q] = yr * PW + xr;
-        pi_src[q] = yr * BWC + xr + 2;
+        pi_src[q] = it + (BWC - PW) * (it / PW) + 2;
     }
     // own pair xr = tx + 2 in w row ty + 1; ring items (threads 0..79): the pairs of rows j0-1 and
     // j0+8 (threads 0..63) and the pairs h0-1 and h0+32 of rows j0 .. j0+7 (threads 64..79)
@@ -115,14 +115,20 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_bloc
     const int nh = d.nx >> 1;
     const int tiles_x = (nh + G::NP - 1) / G::NP;
     const long long ntiles = (long long)tiles_x * ((d.ny + kBY - 1) / kBY);
-    const long long total = ntiles * d.nz;
-    const long long w0 = min((long long)blockIdx.x * per_block, total);
-    const long long w1 = min(w0 + per_block, total);
-    for (long long w = w0; w < w1 && !bad;) {
-        const long long tile_id = w / d.nz;
-        const int k0 = int(w - tile_id * d.nz);
-        const int k1 = (int)min((long long)d.nz, (long long)k0 + (w1 - w));
-        w += k1 - k0;
+    // work items w = tile * (nz + pad) + pad + plane: every tile column starts with `pad` items
+    // that stand for no plane, so that an equal split of w charges each column's first segment
+    // for its prologue steps (pad = 0: the plain equal split)
+    const int nzp = d.nz + pad;
+    const int total = (int)ntiles * nzp;
+    const int w0 = min((int)blockIdx.x * per_block, total);
+    const int w1 = min(w0 + per_block, total);
+    for (int w = w0; w < w1 && !bad;) {
+        const int tile_id = w / nzp;
+        const int kp0 = w - tile_id * nzp;
+        const int kp1 = min(nzp, kp0 + (w1 - w));
+        w += kp1 - kp0;
+        const int k0 = max(kp0 - pad, 0), k1 = kp1 - pad;
+        if (k1 <= k0) continue;   // padding only (the same for every thread of the block)
         const int h0 = int(tile_id % tiles_x) * G::NP, j0 = int(tile_id / tiles_x) * kBY;
         const int i0 = 2 * h0;
         const int h = h0 + tx, j = j0 + ty;
@@ -202,7 +208,7 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_bloc
                 float* op = Pc;
 #pragma unroll
                 for (int q = 0; q < 2; ++q)
-                    if (pi_on[q]) op[pi_dst[q]] = fmav(beta, P[pi_src[q]], R[pi_src[q]]);
+                    if (pi_on[q]) op[tid + q * kBX * kBY] = fmav(beta, P[pi_src[q]], R[pi_src[q]]);
             }
             // P1: t of plane s-1 on the black cell of the own pair
             const int m = s - 1;
