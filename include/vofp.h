@@ -399,6 +399,17 @@ vofp_status vofp_launch_count(vofp_ctx* ctx, long long* count);
 vofp_status vofp_time_iteration_kernels(vofp_ctx* ctx, int precision, int precond, int reps,
                                         float* stencil_ms, float* update_ms, float* aux_ms);
 
+/* Host-only planning query (no context, no device): how the colour-compact red-black iteration
+ * kernel splits its work over `slots` resident blocks for tiles_x x tiles_y tiles (32 pairs x 8
+ * rows each) and nz planes.  Block b marches the work items [b per, (b+1) per) of
+ * w = tile (nz + pad) + pad + plane (tiles in x-fastest order; the first `pad` items of a tile
+ * column stand for no plane); *blocks = number of blocks (<= slots).  The plan minimises the
+ * plane steps of the costliest block (each tile-column segment adds five steps to its planes)
+ * and keeps a tile's y-neighbour tiles marched at the same plane in the same step where it can
+ * (their halo rows then come from L2).  VOFP_ERR_INVALID_ARG for null outputs, non-positive
+ * sizes, or more work items than an int holds. */
+vofp_status vofp_rbc_split_plan(int tiles_x, int tiles_y, int nz, int slots, int* blocks, int* per, int* pad);
+
 #ifdef __cplusplus
 }
 #endif

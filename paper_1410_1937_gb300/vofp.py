@@ -96,6 +96,8 @@ _sig = {
     "vofp_get_stats": (ctypes.c_int, [_vp, _P(_Stats)]),
     "vofp_residual_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _P(ctypes.c_double)]),
     "vofp_launch_count": (ctypes.c_int, [_vp, _P(ctypes.c_longlong)]),
+    "vofp_rbc_split_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           _P(ctypes.c_int), _P(ctypes.c_int), _P(ctypes.c_int)]),
     "vofp_scaled_pair": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "vofp_nn_create": (ctypes.c_int, [_P(_vp), ctypes.c_ulonglong, _vp]),
     "vofp_nn_destroy": (None, [_vp]),
@@ -145,6 +147,14 @@ def _stream_handle(stream):
 
 def vofp_version() -> str:
     return _lib.vofp_version().decode()
+
+
+def vofp_rbc_split_plan(tiles_x, tiles_y, nz, slots):
+    """(blocks, per, pad) of the colour-compact red-black iteration kernel's work split (host only)."""
+    b, p, q = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    _check(None, _lib.vofp_rbc_split_plan(int(tiles_x), int(tiles_y), int(nz), int(slots), ctypes.byref(b),
+                                          ctypes.byref(p), ctypes.byref(q)))
+    return b.value, p.value, q.value
 
 
 def vofp_create(dx, dy, dz, stream=None):
