@@ -6,7 +6,6 @@
 // +z face, so every face coefficient is computed once and stored once (structure of arrays).
 #include <algorithm>
 #include <cmath>
-#include <unordered_map>
 
 #include "vofp_internal.cuh"
 
@@ -131,20 +130,21 @@ __global__ void k_face_coeffs(Dims d, const double* __restrict__ dx, const doubl
         cell_ijk(d, c, i, j, k);
         const double rc = rho[c];
         double tx = 0.0, ty = 0.0, tz = 0.0, qx = 0.0, qy = 0.0, qz = 0.0;
+        // one FP64 division per face (the FP64 pipe bounds this kernel): T = (A S) (1 / den)
         if (i < d.nx - 1) {
-            const double a = axe[fx_idx(d, i + 1, j, k)], den = 0.5 * (dx[i] * rc + dx[i + 1] * rho[c + 1]);
-            tx = (a * (dz[k] * dy[j])) / den;
-            qx = a > 0.0 ? 1.0 / den : 0.0;
+            const double a = axe[fx_idx(d, i + 1, j, k)], inv = 1.0 / (0.5 * (dx[i] * rc + dx[i + 1] * rho[c + 1]));
+            tx = (a * (dz[k] * dy[j])) * inv;
+            qx = a > 0.0 ? inv : 0.0;
         }
         if (j < d.ny - 1) {
-            const double a = aye[fy_idx(d, i, j + 1, k)], den = 0.5 * (dy[j] * rc + dy[j + 1] * rho[c + d.nx]);
-            ty = (a * (dz[k] * dx[i])) / den;
-            qy = a > 0.0 ? 1.0 / den : 0.0;
+            const double a = aye[fy_idx(d, i, j + 1, k)], inv = 1.0 / (0.5 * (dy[j] * rc + dy[j + 1] * rho[c + d.nx]));
+            ty = (a * (dz[k] * dx[i])) * inv;
+            qy = a > 0.0 ? inv : 0.0;
         }
         if (k < d.nz - 1) {
-            const double a = aze[fz_idx(d, i, j, k + 1)], den = 0.5 * (dz[k] * rc + dz[k + 1] * rho[c + d.plane]);
-            tz = (a * (dy[j] * dx[i])) / den;
-            qz = a > 0.0 ? 1.0 / den : 0.0;
+            const double a = aze[fz_idx(d, i, j, k + 1)], inv = 1.0 / (0.5 * (dz[k] * rc + dz[k + 1] * rho[c + d.plane]));
+            tz = (a * (dy[j] * dx[i])) * inv;
+            qz = a > 0.0 ? inv : 0.0;
         }
         Tx[c] = tx;
         Ty[c] = ty;
@@ -188,8 +188,9 @@ __global__ void k_small_cells(Dims d, double thr, const double* __restrict__ vf,
                               const uint8_t* __restrict__ ina, const double* __restrict__ dx,
                               const double* __restrict__ dy, const double* __restrict__ dz,
                               const double* __restrict__ axe, const double* __restrict__ aye,
-                              const double* __restrict__ aze, unsigned int* count,
-                              long long* cells, long long* targets, int write) {
+                              const double* __restrict__ aze, unsigned int* count, long long cap,
+                              long long* __restrict__ cells, long long* __restrict__ targets,
+                              double* __restrict__ vfs) {
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < d.n;
          c += (long long)gridDim.x * blockDim.x) {
         if (ina[c] || !(vf[c] < thr)) continue;
@@ -207,18 +208,27 @@ __global__ void k_small_cells(Dims d, double thr, const double* __restrict__ vf,
             if (a[f] > a[best]) best = f;
         if (!(a[best] > 0.0)) continue;
         const long long off[6] = {-1, 1, -(long long)d.nx, (long long)d.nx, -d.plane, d.plane};
-        unsigned int slot = atomicAdd(count, 1u);
-        if (write) {
+        // slots in arrival order; the caller grows the lists and runs again if they overflow
+        const unsigned int slot = atomicAdd(count, 1u);
+        if ((long long)slot < cap) {
             cells[slot] = c;
             targets[slot] = c + off[best];
+            vfs[slot] = vf[c];
         }
     }
 }
 
-__global__ void k_gather(int m, const long long* __restrict__ idx, const double* __restrict__ src,
-                         double* __restrict__ out) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < m) out[t] = src[idx[t]];
+// slot_of[cell] = slot of every listed small cell (the other entries were set to -1 before)
+__global__ void k_small_slots(int m, const long long* __restrict__ cells, int32_t* __restrict__ slot_of) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < m) slot_of[cells[t]] = t;
+}
+
+// slot of each small cell's target among the small cells, -1 if the target is not one of them
+__global__ void k_small_target_slots(int m, const long long* __restrict__ targets,
+                                     const int32_t* __restrict__ slot_of, int32_t* __restrict__ tslot) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < m) tslot[t] = slot_of[targets[t]];
 }
 
 __global__ void k_count_u8(long long n, const uint8_t* __restrict__ a, unsigned int* count) {
@@ -450,53 +460,96 @@ void launch_group_fold(vofp_ctx* c, double* v, bool zero_slaves) {
 
 // Resolve merge chains on the host: the root of a small cell is the end of its target chain;
 // a cycle of small cells is rooted at its member of largest open volume (lowest index on ties).
+// Small cells are addressed by their slot in the lists (any order): tslot[t] is the slot of the
+// target of slot t, -1 when the target does not merge. The roots do not depend on the order.
 static void resolve_roots(const std::vector<long long>& cells, const std::vector<long long>& targets,
-                          const std::vector<double>& vfs, std::vector<long long>& roots) {
-    std::unordered_map<long long, size_t> pos_of;
-    pos_of.reserve(cells.size() * 2);
-    for (size_t t = 0; t < cells.size(); ++t) pos_of[cells[t]] = t;
-    std::unordered_map<long long, long long> root_of;
-    root_of.reserve(cells.size() * 2);
-    for (size_t t0 = 0; t0 < cells.size(); ++t0) {
-        std::vector<long long> path;
-        std::unordered_map<long long, size_t> on_path;
-        long long cur = cells[t0], r;
+                          const std::vector<double>& vfs, const std::vector<int32_t>& tslot,
+                          std::vector<long long>& roots) {
+    const long long m = (long long)cells.size();
+    std::vector<long long> root(m, -1);      // resolved root cell per slot
+    std::vector<long long> stamp(m, -1);     // first slot of the walk that last visited it
+    std::vector<long long> where(m, 0);      // its index on that walk's path
+    std::vector<long long> path;
+    for (long long t0 = 0; t0 < m; ++t0) {
+        if (root[t0] >= 0) continue;
+        path.clear();
+        long long q = t0, r;
         while (true) {
-            auto it = root_of.find(cur);
-            if (it != root_of.end()) {
-                r = it->second;
+            if (root[q] >= 0) {
+                r = root[q];
                 break;
             }
-            auto pt = pos_of.find(cur);
-            if (pt == pos_of.end()) {
-                r = cur;
-                break;
-            }
-            auto op = on_path.find(cur);
-            if (op != on_path.end()) {
+            if (stamp[q] == t0) {
+                // a cycle: path[where[q]] .. the end
                 long long best = -1;
                 double bv = -1.0;
-                for (size_t q = op->second; q < path.size(); ++q) {
-                    long long m = path[q];
-                    double vm = vfs[pos_of[m]];
-                    if (vm > bv || (vm == bv && m < best)) {
+                for (size_t k = (size_t)where[q]; k < path.size(); ++k) {
+                    const long long cm = cells[path[k]];
+                    const double vm = vfs[path[k]];
+                    if (vm > bv || (vm == bv && cm < best)) {
                         bv = vm;
-                        best = m;
+                        best = cm;
                     }
                 }
-                for (size_t q = op->second; q < path.size(); ++q) root_of[path[q]] = best;
+                for (size_t k = (size_t)where[q]; k < path.size(); ++k) root[path[k]] = best;
                 r = best;
                 break;
             }
-            on_path[cur] = path.size();
-            path.push_back(cur);
-            cur = targets[pt->second];
+            stamp[q] = t0;
+            where[q] = (long long)path.size();
+            path.push_back(q);
+            if (tslot[q] < 0) {
+                r = targets[q];   // the chain ends at a cell that does not merge
+                break;
+            }
+            q = tslot[q];
         }
-        for (long long m : path)
-            if (!root_of.count(m)) root_of[m] = r;
+        for (long long k : path)
+            if (root[k] < 0) root[k] = r;
     }
-    roots.resize(cells.size());
-    for (size_t t = 0; t < cells.size(); ++t) roots[t] = root_of[cells[t]];
+    roots.assign(root.begin(), root.end());
+}
+
+// Device lists of the small cells, kept across operator builds and grown when they overflow.
+static vofp_status grow_small(vofp_ctx* c, long long cap) {
+    void* old[4] = {c->small_cells, c->small_targets, c->small_vf, c->small_tslot};
+    for (void* p : old)
+        if (p) {
+            cudaFree(p);
+            c->allocs.erase(std::remove(c->allocs.begin(), c->allocs.end(), p), c->allocs.end());
+        }
+    c->bytes -= c->small_cap * (long long)(2 * sizeof(long long) + sizeof(double) + sizeof(int32_t));
+    c->small_cells = c->small_targets = nullptr;
+    c->small_vf = nullptr;
+    c->small_tslot = nullptr;
+    c->small_cap = 0;
+    vofp_status s;
+    if ((s = c->alloc(&c->small_cells, cap)) || (s = c->alloc(&c->small_targets, cap)) ||
+        (s = c->alloc(&c->small_vf, cap)) || (s = c->alloc(&c->small_tslot, cap)))
+        return s;
+    c->small_cap = cap;
+    return VOFP_OK;
+}
+
+// Group arrays (offsets, cells, corrections), kept across builds and grown when too small.
+static vofp_status grow_groups(vofp_ctx* c, long long ng, long long ncells) {
+    if (ng + 1 <= c->gptr_cap && ncells <= c->gcells_cap) return VOFP_OK;
+    void* old[3] = {c->gptr, c->gcells, c->gcorr};
+    for (void* p : old)
+        if (p) {
+            cudaFree(p);
+            c->allocs.erase(std::remove(c->allocs.begin(), c->allocs.end(), p), c->allocs.end());
+        }
+    c->bytes -= c->gptr_cap * (long long)(sizeof(int) + sizeof(double)) + c->gcells_cap * (long long)sizeof(int);
+    c->gptr = c->gcells = nullptr;
+    c->gcorr = nullptr;
+    c->gptr_cap = c->gcells_cap = 0;
+    const long long pc = (ng + 1) * 3 / 2 + 16, cc = ncells * 3 / 2 + 16;
+    vofp_status s;
+    if ((s = c->alloc(&c->gptr, pc)) || (s = c->alloc(&c->gcells, cc)) || (s = c->alloc(&c->gcorr, pc))) return s;
+    c->gptr_cap = pc;
+    c->gcells_cap = cc;
+    return VOFP_OK;
 }
 
 vofp_status build_operator(vofp_ctx* c, const double* F, const double* ax, const double* ay,
@@ -591,50 +644,47 @@ vofp_status build_operator(vofp_ctx* c, const double* F, const double* ax, const
            c->kx, c->ky, c->kz);
     launch(c, k_diag, gN, kNT, st, d, b6, c->dx, c->dy, c->dz, rho, c->axe, c->aye, c->aze, c->Tx, c->Ty, c->Tz, c->diag);
 
-    // merge map (Sec. 2.3): small cells on the device, chains resolved on the host
+    // merge map (Sec. 2.3): small cells listed on the device, chains resolved on the host
     std::vector<long long> cells, targets, roots;
     std::vector<double> vfs;
+    std::vector<int32_t> tslot;
     unsigned int* cnt = c->counters + 33;
     if (vf && phys->merge_threshold > 0.0) {
-        VOFP_CUDA_TRY(c, cudaMemsetAsync(cnt, 0, sizeof(unsigned int), st));
-        launch(c, k_small_cells, gN, kNT, st, d, phys->merge_threshold, vf, c->inactive, c->dx, c->dy, c->dz,
-                                          c->axe, c->aye, c->aze, cnt, nullptr, nullptr, 0);
         unsigned int m = 0;
-        VOFP_CUDA_TRY(c, cudaMemcpyAsync(&m, cnt, sizeof(m), cudaMemcpyDeviceToHost, st));
-        VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
-        if (m > 0) {
-            long long *dcells = nullptr, *dtargets = nullptr;
-            VOFP_CUDA_TRY(c, cudaMallocAsync(&dcells, sizeof(long long) * m * 2, st));
-            dtargets = dcells + m;
+        for (int attempt = 0; attempt < 2; ++attempt) {
             VOFP_CUDA_TRY(c, cudaMemsetAsync(cnt, 0, sizeof(unsigned int), st));
             launch(c, k_small_cells, gN, kNT, st, d, phys->merge_threshold, vf, c->inactive, c->dx, c->dy, c->dz,
-                                              c->axe, c->aye, c->aze, cnt, dcells, dtargets, 1);
-            std::vector<long long> hc(m), ht(m);
-            VOFP_CUDA_TRY(c, cudaMemcpyAsync(hc.data(), dcells, sizeof(long long) * m, cudaMemcpyDeviceToHost, st));
-            VOFP_CUDA_TRY(c, cudaMemcpyAsync(ht.data(), dtargets, sizeof(long long) * m, cudaMemcpyDeviceToHost, st));
+                   c->axe, c->aye, c->aze, cnt, c->small_cap, c->small_cells, c->small_targets, c->small_vf);
+            VOFP_CUDA_TRY(c, cudaMemcpyAsync(&m, cnt, sizeof(m), cudaMemcpyDeviceToHost, st));
             VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
-            std::vector<size_t> order(m);
-            for (size_t t = 0; t < m; ++t) order[t] = t;
-            std::sort(order.begin(), order.end(), [&](size_t a, size_t b) { return hc[a] < hc[b]; });
+            if ((long long)m <= c->small_cap) break;
+            if ((s = grow_small(c, (long long)m + m / 2 + 1024))) return s;
+        }
+        if ((long long)m > c->small_cap) {
+            c->set_error("small-cell count changed between two passes over the same input");
+            return VOFP_ERR_CUDA;
+        }
+        if (m > 0) {
+            // root[] serves as the cell -> slot map here; k_root_init below rewrites it
+            VOFP_CUDA_TRY(c, cudaMemsetAsync(c->root, 0xff, sizeof(int32_t) * N, st));
+            launch(c, k_small_slots, ceil_div(m, kNT), kNT, st, (int)m, (const long long*)c->small_cells, c->root);
+            launch(c, k_small_target_slots, ceil_div(m, kNT), kNT, st, (int)m, (const long long*)c->small_targets,
+                   (const int32_t*)c->root, c->small_tslot);
             cells.resize(m);
             targets.resize(m);
-            for (size_t t = 0; t < m; ++t) {
-                cells[t] = hc[order[t]];
-                targets[t] = ht[order[t]];
-            }
-            // open-volume fractions of the small cells, for the cycle rule
             vfs.resize(m);
-            double* dvf_sel = nullptr;
-            VOFP_CUDA_TRY(c, cudaMallocAsync(&dvf_sel, sizeof(double) * m, st));
-            VOFP_CUDA_TRY(c, cudaMemcpyAsync(dcells, cells.data(), sizeof(long long) * m, cudaMemcpyHostToDevice, st));
-            launch(c, k_gather, ceil_div(m, kNT), kNT, st, (int)m, dcells, vf, dvf_sel);
-            VOFP_CUDA_TRY(c, cudaMemcpyAsync(vfs.data(), dvf_sel, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+            tslot.resize(m);
+            VOFP_CUDA_TRY(c, cudaMemcpyAsync(cells.data(), c->small_cells, sizeof(long long) * m,
+                                             cudaMemcpyDeviceToHost, st));
+            VOFP_CUDA_TRY(c, cudaMemcpyAsync(targets.data(), c->small_targets, sizeof(long long) * m,
+                                             cudaMemcpyDeviceToHost, st));
+            VOFP_CUDA_TRY(c, cudaMemcpyAsync(vfs.data(), c->small_vf, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+            VOFP_CUDA_TRY(c, cudaMemcpyAsync(tslot.data(), c->small_tslot, sizeof(int32_t) * m,
+                                             cudaMemcpyDeviceToHost, st));
             VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
-            VOFP_CUDA_TRY(c, cudaFreeAsync(dvf_sel, st));
-            VOFP_CUDA_TRY(c, cudaFreeAsync(dcells, st));
         }
     }
-    resolve_roots(cells, targets, vfs, roots);
+    resolve_roots(cells, targets, vfs, tslot, roots);
     launch(c, k_root_init, gN, kNT, st, d, c->inactive, c->root);
     // groups: cells whose root differs from themselves, plus the roots
     std::vector<std::pair<long long, long long>> members;   // (root, cell)
@@ -651,34 +701,26 @@ vofp_status build_operator(vofp_ctx* c, const double* F, const double* ax, const
     c->ngroups = (int)gptr.size() - 1;
     c->n_merged = (long long)members.size();
     c->n_unknowns = N - c->n_inactive - c->n_merged;
-    if (c->gptr) {
-        cudaFree(c->gptr);
-        cudaFree(c->gcells);
-        cudaFree(c->gcorr);
-        c->allocs.erase(std::remove_if(c->allocs.begin(), c->allocs.end(), [&](void* p) {
-                            return p == c->gptr || p == c->gcells || p == c->gcorr;
-                        }), c->allocs.end());
-        c->gptr = nullptr;
-        c->gcells = nullptr;
-        c->gcorr = nullptr;
-    }
     if (c->ngroups > 0) {
-        if ((s = c->alloc(&c->gptr, gptr.size())) || (s = c->alloc(&c->gcells, gcells.size())) ||
-            (s = c->alloc(&c->gcorr, c->ngroups)))
-            return s;
+        if ((s = grow_groups(c, c->ngroups, (long long)gcells.size()))) return s;
         VOFP_CUDA_TRY(c, cudaMemcpyAsync(c->gptr, gptr.data(), sizeof(int) * gptr.size(), cudaMemcpyHostToDevice, st));
         VOFP_CUDA_TRY(c, cudaMemcpyAsync(c->gcells, gcells.data(), sizeof(int) * gcells.size(), cudaMemcpyHostToDevice, st));
+        // (cell, root) of every merged cell, through the small-cell lists (there are no more
+        // merged cells than small cells); copies from pageable host memory are staged before
+        // cudaMemcpyAsync returns, so the vectors may go out of scope
         std::vector<long long> mc, mr;
+        mc.reserve(members.size());
+        mr.reserve(members.size());
         for (auto& pr : members) {
             mc.push_back(pr.second);
             mr.push_back(pr.first);
         }
-        long long* dm = nullptr;
-        VOFP_CUDA_TRY(c, cudaMallocAsync(&dm, sizeof(long long) * mc.size() * 2, st));
-        VOFP_CUDA_TRY(c, cudaMemcpyAsync(dm, mc.data(), sizeof(long long) * mc.size(), cudaMemcpyHostToDevice, st));
-        VOFP_CUDA_TRY(c, cudaMemcpyAsync(dm + mc.size(), mr.data(), sizeof(long long) * mr.size(), cudaMemcpyHostToDevice, st));
-        launch(c, k_root_scatter, ceil_div((long long)mc.size(), kNT), kNT, st, (int)mc.size(), dm, dm + mc.size(), c->root);
-        VOFP_CUDA_TRY(c, cudaFreeAsync(dm, st));
+        VOFP_CUDA_TRY(c, cudaMemcpyAsync(c->small_cells, mc.data(), sizeof(long long) * mc.size(),
+                                         cudaMemcpyHostToDevice, st));
+        VOFP_CUDA_TRY(c, cudaMemcpyAsync(c->small_targets, mr.data(), sizeof(long long) * mr.size(),
+                                         cudaMemcpyHostToDevice, st));
+        launch(c, k_root_scatter, ceil_div((long long)mc.size(), kNT), kNT, st, (int)mc.size(),
+               (const long long*)c->small_cells, (const long long*)c->small_targets, c->root);
     }
     // symmetric scaling s = diag(A_hat)^-1/2 per group
     launch(c, k_scale_cells, gN, kNT, st, d, c->inactive, c->diag, c->s, c->sq);

@@ -102,6 +102,12 @@ struct vofp_ctx {
     int ngroups = 0;
     int *gptr = nullptr, *gcells = nullptr;
     double* gcorr = nullptr;
+    long long gptr_cap = 0, gcells_cap = 0;   // allocated entries of gptr (and gcorr) and gcells
+    // small cells of the last build, in arrival order (device; kept across builds)
+    long long small_cap = 0;
+    long long *small_cells = nullptr, *small_targets = nullptr;
+    double* small_vf = nullptr;
+    int32_t* small_tslot = nullptr;
     long long n_unknowns = 0, n_inactive = 0, n_merged = 0;
 
     // Krylov workspace
