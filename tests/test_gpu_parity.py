@@ -64,6 +64,38 @@ def test_merge_map_bit_exact(vofp, oracle, case):
     assert st["unknowns"] == s.M and st["inactive"] == int((s.root < 0).sum())
 
 
+def test_rebuilds_on_one_context_grow_and_reuse_the_merge_lists(vofp, oracle):
+    """One context rebuilt with merge thresholds that first raise the number of small cells (the
+    device lists and group arrays kept from the previous build overflow and grow), then drop it to
+    none and raise it again (stale lists and groups are reused): every merge map is bit-exact
+    against the oracle, a solve after the last rebuild meets its tolerance, and rebuilding the same
+    operator again does not change the device memory the context holds."""
+    # about 80 small cells, then about 2500 (past the lists' slack of half their size plus 1024 and
+    # past the group arrays), then fewer, none, and some again
+    prob = ragged_sphere(threshold=0.002)
+    ctx, t = vofp.context_for(prob)
+    for thr in (0.002, 0.9, 0.1, 0.0, 0.3):
+        prob.merge_threshold = thr
+        ctx.vofp_build_operator(t["F"], t["ax"], t["ay"], t["az"], t["vf"], prob.bc, prob.rho_liquid,
+                                prob.rho_gas, thr, prob.density_smoothing, prob.dt)
+        s = oracle.System(prob)
+        root = ctx.vofp_merge_map().cpu().numpy()
+        np.testing.assert_array_equal(root, s.root.astype(np.int32), err_msg=f"threshold {thr}")
+        st = ctx.vofp_get_stats()
+        merged = (s.root >= 0) & (s.root != np.arange(prob.n))
+        assert st["unknowns"] == s.M and st["groups"] == len(set(s.root[merged].tolist()))
+    bytes0 = ctx.vofp_get_stats()["device_bytes"]
+    b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
+    x, info = ctx.vofp_solve(b, rtol=1e-8, mode=vofp.MODE_MIXED, precond=vofp.PRECOND_RBSGS)
+    assert info["status"] == 0, info
+    assert s.residual(host(x, prob.shape)) <= 1e-8 * 1.01
+    bytes1 = ctx.vofp_get_stats()["device_bytes"]
+    ctx.vofp_build_operator(t["F"], t["ax"], t["ay"], t["az"], t["vf"], prob.bc, prob.rho_liquid,
+                            prob.rho_gas, 0.3, prob.density_smoothing, prob.dt)
+    assert ctx.vofp_get_stats()["device_bytes"] == bytes1 >= bytes0
+    ctx.close()
+
+
 @pytest.mark.parametrize("case", list(CASES))
 def test_rhs_matches_oracle(vofp, oracle, case):
     prob = CASES[case]()
