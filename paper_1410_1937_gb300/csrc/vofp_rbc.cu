@@ -661,14 +661,16 @@ void rbc_aux(vofp_ctx* c, cudaStream_t st, const float* po, float* pn, bool pdl)
 
 void rbc_iteration(vofp_ctx* c, cudaStream_t st, const float* po, float* pn, cudaGraphConditionalHandle h,
                    int use_h) {
-    // the four kernels of an iteration (and the next iteration's first) chained by programmatic
+    // In the solve's graph (use_h set; a refused launch is caught when the capture ends) the four
+    // kernels of an iteration, and the next iteration's first, are chained by programmatic
     // dependent launch: each waits for its predecessor before it reads, so only the launch
     // latency and the block set-up overlap the predecessor's drain. The two short exception and
     // fix kernels release their successor's blocks at once; the iteration kernel and the update
     // release theirs as their own blocks end (blocks of the next kernel resident early beside the
     // streaming ones slowed the solve: 395.2 ms with every kernel releasing early, 387.8 ms with
-    // the update also releasing, 386.2 ms as here, 388.2 ms without the chaining)
-    const bool pdl = c->pdl != 0;
+    // the update also releasing, 386.2 ms as here, 388.2 ms without the chaining). The
+    // host-driven loop launches them as ordinary kernels.
+    const bool pdl = c->pdl != 0 && use_h != 0;
     launch_main(c, st, po, pn, pdl);
     rbc_aux(c, st, po, pn, pdl);
     const long long nc = c->rbc_nh + c->rbc_ne;

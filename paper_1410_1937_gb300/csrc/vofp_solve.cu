@@ -726,9 +726,11 @@ vofp_status build_graph_mixed_once(vofp_ctx* c, int U, bool rb) {
 vofp_status build_graph_mixed(vofp_ctx* c, int U, bool rb) {
     if (c->graph_mixed && c->graph_mixed_key == graph_key(U, rb)) return VOFP_OK;
     c->launch_err = cudaSuccess;
+    const long long launches0 = c->launches;
     vofp_status s = build_graph_mixed_once(c, U, rb);
     if ((s != VOFP_OK || c->launch_err != cudaSuccess) && c->pdl) {
         (void)cudaGetLastError();
+        c->launches = launches0;
         if (c->graph_mixed) {
             cudaGraphExecDestroy(c->graph_mixed);
             c->graph_mixed = nullptr;
