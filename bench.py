@@ -131,6 +131,12 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+def workload_name(shape):
+    """The workload both arms are quoted on (512x256x128 hull in waves by default)."""
+    n = shape[0] * shape[1] * shape[2]
+    return f"hull-in-waves {shape[0]}x{shape[1]}x{shape[2]} ({n} cells) Dirichlet exit, rtol 1e-8"
+
+
 def make_problem(shape, seed=2):
     from paper_1410_1937_gb300 import inputs as I
     return I.config2(seed=seed, shape=shape)
@@ -216,7 +222,8 @@ def run_reference(args, rank, world):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_solve * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": f"hull-in-waves {args.shape[0]}x{args.shape[1]}x{args.shape[2]} rtol 1e-8"},
+           "config": {"workload": workload_name(args.shape), "mode": "fp64", "precond": "jacobi",
+                      "parallelism": "host cores (oracle)"},
            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": threads, "kind": "oracle",
                             "sample": f"each step {iters} oracle Jacobi-PCG iterations; solve extrapolated "
                                       f"to {args.ref_fp64_iterations} iterations plus assembly "
@@ -371,8 +378,7 @@ def run_ours(args, rank, world, local_rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == 32 else "f64",
         "data": "synthetic",
-        "config": {"workload": f"hull-in-waves {args.shape[0]}x{args.shape[1]}x{args.shape[2]} "
-                               f"({n} cells) Dirichlet exit, rtol 1e-8",
+        "config": {"workload": workload_name(args.shape),
                    "mode": args.mode, "precond": args.precond,
                    "parallelism": "replicas" if world > 1 else "single-gpu",
                    "l2": "inputs larger than L2 (8 FP64 arrays of 134 MB)"},
@@ -568,7 +574,10 @@ def main():
     ap.add_argument("--no-paper-bc", action="store_true",
                     help="skip the all-Neumann radiation-exit and density-smoothing solves")
     ap.add_argument("--ref-iters", type=int, default=20)
-    ap.add_argument("--ref-fp64-iterations", type=int, default=2000)
+    ap.add_argument("--ref-fp64-iterations", type=int, default=3712,
+                    help="reference arm: iterations of a whole FP64 Jacobi-PCG solve to 1e-8 on the "
+                         "workload (3712 on the 512x256x128 hull in waves: the FP64 Jacobi solve, the "
+                         "same iteration in exact arithmetic)")
     ap.add_argument("--profile-vof", action="store_true",
                     help="profiling run: also one VOF step after the capped solve")
     ap.add_argument("--profile-iters", type=int, default=0,
