@@ -54,9 +54,10 @@ typedef enum {
     VOFP_ERR_INVALID_ARG = 1,     /* bad pointer, size or option                                  */
     VOFP_ERR_CUDA = 2,            /* a CUDA runtime call failed (message in vofp_last_error)      */
     VOFP_ERR_OOM = 3,             /* device allocation failed                                     */
-    VOFP_ERR_NOT_CONVERGED = 4,   /* max_iter reached before rtol                                 */
+    VOFP_ERR_NOT_CONVERGED = 4,   /* max_iter reached before rtol (or 200 refinement steps)       */
     VOFP_ERR_BREAKDOWN = 5,       /* p.Ap <= 0, r.z <= 0 or a non-finite scalar in the iteration  */
-    VOFP_ERR_STAGNATED = 6,       /* residual stopped decreasing (stag_window / stag_ratio)       */
+    VOFP_ERR_STAGNATED = 6,       /* the iteration met rtol on its own residual but the residual  */
+                                  /* recomputed from x stayed above rtol through restarts from x  */
     VOFP_ERR_INCOMPATIBLE_RHS = 7,/* all-Neumann problem whose right-hand side does not sum to 0  */
     VOFP_ERR_NOT_BUILT = 8,       /* vofp_build_operator has not succeeded on this context        */
     VOFP_ERR_DEVICE_TIMEOUT = 9   /* a bounded device-side wait (a bulk copy into shared memory)  */
@@ -100,8 +101,13 @@ typedef struct {
  *               residual b - A x and solution update are FP64 while the inner PCG runs with FP32
  *               coefficients and vectors and FP64-accumulated dot products.
  *   precond     VOFP_PRECOND_JACOBI (diagonal) or VOFP_PRECOND_RBSGS (red-black symmetric
- *               Gauss-Seidel; FP64 mode only).
- *   rtol        stop when ||b_hat - A_hat x|| <= rtol ||b_hat|| (2-norm over the unknowns).
+ *               Gauss-Seidel, applied as CG on the black unknowns after eliminating the red ones
+ *               (Eisenstat's form); both modes, and the bench default in mixed mode).
+ *   rtol        the solve returns VOFP_OK only when the residual recomputed from the returned x,
+ *               ||b_hat - A_hat x|| (2-norm over the unknowns, FP64), is at most rtol ||b_hat||.
+ *               The iteration aims slightly below rtol; when the recomputed residual is still
+ *               above rtol it restarts from x (a fresh residual), up to three times, each
+ *               restart having to halve it (else VOFP_ERR_STAGNATED).
  *   max_iter    cap on PCG iterations (inner iterations summed in mixed mode).
  *   inner_rtol  mixed mode: relative residual reduction of each inner solve; 0 selects the
  *               default, 0.2 with inner_restart = 0 and 1e-3 with inner_restart = 1.
@@ -347,8 +353,12 @@ vofp_status vofp_get_stats(vofp_ctx* ctx, vofp_stats* stats);
  * until the process exits), enough for operators with at most 65536 merge groups; an operator with
  * more groups is rejected with VOFP_ERR_INVALID_ARG and a message.  The first call on each device
  * looks up the array's device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  All calls share the array: calls that overlap on the GPU
- * (other streams or threads) race.  Synchronises the context stream; *rel is a host double. */
+ * first call before any stream capture.  That first call is also where the CUDA runtime loads
+ * this entry point's kernels and its array onto the device (lazy module loading, the default
+ * since CUDA 12.2), a one-time reservation of about 1 MB plus code made by the runtime, not by
+ * this call: make it during set-up, before a caching allocator takes the free device memory.
+ * Later calls reserve nothing.  All calls share the array: calls that overlap on the GPU (other
+ * streams or threads) race.  Synchronises the context stream; *rel is a host double. */
 vofp_status vofp_residual_noalloc(vofp_ctx* ctx, const double* b, const double* x, double* rel);
 
 /* Training pair in the scaled variables the solvers and the network use: r_scaled = S b_hat

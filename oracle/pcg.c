@@ -15,16 +15,28 @@
  *
  * Reductions are summed over fixed 65536-element chunks in chunk order, so the result does not
  * depend on the number of OpenMP threads.
+ *
+ * A solve can also report when it first passed a looser tolerance (mark_rtol): the iteration and
+ * the wall time since the start of the solve at which |r| <= mark_rtol |b| first held.  One solve
+ * to a tight tolerance then also times the solve to the looser one, with the same iterates.
  */
+#define _POSIX_C_SOURCE 199309L
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
 
 #define CHUNK 65536
+
+static double wall_seconds(void) {
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
 
 static void csr_matvec(int64_t n, const int64_t* ip, const int32_t* ix, const double* a,
                        const double* x, double* y) {
@@ -67,11 +79,17 @@ void oracle_csr_matvec(int64_t n, const int64_t* ip, const int32_t* ix, const do
 
 /* Returns 0 on convergence, 1 if maxit was reached, 2 on breakdown (p.q <= 0 or not finite),
  * 3 on a non-positive diagonal.  x holds the initial guess on entry and the iterate on exit.
- * alpha_hist / beta_hist (may be NULL) receive the CG coefficients of each iteration. */
+ * alpha_hist / beta_hist (may be NULL) receive the CG coefficients of each iteration.
+ * mark_iter / mark_seconds (may be NULL) receive the first iteration at which the updated
+ * residual met mark_rtol and the seconds from entry to that point (-1 if it never did). */
 int oracle_jacobi_pcg(int64_t n, const int64_t* ip, const int32_t* ix, const double* a,
                       const double* b, double* x, double rtol, int64_t maxit,
                       int64_t* iters_out, double* relres_out,
-                      double* alpha_hist, double* beta_hist) {
+                      double* alpha_hist, double* beta_hist,
+                      double mark_rtol, int64_t* mark_iter, double* mark_seconds) {
+    const double t_start = wall_seconds();
+    if (mark_iter) *mark_iter = -1;
+    if (mark_seconds) *mark_seconds = -1.0;
     double* dinv = (double*)malloc(sizeof(double) * n);
     double* r = (double*)malloc(sizeof(double) * n);
     double* z = (double*)malloc(sizeof(double) * n);
@@ -97,7 +115,12 @@ int oracle_jacobi_pcg(int64_t n, const int64_t* ip, const int32_t* ix, const dou
         p[i] = z[i];
     }
     double rz = dot(n, r, z, part);
-    if (bnorm == 0.0 || sqrt(dot(n, r, r, part)) <= rtol * bnorm) { status = 0; goto done; }
+    double rr0 = sqrt(dot(n, r, r, part));
+    if (mark_iter && (bnorm == 0.0 || rr0 <= mark_rtol * bnorm)) {
+        *mark_iter = 0;
+        if (mark_seconds) *mark_seconds = wall_seconds() - t_start;
+    }
+    if (bnorm == 0.0 || rr0 <= rtol * bnorm) { status = 0; goto done; }
     for (it = 1; it <= maxit; ++it) {
         csr_matvec(n, ip, ix, a, p, q);
         double pq = dot(n, p, q, part);
@@ -110,6 +133,10 @@ int oracle_jacobi_pcg(int64_t n, const int64_t* ip, const int32_t* ix, const dou
         }
         double rr = dot(n, r, r, part);
         if (alpha_hist) alpha_hist[it - 1] = alpha;
+        if (mark_iter && *mark_iter < 0 && sqrt(rr) <= mark_rtol * bnorm) {
+            *mark_iter = it;
+            if (mark_seconds) *mark_seconds = wall_seconds() - t_start;
+        }
         if (sqrt(rr) <= rtol * bnorm) { status = 0; if (beta_hist) beta_hist[it - 1] = 0.0; break; }
 #pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; ++i) z[i] = dinv[i] * r[i];

@@ -72,7 +72,7 @@ def _lib():
             ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)
         lib.oracle_jacobi_pcg.restype = ctypes.c_int
         lib.oracle_jacobi_pcg.argtypes = [i64, ip64, ip32, dp, dp, dp, ctypes.c_double, i64,
-                                          ip64, dp, dp, dp]
+                                          ip64, dp, dp, dp, ctypes.c_double, ip64, dp]
         lib.oracle_csr_matvec.restype = None
         lib.oracle_csr_matvec.argtypes = [i64, ip64, ip32, dp, dp, dp]
         lib.oracle_set_threads.restype = ctypes.c_int
@@ -395,11 +395,23 @@ class System:
         if self.dirichlet:
             ph = np.linalg.solve(Ad, self.bhat)
         else:
+            c = self.compatibility()
+            if not c <= 1e-12:
+                raise ValueError(f"incompatible all-Neumann right-hand side: |sum b| / sum |b| = {c:.3e}")
             ph = np.linalg.lstsq(Ad, self.bhat, rcond=None)[0]
             ph -= ph.mean()
         return self.expand(ph)
 
-    def solve_pcg(self, rtol=1e-12, maxit=200000, x0=None, history=False):
+    def compatibility(self):
+        """|sum of b_hat| relative to sum of |b_hat|: the integral form (Sec. 2.3) over the whole
+        domain makes the net outward flux vanish when every boundary is free-slip, so an
+        all-Neumann problem has a solution only when this is at rounding level."""
+        tot = np.abs(self.bhat).sum()
+        return abs(self.bhat.sum()) / tot if tot > 0 else 0.0
+
+    def solve_pcg(self, rtol=1e-12, maxit=200000, x0=None, history=False, mark_rtol=None):
+        """Jacobi-PCG (oracle/pcg.c) to ``rtol``.  ``mark_rtol``: also report the iteration and the
+        seconds at which the updated residual first met that looser tolerance (info["mark"])."""
         lib = _lib()
         Ah = self.Ahat
         ip = Ah.indptr.astype(np.int64)
@@ -407,25 +419,38 @@ class System:
         a = np.ascontiguousarray(Ah.data, dtype=np.float64)
         b = np.ascontiguousarray(self.bhat, dtype=np.float64)
         if not self.dirichlet:
-            # Neumann compatibility (integral form, Sec. 2.3): sum of b_hat must vanish
+            # All-Neumann: only a compatible right-hand side has a solution (reading 11 of the
+            # integral form); an incompatible one is an error, not something to project away.
+            # What remains of a compatible one is rounding, removed with the constant null space.
+            c = self.compatibility()
+            if not c <= 1e-12:
+                raise ValueError(f"incompatible all-Neumann right-hand side: |sum b| / sum |b| = {c:.3e}")
             b = b - b.mean()
         x = np.zeros(self.M) if x0 is None else self.restrict(x0).copy()
         it = ctypes.c_int64(0)
         rr = ctypes.c_double(0.0)
         ah = np.zeros(maxit) if history else None
         bh = np.zeros(maxit) if history else None
+        mi = ctypes.c_int64(-1)
+        ms = ctypes.c_double(-1.0)
+        want_mark = mark_rtol is not None
         t0 = time.perf_counter()
         st = lib.oracle_jacobi_pcg(self.M, _ptr(ip, ctypes.c_int64), _ptr(ix, ctypes.c_int32),
                                    _ptr(a, ctypes.c_double), _ptr(b, ctypes.c_double),
                                    _ptr(x, ctypes.c_double), float(rtol), int(maxit),
                                    ctypes.byref(it), ctypes.byref(rr),
                                    _ptr(ah, ctypes.c_double) if history else None,
-                                   _ptr(bh, ctypes.c_double) if history else None)
+                                   _ptr(bh, ctypes.c_double) if history else None,
+                                   float(mark_rtol) if want_mark else 0.0,
+                                   ctypes.byref(mi) if want_mark else None,
+                                   ctypes.byref(ms) if want_mark else None)
         secs = time.perf_counter() - t0
         if not self.dirichlet:
             x -= x.mean()
         info = {"status": int(st), "iterations": int(it.value), "rel_residual": float(rr.value),
                 "seconds": secs, "threads": set_threads(0)}
+        if want_mark:
+            info["mark"] = {"rtol": float(mark_rtol), "iterations": int(mi.value), "seconds": float(ms.value)}
         if history:
             n = int(it.value)
             info["alpha"] = ah[:n]

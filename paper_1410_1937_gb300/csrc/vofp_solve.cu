@@ -837,9 +837,20 @@ vofp_status residual(vofp_ctx* c, const double* b, const double* x, double* rel)
     return VOFP_OK;
 }
 
-vofp_status solve(vofp_ctx* c, const double* b, double* x, const vofp_solve_opts* o, vofp_solve_info* info) {
-    prepare_kernels(c);
-    if (o->mode == VOFP_MODE_FCG_NN) return solve_fcg(c, b, x, o, info);
+namespace {
+
+// The loops stop on a residual that the iteration itself carries (the recursively updated one in
+// FP64 mode, an FP64 residual summed in another order in mixed mode), while the contract is on
+// the residual recomputed from x at the end.  They aim a little below rtol so that the two agree
+// without a restart in the usual case.
+constexpr double kLoopMargin = 0.99;
+// Restarts from the current iterate when the recomputed residual is still above rtol; each must
+// at least halve it, else the solve reports VOFP_ERR_STAGNATED.
+constexpr int kMaxRestarts = 3;
+
+// One pass of the FP64 or mixed-precision solve from x (or 0); fills every field of *info
+// (rel_residual recomputed from x) and returns the loop's own status.
+vofp_status solve_pass(vofp_ctx* c, const double* b, double* x, const vofp_solve_opts* o, vofp_solve_info* info) {
     vofp_status s = ensure_workspace(c);
     if (s) return s;
     // colour-compact vectors of the red-black inner solve (built once per operator)
@@ -885,7 +896,8 @@ vofp_status solve(vofp_ctx* c, const double* b, double* x, const vofp_solve_opts
     }
     CgScalars h{};
     h.status = VOFP_OK;
-    h.rtol = o->rtol;
+    const double rtol_loop = kLoopMargin * o->rtol;
+    h.rtol = rtol_loop;
     // default reduction per refinement step: 0.2 when the direction is kept (a frequent FP64
     // residual keeps the FP32 recurrence close to it), 1e-3 for restarted inner solves
     h.inner_rtol = o->inner_rtol > 0 ? o->inner_rtol : (o->inner_restart ? 1e-3 : 0.2);
@@ -911,7 +923,7 @@ vofp_status solve(vofp_ctx* c, const double* b, double* x, const vofp_solve_opts
         c->set_error("non-finite right-hand side or initial residual");
         return VOFP_ERR_BREAKDOWN;
     }
-    const bool converged0 = !(h.rnorm2 > o->rtol * o->rtol * h.ref2);
+    const bool converged0 = !(h.rnorm2 > rtol_loop * rtol_loop * h.ref2);
     if (o->host_loop && !converged0) {
         if ((s = host_loop(c, mixed, rb, U))) return s;
     }
@@ -960,21 +972,68 @@ vofp_status solve(vofp_ctx* c, const double* b, double* x, const vofp_solve_opts
         else
             c->launches += (h.iter_total / U) * fp64_body_kernels(c, U, rb);
     }
-    vofp_status result = (vofp_status)h.status;
-    if (result == VOFP_OK && !(rel <= o->rtol * 1.0000001) && !converged0) {
-        // the recursively updated residual met the tolerance but the recomputed one did not
-        if (!(rel <= o->rtol * 10.0)) result = VOFP_ERR_NOT_CONVERGED;
-    }
-    if (info) {
-        info->iterations = (int)h.iter_total;
-        info->outer_iterations = o->mode == VOFP_MODE_MIXED ? h.outer : 1;
-        info->rel_residual = rel;
-        info->seconds = ms * 1e-3;
-        info->status = result;
-    }
-    if (result != VOFP_OK)
-        c->set_error(result == VOFP_ERR_NOT_CONVERGED ? "solve did not reach rtol" : "CG breakdown");
+    const vofp_status result = (vofp_status)h.status;
+    info->iterations = (int)h.iter_total;
+    info->outer_iterations = o->mode == VOFP_MODE_MIXED ? h.outer : 1;
+    info->rel_residual = rel;
+    info->seconds = ms * 1e-3;
+    info->status = result;
+    info->nn_applications = 0;
+    info->fell_back = 0;
     return result;
+}
+
+const char* status_text(vofp_status s) {
+    switch (s) {
+        case VOFP_ERR_NOT_CONVERGED: return "solve did not reach rtol within max_iter";
+        case VOFP_ERR_STAGNATED: return "restarts from the iterate stopped reducing the recomputed residual";
+        case VOFP_ERR_BREAKDOWN: return "CG breakdown";
+        case VOFP_ERR_DEVICE_TIMEOUT: return "a bounded device-side wait ran out";
+        default: return "solve failed";
+    }
+}
+
+}  // namespace
+
+// The solve of the contract: VOFP_OK only when the residual recomputed from the returned x is at
+// most rtol.  A pass that stops with its own residual below rtol but the recomputed one above it
+// is restarted from its iterate (a fresh true residual); VOFP_ERR_STAGNATED when a restart fails
+// to halve the recomputed residual or kMaxRestarts do not reach rtol, VOFP_ERR_NOT_CONVERGED when
+// max_iter runs out first.
+vofp_status solve(vofp_ctx* c, const double* b, double* x, const vofp_solve_opts* o, vofp_solve_info* info) {
+    prepare_kernels(c);
+    if (o->mode == VOFP_MODE_FCG_NN) return solve_fcg(c, b, x, o, info);
+    vofp_solve_info acc{};
+    vofp_status r = solve_pass(c, b, x, o, &acc);
+    const long long max_iter = o->max_iter > 0 ? o->max_iter : 100000;
+    for (int restart = 0; r == VOFP_OK && !(acc.rel_residual <= o->rtol); ++restart) {
+        if (acc.iterations >= max_iter) {
+            r = VOFP_ERR_NOT_CONVERGED;
+            break;
+        }
+        if (restart == kMaxRestarts) {
+            r = VOFP_ERR_STAGNATED;
+            break;
+        }
+        vofp_solve_opts o2 = *o;
+        o2.x0_zero = 0;
+        o2.max_iter = (int)(max_iter - acc.iterations);
+        vofp_solve_info i2{};
+        const double before = acc.rel_residual;
+        r = solve_pass(c, b, x, &o2, &i2);
+        acc.iterations += i2.iterations;
+        acc.outer_iterations += i2.outer_iterations;
+        acc.seconds += i2.seconds;
+        acc.rel_residual = i2.rel_residual;
+        if (r == VOFP_OK && !(acc.rel_residual <= o->rtol) && !(acc.rel_residual <= 0.5 * before)) {
+            r = VOFP_ERR_STAGNATED;
+            break;
+        }
+    }
+    acc.status = r;
+    if (info) *info = acc;
+    if (r != VOFP_OK && c->err.empty()) c->set_error(status_text(r));
+    return r;
 }
 
 vofp_status scaled_pair(vofp_ctx* c, const double* b, const double* x, float* r_scaled, float* x_scaled) {
@@ -1054,7 +1113,7 @@ vofp_status solve_fcg(vofp_ctx* c, const double* b, double* x, const vofp_solve_
             result = VOFP_ERR_BREAKDOWN;
             break;
         }
-        if (rnorm2 <= o->rtol * o->rtol * bnorm2) break;
+        if (rnorm2 <= kLoopMargin * kLoopMargin * o->rtol * o->rtol * bnorm2) break;
         if (iters >= max_iter || outer >= 200) {
             result = VOFP_ERR_NOT_CONVERGED;
             break;
@@ -1144,7 +1203,7 @@ vofp_status solve_fcg(vofp_ctx* c, const double* b, double* x, const vofp_solve_
     }
     double rel = 0.0;
     if ((s = residual(c, b, x, &rel))) return s;
-    if (result == VOFP_OK && !(rel <= o->rtol * 10.0)) result = VOFP_ERR_NOT_CONVERGED;
+    if (result == VOFP_OK && !(rel <= o->rtol)) result = VOFP_ERR_NOT_CONVERGED;
     if (info) {
         info->iterations = it_total;
         info->outer_iterations = outer_total;

@@ -25,9 +25,15 @@ def random_params(rng):
 
 
 def test_bf16_rounding():
-    assert R.bf16_round(1.0 + 2.0 ** -9) == 1.0                  # tie -> even
-    assert R.bf16_round(1.0 + 3 * 2.0 ** -9) == 1.0 + 2.0 ** -7   # tie -> even (up)
-    assert R.bf16_round(1.0 + 2.0 ** -8) == 1.0 + 2.0 ** -7 or R.bf16_round(1.0 + 2.0 ** -8) == 1.0
+    # BF16 keeps 7 fraction bits: next to 1 the spacing is 2^-7, so 1 + 2^-8 is halfway
+    assert R.bf16_round(1.0 + 2.0 ** -9) == 1.0                   # below halfway -> down
+    assert R.bf16_round(1.0 + 3 * 2.0 ** -9) == 1.0 + 2.0 ** -7    # above halfway -> up
+    # exact ties go to the even fraction: 1 (fraction 0) and 1 + 2^-6 (fraction 2), never to the
+    # odd neighbour 1 + 2^-7 (fraction 1)
+    assert R.bf16_round(1.0 + 2.0 ** -8) == 1.0
+    assert R.bf16_round(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6
+    assert R.bf16_round(-(1.0 + 2.0 ** -8)) == -1.0
+    assert R.bf16_round(2.0 + 2.0 ** -7) == 2.0                     # tie at the next binade (spacing 2^-6)
     assert R.bf16_round(3.0) == 3.0 and R.bf16_round(-0.0) == 0.0
 
 
@@ -100,6 +106,40 @@ def test_adam_reference_step():
     p1, m, v = R.adam_step(p, g, np.zeros(2), np.zeros(2), 1, 1e-3)
     # first step moves every parameter by lr against the sign of its gradient
     np.testing.assert_allclose(p1, p - 1e-3 * np.sign(g), rtol=1e-6)
+
+
+def test_adam_closed_forms_over_three_steps():
+    """Adam (Kingma & Ba 2015, Sec. 2, the step-size form alpha_t = alpha sqrt(1 - b2^t) / (1 - b1^t)
+    with epsilon added to sqrt(v)) in closed form.  One gradient g at step 1 and none after:
+    m_t = b1^(t-1) (1-b1) g and v_t = b2^(t-1) (1-b2) g^2, so with epsilon = 0 the steps are
+        step 1: lr sign(g)
+        step 2: lr sign(g) b1 / (1 + b1) sqrt((1 + b2) / b2)
+        step 3: lr sign(g) b1^2 / (1 + b1 + b1^2) sqrt(1 + b2 + b2^2) / b2
+    A wrong decay rate, a missing or stale bias correction, or m and v swapped fails these."""
+    lr, b1, b2 = 1e-2, 0.9, 0.999
+    g = np.array([3.0, -0.5])
+    p = np.zeros(2)
+    m = v = np.zeros(2)
+    expect = [1.0, b1 / (1 + b1) * np.sqrt((1 + b2) / b2),
+              b1 ** 2 / (1 + b1 + b1 ** 2) * np.sqrt(1 + b2 + b2 ** 2) / b2]
+    for t in (1, 2, 3):
+        p_new, m, v = R.adam_step(p, g if t == 1 else np.zeros(2), m, v, t, lr, eps=0.0)
+        np.testing.assert_allclose(p - p_new, lr * np.sign(g) * expect[t - 1], rtol=1e-7)
+        p = p_new
+    # epsilon sits beside sqrt(v) of the uncorrected second moment: at step 1 with |g| = eps the
+    # step is lr g / (|g| + eps / sqrt(1 - b2)), a 1 / (1 + 1/sqrt(1 - b2)) fraction of lr
+    eps = 1e-8
+    p1, _, _ = R.adam_step(np.zeros(1), np.array([eps]), np.zeros(1), np.zeros(1), 1, lr, eps=eps)
+    np.testing.assert_allclose(-p1, lr / (1.0 + 1.0 / np.sqrt(1.0 - b2)), rtol=1e-9)
+    # a constant gradient: every step is lr sign(g) |g| sqrt(1-b2^t) / (|g| sqrt(1-b2^t) + eps)
+    p = np.zeros(1)
+    m = v = np.zeros(1)
+    gc = np.array([-2e-7])
+    for t in (1, 2, 3):
+        p_new, m, v = R.adam_step(p, gc, m, v, t, lr, eps=eps)
+        q = abs(gc[0]) * np.sqrt(1 - b2 ** t)
+        np.testing.assert_allclose(p_new - p, lr * q / (q + eps), rtol=1e-9)
+        p = p_new
 
 
 # ---------------------------------------------------------------------------------------------
@@ -190,12 +230,18 @@ def test_gpu_adam_step_matches_reference(gpu):
     rng = np.random.default_rng(10)
     rd = torch.from_numpy(rng.normal(size=prob.n).astype(np.float32)).cuda()
     td = torch.from_numpy(rng.normal(size=prob.n).astype(np.float32)).cuda()
-    p0 = net.get_params().astype(np.float64)
-    net.train_step(rd, td, lr=1e-3, update=True)
-    g = net.get_params(grads=True).astype(np.float64)     # the gradients this step used
-    p1 = net.get_params().astype(np.float64)
-    ref, _, _ = R.adam_step(p0, g, np.zeros_like(p0), np.zeros_like(p0), 1, 1e-3)
-    assert np.abs(p1 - ref).max() < 1e-6
+    # three steps: the moments m and v carry over, and the bias corrections change per step; the
+    # oracle replays the gradients each GPU step used
+    p = net.get_params().astype(np.float64)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    for step in (1, 2, 3):
+        net.train_step(rd, td, lr=1e-3, update=True)
+        g = net.get_params(grads=True).astype(np.float64)     # the gradients this step used
+        got = net.get_params().astype(np.float64)
+        ref, m, v = R.adam_step(p, g, m, v, step, 1e-3)
+        assert np.abs(got - ref).max() < 1e-6, step
+        p = got
 
 
 @pytest.mark.gpu

@@ -97,6 +97,23 @@ def test_smoothing_filter_conserves_interior_mass(oracle):
     assert abs(rho.sum() - 1.0) < 1e-15 and abs(rho[2, 3, 3] - 0.125) < 1e-15
 
 
+def test_smoothing_filter_reflects_at_the_wall(oracle):
+    # Sec. 2.10's (1/4, 1/2, 1/4) filter at a domain wall takes the cell itself as the missing
+    # neighbour (reading 4): an impulse in a corner cell keeps 3/4 per axis and passes 1/4 to its
+    # one neighbour per axis, so the corner ends at (3/4)^3 and the mass is conserved.  Dropping
+    # the missing neighbour (a zero there) would leave 1/2 per axis and lose mass.
+    F = np.zeros((4, 5, 6))
+    F[0, 0, 0] = 1.0
+    rho = oracle.density(F, 3.0, 1.0, smoothing=True)   # rho = 1 + 2 * smoothed(F)
+    w = np.array([0.75, 0.25])
+    ref = np.ones_like(F)
+    ref[:2, :2, :2] += 2.0 * w[:, None, None] * w[None, :, None] * w[None, None, :]
+    np.testing.assert_allclose(rho, ref, rtol=0, atol=1e-15)
+    # the far corner: same closed form mirrored
+    F2 = F[::-1, ::-1, ::-1].copy()
+    np.testing.assert_allclose(oracle.density(F2, 3.0, 1.0, smoothing=True), ref[::-1, ::-1, ::-1], atol=1e-15)
+
+
 def test_manufactured_solution_second_order(oracle):
     errs = []
     for n in (8, 16, 32, 64):
@@ -198,6 +215,32 @@ def test_all_neumann_nullspace_and_compatibility(oracle):
     assert abs(s.bhat.sum()) <= 1e-13 * np.abs(s.bhat).sum()
     x = s.solve_dense()
     assert s.residual(x) < 1e-12
+
+
+def test_incompatible_all_neumann_rhs_is_an_error(oracle):
+    # an all-Neumann right-hand side that does not sum to zero has no solution: the oracle refuses
+    # it instead of projecting it onto the compatible subspace
+    p = I.tiny_sphere()
+    p.bc = (I.NEUMANN,) * 6
+    s = oracle.System(p)
+    s.bhat = s.bhat + 1e-3 * np.abs(s.bhat).max()
+    assert s.compatibility() > 1e-6
+    with pytest.raises(ValueError, match="incompatible"):
+        s.solve_pcg(rtol=1e-10)
+    with pytest.raises(ValueError, match="incompatible"):
+        s.solve_dense()
+
+
+def test_pcg_mark_is_the_same_iterate_as_a_looser_solve(oracle):
+    # the iteration at which a tight solve first meets a looser tolerance is the iteration count of
+    # a solve to that tolerance (the same iterates), and its time lies inside the whole solve's
+    p = I.config1(shape=(32, 16, 16))
+    s = oracle.System(p)
+    _, loose = s.solve_pcg(rtol=1e-6)
+    _, tight = s.solve_pcg(rtol=1e-11, mark_rtol=1e-6)
+    assert tight["mark"]["iterations"] == loose["iterations"] > 0
+    assert 0.0 < tight["mark"]["seconds"] <= tight["seconds"]
+    assert tight["iterations"] > loose["iterations"]
 
 
 def test_projection_makes_velocity_divergence_free(oracle):
