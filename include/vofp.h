@@ -409,6 +409,14 @@ vofp_status vofp_launch_count(vofp_ctx* ctx, long long* count);
 vofp_status vofp_time_iteration_kernels(vofp_ctx* ctx, int precision, int precond, int reps,
                                         float* stencil_ms, float* update_ms, float* aux_ms);
 
+/* Measurement hook (no context): the current device's fused multiply-add throughput in FP64 and
+ * FP32, in TFLOP/s (two flops per FMA), from a kernel of independent FMA chains on every SM timed
+ * with CUDA events on `stream` (best of three launches after a warm-up; about 40 ms in all).  It
+ * is the roof of kernels bound by the FP64 pipe (the FP64 CG iteration, the VOF stages); the paper
+ * has no counterpart.  Synchronises the stream.  VOFP_ERR_INVALID_ARG for null outputs,
+ * VOFP_ERR_CUDA if a launch or event call fails. */
+vofp_status vofp_measure_fma_peaks(vofp_stream stream, double* fp64_tflops, double* fp32_tflops);
+
 /* Host-only planning query (no context, no device): how the colour-compact red-black iteration
  * kernel splits its work over `slots` resident blocks for tiles_x x tiles_y tiles (32 pairs x 8
  * rows each) and nz planes.  Block b marches the work items [b per, (b+1) per) of

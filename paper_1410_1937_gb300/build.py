@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvofp.so")
-SOURCES = ["vofp_api.cu", "vofp_assemble.cu", "vofp_solve.cu", "vofp_tma.cu", "vofp_rb_tma.cu", "vofp_rbc.cu", "vofp_project.cu", "vofp_exit.cu", "vofp_vof.cu", "vofp_rk2.cu", "vofp_noalloc.cu", "vofp_nn.cu"]
+SOURCES = ["vofp_api.cu", "vofp_assemble.cu", "vofp_solve.cu", "vofp_tma.cu", "vofp_rb_tma.cu", "vofp_rbc.cu", "vofp_project.cu", "vofp_exit.cu", "vofp_vof.cu", "vofp_rk2.cu", "vofp_noalloc.cu", "vofp_nn.cu", "vofp_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xcompiler", "-Wall"]

@@ -99,6 +99,7 @@ _sig = {
     "vofp_rbc_split_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            _P(ctypes.c_int), _P(ctypes.c_int), _P(ctypes.c_int)]),
     "vofp_scaled_pair": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "vofp_measure_fma_peaks": (ctypes.c_int, [_vp, _P(ctypes.c_double), _P(ctypes.c_double)]),
     "vofp_nn_create": (ctypes.c_int, [_P(_vp), ctypes.c_ulonglong, _vp]),
     "vofp_nn_destroy": (None, [_vp]),
     "vofp_nn_last_error": (ctypes.c_char_p, [_vp]),
@@ -155,6 +156,13 @@ def vofp_rbc_split_plan(tiles_x, tiles_y, nz, slots):
     _check(None, _lib.vofp_rbc_split_plan(int(tiles_x), int(tiles_y), int(nz), int(slots), ctypes.byref(b),
                                           ctypes.byref(p), ctypes.byref(q)))
     return b.value, p.value, q.value
+
+
+def vofp_measure_fma_peaks(stream=None):
+    """(FP64, FP32) fused multiply-add throughput of the current device in TFLOP/s."""
+    a, b = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(None, _lib.vofp_measure_fma_peaks(_stream_handle(stream), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def vofp_create(dx, dy, dz, stream=None):

@@ -5,6 +5,7 @@ import json
 import os
 import subprocess
 import sys
+import time
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -17,8 +18,10 @@ def load_bench():
 
 
 def test_reference_arm_prints_the_contract_line():
+    t0 = time.perf_counter()
     out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--shape", "64", "32", "32",
                           "--steps", "2", "--warmup", "1"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    wall = time.perf_counter() - t0
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1, out.stdout
@@ -31,6 +34,9 @@ def test_reference_arm_prints_the_contract_line():
     assert d["unit"] == "solves/s" and d["higher_is_better"] is True and d["value"] > 0
     assert d["steps"] == 2 and d["warmup"] == 1 and d["n_gpus"] == 1
     assert d["config"]["workload"] == bench.workload_name((64, 32, 32))
+    # the same config dict as the GPU arm's line, and a claimed time that the run really took
+    assert d["config"] == bench.bench_config((64, 32, 32))
+    assert d["steps"] * d["ms_per_step"] * 1e-3 <= wall
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"] == {"value": d["value"], "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
