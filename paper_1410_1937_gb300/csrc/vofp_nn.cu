@@ -4,26 +4,296 @@
 // of the scaled pressure system.  The paper has no counterpart: the network is used as the
 // preconditioner and initial guess of a flexible CG around the paper's conjugate-gradient solve.
 //
-// Activations are BF16 in channels-last layout ((z*ny + y)*nx + x)*C + c; weights are kept as FP32
-// masters (Adam) with BF16 copies; every 3x3x3 convolution is an implicit GEMM on the tensor cores
-// (mma.sync m16n8k16, BF16 inputs, FP32 accumulation): M = 16 output voxels along x per warp,
-// N = output channels, K = 27 taps x input channels.
+// Activations are BF16 in a chunk-planar layout: channels in groups of eight, each group a plane
+// of 16-byte voxel records, ((c / 8) * V + v) * 8 + c % 8 for voxel v of V.  A voxel's eight
+// channels of one group are then one row of a tensor-core operand, a box of voxels of one group is
+// one contiguous block, and concatenating channels is placing groups side by side (the skip
+// connections write straight into the concatenated buffers).
+//
+// Every 3x3x3 convolution, forward and data gradient, is an implicit GEMM on the fifth-generation
+// tensor cores (k_conv3_umma): a block owns an 8 x 16 voxel tile of a plane (M = 128) and marches
+// it in z; a bulk tensor copy brings each input plane with its one-voxel halo into a ring of
+// shared-memory slots; one thread issues, per output plane, 27 taps x (input channels / 16)
+// tcgen05.mma instructions whose A operand is the halo'd plane shifted by the tap (a different
+// descriptor start address) and whose B operand is that tap's weights, accumulating in FP32 in
+// tensor memory; four warps read the accumulator back, add the bias, apply ReLU and store BF16.
+// Weight gradients use warp-level mma.sync over voxel rows (a training-only path).
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <new>
 #include <random>
+#include <tuple>
 #include <vector>
 
 #include "vofp_internal.cuh"
+#include "vofp_tma.cuh"
+#include "vofp_umma.cuh"
 
 namespace vofp {
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
+
 namespace nn {
 
 using bf16 = __nv_bfloat16;
 
+// channel c of voxel v in a chunk-planar tensor of V voxels
+__host__ __device__ __forceinline__ long long aidx(long long v, int c, long long V) {
+    return ((long long)(c >> 3) * V + v) * 8 + (c & 7);
+}
+
+// ---- 3x3x3 convolution on the tensor cores ---------------------------------------------------
+// Tile of one block: 8 voxels along x (one core-matrix row group) by 16 along y, one plane; its
+// input box is 10 x 18 voxels (one-voxel halo) of every input channel group.
+constexpr int kTileX = 8, kTileY = 16, kBoxX = kTileX + 2, kBoxY = kTileY + 2;
+constexpr int kGroupBytes = kBoxX * kBoxY * 16;   // one channel group of one halo'd plane
+constexpr int kConvThreads = 192;                 // warp 0 copies, warp 1 issues MMAs, 2..5 store
+
+__host__ __device__ constexpr size_t al128(size_t b) { return (b + 127) / 128 * 128; }
+
+template <int CIN, int NOUT, int R>
+struct ConvCfg {
+    static_assert(CIN % 16 == 0 && NOUT % 16 == 0 && NOUT <= 64, "shape");
+    static constexpr int KCH = CIN / 8;                               // input channel groups
+    static constexpr uint32_t PLANE = (uint32_t)KCH * kGroupBytes;    // bytes of one ring slot
+    static constexpr uint32_t WBYTES = 27u * CIN * NOUT * 2u;         // this block's weights
+    static constexpr uint32_t TCOLS = 2 * NOUT <= 32 ? 32 : (2 * NOUT <= 64 ? 64 : 128);
+    static constexpr size_t oW = 0;
+    static constexpr size_t oRing = al128(WBYTES);
+    static constexpr size_t oBar = oRing + al128((size_t)R * PLANE);
+    static constexpr size_t oBias = oBar + 8 * (2 * R + 5) + 8;
+    static constexpr size_t SMEM = al128(oBias + 4 * NOUT) + 128;     // + alignment slack
+};
+
+struct ConvArgs {
+    int nx, ny, nz;
+    int tiles_x, tiles_y;
+    int seg, nseg;            // planes per z segment, segments
+    long long V;              // voxels of the level
+    const float* bias;        // per output channel (null: none)
+    int relu;
+    const bf16* wblob;        // [split][27][CIN/8][NOUT][8]
+    bf16* out;                // chunk-planar output tensor
+    int out_chunk0;           // first channel group of this convolution's outputs in `out`
+    int* err;                 // set to 1 when a bounded wait runs out
+};
+
+// Block order: x tiles fastest, then y tiles, z segments, output-channel splits (neighbouring
+// blocks share halo rows through L2).
+template <int CIN, int NOUT, int R>
+__global__ void __launch_bounds__(kConvThreads, 1)
+k_conv3_umma(const __grid_constant__ CUtensorMap in_map, const ConvArgs a) {
+    using G = ConvCfg<CIN, NOUT, R>;
+    extern __shared__ unsigned char smraw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 127) & ~uintptr_t(127));
+    unsigned char* wsm = sm + G::oW;
+    unsigned char* ring = sm + G::oRing;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + G::oBar);
+    uint64_t* empty = full + R;
+    uint64_t* accf = empty + R;
+    uint64_t* acce = accf + 2;
+    uint64_t* wbar = acce + 2;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(wbar + 1);
+    float* bsm = reinterpret_cast<float*>(sm + G::oBias);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int b = blockIdx.x;
+    const int tx = b % a.tiles_x;
+    b /= a.tiles_x;
+    const int ty = b % a.tiles_y;
+    b /= a.tiles_y;
+    const int sg = b % a.nseg, split = b / a.nseg;
+    const int x0 = tx * kTileX, y0 = ty * kTileY;
+    const int z0 = sg * a.seg;
+    const int nout = min(a.nz, z0 + a.seg) - z0;   // output planes of this block (>= 1)
+    const int nin = nout + 2;                       // input planes z0-1 .. z0+nout
+    if (tid == 0) {
+        for (int i = 0; i < R; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        mbar_init(&accf[0], 1);
+        mbar_init(&accf[1], 1);
+        mbar_init(&acce[0], 128);
+        mbar_init(&acce[1], 128);
+        mbar_init(wbar, 1);
+        fence_mbar_init();
+    }
+    if (tid < NOUT) bsm[tid] = a.bias ? a.bias[split * NOUT + tid] : 0.f;
+    if (warp == 0) umma::tmem_alloc(tslot, G::TCOLS);
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    bool fail = false;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer: the block's weights once, then the input planes through the ring
+            mbar_expect_tx(wbar, G::WBYTES);
+            umma::bulk_load(wsm, reinterpret_cast<const unsigned char*>(a.wblob) + (size_t)split * G::WBYTES,
+                            G::WBYTES, wbar);
+            int issued = 0;
+            for (int lp = 0; lp < nin; ++lp) {
+                const int s = lp % R;
+                if (lp >= R && !mbar_wait_bounded(&empty[s], (uint32_t)((lp / R) - 1) & 1u)) {
+                    fail = true;
+                    break;
+                }
+                mbar_expect_tx(&full[s], G::PLANE);
+                umma::tma_load_5d(ring + (size_t)s * G::PLANE, &in_map, &full[s], 0, x0 - 1, y0 - 1, z0 - 1 + lp, 0);
+                ++issued;
+            }
+            // every copy issued must have landed before the block may leave
+            for (int lp = max(0, issued - R); lp < issued; ++lp)
+                if (!mbar_wait_bounded(&full[lp % R], (uint32_t)(lp / R) & 1u)) fail = true;
+            if (!mbar_wait_bounded(wbar, 0)) fail = true;
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = umma::idesc_bf16(128, NOUT);
+            const uint32_t wbase = umma::saddr(wsm), rbase = umma::saddr(ring);
+            if (!mbar_wait_bounded(wbar, 0)) fail = true;
+            int waited = 0;   // input planes whose copy has been waited for
+            for (int lz = 0; lz < nout && !fail; ++lz) {
+                // output plane z0 + lz reads local input planes lz, lz+1, lz+2
+                while (waited < lz + 3) {
+                    if (!mbar_wait_bounded(&full[waited % R], (uint32_t)(waited / R) & 1u)) {
+                        fail = true;
+                        break;
+                    }
+                    ++waited;
+                }
+                if (fail) break;
+                const int buf = lz & 1;
+                if (lz >= 2 && !mbar_wait_bounded(&acce[buf], (uint32_t)((lz >> 1) - 1) & 1u)) {
+                    fail = true;
+                    break;
+                }
+                umma::fence_after_sync();
+                const uint32_t d = tmem + (uint32_t)buf * (G::TCOLS / 2);
+                uint32_t acc = 0;
+#pragma unroll 1
+                for (int dz = 0; dz < 3; ++dz) {
+                    const uint32_t slot = rbase + (uint32_t)((lz + dz) % R) * G::PLANE;
+#pragma unroll 1
+                    for (int t = 0; t < 9; ++t) {
+                        const int dy = t / 3, dx = t % 3;
+                        const uint32_t abase = slot + (uint32_t)(dy * kBoxX + dx) * 16u;
+                        const uint32_t bbase = wbase + (uint32_t)(dz * 9 + t) * (uint32_t)(CIN * NOUT * 2);
+#pragma unroll
+                        for (int ks = 0; ks < CIN / 16; ++ks) {
+                            const uint64_t ad = umma::smem_desc(abase + 2u * ks * kGroupBytes, kGroupBytes, kBoxX * 16);
+                            const uint64_t bd = umma::smem_desc(bbase + 2u * ks * NOUT * 16, NOUT * 16, 128);
+                            umma::mma_bf16(d, ad, bd, idesc, acc);
+                            acc = 1;
+                        }
+                    }
+                }
+                umma::commit(&accf[buf]);
+                umma::commit(&empty[lz % R]);   // local plane lz (input z0+lz-1) is read for the last time
+            }
+        }
+    } else {
+        // epilogue: TMEM lane quadrant (warp % 4) of the 128 rows; row m = voxel (m % 8, m / 8)
+        const int q = warp & 3;
+        const int m = q * 32 + lane;
+        const int xi = x0 + (m & 7), yi = y0 + (m >> 3);
+        const bool inside = xi < a.nx && yi < a.ny;
+        for (int lz = 0; lz < nout; ++lz) {
+            const int buf = lz & 1;
+            if (!fail && !mbar_wait_bounded(&accf[buf], (uint32_t)(lz >> 1) & 1u)) fail = true;
+            if (__any_sync(0xffffffffu, fail)) {
+                fail = true;
+                break;
+            }
+            umma::fence_after_sync();
+            float v[NOUT];
+#pragma unroll
+            for (int c0 = 0; c0 < NOUT; c0 += 16) {
+                uint32_t r[16];
+                umma::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * (G::TCOLS / 2) + c0, r);
+                umma::tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[c0 + j] = __uint_as_float(r[j]);
+            }
+            umma::fence_before_sync();
+            umma::mbar_arrive(&acce[buf]);
+            if (inside) {
+                const long long vox = ((long long)(z0 + lz) * a.ny + yi) * a.nx + xi;
+#pragma unroll
+                for (int oc = 0; oc < NOUT / 8; ++oc) {
+                    uint32_t w4[4];
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        float lo = v[oc * 8 + 2 * h] + bsm[oc * 8 + 2 * h];
+                        float hi = v[oc * 8 + 2 * h + 1] + bsm[oc * 8 + 2 * h + 1];
+                        if (a.relu) {
+                            lo = fmaxf(lo, 0.f);
+                            hi = fmaxf(hi, 0.f);
+                        }
+                        const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
+                        w4[h] = *reinterpret_cast<const uint32_t*>(&p);
+                    }
+                    const long long grp = a.out_chunk0 + (long long)split * (NOUT / 8) + oc;
+                    *reinterpret_cast<uint4*>(a.out + (grp * a.V + vox) * 8) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+                }
+            }
+        }
+    }
+    if (fail) atomicExch(a.err, 1);
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        umma::fence_after_sync();
+        umma::tmem_dealloc(tmem, G::TCOLS);
+    }
+}
+
+// ---- weight blobs for the tensor-core convolution ---------------------------------------------
+// forward: blob[s][tap][k][n][e] = W[tap][s nout + n][8 k + e]  (W[27][cout][cin], FP32 masters)
+__global__ void k_blob_fwd(const float* __restrict__ w, int cout, int cin, int nout, bf16* __restrict__ blob) {
+    const long long total = 27LL * cout * cin;
+    const int kch = cin / 8;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        long long t = i;
+        const int e = int(t & 7);
+        t >>= 3;
+        const int n = int(t % nout);
+        t /= nout;
+        const int k = int(t % kch);
+        t /= kch;
+        const int tap = int(t % 27);
+        const int s = int(t / 27);
+        blob[i] = __float2bfloat16(w[((long long)tap * cout + s * nout + n) * cin + 8 * k + e]);
+    }
+}
+// data gradient: the layer run backwards (inputs: its cout channels; outputs: its cin channels;
+// taps mirrored): blob[s][tap][k][n][e] = W[26 - tap][8 k + e][s nout + n]
+__global__ void k_blob_dgrad(const float* __restrict__ w, int cout, int cin, int nout, bf16* __restrict__ blob) {
+    const long long total = 27LL * cout * cin;
+    const int kch = cout / 8;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        long long t = i;
+        const int e = int(t & 7);
+        t >>= 3;
+        const int n = int(t % nout);
+        t /= nout;
+        const int k = int(t % kch);
+        t /= kch;
+        const int tap = int(t % 27);
+        const int s = int(t / 27);
+        blob[i] = __float2bfloat16(w[((long long)(26 - tap) * cout + 8 * k + e) * cin + s * nout + n]);
+    }
+}
+
+__device__ __forceinline__ uint32_t ld32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+__device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi) {
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
 __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
     asm volatile(
         "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -32,66 +302,7 @@ __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ uint32_t ld32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
-__device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi) {
-    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
-
-// ---- 3x3x3 convolution, forward (also the data gradient, with flipped/transposed weights) ----
-// in: (nx,ny,nz,cin) BF16, cin % 16 == 0; w: [27][COUT][cin] BF16; out: (nx,ny,nz,COUT) BF16.
-// bias may be null; relu applies max(0, .).  A warp owns 16 consecutive voxels of one x-row.
-template <int COUT>
-__global__ void __launch_bounds__(128)
-k_conv3(const bf16* __restrict__ in, int cin, const bf16* __restrict__ w, const float* __restrict__ bias,
-        bf16* __restrict__ out, int nx, int ny, int nz, int relu) {
-    constexpr int NT = COUT / 8;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, t = lane & 3;
-    const int x0 = (blockIdx.x * 4 + warp) * 16;
-    const int y = blockIdx.y, z = blockIdx.z;
-    if (x0 >= nx) return;
-    float acc[NT][4];
-#pragma unroll
-    for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-    const int xa = x0 + g, xb = x0 + g + 8;
-    for (int tap = 0; tap < 27; ++tap) {
-        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-        const int iz = z + dz, iy = y + dy;
-        if (iz < 0 || iz >= nz || iy < 0 || iy >= ny) continue;
-        const int ixa = xa + dx, ixb = xb + dx;
-        const bool va = ixa >= 0 && ixa < nx && xa < nx, vb = ixb >= 0 && ixb < nx && xb < nx;
-        const long long rowbase = ((long long)iz * ny + iy) * nx;
-        const bf16* pa = in + (rowbase + ixa) * cin;
-        const bf16* pb = in + (rowbase + ixb) * cin;
-        const bf16* wt = w + (long long)tap * COUT * cin;
-        for (int kc = 0; kc < cin; kc += 16) {
-            uint32_t a[4];
-            a[0] = va ? ld32(pa + kc + 2 * t) : 0u;
-            a[1] = vb ? ld32(pb + kc + 2 * t) : 0u;
-            a[2] = va ? ld32(pa + kc + 2 * t + 8) : 0u;
-            a[3] = vb ? ld32(pb + kc + 2 * t + 8) : 0u;
-#pragma unroll
-            for (int n = 0; n < NT; ++n) {
-                const bf16* pw = wt + (long long)(n * 8 + g) * cin + kc + 2 * t;
-                mma16816(acc[n], a, ld32(pw), ld32(pw + 8));
-            }
-        }
-    }
-    const long long ob = ((long long)z * ny + y) * nx;
-#pragma unroll
-    for (int n = 0; n < NT; ++n) {
-        const int co = n * 8 + 2 * t;
-        float b0 = bias ? bias[co] : 0.f, b1 = bias ? bias[co + 1] : 0.f;
-        float v0 = acc[n][0] + b0, v1 = acc[n][1] + b1, v2 = acc[n][2] + b0, v3 = acc[n][3] + b1;
-        if (relu) {
-            v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); v2 = fmaxf(v2, 0.f); v3 = fmaxf(v3, 0.f);
-        }
-        if (xa < nx) *reinterpret_cast<__nv_bfloat162*>(out + (ob + xa) * COUT + co) = __floats2bfloat162_rn(v0, v1);
-        if (xb < nx) *reinterpret_cast<__nv_bfloat162*>(out + (ob + xb) * COUT + co) = __floats2bfloat162_rn(v2, v3);
-    }
-}
-
-// ---- 3x3x3 convolution, weight gradient ---------------------------------------------------
+// ---- 3x3x3 convolution, weight gradient (training) ----------------------------------------------
 // dw[tap][co][ci] += sum over voxels v of dy[v][co] * x[v + tap - 1][ci] (FP32 atomics into dw).
 // GEMM per tap: M = 16 output channels (co tile), N = input channels, K = 16 voxels of an x-row.
 template <int CIN>
@@ -104,6 +315,7 @@ k_conv3_wgrad(const bf16* __restrict__ x, const bf16* __restrict__ dy, int cout,
     const int cotiles = cout / 16;
     const int tap = blockIdx.x / cotiles, co0 = (blockIdx.x % cotiles) * 16;
     const int dz = tap / 9 - 1, dy_ = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+    const long long V = (long long)nx * ny * nz;
     float acc[NT][4];
 #pragma unroll
     for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
@@ -118,13 +330,13 @@ k_conv3_wgrad(const bf16* __restrict__ x, const bf16* __restrict__ dy, int cout,
         const long long ob = row * nx, ib = ((long long)iz * ny + iy) * nx;
         for (int xs = warp * 16; xs < nx; xs += 64) {
             // K index k = voxel xs + k of this row
-            auto dyv = [&](int k, int m) -> bf16 {
+            auto dyv = [&](int k, int mm) -> bf16 {
                 const int xx = xs + k;
-                return xx < nx ? dy[(ob + xx) * cout + co0 + m] : zero;
+                return xx < nx ? dy[aidx(ob + xx, co0 + mm, V)] : zero;
             };
             auto xv = [&](int k, int ci) -> bf16 {
                 const int xx = xs + k, ix = xx + dx;
-                return (rowok && xx < nx && ix >= 0 && ix < nx) ? x[(ib + ix) * CIN + ci] : zero;
+                return (rowok && xx < nx && ix >= 0 && ix < nx) ? x[aidx(ib + ix, ci, V)] : zero;
             };
             uint32_t a[4];
             a[0] = pack2(dyv(2 * t, g), dyv(2 * t + 1, g));
@@ -152,20 +364,8 @@ k_conv3_wgrad(const bf16* __restrict__ x, const bf16* __restrict__ dy, int cout,
     }
 }
 
-// ---- small kernels --------------------------------------------------------------------------
-// BF16 weights: wb[tap][co][ci] from FP32 masters; the data-gradient copy wt[26-tap][ci][co]
-__global__ void k_weights_bf16(const float* __restrict__ w, bf16* __restrict__ wb, bf16* __restrict__ wt,
-                               int cout, int cin) {
-    const int n = 27 * cout * cin;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int ci = i % cin, co = (i / cin) % cout, tap = i / (cin * cout);
-        const bf16 v = __float2bfloat16(w[i]);
-        wb[i] = v;
-        if (wt) wt[((long long)(26 - tap) * cin + ci) * cout + co] = v;
-    }
-}
-
-// dpre = dy where y > 0 (ReLU gradient), in place on dy
+// ---- small kernels (chunk-planar tensors) ---------------------------------------------------------
+// dpre = dy where y > 0 (ReLU gradient), in place on dy (same layout and channel count)
 __global__ void k_relu_bwd(bf16* __restrict__ dy, const bf16* __restrict__ y, long long n) {
     const bf16 zero = __float2bfloat16(0.f);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -178,7 +378,7 @@ __global__ void k_bias_grad(const bf16* __restrict__ dy, int C, long long nv, fl
     const int c = blockIdx.y;
     float s = 0.f;
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv; v += (long long)gridDim.x * blockDim.x)
-        s += __bfloat162float(dy[v * C + c]);
+        s += __bfloat162float(dy[aidx(v, c, nv)]);
     sh[threadIdx.x] = s;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
@@ -188,78 +388,120 @@ __global__ void k_bias_grad(const bf16* __restrict__ dy, int C, long long nv, fl
     if (threadIdx.x == 0) atomicAdd(db + c, sh[0]);
 }
 
-// 2x2x2 average pooling: (nx,ny,nz,C) -> (nx/2,ny/2,nz/2,C)
-__global__ void k_pool(const bf16* __restrict__ in, bf16* __restrict__ out, int nx, int ny, int nz, int C) {
+__device__ __forceinline__ void unpack8(const uint4& u, float (&f)[8]) {
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        f[2 * h] = __uint_as_float(w[h] << 16);
+        f[2 * h + 1] = __uint_as_float(w[h] & 0xFFFF0000u);
+    }
+}
+__device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
+    uint32_t w[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const __nv_bfloat162 p = __floats2bfloat162_rn(f[2 * h], f[2 * h + 1]);
+        w[h] = *reinterpret_cast<const uint32_t*>(&p);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+__device__ __forceinline__ long long parent_voxel(long long v, int nx, int ny) {
+    const int x = int(v % nx), y = int((v / nx) % ny);
+    const long long z = v / ((long long)nx * ny);
+    return ((z / 2) * (ny / 2) + y / 2) * (nx / 2) + x / 2;
+}
+
+// 2x2x2 average pooling of `groups` channel groups: (nx,ny,nz) -> (nx/2,ny/2,nz/2)
+__global__ void k_pool(const bf16* __restrict__ in, bf16* __restrict__ out, int nx, int ny, int nz, int groups) {
     const int hx = nx / 2, hy = ny / 2, hz = nz / 2;
-    const long long n = (long long)hx * hy * hz * C;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int c = int(i % C);
-        long long v = i / C;
+    const long long Vf = (long long)nx * ny * nz, Vc = (long long)hx * hy * hz;
+    const uint4* src = reinterpret_cast<const uint4*>(in);
+    uint4* dst = reinterpret_cast<uint4*>(out);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < Vc * groups; i += (long long)gridDim.x * blockDim.x) {
+        const int k = int(i / Vc);
+        const long long v = i % Vc;
         const int x = int(v % hx), y = int((v / hx) % hy), z = int(v / ((long long)hx * hy));
-        float s = 0.f;
+        float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (int q = 0; q < 8; ++q) {
             const int xx = 2 * x + (q & 1), yy = 2 * y + ((q >> 1) & 1), zz = 2 * z + (q >> 2);
-            s += __bfloat162float(in[(((long long)zz * ny + yy) * nx + xx) * C + c]);
+            float f[8];
+            unpack8(src[k * Vf + ((long long)zz * ny + yy) * nx + xx], f);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) s[e] += f[e];
         }
-        out[i] = __float2bfloat16(0.125f * s);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) s[e] *= 0.125f;
+        dst[k * Vc + v] = pack8(s);
     }
 }
 
-// gradient of the pooling, added into din (din += dout(parent) / 8)
-__global__ void k_pool_bwd(const bf16* __restrict__ dout, bf16* __restrict__ din, int nx, int ny, int nz, int C,
+// gradient of the pooling, added into din (din += dout(parent) / 8), `groups` channel groups
+__global__ void k_pool_bwd(const bf16* __restrict__ dout, bf16* __restrict__ din, int nx, int ny, int nz, int groups,
                            int accumulate) {
-    const long long n = (long long)nx * ny * nz * C;
-    const int hx = nx / 2, hy = ny / 2;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int c = int(i % C);
-        const long long v = i / C;
-        const int x = int(v % nx), y = int((v / nx) % ny), z = int(v / ((long long)nx * ny));
-        const float g = 0.125f * __bfloat162float(dout[(((long long)(z / 2) * hy + y / 2) * hx + x / 2) * C + c]);
-        din[i] = __float2bfloat16(accumulate ? __bfloat162float(din[i]) + g : g);
+    const long long Vf = (long long)nx * ny * nz, Vc = Vf / 8;
+    const uint4* src = reinterpret_cast<const uint4*>(dout);
+    uint4* dst = reinterpret_cast<uint4*>(din);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < Vf * groups; i += (long long)gridDim.x * blockDim.x) {
+        const int k = int(i / Vf);
+        const long long v = i % Vf;
+        float g[8], d[8];
+        unpack8(src[k * Vc + parent_voxel(v, nx, ny)], g);
+        if (accumulate) unpack8(dst[i], d);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) d[e] = accumulate ? d[e] + 0.125f * g[e] : 0.125f * g[e];
+        dst[i] = pack8(d);
     }
 }
 
-// nearest upsampling of a (coarse, Ca channels) concatenated with b (fine, Cb channels)
-__global__ void k_upcat(const bf16* __restrict__ a, int Ca, const bf16* __restrict__ b, int Cb,
-                        bf16* __restrict__ out, int nx, int ny, int nz) {
-    const int C = Ca + Cb, hx = nx / 2, hy = ny / 2;
-    const long long n = (long long)nx * ny * nz * C;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int c = int(i % C);
-        const long long v = i / C;
-        if (c < Ca) {
-            const int x = int(v % nx), y = int((v / nx) % ny), z = int(v / ((long long)nx * ny));
-            out[i] = a[(((long long)(z / 2) * hy + y / 2) * hx + x / 2) * Ca + c];
-        } else {
-            out[i] = b[v * Cb + (c - Ca)];
-        }
+// nearest upsampling of `groups` coarse channel groups into the first groups of a fine tensor
+__global__ void k_upsample(const bf16* __restrict__ coarse, bf16* __restrict__ fine, int nx, int ny, int nz, int groups) {
+    const long long Vf = (long long)nx * ny * nz, Vc = Vf / 8;
+    const uint4* src = reinterpret_cast<const uint4*>(coarse);
+    uint4* dst = reinterpret_cast<uint4*>(fine);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < Vf * groups; i += (long long)gridDim.x * blockDim.x) {
+        const int k = int(i / Vf);
+        dst[i] = src[k * Vc + parent_voxel(i % Vf, nx, ny)];
     }
 }
 
-// gradient of upcat: da (coarse) = sum of the 8 children's first Ca channels; db += last Cb
-__global__ void k_upcat_bwd_a(const bf16* __restrict__ dcat, int Ca, int Cb, bf16* __restrict__ da, int nx, int ny,
-                              int nz) {
-    const int C = Ca + Cb, hx = nx / 2, hy = ny / 2, hz = nz / 2;
-    const long long n = (long long)hx * hy * hz * Ca;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int c = int(i % Ca);
-        const long long v = i / Ca;
+// gradient of the upsampling: coarse (groups) = sum over each voxel's 8 children (fine groups 0..)
+__global__ void k_upsample_bwd(const bf16* __restrict__ dfine, bf16* __restrict__ dcoarse, int nx, int ny, int nz,
+                               int groups) {
+    const int hx = nx / 2, hy = ny / 2, hz = nz / 2;
+    const long long Vf = (long long)nx * ny * nz, Vc = (long long)hx * hy * hz;
+    const uint4* src = reinterpret_cast<const uint4*>(dfine);
+    uint4* dst = reinterpret_cast<uint4*>(dcoarse);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < Vc * groups; i += (long long)gridDim.x * blockDim.x) {
+        const int k = int(i / Vc);
+        const long long v = i % Vc;
         const int x = int(v % hx), y = int((v / hx) % hy), z = int(v / ((long long)hx * hy));
-        float s = 0.f;
+        float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (int q = 0; q < 8; ++q) {
             const int xx = 2 * x + (q & 1), yy = 2 * y + ((q >> 1) & 1), zz = 2 * z + (q >> 2);
-            s += __bfloat162float(dcat[(((long long)zz * ny + yy) * nx + xx) * C + c]);
+            float f[8];
+            unpack8(src[k * Vf + ((long long)zz * ny + yy) * nx + xx], f);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) s[e] += f[e];
         }
-        da[i] = __float2bfloat16(s);
+        dst[i] = pack8(s);
     }
 }
-__global__ void k_upcat_bwd_b(const bf16* __restrict__ dcat, int Ca, int Cb, bf16* __restrict__ db, long long nv) {
-    const int C = Ca + Cb;
-    const long long n = nv * Cb;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const long long v = i / Cb;
-        const int c = int(i % Cb);
-        db[i] = __float2bfloat16(__bfloat162float(db[i]) + __bfloat162float(dcat[v * C + Ca + c]));
+
+// dst (+)= src over n 8-channel records (the skip branch of a concatenation's gradient)
+__global__ void k_add_groups(const bf16* __restrict__ src, bf16* __restrict__ dst, long long nrec, int accumulate) {
+    const uint4* s4 = reinterpret_cast<const uint4*>(src);
+    uint4* d4 = reinterpret_cast<uint4*>(dst);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nrec; i += (long long)gridDim.x * blockDim.x) {
+        if (!accumulate) {
+            d4[i] = s4[i];
+            continue;
+        }
+        float a[8], b[8];
+        unpack8(s4[i], a);
+        unpack8(d4[i], b);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) b[e] += a[e];
+        d4[i] = pack8(b);
     }
 }
 
@@ -314,15 +556,19 @@ using vofp::nn::bf16;
 
 struct Layer {
     int cin, cout, cin_real;
+    int nout_f, nout_b;      // output channels per block of the forward / data-gradient convolution
     float *w = nullptr, *b = nullptr, *gw = nullptr, *gb = nullptr;
     float *mw = nullptr, *vw = nullptr, *mb = nullptr, *vb = nullptr;
-    bf16 *wb = nullptr, *wt = nullptr;
+    bf16 *blob_f = nullptr, *blob_b = nullptr;
     long long nw() const { return 27LL * cout * cin; }
 };
 
-// encoder 1, 2, 3, decoder 2, 1 (two 3x3x3 convolutions each)
-const int kLayers[10][3] = {{16, 16, 8},  {16, 16, 16}, {16, 32, 16}, {32, 32, 32}, {32, 64, 32},
-                            {64, 64, 64}, {96, 32, 96}, {32, 32, 32}, {48, 16, 48}, {16, 16, 16}};
+// encoder 1, 2, 3, decoder 2, 1 (two 3x3x3 convolutions each): stored input channels, output
+// channels, real input channels, output channels per block forward and for the data gradient
+// (the widest ones split so that weights and input ring fit one block's shared memory)
+const int kLayers[10][5] = {{16, 16, 8, 16, 16},  {16, 16, 16, 16, 16}, {16, 32, 16, 32, 16}, {32, 32, 32, 32, 32},
+                            {32, 64, 32, 64, 32}, {64, 64, 64, 32, 32}, {96, 32, 96, 16, 48}, {32, 32, 32, 32, 32},
+                            {48, 16, 48, 16, 48}, {16, 16, 16, 16, 16}};
 
 }  // namespace
 
@@ -336,26 +582,30 @@ struct vofp_nn {
     int step = 0;
     std::vector<void*> allocs;
     size_t bytes = 0;
+    int* derr = nullptr;      // device flag of the convolutions' bounded waits
     // grid-dependent
     int nx = 0, ny = 0, nz = 0;
     long long V1 = 0, V2 = 0, V3 = 0;
-    std::vector<void*> grid_allocs;
-    bf16 *geo = nullptr, *x0 = nullptr, *a1 = nullptr, *s1 = nullptr, *p1 = nullptr, *a2 = nullptr, *s2 = nullptr;
-    bf16 *p2 = nullptr, *a3 = nullptr, *b3 = nullptr, *c2 = nullptr, *d2a = nullptr, *d2b = nullptr, *c1 = nullptr;
-    bf16 *d1a = nullptr, *d1b = nullptr;
+    std::vector<void*> grid_allocs, grad_allocs;
+    // forward activations; s1 and s2 live in the last groups of the concatenations c1 and c2
+    bf16 *geo = nullptr, *x0 = nullptr, *a1 = nullptr, *c1 = nullptr, *p1 = nullptr, *a2 = nullptr, *c2 = nullptr;
+    bf16 *p2 = nullptr, *a3 = nullptr, *b3 = nullptr, *d2a = nullptr, *d2b = nullptr, *d1a = nullptr, *d1b = nullptr;
+    bf16 *s1 = nullptr, *s2 = nullptr;
+    // gradients (allocated by the first training step)
     bf16 *g16a = nullptr, *g16b = nullptr, *g48 = nullptr, *g32a = nullptr, *g32b = nullptr, *g96 = nullptr;
     bf16 *g64a = nullptr, *g64b = nullptr, *gs1 = nullptr, *gs2 = nullptr, *gp1 = nullptr, *gp2 = nullptr;
     float *mask = nullptr, *out = nullptr, *scal = nullptr;   // scal: sum r^2, count, scale, inv scale, loss
-    bool bound = false;
+    bool bound = false, grads_ready = false;
+    std::map<std::tuple<const void*, int, int, int, int>, CUtensorMap> maps;
 
     template <typename T>
-    vofp_status alloc(T** p, size_t count, bool grid) {
+    vofp_status alloc(T** p, size_t count, std::vector<void*>& list) {
         void* q = nullptr;
         if (cudaMalloc(&q, sizeof(T) * (count ? count : 1)) != cudaSuccess) {
             err = "cudaMalloc failed";
             return VOFP_ERR_OOM;
         }
-        (grid ? grid_allocs : allocs).push_back(q);
+        list.push_back(q);
         bytes += sizeof(T) * count;
         *p = reinterpret_cast<T*>(q);
         return VOFP_OK;
@@ -399,24 +649,33 @@ __global__ void k_rms_finish(float* scal) {
     scal[2] = rms;
     scal[3] = rms > 0.f ? 1.f / rms : 0.f;
 }
+// first channel group of the input: the seven geometry channels and the residual over its RMS
+// (the second group stays zero)
 __global__ void k_pack_input_dev(const bf16* __restrict__ geo, const float* __restrict__ r, const float* scal,
                                  bf16* __restrict__ x, long long nv) {
     const float inv = scal[3];
+    const uint4* g4 = reinterpret_cast<const uint4*>(geo);
+    uint4* x4 = reinterpret_cast<uint4*>(x);
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv; v += (long long)gridDim.x * blockDim.x) {
-#pragma unroll
-        for (int c = 0; c < 7; ++c) x[v * 16 + c] = geo[v * 8 + c];
-        x[v * 16 + 7] = __float2bfloat16(r[v] * inv);
-#pragma unroll
-        for (int c = 8; c < 16; ++c) x[v * 16 + c] = __float2bfloat16(0.f);
+        uint4 u = g4[v];
+        const __nv_bfloat16 rb = __float2bfloat16(r[v] * inv);
+        u.w = (u.w & 0x0000FFFFu) | ((uint32_t)__bfloat16_as_ushort(rb) << 16);
+        x4[v] = u;
     }
 }
 __global__ void k_head_dev(const bf16* __restrict__ h, const float* __restrict__ w, const float* __restrict__ b,
                            const float* scal, const float* __restrict__ mask, float* __restrict__ out, long long nv) {
     const float scale = scal[2];
+    const uint4* h4 = reinterpret_cast<const uint4*>(h);
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv; v += (long long)gridDim.x * blockDim.x) {
+        float f0[8], f1[8];
+        unpack8(h4[v], f0);
+        unpack8(h4[nv + v], f1);
         float s = b[0];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) s = fmaf(w[c], __bfloat162float(h[v * 16 + c]), s);
+        for (int c = 0; c < 8; ++c) s = fmaf(w[c], f0[c], s);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) s = fmaf(w[8 + c], f1[c], s);
         out[v] = mask[v] * s * scale;
     }
 }
@@ -428,16 +687,23 @@ __global__ void k_head_bwd_dev(const bf16* __restrict__ h, const float* __restri
     float lw[16], lb = 0.f, ll = 0.f;
 #pragma unroll
     for (int c = 0; c < 16; ++c) lw[c] = 0.f;
+    const uint4* h4 = reinterpret_cast<const uint4*>(h);
+    uint4* d4 = reinterpret_cast<uint4*>(dh);
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv; v += (long long)gridDim.x * blockDim.x) {
         const float e = mask[v] * (out[v] - target[v]) * inv_scale;
         ll += e * e;
         const float go = 2.f * e * inv_count;
         lb += go;
+        float f[2][8], g[2][8];
+        unpack8(h4[v], f[0]);
+        unpack8(h4[nv + v], f[1]);
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
-            lw[c] = fmaf(go, __bfloat162float(h[v * 16 + c]), lw[c]);
-            dh[v * 16 + c] = __float2bfloat16(go * w[c]);
+            lw[c] = fmaf(go, f[c >> 3][c & 7], lw[c]);
+            g[c >> 3][c & 7] = go * w[c];
         }
+        d4[v] = pack8(g[0]);
+        d4[nv + v] = pack8(g[1]);
     }
 #pragma unroll
     for (int c = 0; c < 16; ++c) sh[c][threadIdx.x] = lw[c];
@@ -454,22 +720,93 @@ __global__ void k_head_bwd_dev(const bf16* __restrict__ h, const float* __restri
     if (threadIdx.x == 17) atomicAdd(scal + 4, sh[17][0] * inv_count);
 }
 
-void conv_fwd(vofp_nn* n, const bf16* in, int cin, const Layer& l, bf16* out, int nx, int ny, int nz, bool relu,
-              bool transposed_weights, int cout_override) {
-    const int cout = transposed_weights ? cout_override : l.cout;
-    const bf16* w = transposed_weights ? l.wt : l.wb;
-    const float* bias = transposed_weights ? nullptr : l.b;
-    dim3 grid((nx + 63) / 64, ny, nz);
-    cudaStream_t st = n->stream;
-    const int r = relu ? 1 : 0;
-    switch (cout) {
-        case 16: k_conv3<16><<<grid, 128, 0, st>>>(in, cin, w, bias, out, nx, ny, nz, r); break;
-        case 32: k_conv3<32><<<grid, 128, 0, st>>>(in, cin, w, bias, out, nx, ny, nz, r); break;
-        case 48: k_conv3<48><<<grid, 128, 0, st>>>(in, cin, w, bias, out, nx, ny, nz, r); break;
-        case 64: k_conv3<64><<<grid, 128, 0, st>>>(in, cin, w, bias, out, nx, ny, nz, r); break;
-        case 96: k_conv3<96><<<grid, 128, 0, st>>>(in, cin, w, bias, out, nx, ny, nz, r); break;
-        default: break;
+// chunk-planar tensor map: five dimensions (8 channels, x, y, z, channel group), box of one
+// halo'd 10 x 18 tile plane of every group (cached per tensor and level)
+const CUtensorMap* act_map(vofp_nn* n, const bf16* ptr, int nx, int ny, int nz, int groups) {
+    const auto key = std::make_tuple((const void*)ptr, nx, ny, nz, groups);
+    auto it = n->maps.find(key);
+    if (it != n->maps.end()) return &it->second;
+    auto enc = tensor_map_encoder();
+    if (!enc) return nullptr;
+    CUtensorMap m;
+    std::memset(&m, 0, sizeof(m));
+    const cuuint64_t V = (cuuint64_t)nx * ny * nz;
+    const cuuint64_t dims[5] = {8, (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)groups};
+    const cuuint64_t strides[4] = {16, (cuuint64_t)nx * 16, (cuuint64_t)nx * ny * 16, V * 16};
+    const cuuint32_t box[5] = {8, (cuuint32_t)kBoxX, (cuuint32_t)kBoxY, 1, (cuuint32_t)groups};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    const CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16*>(ptr), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return nullptr;
+    return &(n->maps[key] = m);
+}
+
+template <int CIN, int NOUT, int R>
+vofp_status conv_umma(vofp_nn* n, const CUtensorMap* map, ConvArgs a, int nsplit) {
+    using G = ConvCfg<CIN, NOUT, R>;
+    auto kern = k_conv3_umma<CIN, NOUT, R>;
+    static int occ = -1;   // resident blocks per SM (per instantiation; one device per process)
+    if (occ < 0) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kConvThreads, G::SMEM) != cudaSuccess || occ < 1) {
+            occ = -1;
+            n->err = "tensor-core convolution: shared memory opt-in failed";
+            return VOFP_ERR_CUDA;
+        }
     }
+    // z segments: at least two waves of resident blocks, each segment re-reading a 2-plane halo
+    const long long cols = (long long)a.tiles_x * a.tiles_y * nsplit;
+    const long long slots = (long long)occ * num_sms();
+    long long nseg = std::max(1LL, std::min((long long)a.nz, (2 * slots + cols - 1) / cols));
+    a.seg = (int)((a.nz + nseg - 1) / nseg);
+    a.nseg = (a.nz + a.seg - 1) / a.seg;
+    a.err = n->derr;
+    const long long blocks = cols * a.nseg;
+    kern<<<(unsigned)blocks, kConvThreads, G::SMEM, n->stream>>>(*map, a);
+    return cudaGetLastError() == cudaSuccess ? VOFP_OK : VOFP_ERR_CUDA;
+}
+
+// One 3x3x3 convolution of `in` (cin channels) into groups [out_chunk0, ...) of `out` (cout
+// channels in blocks of nout): the layer's forward weights, or its data-gradient weights (taps
+// mirrored, channels transposed; no bias, no ReLU).
+vofp_status conv(vofp_nn* n, const bf16* in, int cin, const bf16* blob, int cout, int nout, const float* bias,
+                 bool relu, bf16* out, int out_chunk0, int nx, int ny, int nz) {
+    const CUtensorMap* map = act_map(n, in, nx, ny, nz, cin / 8);
+    if (!map) {
+        n->err = "tensor map of an activation could not be built";
+        return VOFP_ERR_CUDA;
+    }
+    ConvArgs a{};
+    a.nx = nx;
+    a.ny = ny;
+    a.nz = nz;
+    a.tiles_x = (nx + kTileX - 1) / kTileX;
+    a.tiles_y = (ny + kTileY - 1) / kTileY;
+    a.V = (long long)nx * ny * nz;
+    a.bias = bias;
+    a.relu = relu ? 1 : 0;
+    a.wblob = blob;
+    a.out = out;
+    a.out_chunk0 = out_chunk0;
+    const int ns = cout / nout;
+    switch (cin * 1000 + nout) {
+        case 16016: return conv_umma<16, 16, 4>(n, map, a, ns);
+        case 16032: return conv_umma<16, 32, 4>(n, map, a, ns);
+        case 16048: return conv_umma<16, 48, 4>(n, map, a, ns);
+        case 32016: return conv_umma<32, 16, 4>(n, map, a, ns);
+        case 32032: return conv_umma<32, 32, 4>(n, map, a, ns);
+        case 32048: return conv_umma<32, 48, 4>(n, map, a, ns);
+        case 32064: return conv_umma<32, 64, 4>(n, map, a, ns);
+        case 48016: return conv_umma<48, 16, 4>(n, map, a, ns);
+        case 64032: return conv_umma<64, 32, 4>(n, map, a, ns);
+        case 96016: return conv_umma<96, 16, 3>(n, map, a, ns);
+        default: n->err = "no tensor-core convolution for this shape"; return VOFP_ERR_INVALID_ARG;
+    }
+}
+
+vofp_status conv_fwd(vofp_nn* n, const Layer& l, const bf16* in, bf16* out, int out_chunk0, int nx, int ny, int nz) {
+    return conv(n, in, l.cin, l.blob_f, l.cout, l.nout_f, l.b, true, out, out_chunk0, nx, ny, nz);
 }
 
 void conv_wgrad(vofp_nn* n, const bf16* x, const bf16* dy, const Layer& l, int nx, int ny, int nz) {
@@ -491,43 +828,59 @@ void conv_wgrad(vofp_nn* n, const bf16* x, const bf16* dy, const Layer& l, int n
     k_bias_grad<<<dim3(gs(nv), l.cout), 256, 0, st>>>(dy, l.cout, nv, l.gb);
 }
 
-void refresh_bf16(vofp_nn* n) {
-    for (auto& l : n->L) k_weights_bf16<<<gs(l.nw()), 256, 0, n->stream>>>(l.w, l.wb, l.wt, l.cout, l.cin);
+void refresh_blobs(vofp_nn* n) {
+    for (auto& l : n->L) {
+        k_blob_fwd<<<gs(l.nw()), 256, 0, n->stream>>>(l.w, l.cout, l.cin, l.nout_f, l.blob_f);
+        k_blob_dgrad<<<gs(l.nw()), 256, 0, n->stream>>>(l.w, l.cout, l.cin, l.nout_b, l.blob_b);
+    }
 }
 
+vofp_status check_err(vofp_nn* n) {
+    if (cudaGetLastError() != cudaSuccess) {
+        n->err = "kernel launch failed";
+        return VOFP_ERR_CUDA;
+    }
+    return VOFP_OK;
+}
+
+// forward pass on stream st (the network's own stream unless a caller orders it elsewhere)
 vofp_status forward(vofp_nn* n, const float* r) {
     cudaStream_t st = n->stream;
     const int X = n->nx, Y = n->ny, Z = n->nz;
+    const int X2 = X / 2, Y2 = Y / 2, Z2 = Z / 2, X4 = X / 4, Y4 = Y / 4, Z4 = Z / 4;
     cudaMemsetAsync(n->scal, 0, sizeof(float) * 8, st);
     k_rms<<<gs(n->V1), 256, 0, st>>>(r, n->mask, n->V1, n->scal);
     k_rms_finish<<<1, 1, 0, st>>>(n->scal);
     k_pack_input_dev<<<gs(n->V1), 256, 0, st>>>(n->geo, r, n->scal, n->x0, n->V1);
     auto& L = n->L;
-    conv_fwd(n, n->x0, 16, L[0], n->a1, X, Y, Z, true, false, 0);
-    conv_fwd(n, n->a1, 16, L[1], n->s1, X, Y, Z, true, false, 0);
-    k_pool<<<gs(n->V2 * 16), 256, 0, st>>>(n->s1, n->p1, X, Y, Z, 16);
-    conv_fwd(n, n->p1, 16, L[2], n->a2, X / 2, Y / 2, Z / 2, true, false, 0);
-    conv_fwd(n, n->a2, 32, L[3], n->s2, X / 2, Y / 2, Z / 2, true, false, 0);
-    k_pool<<<gs(n->V3 * 32), 256, 0, st>>>(n->s2, n->p2, X / 2, Y / 2, Z / 2, 32);
-    conv_fwd(n, n->p2, 32, L[4], n->a3, X / 4, Y / 4, Z / 4, true, false, 0);
-    conv_fwd(n, n->a3, 64, L[5], n->b3, X / 4, Y / 4, Z / 4, true, false, 0);
-    k_upcat<<<gs(n->V2 * 96), 256, 0, st>>>(n->b3, 64, n->s2, 32, n->c2, X / 2, Y / 2, Z / 2);
-    conv_fwd(n, n->c2, 96, L[6], n->d2a, X / 2, Y / 2, Z / 2, true, false, 0);
-    conv_fwd(n, n->d2a, 32, L[7], n->d2b, X / 2, Y / 2, Z / 2, true, false, 0);
-    k_upcat<<<gs(n->V1 * 48), 256, 0, st>>>(n->d2b, 32, n->s1, 16, n->c1, X, Y, Z);
-    conv_fwd(n, n->c1, 48, L[8], n->d1a, X, Y, Z, true, false, 0);
-    conv_fwd(n, n->d1a, 16, L[9], n->d1b, X, Y, Z, true, false, 0);
+    vofp_status s;
+    if ((s = conv_fwd(n, L[0], n->x0, n->a1, 0, X, Y, Z)) || (s = conv_fwd(n, L[1], n->a1, n->c1, 4, X, Y, Z)))
+        return s;
+    k_pool<<<gs(n->V2 * 2), 256, 0, st>>>(n->s1, n->p1, X, Y, Z, 2);
+    if ((s = conv_fwd(n, L[2], n->p1, n->a2, 0, X2, Y2, Z2)) || (s = conv_fwd(n, L[3], n->a2, n->c2, 8, X2, Y2, Z2)))
+        return s;
+    k_pool<<<gs(n->V3 * 4), 256, 0, st>>>(n->s2, n->p2, X2, Y2, Z2, 4);
+    if ((s = conv_fwd(n, L[4], n->p2, n->a3, 0, X4, Y4, Z4)) || (s = conv_fwd(n, L[5], n->a3, n->b3, 0, X4, Y4, Z4)))
+        return s;
+    k_upsample<<<gs(n->V2 * 8), 256, 0, st>>>(n->b3, n->c2, X2, Y2, Z2, 8);
+    if ((s = conv_fwd(n, L[6], n->c2, n->d2a, 0, X2, Y2, Z2)) || (s = conv_fwd(n, L[7], n->d2a, n->d2b, 0, X2, Y2, Z2)))
+        return s;
+    k_upsample<<<gs(n->V1 * 4), 256, 0, st>>>(n->d2b, n->c1, X, Y, Z, 4);
+    if ((s = conv_fwd(n, L[8], n->c1, n->d1a, 0, X, Y, Z)) || (s = conv_fwd(n, L[9], n->d1a, n->d1b, 0, X, Y, Z)))
+        return s;
     k_head_dev<<<gs(n->V1), 256, 0, st>>>(n->d1b, n->hw, n->hb, n->scal, n->mask, n->out, n->V1);
-    return cudaGetLastError() == cudaSuccess ? VOFP_OK : VOFP_ERR_CUDA;
+    return check_err(n);
 }
 
 // gradient of one conv layer y = relu(conv(x)): dy (BF16, in place -> dpre), weight/bias grads,
-// and optionally the input gradient dx
-void layer_bwd(vofp_nn* n, const Layer& l, const bf16* x, const bf16* y, bf16* dy, bf16* dx, int nx, int ny, int nz) {
+// and optionally the input gradient dx (data-gradient convolution on the tensor cores)
+vofp_status layer_bwd(vofp_nn* n, const Layer& l, const bf16* x, const bf16* y, bf16* dy, bf16* dx, int nx, int ny,
+                      int nz) {
     const long long nv = (long long)nx * ny * nz;
     k_relu_bwd<<<gs(nv * l.cout), 256, 0, n->stream>>>(dy, y, nv * l.cout);
     conv_wgrad(n, x, dy, l, nx, ny, nz);
-    if (dx) conv_fwd(n, dy, l.cout, l, dx, nx, ny, nz, false, true, l.cin);
+    if (dx) return conv(n, dy, l.cout, l.blob_b, l.cin, l.nout_b, nullptr, false, dx, 0, nx, ny, nz);
+    return VOFP_OK;
 }
 
 vofp_status backward(vofp_nn* n, const float* target) {
@@ -543,25 +896,24 @@ vofp_status backward(vofp_nn* n, const float* target) {
     cudaMemsetAsync(n->ghb, 0, sizeof(float), st);
     k_head_bwd_dev<<<gs(n->V1, 128), 128, 0, st>>>(n->d1b, n->hw, n->out, target, n->mask, n->scal, n->g16a, n->ghw,
                                                    n->ghb, n->V1);
-    layer_bwd(n, L[9], n->d1a, n->d1b, n->g16a, n->g16b, X, Y, Z);           // -> d(d1a)
-    layer_bwd(n, L[8], n->c1, n->d1a, n->g16b, n->g48, X, Y, Z);             // -> d(c1)
-    cudaMemsetAsync(n->gs1, 0, sizeof(bf16) * n->V1 * 16, st);
-    k_upcat_bwd_a<<<gs(n->V2 * 32), 256, 0, st>>>(n->g48, 32, 16, n->g32a, X, Y, Z);   // -> d(d2b)
-    k_upcat_bwd_b<<<gs(n->V1 * 16), 256, 0, st>>>(n->g48, 32, 16, n->gs1, n->V1);      // skip 1
-    layer_bwd(n, L[7], n->d2a, n->d2b, n->g32a, n->g32b, X2, Y2, Z2);        // -> d(d2a)
-    layer_bwd(n, L[6], n->c2, n->d2a, n->g32b, n->g96, X2, Y2, Z2);          // -> d(c2)
-    cudaMemsetAsync(n->gs2, 0, sizeof(bf16) * n->V2 * 32, st);
-    k_upcat_bwd_a<<<gs(n->V3 * 64), 256, 0, st>>>(n->g96, 64, 32, n->g64a, X2, Y2, Z2);  // -> d(b3)
-    k_upcat_bwd_b<<<gs(n->V2 * 32), 256, 0, st>>>(n->g96, 64, 32, n->gs2, n->V2);       // skip 2
-    layer_bwd(n, L[5], n->a3, n->b3, n->g64a, n->g64b, X4, Y4, Z4);          // -> d(a3)
-    layer_bwd(n, L[4], n->p2, n->a3, n->g64b, n->gp2, X4, Y4, Z4);           // -> d(p2)
-    k_pool_bwd<<<gs(n->V2 * 32), 256, 0, st>>>(n->gp2, n->gs2, X2, Y2, Z2, 32, 1);
-    layer_bwd(n, L[3], n->a2, n->s2, n->gs2, n->g32a, X2, Y2, Z2);           // -> d(a2)
-    layer_bwd(n, L[2], n->p1, n->a2, n->g32a, n->gp1, X2, Y2, Z2);           // -> d(p1)
-    k_pool_bwd<<<gs(n->V1 * 16), 256, 0, st>>>(n->gp1, n->gs1, X, Y, Z, 16, 1);
-    layer_bwd(n, L[1], n->a1, n->s1, n->gs1, n->g16a, X, Y, Z);              // -> d(a1)
-    layer_bwd(n, L[0], n->x0, n->a1, n->g16a, nullptr, X, Y, Z);
-    return cudaGetLastError() == cudaSuccess ? VOFP_OK : VOFP_ERR_CUDA;
+    vofp_status s;
+    if ((s = layer_bwd(n, L[9], n->d1a, n->d1b, n->g16a, n->g16b, X, Y, Z))) return s;   // -> d(d1a)
+    if ((s = layer_bwd(n, L[8], n->c1, n->d1a, n->g16b, n->g48, X, Y, Z))) return s;     // -> d(c1)
+    k_upsample_bwd<<<gs(n->V2 * 4), 256, 0, st>>>(n->g48, n->g32a, X, Y, Z, 4);          // -> d(d2b)
+    k_add_groups<<<gs(n->V1 * 2), 256, 0, st>>>(n->g48 + 4 * n->V1 * 8, n->gs1, n->V1 * 2, 0);   // skip 1
+    if ((s = layer_bwd(n, L[7], n->d2a, n->d2b, n->g32a, n->g32b, X2, Y2, Z2))) return s;  // -> d(d2a)
+    if ((s = layer_bwd(n, L[6], n->c2, n->d2a, n->g32b, n->g96, X2, Y2, Z2))) return s;    // -> d(c2)
+    k_upsample_bwd<<<gs(n->V3 * 8), 256, 0, st>>>(n->g96, n->g64a, X2, Y2, Z2, 8);        // -> d(b3)
+    k_add_groups<<<gs(n->V2 * 4), 256, 0, st>>>(n->g96 + 8 * n->V2 * 8, n->gs2, n->V2 * 4, 0);   // skip 2
+    if ((s = layer_bwd(n, L[5], n->a3, n->b3, n->g64a, n->g64b, X4, Y4, Z4))) return s;    // -> d(a3)
+    if ((s = layer_bwd(n, L[4], n->p2, n->a3, n->g64b, n->gp2, X4, Y4, Z4))) return s;     // -> d(p2)
+    k_pool_bwd<<<gs(n->V2 * 4), 256, 0, st>>>(n->gp2, n->gs2, X2, Y2, Z2, 4, 1);
+    if ((s = layer_bwd(n, L[3], n->a2, n->s2, n->gs2, n->g32a, X2, Y2, Z2))) return s;     // -> d(a2)
+    if ((s = layer_bwd(n, L[2], n->p1, n->a2, n->g32a, n->gp1, X2, Y2, Z2))) return s;     // -> d(p1)
+    k_pool_bwd<<<gs(n->V1 * 2), 256, 0, st>>>(n->gp1, n->gs1, X, Y, Z, 2, 1);
+    if ((s = layer_bwd(n, L[1], n->a1, n->s1, n->gs1, n->g16a, X, Y, Z))) return s;        // -> d(a1)
+    if ((s = layer_bwd(n, L[0], n->x0, n->a1, n->g16a, nullptr, X, Y, Z))) return s;
+    return check_err(n);
 }
 
 void adam(vofp_nn* n, float lr) {
@@ -574,7 +926,12 @@ void adam(vofp_nn* n, float lr) {
     }
     k_adam<<<1, 32, 0, n->stream>>>(n->hw, n->ghw, n->mhw, n->vhw, 16, lr_t, b1, b2, eps);
     k_adam<<<1, 32, 0, n->stream>>>(n->hb, n->ghb, n->mhb, n->vhb, 1, lr_t, b1, b2, eps);
-    refresh_bf16(n);
+    refresh_blobs(n);
+}
+
+void free_list(std::vector<void*>& list) {
+    for (void* p : list) cudaFree(p);
+    list.clear();
 }
 
 vofp_status ensure_grid(vofp_nn* n, int nx, int ny, int nz) {
@@ -584,8 +941,11 @@ vofp_status ensure_grid(vofp_nn* n, int nx, int ny, int nz) {
     }
     if (n->bound && n->nx == nx && n->ny == ny && n->nz == nz) return VOFP_OK;
     cudaStreamSynchronize(n->stream);
-    for (void* p : n->grid_allocs) cudaFree(p);
-    n->grid_allocs.clear();
+    free_list(n->grid_allocs);
+    free_list(n->grad_allocs);
+    n->maps.clear();
+    n->bound = false;
+    n->grads_ready = false;
     n->nx = nx;
     n->ny = ny;
     n->nz = nz;
@@ -593,24 +953,36 @@ vofp_status ensure_grid(vofp_nn* n, int nx, int ny, int nz) {
     n->V2 = n->V1 / 8;
     n->V3 = n->V1 / 64;
     const long long V1 = n->V1, V2 = n->V2, V3 = n->V3;
+    auto& g = n->grid_allocs;
     vofp_status s;
-    if ((s = n->alloc(&n->geo, V1 * 8, true)) || (s = n->alloc(&n->x0, V1 * 16, true)) ||
-        (s = n->alloc(&n->a1, V1 * 16, true)) || (s = n->alloc(&n->s1, V1 * 16, true)) ||
-        (s = n->alloc(&n->p1, V2 * 16, true)) || (s = n->alloc(&n->a2, V2 * 32, true)) ||
-        (s = n->alloc(&n->s2, V2 * 32, true)) || (s = n->alloc(&n->p2, V3 * 32, true)) ||
-        (s = n->alloc(&n->a3, V3 * 64, true)) || (s = n->alloc(&n->b3, V3 * 64, true)) ||
-        (s = n->alloc(&n->c2, V2 * 96, true)) || (s = n->alloc(&n->d2a, V2 * 32, true)) ||
-        (s = n->alloc(&n->d2b, V2 * 32, true)) || (s = n->alloc(&n->c1, V1 * 48, true)) ||
-        (s = n->alloc(&n->d1a, V1 * 16, true)) || (s = n->alloc(&n->d1b, V1 * 16, true)) ||
-        (s = n->alloc(&n->g16a, V1 * 16, true)) || (s = n->alloc(&n->g16b, V1 * 16, true)) ||
-        (s = n->alloc(&n->g48, V1 * 48, true)) || (s = n->alloc(&n->g32a, V2 * 32, true)) ||
-        (s = n->alloc(&n->g32b, V2 * 32, true)) || (s = n->alloc(&n->g96, V2 * 96, true)) ||
-        (s = n->alloc(&n->g64a, V3 * 64, true)) || (s = n->alloc(&n->g64b, V3 * 64, true)) ||
-        (s = n->alloc(&n->gs1, V1 * 16, true)) || (s = n->alloc(&n->gs2, V2 * 32, true)) ||
-        (s = n->alloc(&n->gp1, V2 * 16, true)) || (s = n->alloc(&n->gp2, V3 * 32, true)) ||
-        (s = n->alloc(&n->mask, V1, true)) || (s = n->alloc(&n->out, V1, true)))
+    if ((s = n->alloc(&n->geo, V1 * 8, g)) || (s = n->alloc(&n->x0, V1 * 16, g)) || (s = n->alloc(&n->a1, V1 * 16, g)) ||
+        (s = n->alloc(&n->c1, V1 * 48, g)) || (s = n->alloc(&n->p1, V2 * 16, g)) || (s = n->alloc(&n->a2, V2 * 32, g)) ||
+        (s = n->alloc(&n->c2, V2 * 96, g)) || (s = n->alloc(&n->p2, V3 * 32, g)) || (s = n->alloc(&n->a3, V3 * 64, g)) ||
+        (s = n->alloc(&n->b3, V3 * 64, g)) || (s = n->alloc(&n->d2a, V2 * 32, g)) || (s = n->alloc(&n->d2b, V2 * 32, g)) ||
+        (s = n->alloc(&n->d1a, V1 * 16, g)) || (s = n->alloc(&n->d1b, V1 * 16, g)) || (s = n->alloc(&n->mask, V1, g)) ||
+        (s = n->alloc(&n->out, V1, g)))
         return s;
+    n->s1 = n->c1 + 4 * V1 * 8;   // the skip tensors are the last groups of the concatenations
+    n->s2 = n->c2 + 8 * V2 * 8;
+    // the input's second channel group is always zero (seven geometry channels and the residual)
+    if (cudaMemsetAsync(n->x0 + V1 * 8, 0, sizeof(bf16) * V1 * 8, n->stream) != cudaSuccess) return VOFP_ERR_CUDA;
     n->bound = true;
+    return VOFP_OK;
+}
+
+vofp_status ensure_grads(vofp_nn* n) {
+    if (n->grads_ready) return VOFP_OK;
+    const long long V1 = n->V1, V2 = n->V2, V3 = n->V3;
+    auto& g = n->grad_allocs;
+    vofp_status s;
+    if ((s = n->alloc(&n->g16a, V1 * 16, g)) || (s = n->alloc(&n->g16b, V1 * 16, g)) ||
+        (s = n->alloc(&n->g48, V1 * 48, g)) || (s = n->alloc(&n->g32a, V2 * 32, g)) ||
+        (s = n->alloc(&n->g32b, V2 * 32, g)) || (s = n->alloc(&n->g96, V2 * 96, g)) ||
+        (s = n->alloc(&n->g64a, V3 * 64, g)) || (s = n->alloc(&n->g64b, V3 * 64, g)) ||
+        (s = n->alloc(&n->gs1, V1 * 16, g)) || (s = n->alloc(&n->gs2, V2 * 32, g)) ||
+        (s = n->alloc(&n->gp1, V2 * 16, g)) || (s = n->alloc(&n->gp2, V3 * 32, g)))
+        return s;
+    n->grads_ready = true;
     return VOFP_OK;
 }
 
@@ -623,6 +995,20 @@ std::vector<std::pair<float*, long long>> param_list(vofp_nn* n, bool grads) {
     v.push_back({grads ? n->ghw : n->hw, 16});
     v.push_back({grads ? n->ghb : n->hb, 1});
     return v;
+}
+
+// the convolutions' device flag: a bounded wait that ran out is an error of the whole pass
+vofp_status read_err(vofp_nn* n) {
+    int h = 0;
+    if (cudaMemcpyAsync(&h, n->derr, sizeof(int), cudaMemcpyDeviceToHost, n->stream) != cudaSuccess ||
+        cudaStreamSynchronize(n->stream) != cudaSuccess)
+        return VOFP_ERR_CUDA;
+    if (h) {
+        n->err = "a tensor-core convolution's bounded wait ran out";
+        cudaMemsetAsync(n->derr, 0, sizeof(int), n->stream);
+        return VOFP_ERR_DEVICE_TIMEOUT;
+    }
+    return VOFP_OK;
 }
 
 }  // namespace
@@ -648,16 +1034,22 @@ vofp_status vofp_nn_create(vofp_nn** out, unsigned long long seed, vofp_stream s
     n->stream = reinterpret_cast<cudaStream_t>(stream);
     std::mt19937_64 rng(seed);
     vofp_status s;
+    if ((s = n->alloc(&n->derr, 1, n->allocs)) || cudaMemset(n->derr, 0, sizeof(int)) != cudaSuccess) {
+        vofp_nn_destroy(n);
+        return s ? s : VOFP_ERR_CUDA;
+    }
     for (int i = 0; i < 10; ++i) {
         Layer l;
         l.cin = kLayers[i][0];
         l.cout = kLayers[i][1];
         l.cin_real = kLayers[i][2];
-        if ((s = n->alloc(&l.w, l.nw(), false)) || (s = n->alloc(&l.b, l.cout, false)) ||
-            (s = n->alloc(&l.gw, l.nw(), false)) || (s = n->alloc(&l.gb, l.cout, false)) ||
-            (s = n->alloc(&l.mw, l.nw(), false)) || (s = n->alloc(&l.vw, l.nw(), false)) ||
-            (s = n->alloc(&l.mb, l.cout, false)) || (s = n->alloc(&l.vb, l.cout, false)) ||
-            (s = n->alloc(&l.wb, l.nw(), false)) || (s = n->alloc(&l.wt, l.nw(), false))) {
+        l.nout_f = kLayers[i][3];
+        l.nout_b = kLayers[i][4];
+        auto& A = n->allocs;
+        if ((s = n->alloc(&l.w, l.nw(), A)) || (s = n->alloc(&l.b, l.cout, A)) || (s = n->alloc(&l.gw, l.nw(), A)) ||
+            (s = n->alloc(&l.gb, l.cout, A)) || (s = n->alloc(&l.mw, l.nw(), A)) || (s = n->alloc(&l.vw, l.nw(), A)) ||
+            (s = n->alloc(&l.mb, l.cout, A)) || (s = n->alloc(&l.vb, l.cout, A)) ||
+            (s = n->alloc(&l.blob_f, l.nw(), A)) || (s = n->alloc(&l.blob_b, l.nw(), A))) {
             vofp_nn_destroy(n);
             return s;
         }
@@ -675,9 +1067,10 @@ vofp_status vofp_nn_create(vofp_nn** out, unsigned long long seed, vofp_stream s
         n->nparams += l.nw() + l.cout;
         n->L.push_back(l);
     }
-    if ((s = n->alloc(&n->hw, 16, false)) || (s = n->alloc(&n->hb, 1, false)) || (s = n->alloc(&n->ghw, 16, false)) ||
-        (s = n->alloc(&n->ghb, 1, false)) || (s = n->alloc(&n->mhw, 16, false)) || (s = n->alloc(&n->vhw, 16, false)) ||
-        (s = n->alloc(&n->mhb, 1, false)) || (s = n->alloc(&n->vhb, 1, false)) || (s = n->alloc(&n->scal, 8, false))) {
+    auto& A = n->allocs;
+    if ((s = n->alloc(&n->hw, 16, A)) || (s = n->alloc(&n->hb, 1, A)) || (s = n->alloc(&n->ghw, 16, A)) ||
+        (s = n->alloc(&n->ghb, 1, A)) || (s = n->alloc(&n->mhw, 16, A)) || (s = n->alloc(&n->vhw, 16, A)) ||
+        (s = n->alloc(&n->mhb, 1, A)) || (s = n->alloc(&n->vhb, 1, A)) || (s = n->alloc(&n->scal, 8, A))) {
         vofp_nn_destroy(n);
         return s;
     }
@@ -691,7 +1084,7 @@ vofp_status vofp_nn_create(vofp_nn** out, unsigned long long seed, vofp_stream s
     cudaMemset(n->mhb, 0, sizeof(float));
     cudaMemset(n->vhb, 0, sizeof(float));
     n->nparams += 17;
-    refresh_bf16(n);
+    refresh_blobs(n);
     if (cudaStreamSynchronize(n->stream) != cudaSuccess) {
         vofp_nn_destroy(n);
         return VOFP_ERR_CUDA;
@@ -703,8 +1096,9 @@ vofp_status vofp_nn_create(vofp_nn** out, unsigned long long seed, vofp_stream s
 void vofp_nn_destroy(vofp_nn* n) {
     if (!n) return;
     cudaStreamSynchronize(n->stream);
-    for (void* p : n->grid_allocs) cudaFree(p);
-    for (void* p : n->allocs) cudaFree(p);
+    free_list(n->grad_allocs);
+    free_list(n->grid_allocs);
+    free_list(n->allocs);
     delete n;
 }
 
@@ -737,7 +1131,7 @@ vofp_status vofp_nn_set_params(vofp_nn* n, const float* host, long long count) {
             return VOFP_ERR_CUDA;
         off += pr.second;
     }
-    refresh_bf16(n);
+    refresh_blobs(n);
     return cudaStreamSynchronize(n->stream) == cudaSuccess ? VOFP_OK : VOFP_ERR_CUDA;
 }
 
@@ -792,13 +1186,13 @@ vofp_status vofp_nn_train_step(vofp_nn* n, const float* r, const float* target, 
         return VOFP_ERR_NOT_BUILT;
     }
     vofp_status s;
-    if ((s = forward(n, r)) || (s = backward(n, target))) return s;
+    if ((s = ensure_grads(n)) || (s = forward(n, r)) || (s = backward(n, target))) return s;
     if (update) adam(n, lr);
     if (loss) {
         if (cudaMemcpyAsync(loss, n->scal + 4, sizeof(float), cudaMemcpyDeviceToHost, n->stream) != cudaSuccess)
             return VOFP_ERR_CUDA;
-        if (cudaStreamSynchronize(n->stream) != cudaSuccess) return VOFP_ERR_CUDA;
     }
+    if ((s = read_err(n))) return s;
     return cudaGetLastError() == cudaSuccess ? VOFP_OK : VOFP_ERR_CUDA;
 }
 

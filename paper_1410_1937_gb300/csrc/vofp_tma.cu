@@ -9,14 +9,9 @@
 #include "vofp_tma.cuh"
 
 namespace vofp {
-namespace {
 
-// TMA stencil configurations: FP32 two cells per thread (64 x 8 tiles), FP64 one (32 x 8); both
-// four stages, three resident blocks per SM.  VOFP_TMA_FP32_CPT=1 selects the 32 x 8 FP32 kernel
-// with six stages (four blocks per SM).
-constexpr int kTmaStages64 = 4;
-
-// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime (null when the
+// driver does not provide it)
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static std::once_flag once;
@@ -30,6 +25,13 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     });
     return fn;
 }
+
+namespace {
+
+// TMA stencil configurations: FP32 two cells per thread (64 x 8 tiles), FP64 one (32 x 8); both
+// four stages, three resident blocks per SM.  VOFP_TMA_FP32_CPT=1 selects the 32 x 8 FP32 kernel
+// with six stages (four blocks per SM).
+constexpr int kTmaStages64 = 4;
 
 // 3-D tensor map of one nx x ny x nz array with a box of bw x bh cells of one plane (cached).
 // L2 promotion 64 B: the boxes' rows are 128-160 B, and wider promotion pulls neighbouring tiles'
