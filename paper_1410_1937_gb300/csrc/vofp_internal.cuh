@@ -113,7 +113,8 @@ struct vofp_ctx {
     // Krylov workspace
     double *xt = nullptr, *r = nullptr, *p0 = nullptr, *p1 = nullptr, *q = nullptr, *bt = nullptr;
     float *rf = nullptr, *pf0 = nullptr, *pf1 = nullptr, *qf = nullptr, *xf = nullptr;
-    float *zf = nullptr, *qf2 = nullptr;   // flexible CG (learned preconditioner)
+    float* qf2 = nullptr;             // flexible CG (learned preconditioner): second q buffer
+    char* fcg = nullptr;              // flexible CG scalars (device)
     double* partials = nullptr;       // block partial sums
     unsigned int* counters = nullptr; // last-block tickets
     vofp::CgScalars* sc = nullptr;
@@ -338,6 +339,12 @@ inline void launch_dep(vofp_ctx* c, bool pdl, void (*k)(KArgs...), dim3 g, dim3 
 namespace nn {
 long long bound_cells(const vofp_nn* n);
 cudaStream_t stream_of(const vofp_nn* n);
+// one forward pass of the bound network on stream st (r: scaled residual, FP32 cells); the result
+// stays in the network's output buffer, output(n)
+vofp_status forward_on(vofp_nn* n, cudaStream_t st, const float* r);
+float* output(vofp_nn* n);
+int forward_kernels(const vofp_nn* n);           // kernels one forward pass launches
+vofp_status read_device_error(vofp_nn* n);       // VOFP_ERR_DEVICE_TIMEOUT if a bounded wait ran out
 }  // namespace nn
 
 inline int ceil_div(long long a, long long b) { return int((a + b - 1) / b); }

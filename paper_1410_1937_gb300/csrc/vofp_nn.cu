@@ -47,36 +47,55 @@ __host__ __device__ __forceinline__ long long aidx(long long v, int c, long long
 }
 
 // ---- 3x3x3 convolution on the tensor cores ---------------------------------------------------
-// Tile of one block: 8 voxels along x (one core-matrix row group) by 16 along y, one plane; its
-// input box is 10 x 18 voxels (one-voxel halo) of every input channel group.
+// Tile of one block: 8 voxels along x (one core-matrix row group) by 16 along y (M = 128 rows,
+// row m = voxel (m % 8, m / 8)); its input box is 10 x 18 voxels (one-voxel halo) of every input
+// channel group.  The three z taps are columns of one instruction: input plane p times the
+// weights of the three z taps (N = 3 NOUT) gives in one MMA the contributions of p to output
+// planes p+1, p and p-1, which sit in consecutive TMEM column blocks (block j: z tap j, output
+// p+1-j).  Output plane o therefore owns columns NOUT (S + 1 - (o - z0)) of a segment of S planes
+// starting at z0 (descending in o), with one block above and two below for the contributions that
+// fall outside the segment.  Each input plane is read by 9 taps x (Cin/16) MMAs and released.
 constexpr int kTileX = 8, kTileY = 16, kBoxX = kTileX + 2, kBoxY = kTileY + 2;
 constexpr int kGroupBytes = kBoxX * kBoxY * 16;   // one channel group of one halo'd plane
 constexpr int kConvThreads = 192;                 // warp 0 copies, warp 1 issues MMAs, 2..5 store
 
 __host__ __device__ constexpr size_t al128(size_t b) { return (b + 127) / 128 * 128; }
+__host__ __device__ constexpr uint32_t pow2_at_least(uint32_t v) {
+    return v <= 32 ? 32 : (v <= 64 ? 64 : (v <= 128 ? 128 : (v <= 256 ? 256 : 512)));
+}
 
 template <int CIN, int NOUT, int R>
 struct ConvCfg {
-    static_assert(CIN % 16 == 0 && NOUT % 16 == 0 && NOUT <= 64, "shape");
+    static_assert(CIN % 16 == 0 && NOUT % 16 == 0 && 3 * NOUT <= 256, "shape");
     static constexpr int KCH = CIN / 8;                               // input channel groups
+    // output planes per segment: the accumulators of S + 4 planes (S outputs and the blocks that
+    // fall outside the segment) in TMEM; two blocks per SM for 16 output channels, one otherwise
+    static constexpr int S = NOUT == 16 ? 12 : (NOUT == 32 ? 12 : (NOUT == 48 ? 6 : 4));
+    static constexpr uint32_t TCOLS = pow2_at_least((uint32_t)NOUT * (S + 4));
     static constexpr uint32_t PLANE = (uint32_t)KCH * kGroupBytes;    // bytes of one ring slot
     static constexpr uint32_t WBYTES = 27u * CIN * NOUT * 2u;         // this block's weights
-    static constexpr uint32_t TCOLS = 2 * NOUT <= 32 ? 32 : (2 * NOUT <= 64 ? 64 : 128);
+    static constexpr uint32_t WTAP = (uint32_t)KCH * 3 * NOUT * 16;   // weights of one (y, x) tap
     static constexpr size_t oW = 0;
     static constexpr size_t oRing = al128(WBYTES);
     static constexpr size_t oBar = oRing + al128((size_t)R * PLANE);
-    static constexpr size_t oBias = oBar + 8 * (2 * R + 5) + 8;
-    static constexpr size_t SMEM = al128(oBias + 4 * NOUT) + 128;     // + alignment slack
+    static constexpr size_t oBias = oBar + 8 * (2 * R + S + 1) + 8;
+    static constexpr size_t SMEM_USED = al128(oBias + 4 * NOUT) + 128;   // + alignment slack
+    // requested shared memory: at least enough to keep the blocks per SM within what tensor memory
+    // holds (512 columns per SM), so that no block waits inside its TMEM allocation
+    static constexpr size_t SMEM = TCOLS == 512 ? (SMEM_USED > 120 * 1024 ? SMEM_USED : 120 * 1024)
+                                 : TCOLS == 256 ? (SMEM_USED > 80 * 1024 ? SMEM_USED : 80 * 1024) : SMEM_USED;
+    static_assert(SMEM <= 232448, "shared memory per block");
+    static_assert(TCOLS <= 512, "tensor memory");
 };
 
 struct ConvArgs {
     int nx, ny, nz;
     int tiles_x, tiles_y;
-    int seg, nseg;            // planes per z segment, segments
+    int seg, nseg;            // planes per z segment (<= S), segments
     long long V;              // voxels of the level
     const float* bias;        // per output channel (null: none)
     int relu;
-    const bf16* wblob;        // [split][27][CIN/8][NOUT][8]
+    const bf16* wblob;        // [split][9 (y, x) taps][CIN/8][3 z taps x NOUT][8]
     bf16* out;                // chunk-planar output tensor
     int out_chunk0;           // first channel group of this convolution's outputs in `out`
     int* err;                 // set to 1 when a bounded wait runs out
@@ -88,15 +107,15 @@ template <int CIN, int NOUT, int R>
 __global__ void __launch_bounds__(kConvThreads, 1)
 k_conv3_umma(const __grid_constant__ CUtensorMap in_map, const ConvArgs a) {
     using G = ConvCfg<CIN, NOUT, R>;
+    constexpr int S = G::S;
     extern __shared__ unsigned char smraw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 127) & ~uintptr_t(127));
     unsigned char* wsm = sm + G::oW;
     unsigned char* ring = sm + G::oRing;
     uint64_t* full = reinterpret_cast<uint64_t*>(sm + G::oBar);
     uint64_t* empty = full + R;
-    uint64_t* accf = empty + R;
-    uint64_t* acce = accf + 2;
-    uint64_t* wbar = acce + 2;
+    uint64_t* accf = empty + R;   // one per output plane of the segment
+    uint64_t* wbar = accf + S;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(wbar + 1);
     float* bsm = reinterpret_cast<float*>(sm + G::oBias);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -108,17 +127,14 @@ k_conv3_umma(const __grid_constant__ CUtensorMap in_map, const ConvArgs a) {
     const int sg = b % a.nseg, split = b / a.nseg;
     const int x0 = tx * kTileX, y0 = ty * kTileY;
     const int z0 = sg * a.seg;
-    const int nout = min(a.nz, z0 + a.seg) - z0;   // output planes of this block (>= 1)
+    const int nout = min(a.nz, z0 + a.seg) - z0;   // output planes of this block (1 .. S)
     const int nin = nout + 2;                       // input planes z0-1 .. z0+nout
     if (tid == 0) {
         for (int i = 0; i < R; ++i) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
         }
-        mbar_init(&accf[0], 1);
-        mbar_init(&accf[1], 1);
-        mbar_init(&acce[0], 128);
-        mbar_init(&acce[1], 128);
+        for (int i = 0; i < S; ++i) mbar_init(&accf[i], 1);
         mbar_init(wbar, 1);
         fence_mbar_init();
     }
@@ -154,47 +170,42 @@ k_conv3_umma(const __grid_constant__ CUtensorMap in_map, const ConvArgs a) {
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t idesc = umma::idesc_bf16(128, NOUT);
+            constexpr uint32_t id1 = umma::idesc_bf16(128, NOUT), id2 = umma::idesc_bf16(128, 2 * NOUT),
+                               id3 = umma::idesc_bf16(128, 3 * NOUT);
             const uint32_t wbase = umma::saddr(wsm), rbase = umma::saddr(ring);
             if (!mbar_wait_bounded(wbar, 0)) fail = true;
-            int waited = 0;   // input planes whose copy has been waited for
-            for (int lz = 0; lz < nout && !fail; ++lz) {
-                // output plane z0 + lz reads local input planes lz, lz+1, lz+2
-                while (waited < lz + 3) {
-                    if (!mbar_wait_bounded(&full[waited % R], (uint32_t)(waited / R) & 1u)) {
-                        fail = true;
-                        break;
-                    }
-                    ++waited;
-                }
-                if (fail) break;
-                const int buf = lz & 1;
-                if (lz >= 2 && !mbar_wait_bounded(&acce[buf], (uint32_t)((lz >> 1) - 1) & 1u)) {
+            for (int lp = 0; lp < nin && !fail; ++lp) {
+                const int s = lp % R;
+                if (!mbar_wait_bounded(&full[s], (uint32_t)(lp / R) & 1u)) {
                     fail = true;
                     break;
                 }
                 umma::fence_after_sync();
-                const uint32_t d = tmem + (uint32_t)buf * (G::TCOLS / 2);
-                uint32_t acc = 0;
+                // input plane z0-1+lp: block j of the result is output plane z0+lp-j
+                const uint32_t d = tmem + (uint32_t)(NOUT * (S + 1 - lp));
+                const uint32_t slot = rbase + (uint32_t)s * G::PLANE;
 #pragma unroll 1
-                for (int dz = 0; dz < 3; ++dz) {
-                    const uint32_t slot = rbase + (uint32_t)((lz + dz) % R) * G::PLANE;
-#pragma unroll 1
-                    for (int t = 0; t < 9; ++t) {
-                        const int dy = t / 3, dx = t % 3;
-                        const uint32_t abase = slot + (uint32_t)(dy * kBoxX + dx) * 16u;
-                        const uint32_t bbase = wbase + (uint32_t)(dz * 9 + t) * (uint32_t)(CIN * NOUT * 2);
+                for (int t = 0; t < 9; ++t) {
+                    const int dy = t / 3, dx = t % 3;
+                    const uint32_t abase = slot + (uint32_t)(dy * kBoxX + dx) * 16u;
+                    const uint32_t bbase = wbase + (uint32_t)t * G::WTAP;
 #pragma unroll
-                        for (int ks = 0; ks < CIN / 16; ++ks) {
-                            const uint64_t ad = umma::smem_desc(abase + 2u * ks * kGroupBytes, kGroupBytes, kBoxX * 16);
-                            const uint64_t bd = umma::smem_desc(bbase + 2u * ks * NOUT * 16, NOUT * 16, 128);
-                            umma::mma_bf16(d, ad, bd, idesc, acc);
-                            acc = 1;
+                    for (int ks = 0; ks < CIN / 16; ++ks) {
+                        const uint64_t ad = umma::smem_desc(abase + 2u * ks * kGroupBytes, kGroupBytes, kBoxX * 16);
+                        const uint32_t bk = bbase + 2u * ks * (3 * NOUT * 16);
+                        if (t == 0 && ks == 0) {
+                            // block 0 starts output plane z0+lp afresh; blocks 1, 2 add to planes
+                            // that earlier input planes began
+                            umma::mma_bf16(d, ad, umma::smem_desc(bk, 3 * NOUT * 16, 128), id1, 0u);
+                            umma::mma_bf16(d + NOUT, ad, umma::smem_desc(bk + (NOUT / 8) * 128, 3 * NOUT * 16, 128),
+                                           id2, 1u);
+                        } else {
+                            umma::mma_bf16(d, ad, umma::smem_desc(bk, 3 * NOUT * 16, 128), id3, 1u);
                         }
                     }
                 }
-                umma::commit(&accf[buf]);
-                umma::commit(&empty[lz % R]);   // local plane lz (input z0+lz-1) is read for the last time
+                umma::commit(&empty[s]);                     // the plane's slot may be refilled
+                if (lp >= 2) umma::commit(&accf[lp - 2]);    // output plane z0+lp-2 is complete
             }
         }
     } else {
@@ -204,24 +215,22 @@ k_conv3_umma(const __grid_constant__ CUtensorMap in_map, const ConvArgs a) {
         const int xi = x0 + (m & 7), yi = y0 + (m >> 3);
         const bool inside = xi < a.nx && yi < a.ny;
         for (int lz = 0; lz < nout; ++lz) {
-            const int buf = lz & 1;
-            if (!fail && !mbar_wait_bounded(&accf[buf], (uint32_t)(lz >> 1) & 1u)) fail = true;
+            if (!fail && !mbar_wait_bounded(&accf[lz], 0u)) fail = true;
             if (__any_sync(0xffffffffu, fail)) {
                 fail = true;
                 break;
             }
             umma::fence_after_sync();
+            const uint32_t col = (uint32_t)(NOUT * (S + 1 - lz));
             float v[NOUT];
 #pragma unroll
             for (int c0 = 0; c0 < NOUT; c0 += 16) {
                 uint32_t r[16];
-                umma::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * (G::TCOLS / 2) + c0, r);
+                umma::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + col + c0, r);
                 umma::tmem_wait_ld();
 #pragma unroll
                 for (int j = 0; j < 16; ++j) v[c0 + j] = __uint_as_float(r[j]);
             }
-            umma::fence_before_sync();
-            umma::mbar_arrive(&acce[buf]);
             if (inside) {
                 const long long vox = ((long long)(z0 + lz) * a.ny + yi) * a.nx + xi;
 #pragma unroll
@@ -254,39 +263,42 @@ k_conv3_umma(const __grid_constant__ CUtensorMap in_map, const ConvArgs a) {
 }
 
 // ---- weight blobs for the tensor-core convolution ---------------------------------------------
-// forward: blob[s][tap][k][n][e] = W[tap][s nout + n][8 k + e]  (W[27][cout][cin], FP32 masters)
+// forward: blob[s][t][k][j nout + n][e] = W[9 j + t][s nout + n][8 k + e]  (W[27][cout][cin], FP32
+// masters; t = (y, x) tap, j = z tap)
 __global__ void k_blob_fwd(const float* __restrict__ w, int cout, int cin, int nout, bf16* __restrict__ blob) {
     const long long total = 27LL * cout * cin;
     const int kch = cin / 8;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        long long t = i;
-        const int e = int(t & 7);
-        t >>= 3;
-        const int n = int(t % nout);
-        t /= nout;
-        const int k = int(t % kch);
-        t /= kch;
-        const int tap = int(t % 27);
-        const int s = int(t / 27);
-        blob[i] = __float2bfloat16(w[((long long)tap * cout + s * nout + n) * cin + 8 * k + e]);
+        long long q = i;
+        const int e = int(q & 7);
+        q >>= 3;
+        const int jn = int(q % (3 * nout));
+        q /= 3 * nout;
+        const int k = int(q % kch);
+        q /= kch;
+        const int t = int(q % 9);
+        const int s = int(q / 9);
+        const int j = jn / nout, n = jn % nout;
+        blob[i] = __float2bfloat16(w[((long long)(9 * j + t) * cout + s * nout + n) * cin + 8 * k + e]);
     }
 }
 // data gradient: the layer run backwards (inputs: its cout channels; outputs: its cin channels;
-// taps mirrored): blob[s][tap][k][n][e] = W[26 - tap][8 k + e][s nout + n]
+// taps mirrored): blob[s][t][k][j nout + n][e] = W[26 - (9 j + t)][8 k + e][s nout + n]
 __global__ void k_blob_dgrad(const float* __restrict__ w, int cout, int cin, int nout, bf16* __restrict__ blob) {
     const long long total = 27LL * cout * cin;
     const int kch = cout / 8;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        long long t = i;
-        const int e = int(t & 7);
-        t >>= 3;
-        const int n = int(t % nout);
-        t /= nout;
-        const int k = int(t % kch);
-        t /= kch;
-        const int tap = int(t % 27);
-        const int s = int(t / 27);
-        blob[i] = __float2bfloat16(w[((long long)(26 - tap) * cout + 8 * k + e) * cin + s * nout + n]);
+        long long q = i;
+        const int e = int(q & 7);
+        q >>= 3;
+        const int jn = int(q % (3 * nout));
+        q /= 3 * nout;
+        const int k = int(q % kch);
+        q /= kch;
+        const int t = int(q % 9);
+        const int s = int(q / 9);
+        const int j = jn / nout, n = jn % nout;
+        blob[i] = __float2bfloat16(w[((long long)(26 - (9 * j + t)) * cout + 8 * k + e) * cin + s * nout + n]);
     }
 }
 
@@ -755,11 +767,11 @@ vofp_status conv_umma(vofp_nn* n, const CUtensorMap* map, ConvArgs a, int nsplit
             return VOFP_ERR_CUDA;
         }
     }
-    // z segments: at least two waves of resident blocks, each segment re-reading a 2-plane halo
+    // z segments of at most S planes (the accumulators one block keeps in tensor memory), equal
+    // in length; each re-reads a 2-plane halo
     const long long cols = (long long)a.tiles_x * a.tiles_y * nsplit;
-    const long long slots = (long long)occ * num_sms();
-    long long nseg = std::max(1LL, std::min((long long)a.nz, (2 * slots + cols - 1) / cols));
-    a.seg = (int)((a.nz + nseg - 1) / nseg);
+    const int nseg = (a.nz + G::S - 1) / G::S;
+    a.seg = (a.nz + nseg - 1) / nseg;
     a.nseg = (a.nz + a.seg - 1) / a.seg;
     a.err = n->derr;
     const long long blocks = cols * a.nseg;
@@ -800,7 +812,7 @@ vofp_status conv(vofp_nn* n, const bf16* in, int cin, const bf16* blob, int cout
         case 32064: return conv_umma<32, 64, 4>(n, map, a, ns);
         case 48016: return conv_umma<48, 16, 4>(n, map, a, ns);
         case 64032: return conv_umma<64, 32, 4>(n, map, a, ns);
-        case 96016: return conv_umma<96, 16, 3>(n, map, a, ns);
+        case 96016: return conv_umma<96, 16, 4>(n, map, a, ns);
         default: n->err = "no tensor-core convolution for this shape"; return VOFP_ERR_INVALID_ARG;
     }
 }
@@ -1021,6 +1033,17 @@ namespace vofp {
 namespace nn {
 long long bound_cells(const vofp_nn* n) { return n && n->bound ? n->V1 : -1; }
 cudaStream_t stream_of(const vofp_nn* n) { return n ? n->stream : nullptr; }
+vofp_status forward_on(vofp_nn* n, cudaStream_t st, const float* r) {
+    const cudaStream_t own = n->stream;
+    n->stream = st;
+    const vofp_status s = forward(n, r);
+    n->stream = own;
+    return s;
+}
+float* output(vofp_nn* n) { return n->out; }
+// rms, its finish, input packing, ten convolutions, two poolings, two upsamplings, output layer
+int forward_kernels(const vofp_nn*) { return 18; }
+vofp_status read_device_error(vofp_nn* n) { return read_err(n); }
 }  // namespace nn
 }  // namespace vofp
 

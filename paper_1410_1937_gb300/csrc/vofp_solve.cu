@@ -375,51 +375,151 @@ dim3 rows_grid(const vofp_ctx* c, int threads) {
 }
 
 // ---- flexible CG with the learned preconditioner -----------------------------------------
-// up to three dot products of FP32 vectors over cells outside `bits`, accumulated with the
-// compensated (Dot2) scheme and reduced in FP64 into out[0..2]
+// FCG(1) (Notay 2000): each direction is made A-orthogonal to the previous one, which keeps CG's
+// short recurrence valid for a preconditioner that changes from one application to the next.
+// Every scalar lives in device memory; the kernels of one iteration read what the previous one
+// wrote, so the inner loop runs as a CUDA graph with no host round trip.
+constexpr int kFcgHist = 64;
+struct FcgScalars {
+    double zq;               // z . q_prev
+    double pq, pr;           // p . q and p . r of the current iteration
+    double pq_prev;
+    double rr, rr0;          // r . r now and at the start of the inner solve
+    double target2;          // the inner solve stops at rr <= target2 rr0
+    double alpha, beta;
+    long long k;             // iterations of the current inner solve
+    long long total;         // iterations of the whole solve
+    long long max_total;
+    int window;              // stagnation window (iterations)
+    int done;                // inner solve finished
+    int fell_back;           // stagnation, breakdown or a non-finite value
+    double hist[kFcgHist];   // rr of the last iterations (ring)
+};
+
+// r_f = r * inv (FP32), x_f = 0, r_f.r_f; the inner solve's scalars
 __global__ void __launch_bounds__(kNT)
-k_fdots(long long n, const float* __restrict__ a0, const float* __restrict__ b0, const float* __restrict__ a1,
-        const float* __restrict__ b1, const float* __restrict__ a2, const float* __restrict__ b2,
-        const uint32_t* __restrict__ bits, double* __restrict__ partials, unsigned int* __restrict__ counter,
-        double* out) {
+k_fcg_start(long long n, const double* __restrict__ r, double inv, float* __restrict__ rf, float* __restrict__ xf,
+            const uint32_t* __restrict__ bits, double* __restrict__ partials, unsigned int* __restrict__ counter,
+            FcgScalars* fs, double target2, long long max_total, int window) {
     __shared__ double sh[32];
-    AccF2 s0, s1, s2;
+    AccF2 acc;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        if (is_slave(bits, c)) continue;
-        s0.add(a0[c], b0[c]);
-        if (a1) s1.add(a1[c], b1[c]);
-        if (a2) s2.add(a2[c], b2[c]);
+        const float v = (float)(r[c] * inv);
+        rf[c] = v;
+        xf[c] = 0.0f;
+        if (!is_slave(bits, c)) acc.add(v, v);
     }
     double t;
-    if (grid_reduce(s0.value(), partials, counter, sh, &t)) out[0] = t;
-    __syncthreads();
-    if (grid_reduce(s1.value(), partials + kMaxPartials / 4, counter + 1, sh, &t)) out[1] = t;
-    __syncthreads();
-    if (grid_reduce(s2.value(), partials + kMaxPartials / 2, counter + 2, sh, &t)) out[2] = t;
-}
-
-// p = z + beta p_prev
-__global__ void k_fdir(long long n, const float* __restrict__ z, float beta, const float* __restrict__ pp,
-                       float* __restrict__ p) {
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
-        p[c] = pp ? __fmaf_rn(beta, pp[c], z[c]) : z[c];
-}
-
-// x += alpha p, r -= alpha q
-__global__ void k_fupd(long long n, float alpha, const float* __restrict__ p, const float* __restrict__ q,
-                       float* __restrict__ x, float* __restrict__ r) {
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        x[c] = __fmaf_rn(alpha, p[c], x[c]);
-        r[c] = __fmaf_rn(-alpha, q[c], r[c]);
+    if (grid_reduce(acc.value(), partials, counter, sh, &t)) {
+        fs->rr = fs->rr0 = t;
+        fs->target2 = target2;
+        fs->k = 0;
+        fs->max_total = max_total;
+        fs->window = window;
+        fs->done = (fs->total >= max_total || !(t > 0.0)) ? 1 : 0;
+        fs->fell_back = 0;
+        fs->pq_prev = 0.0;
+        fs->beta = 0.0;
     }
 }
 
-// r_f = r * inv (FP32), x_f = 0
-__global__ void k_fstart(long long n, const double* __restrict__ r, double inv, float* __restrict__ rf,
-                         float* __restrict__ xf) {
+// beta = -(z . q_prev) / (p_prev . q_prev) (0 on the first iteration)
+__global__ void __launch_bounds__(kNT)
+k_fcg_beta(long long n, const float* __restrict__ z, const float* __restrict__ qp, const uint32_t* __restrict__ bits,
+           double* __restrict__ partials, unsigned int* __restrict__ counter, FcgScalars* fs) {
+    __shared__ double sh[32];
+    if (fs->done || fs->k == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0 && !fs->done) fs->beta = 0.0;
+        return;
+    }
+    AccF2 acc;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+        if (!is_slave(bits, c)) acc.add(z[c], qp[c]);
+    double t;
+    if (grid_reduce(acc.value(), partials, counter, sh, &t)) {
+        fs->zq = t;
+        fs->beta = -t / fs->pq_prev;
+    }
+}
+
+// p = z + beta p_prev (p = z on the first iteration: p_prev holds no direction of this solve)
+__global__ void k_fcg_dir(long long n, const float* __restrict__ z, const float* __restrict__ pp,
+                          float* __restrict__ p, const FcgScalars* fs) {
+    if (fs->done) return;
+    const bool first = fs->k == 0;
+    const float beta = (float)fs->beta;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+        p[c] = first ? z[c] : __fmaf_rn(beta, pp[c], z[c]);
+}
+
+// p . q and p . r; alpha = p.r / p.q, or a breakdown
+__global__ void __launch_bounds__(kNT)
+k_fcg_dots(long long n, const float* __restrict__ p, const float* __restrict__ q, const float* __restrict__ r,
+           const uint32_t* __restrict__ bits, double* __restrict__ partials, unsigned int* __restrict__ counter,
+           FcgScalars* fs) {
+    __shared__ double sh[32];
+    if (fs->done) return;
+    AccF2 a, b;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        rf[c] = (float)(r[c] * inv);
-        xf[c] = 0.0f;
+        if (is_slave(bits, c)) continue;
+        a.add(p[c], q[c]);
+        b.add(p[c], r[c]);
+    }
+    double t;
+    if (grid_reduce(a.value(), partials, counter, sh, &t)) fs->pq = t;
+    __syncthreads();
+    if (grid_reduce(b.value(), partials + kMaxPartials / 2, counter + 1, sh, &t)) {
+        fs->pr = t;
+        const double pq = fs->pq;
+        if (!(pq > 0.0) || !isfinite(pq) || !isfinite(t)) {
+            fs->fell_back = 1;
+            fs->done = 1;
+        } else {
+            fs->alpha = t / pq;
+        }
+    }
+}
+
+// x += alpha p, r -= alpha q, r.r; convergence, stagnation (residual norm down by less than 10 %
+// over `window` iterations) and the iteration cap end the inner loop
+__global__ void __launch_bounds__(kNT)
+k_fcg_update(long long n, const float* __restrict__ p, const float* __restrict__ q, float* __restrict__ x,
+             float* __restrict__ r, const uint32_t* __restrict__ bits, double* __restrict__ partials,
+             unsigned int* __restrict__ counter, FcgScalars* fs, cudaGraphConditionalHandle h, int use_h) {
+    __shared__ double sh[32];
+    if (fs->done) {
+        if (use_h && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
+        return;
+    }
+    const float alpha = (float)fs->alpha;
+    AccF2 acc;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        x[c] = __fmaf_rn(alpha, p[c], x[c]);
+        const float v = __fmaf_rn(-alpha, q[c], r[c]);
+        r[c] = v;
+        if (!is_slave(bits, c)) acc.add(v, v);
+    }
+    double t;
+    if (grid_reduce(acc.value(), partials, counter, sh, &t)) {
+        fs->rr = t;
+        fs->pq_prev = fs->pq;
+        const long long k = fs->k;
+        fs->k = k + 1;
+        fs->total += 1;
+        int done = 0;
+        if (!isfinite(t)) {
+            fs->fell_back = 1;
+            done = 1;
+        } else if (t <= fs->target2 * fs->rr0 || fs->total >= fs->max_total) {
+            done = 1;
+        } else if (k + 1 > fs->window && !(t < 0.81 * fs->hist[(k + 1 - fs->window) % kFcgHist])) {
+            fs->fell_back = 1;
+            done = 1;
+        }
+        fs->hist[(k + 1) % kFcgHist] = t;
+        if (k == 0) fs->hist[0] = fs->rr0;
+        fs->done = done;
+        if (use_h) cudaGraphSetConditional(h, done ? 0u : 1u);
     }
 }
 
@@ -1056,53 +1156,114 @@ vofp_status scaled_pair(vofp_ctx* c, const double* b, const double* x, float* r_
     return VOFP_OK;
 }
 
-// FP64 refinement around a flexible CG (FCG(1): each new direction is A-orthogonalised against the
-// previous one, which keeps CG's short recurrence valid for a preconditioner that changes from
-// one application to the next) whose preconditioner is the network.
+// FP64 refinement around a flexible CG (FCG(1)) whose preconditioner is the network; the network
+// also gives the initial guess (the first step is the optimally scaled x0 = alpha NN(b)).  The
+// refinement steps run on the host (a few per solve); each inner solve is one launch of a graph
+// whose WHILE body holds two FCG iterations (network forward on this stream, beta, direction,
+// operator apply, step length, update with the stop tests), so the inner loop has no host round
+// trip.  A stagnating inner solve hands over to mixed-precision PCG from the current iterate.
 vofp_status solve_fcg(vofp_ctx* c, const double* b, double* x, const vofp_solve_opts* o, vofp_solve_info* info) {
     vofp_status s = ensure_workspace(c);
     if (s) return s;
     const long long N = c->d.n;
     cudaStream_t st = c->stream;
-    if (!c->zf) {
-        if ((s = c->alloc(&c->zf, N)) || (s = c->alloc(&c->qf2, N))) return s;
+    if (!c->qf2) {
+        if ((s = c->alloc(&c->qf2, N))) return s;
     }
+    if (!c->fcg) {
+        if ((s = c->alloc(&c->fcg, sizeof(FcgScalars)))) return s;
+        VOFP_CUDA_TRY(c, cudaMemsetAsync(c->fcg, 0, sizeof(FcgScalars), st));
+    }
+    FcgScalars* fs = reinterpret_cast<FcgScalars*>(c->fcg);
     vofp_nn* nn = o->nn;
     if (nn::bound_cells(nn) != N) {
         c->set_error("the network is not bound to this grid (vofp_nn_bind)");
         return VOFP_ERR_INVALID_ARG;
     }
-    cudaStream_t nst = nn::stream_of(nn);
-    const int W = o->stag_window > 0 ? o->stag_window : 20;
+    const int W = std::min(kFcgHist - 1, std::max(1, o->stag_window > 0 ? o->stag_window : 20));
     const long long max_iter = o->max_iter > 0 ? o->max_iter : 100000;
-    VOFP_CUDA_TRY(c, cudaEventRecord(c->ev0, st));
-    double sums[3];
-    if ((s = prepare_rhs(c, b, sums))) return s;
-    const double bnorm2 = sums[2];
-    launch(c, k_init_x, stream_grid(N), kNT, st, N, x, (const int32_t*)c->root, (const double*)c->sq, c->xt,
-           o->x0_zero);
-    double* dres = c->partials + kMaxPartials - 40;
     const uint32_t* bits = c->slave_bits;
-    auto dots = [&](const float* a0, const float* b0, const float* a1, const float* b1, const float* a2,
-                    const float* b2, double* h) -> vofp_status {
-        launch(c, k_fdots, stream_grid(N), kNT, st, N, a0, b0, a1, b1, a2, b2, bits, c->partials, c->counters, dres);
-        VOFP_CUDA_TRY(c, cudaMemcpyAsync(h, dres, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
-        VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
-        return VOFP_OK;
-    };
-    auto apply_f = [&](const float* p, float* q) {
-        launch(c, k_stencil<float, ST_APPLY_SCALED, 2>, stencil_grid(c), dim3(kBX, kBY), st, c->d,
+    // the network's first pass runs before any capture: it sets up its kernels and tensor maps
+    if ((s = nn::forward_on(nn, st, c->rf))) {
+        c->set_error(std::string("network: ") + vofp_nn_last_error(nn));
+        return s;
+    }
+    float* z = nn::output(nn);
+    auto apply_f = [&](cudaStream_t ss, const float* p, float* q) {
+        launch(c, k_stencil<float, ST_APPLY_SCALED, 2>, stencil_grid(c), dim3(kBX, kBY), ss, c->d,
                stencil_per_block(c), (const float*)c->Txf, (const float*)c->Tyf, (const float*)c->Tzf,
                (const double*)nullptr, p, (const float*)nullptr, (float*)nullptr, (float*)nullptr, q, c->sc,
                c->partials, c->counters);
         if (c->ngroups > 0)
-            launch(c, k_group_patch<float>, ceil_div(c->ngroups, kNT), kNT, st, c->ngroups, (const int*)c->gptr,
+            launch(c, k_group_patch<float>, ceil_div(c->ngroups, kNT), kNT, ss, c->ngroups, (const int*)c->gptr,
                    (const int*)c->gcells, (const double*)c->gcorr, q, p, 0, c->sc, c->partials, c->counters);
     };
-    long long iters = 0;
-    int outer = 0, napp = 0, fell_back = 0;
+    // one FCG iteration: direction and step into (p, q), previous direction in (pp, qp)
+    auto iteration = [&](cudaStream_t ss, float* p, float* q, const float* pp, const float* qp,
+                         cudaGraphConditionalHandle h, int use_h) -> vofp_status {
+        vofp_status r = nn::forward_on(nn, ss, c->rf);
+        if (r) return r;
+        if (c->ngroups > 0)
+            launch(c, k_group_expand_f, ceil_div(c->ngroups, kNT), kNT, ss, c->ngroups, (const int*)c->gptr,
+                   (const int*)c->gcells, z);
+        launch(c, k_fcg_beta, stream_grid(N), kNT, ss, N, (const float*)z, qp, bits, c->partials, c->counters, fs);
+        launch(c, k_fcg_dir, stream_grid(N), kNT, ss, N, (const float*)z, pp, p, (const FcgScalars*)fs);
+        apply_f(ss, p, q);
+        launch(c, k_fcg_dots, stream_grid(N), kNT, ss, N, (const float*)p, (const float*)q, (const float*)c->rf, bits,
+               c->partials, c->counters, fs);
+        launch(c, k_fcg_update, stream_grid(N), kNT, ss, N, (const float*)p, (const float*)q, c->xf, c->rf, bits,
+               c->partials, c->counters, fs, h, use_h);
+        return VOFP_OK;
+    };
+    // the inner loop's graph: WHILE { two iterations, the buffers swapping roles }
+    cudaGraphExec_t ge = nullptr;
+    {
+        cudaStream_t cs;
+        VOFP_CUDA_TRY(c, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t g;
+        VOFP_CUDA_TRY(c, cudaGraphCreate(&g, 0));
+        cudaGraphConditionalHandle h;
+        cudaGraph_t body;
+        cudaGraphNode_t node;
+        const long long launches0 = c->launches;
+        if ((s = add_while(c, g, &h, &body, nullptr, 0, &node, 1u))) return s;
+        vofp_status r1 = VOFP_OK;
+        s = capture_into(c, cs, body, [&]() {
+            r1 = iteration(cs, c->pf0, c->qf, c->pf1, c->qf2, h, 1);
+            if (!r1) r1 = iteration(cs, c->pf1, c->qf2, c->pf0, c->qf, h, 1);
+        });
+        c->launches = launches0;
+        if (s || r1) {
+            cudaGraphDestroy(g);
+            cudaStreamDestroy(cs);
+            c->set_error(std::string("capturing the flexible-CG loop: ") + vofp_nn_last_error(nn));
+            return s ? s : r1;
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        cudaStreamDestroy(cs);
+        if (ie != cudaSuccess) {
+            c->set_error(std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+            return VOFP_ERR_CUDA;
+        }
+    }
+    const int body_kernels = 2 * (nn::forward_kernels(nn) + (c->ngroups > 0 ? 2 : 1) + 5);
+    VOFP_CUDA_TRY(c, cudaEventRecord(c->ev0, st));
+    double sums[3];
+    if ((s = prepare_rhs(c, b, sums))) {
+        cudaGraphExecDestroy(ge);
+        return s;
+    }
+    const double bnorm2 = sums[2];
+    launch(c, k_init_x, stream_grid(N), kNT, st, N, x, (const int32_t*)c->root, (const double*)c->sq, c->xt,
+           o->x0_zero);
+    {
+        FcgScalars z0{};
+        VOFP_CUDA_TRY(c, cudaMemcpyAsync(fs, &z0, sizeof(z0), cudaMemcpyHostToDevice, st));
+    }
+    long long iters = 0, bodies = 0;
+    int outer = 0, fell_back = 0;
     vofp_status result = VOFP_OK;
-    double rnorm2 = 0.0;
     for (;;) {
         // FP64 residual of the scaled system and its true (unscaled) norm
         launch_stencil_apply_scaled(c, c->xt, c->q);
@@ -1114,83 +1275,45 @@ vofp_status solve_fcg(vofp_ctx* c, const double* b, double* x, const vofp_solve_
                (const double*)c->sq, bits, c->r, c->sc, c->partials, c->counters);
         VOFP_CUDA_TRY(c, cudaMemcpyAsync(&h, c->sc, sizeof(h), cudaMemcpyDeviceToHost, st));
         VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
-        rnorm2 = h.rnorm2;
+        const double rnorm2 = h.rnorm2;
         if (!std::isfinite(rnorm2)) {
             result = VOFP_ERR_BREAKDOWN;
             break;
         }
-        if (rnorm2 <= kLoopMargin * kLoopMargin * o->rtol * o->rtol * bnorm2) break;
+        if (rnorm2 <= kMixedLoopMargin * kMixedLoopMargin * o->rtol * o->rtol * bnorm2) break;
         if (iters >= max_iter || outer >= 200) {
             result = VOFP_ERR_NOT_CONVERGED;
             break;
         }
         ++outer;
         const double scale = std::sqrt(h.rr);
+        // each inner solve reduces its residual by inner_rtol (default 1e-3), or to 0.3 of what
+        // the outer tolerance still needs, whichever is looser
         const double target = std::max(o->inner_rtol > 0 ? o->inner_rtol : 1e-3,
-                                       std::min(0.5, 0.3 * o->rtol * std::sqrt(bnorm2 / rnorm2)));
-        launch(c, k_fstart, stream_grid(N), kNT, st, N, (const double*)c->r, scale > 0 ? 1.0 / scale : 0.0, c->rf,
-               c->xf);
-        double d[3];
-        if ((s = dots(c->rf, c->rf, nullptr, nullptr, nullptr, nullptr, d))) return s;
-        const double rr0 = d[0];
-        double rr = rr0, pq_prev = 0.0;
-        std::vector<double> hist;
-        float *p = c->pf0, *pp = c->pf1, *q = c->qf, *qp = c->qf2;
-        bool stop_inner = false;
-        for (int k = 0; !stop_inner; ++k) {
-            // z = M(r): the network, expanded over merge groups
-            // the network runs on its own stream: order it after this stream's work and back
-            if (nst != st) VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
-            if ((s = (vofp_status)vofp_nn_forward(nn, c->rf, c->zf))) {
-                c->set_error(std::string("network: ") + vofp_nn_last_error(nn));
-                return s;
-            }
-            if (nst != st) VOFP_CUDA_TRY(c, cudaStreamSynchronize(nst));
-            ++napp;
-            if (c->ngroups > 0)
-                launch(c, k_group_expand_f, ceil_div(c->ngroups, kNT), kNT, st, c->ngroups, (const int*)c->gptr,
-                       (const int*)c->gcells, c->zf);
-            float beta = 0.0f;
-            if (k > 0) {
-                if ((s = dots(c->zf, qp, nullptr, nullptr, nullptr, nullptr, d))) return s;
-                beta = (float)(-d[0] / pq_prev);
-            }
-            launch(c, k_fdir, stream_grid(N), kNT, st, N, (const float*)c->zf, beta, k > 0 ? (const float*)pp : nullptr,
-                   p);
-            apply_f(p, q);
-            if ((s = dots(p, q, p, c->rf, nullptr, nullptr, d))) return s;
-            const double pq = d[0], pr = d[1];
-            if (!(pq > 0.0) || !std::isfinite(pq) || !std::isfinite(pr)) {
-                fell_back = 1;
-                break;
-            }
-            const double alpha = pr / pq;
-            launch(c, k_fupd, stream_grid(N), kNT, st, N, (float)alpha, (const float*)p, (const float*)q, c->xf, c->rf);
-            if ((s = dots(c->rf, c->rf, nullptr, nullptr, nullptr, nullptr, d))) return s;
-            rr = d[0];
-            ++iters;
-            hist.push_back(rr);
-            pq_prev = pq;
-            std::swap(p, pp);
-            std::swap(q, qp);
-            if (!std::isfinite(rr)) {
-                fell_back = 1;
-                break;
-            }
-            if (rr <= target * target * rr0 || iters >= max_iter) stop_inner = true;
-            // stagnation: the residual norm fell by less than 10 % over the last W iterations
-            const size_t m = hist.size();
-            if (!stop_inner && m > (size_t)W && !(hist[m - 1] < 0.81 * hist[m - 1 - W])) {
-                fell_back = 1;
-                stop_inner = true;
-            }
-        }
+                                       std::min(0.5, 0.3 * kMixedLoopMargin * o->rtol * std::sqrt(bnorm2 / rnorm2)));
+        launch(c, k_fcg_start, stream_grid(N), kNT, st, N, (const double*)c->r, scale > 0 ? 1.0 / scale : 0.0, c->rf,
+               c->xf, bits, c->partials, c->counters, fs, target * target, max_iter, W);
+        VOFP_CUDA_TRY(c, cudaGraphLaunch(ge, st));
+        FcgScalars hf{};
+        VOFP_CUDA_TRY(c, cudaMemcpyAsync(&hf, fs, sizeof(hf), cudaMemcpyDeviceToHost, st));
+        VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
+        iters = hf.total;
+        bodies += std::max(1LL, (hf.k + 1) / 2);
         launch(c, k_ffold, stream_grid(N), kNT, st, N, (const float*)c->xf, scale, c->xt);
-        if (fell_back) break;
+        if (hf.fell_back) {
+            fell_back = 1;
+            break;
+        }
     }
+    c->launches += bodies * body_kernels;
+    cudaGraphExecDestroy(ge);
     launch(c, k_unscale, stream_grid(N), kNT, st, N, (const double*)c->xt, (const double*)c->s, x);
     VOFP_CUDA_TRY(c, cudaEventRecord(c->ev1, st));
     VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
+    if ((s = nn::read_device_error(nn))) {
+        c->set_error("the network's convolutions reported a bounded wait that ran out");
+        return s;
+    }
     float ms = 0.0f;
     VOFP_CUDA_TRY(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
     int it_total = (int)iters, outer_total = outer;
@@ -1216,7 +1339,7 @@ vofp_status solve_fcg(vofp_ctx* c, const double* b, double* x, const vofp_solve_
         info->rel_residual = rel;
         info->seconds = seconds;
         info->status = result;
-        info->nn_applications = napp;
+        info->nn_applications = (int)(2 * bodies + 1);
         info->fell_back = fell_back;
     }
     if (result != VOFP_OK) c->set_error("learned-preconditioner solve did not reach rtol");
