@@ -123,9 +123,13 @@ typedef struct {
  *   nn          VOFP_MODE_FCG_NN: a network bound to this operator (vofp_nn_bind).  The solve is
  *               FP64 iterative refinement whose inner solve is a flexible CG (FP32 vectors, FP64-
  *               accurate dots) preconditioned by the network, which also gives the initial guess.
- *               If the inner residual falls by less than 10 % over stag_window iterations, or a
- *               breakdown occurs, the solve falls back to VOFP_MODE_MIXED (precond as given) from
- *               the current iterate. */
+ *               The network's steps continue while the inner residual norm falls at least to
+ *               stag_ratio of its value stag_window iterations before; otherwise (or on a
+ *               breakdown) the solve hands over to VOFP_MODE_MIXED (precond as given) from the
+ *               current iterate.  A network application costs about as much as 30-40 iterations
+ *               of the mixed red-black solve, so the defaults (window 2, ratio 0.6) keep it only
+ *               while it beats those.
+ *   stag_window, stag_ratio  the hand-over test above (0 selects the defaults; window <= 63). */
 typedef struct {
     int mode;
     int precond;
@@ -138,6 +142,7 @@ typedef struct {
     vofp_nn* nn;
     int stag_window;
     int inner_restart;
+    double stag_ratio;
 } vofp_solve_opts;
 
 typedef struct {
@@ -394,6 +399,16 @@ vofp_status vofp_nn_forward(vofp_nn* nn, const float* r, float* z);
  * update = 1 also takes an Adam step with learning rate lr.  *loss (host) may be NULL. */
 vofp_status vofp_nn_train_step(vofp_nn* nn, const float* r, const float* target, float lr, int update,
                                float* loss);
+
+/* Training step of the network as a preconditioner of ctx's operator (the network bound to ctx's
+ * grid): r is a scaled residual and e the exact error it leaves (FP32 device cells, scaled
+ * variables as in vofp_scaled_pair, A_scaled e = r).  The loss is the relative A-norm error of the
+ * network output z, (z - e)' A_scaled (z - e) / (e' A_scaled e) over the unknowns (1 for z = 0),
+ * whose gradient 2 (A_scaled z - r) / (e' r) needs one operator apply; then backward and, with
+ * update = 1, an Adam step with learning rate lr.  *loss (host) may be NULL.  Runs on ctx's stream
+ * and synchronises it.  The paper has no counterpart. */
+vofp_status vofp_nn_train_step_anorm(vofp_nn* nn, vofp_ctx* ctx, const float* r, const float* e, float lr,
+                                     int update, float* loss);
 
 /* *count = number of kernels this context has launched since vofp_create (kernels run inside
  * the solve's CUDA graphs are counted per execution). */

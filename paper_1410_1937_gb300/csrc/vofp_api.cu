@@ -204,6 +204,8 @@ vofp_status vofp_solve(vofp_ctx* c, const double* b, double* x, const vofp_solve
     if (o->mode == VOFP_MODE_MIXED && (o->inner_rtol < 0.0 || o->inner_rtol >= 1.0))
         return invalid(c, "inner_rtol must be in [0, 1)");
     if (o->inner_restart != 0 && o->inner_restart != 1) return invalid(c, "inner_restart must be 0 or 1");
+    if (o->stag_window < 0 || !(o->stag_ratio >= 0.0) || o->stag_ratio >= 1.0)
+        return invalid(c, "stag_window must be >= 0 and stag_ratio in [0, 1)");
     if (info) std::memset(info, 0, sizeof(*info));
     return vofp::solve(c, b, x, o, info);
 }
@@ -266,6 +268,14 @@ vofp_status vofp_scaled_pair(vofp_ctx* c, const double* b, const double* x, floa
     if (s) return s;
     if (!b || !x || !r_scaled || !x_scaled) return invalid(c, "null input");
     return vofp::scaled_pair(c, b, x, r_scaled, x_scaled);
+}
+
+vofp_status vofp_nn_train_step_anorm(vofp_nn* nn, vofp_ctx* c, const float* r, const float* e, float lr, int update,
+                                     float* loss) {
+    vofp_status s = check_ctx(c, true);
+    if (s) return s;
+    if (!nn || !r || !e) return invalid(c, "null input");
+    return vofp::nn_train_anorm(c, nn, r, e, lr, update, loss);
 }
 
 vofp_status vofp_merge_map(vofp_ctx* c, int32_t* master) {

@@ -168,6 +168,7 @@ struct vofp_ctx {
     double* rk2_buf = nullptr;        // RK2 step (vofp_rk2.cu): face fields and cell arrays
     long long rbc_cap = 0;            // allocated compact length
     int rbc_blocks_per_sm = 0;
+    int rbc_rpt = 2;                  // rows per thread of the compact iteration kernel (tile 32 x 8 rpt)
     int rbc_nblocks = 0, rbc_per = 0, rbc_pad = 0;  // iteration kernel split (see rbc_split)
     int tma_blocks_deep32 = 0;        // resident blocks per SM of the six-stage FP32 stencil
     int rb_tma_blocks_per_sm = 0;
@@ -226,6 +227,8 @@ vofp_status solve(vofp_ctx* c, const double* b, double* x, const vofp_solve_opts
                   vofp_solve_info* info);
 vofp_status solve_fcg(vofp_ctx* c, const double* b, double* x, const vofp_solve_opts* o, vofp_solve_info* info);
 vofp_status scaled_pair(vofp_ctx* c, const double* b, const double* x, float* r_scaled, float* x_scaled);
+vofp_status nn_train_anorm(vofp_ctx* c, vofp_nn* nn, const float* r, const float* e, float lr, int update,
+                           float* loss);
 vofp_status time_iteration_kernels(vofp_ctx* c, int precision, bool rb, int reps, float* st, float* up,
                                    float* red);
 
@@ -345,6 +348,9 @@ vofp_status forward_on(vofp_nn* n, cudaStream_t st, const float* r);
 float* output(vofp_nn* n);
 int forward_kernels(const vofp_nn* n);           // kernels one forward pass launches
 vofp_status read_device_error(vofp_nn* n);       // VOFP_ERR_DEVICE_TIMEOUT if a bounded wait ran out
+vofp_status prepare_training(vofp_nn* n);        // gradient buffers
+// after forward_on: gradients from a given dL/dz of the output (FP32 cells), Adam step if update
+vofp_status train_from_grad_on(vofp_nn* n, cudaStream_t st, const float* dz, float lr, int update);
 }  // namespace nn
 
 inline int ceil_div(long long a, long long b) { return int((a + b - 1) / b); }

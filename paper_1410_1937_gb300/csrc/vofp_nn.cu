@@ -732,6 +732,45 @@ __global__ void k_head_bwd_dev(const bf16* __restrict__ h, const float* __restri
     if (threadIdx.x == 17) atomicAdd(scal + 4, sh[17][0] * inv_count);
 }
 
+// output layer's backward pass from a given gradient dL/dz of the network output z
+// (z = mask (b + w . h) scale): dL/ds = dz mask scale per voxel
+__global__ void k_head_bwd_given(const bf16* __restrict__ h, const float* __restrict__ w, const float* __restrict__ dz,
+                                 const float* __restrict__ mask, const float* scal, bf16* __restrict__ dh,
+                                 float* __restrict__ dw, float* __restrict__ db, long long nv) {
+    __shared__ float sh[17][128];
+    const float scale = scal[2];
+    float lw[16], lb = 0.f;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) lw[c] = 0.f;
+    const uint4* h4 = reinterpret_cast<const uint4*>(h);
+    uint4* d4 = reinterpret_cast<uint4*>(dh);
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv; v += (long long)gridDim.x * blockDim.x) {
+        const float go = dz[v] * mask[v] * scale;
+        lb += go;
+        float f[2][8], g[2][8];
+        unpack8(h4[v], f[0]);
+        unpack8(h4[nv + v], f[1]);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            lw[c] = fmaf(go, f[c >> 3][c & 7], lw[c]);
+            g[c >> 3][c & 7] = go * w[c];
+        }
+        d4[v] = pack8(g[0]);
+        d4[nv + v] = pack8(g[1]);
+    }
+#pragma unroll
+    for (int c = 0; c < 16; ++c) sh[c][threadIdx.x] = lw[c];
+    sh[16][threadIdx.x] = lb;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int c = 0; c < 17; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x < 16) atomicAdd(dw + threadIdx.x, sh[threadIdx.x][0]);
+    if (threadIdx.x == 16) atomicAdd(db, sh[16][0]);
+}
+
 // chunk-planar tensor map: five dimensions (8 channels, x, y, z, channel group), box of one
 // halo'd 10 x 18 tile plane of every group (cached per tensor and level)
 const CUtensorMap* act_map(vofp_nn* n, const bf16* ptr, int nx, int ny, int nz, int groups) {
@@ -895,7 +934,9 @@ vofp_status layer_bwd(vofp_nn* n, const Layer& l, const bf16* x, const bf16* y, 
     return VOFP_OK;
 }
 
-vofp_status backward(vofp_nn* n, const float* target) {
+// backward pass after forward(): from the mean-squared error against `target`, or from a given
+// gradient dz of the output when target is null
+vofp_status backward(vofp_nn* n, const float* target, const float* dz = nullptr) {
     cudaStream_t st = n->stream;
     const int X = n->nx, Y = n->ny, Z = n->nz;
     const int X2 = X / 2, Y2 = Y / 2, Z2 = Z / 2, X4 = X / 4, Y4 = Y / 4, Z4 = Z / 4;
@@ -906,8 +947,12 @@ vofp_status backward(vofp_nn* n, const float* target) {
     }
     cudaMemsetAsync(n->ghw, 0, sizeof(float) * 16, st);
     cudaMemsetAsync(n->ghb, 0, sizeof(float), st);
-    k_head_bwd_dev<<<gs(n->V1, 128), 128, 0, st>>>(n->d1b, n->hw, n->out, target, n->mask, n->scal, n->g16a, n->ghw,
-                                                   n->ghb, n->V1);
+    if (target)
+        k_head_bwd_dev<<<gs(n->V1, 128), 128, 0, st>>>(n->d1b, n->hw, n->out, target, n->mask, n->scal, n->g16a,
+                                                       n->ghw, n->ghb, n->V1);
+    else
+        k_head_bwd_given<<<gs(n->V1, 128), 128, 0, st>>>(n->d1b, n->hw, dz, n->mask, n->scal, n->g16a, n->ghw, n->ghb,
+                                                         n->V1);
     vofp_status s;
     if ((s = layer_bwd(n, L[9], n->d1a, n->d1b, n->g16a, n->g16b, X, Y, Z))) return s;   // -> d(d1a)
     if ((s = layer_bwd(n, L[8], n->c1, n->d1a, n->g16b, n->g48, X, Y, Z))) return s;     // -> d(c1)
@@ -1044,6 +1089,16 @@ float* output(vofp_nn* n) { return n->out; }
 // rms, its finish, input packing, ten convolutions, two poolings, two upsamplings, output layer
 int forward_kernels(const vofp_nn*) { return 18; }
 vofp_status read_device_error(vofp_nn* n) { return read_err(n); }
+vofp_status train_from_grad_on(vofp_nn* n, cudaStream_t st, const float* dz, float lr, int update) {
+    const cudaStream_t own = n->stream;
+    n->stream = st;
+    vofp_status s = backward(n, nullptr, dz);
+    if (!s && update) adam(n, lr);
+    n->stream = own;
+    if (s) return s;
+    return read_err(n);
+}
+vofp_status prepare_training(vofp_nn* n) { return ensure_grads(n); }
 }  // namespace nn
 }  // namespace vofp
 

@@ -591,17 +591,30 @@ vofp_status rbc_ensure(vofp_ctx* c) {
     }
     // the zero difference entry behind faces without an exception
     VOFP_CUDA_TRY(c, cudaMemsetAsync(c->rbc_dE + ne, 0, sizeof(float), st));
+    // rows per thread of the iteration kernel: 2 (32 x 16 tiles) unless VOFP_RBC_ROWS=1 (32 x 8)
+    {
+        const char* env = std::getenv("VOFP_RBC_ROWS");
+        c->rbc_rpt = (env && std::strcmp(env, "1") == 0) ? 1 : 2;
+    }
+    const int th = kBY * c->rbc_rpt;
     // the iteration kernel's dynamic shared memory and resident blocks
-    constexpr size_t smem = cg_rbc_smem<kRbcStages>();
-    cudaFuncSetAttribute(k_rbc_tma<kRbcStages>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_rbc_tma<kRbcStages>, kBX * kBY, smem) != cudaSuccess)
-        nb = 0;
+    if (c->rbc_rpt == 1) {
+        constexpr size_t smem = cg_rbc_smem<kRbcStages, 1>();
+        cudaFuncSetAttribute(k_rbc_tma<kRbcStages, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_rbc_tma<kRbcStages, 1>, kBX * kBY, smem) != cudaSuccess)
+            nb = 0;
+    } else {
+        constexpr size_t smem = cg_rbc_smem<kRbcStages, 2>();
+        cudaFuncSetAttribute(k_rbc_tma<kRbcStages, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_rbc_tma<kRbcStages, 2>, kBX * kBY, smem) != cudaSuccess)
+            nb = 0;
+    }
     cudaGetLastError();
     VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
     if (nb <= 0) return VOFP_OK;
     {
-        const long long tiles_x = ceil_div(d.nx / 2, RbcGeom::NP), tiles_y = ceil_div(d.ny, kBY);
+        const long long tiles_x = ceil_div(d.nx / 2, RbcGeom::NP), tiles_y = ceil_div(d.ny, th);
         // the kernel's work index is an int
         if (tiles_x * tiles_y * (d.nz + 2 * kSegSteps) > 0x7fffffffLL) return VOFP_OK;
         rbc_split(tiles_x, tiles_y, d.nz, (long long)num_sms() * nb, &c->rbc_nblocks, &c->rbc_per, &c->rbc_pad);
@@ -621,14 +634,16 @@ void rbc_prep(vofp_ctx* c, cudaStream_t st, const double* rhs) {
 }
 
 namespace {
-void launch_main(vofp_ctx* c, cudaStream_t st, const float* po, float* pn, bool pdl) {
-    using G = RbcGeom;
+template <int RPT>
+void launch_main_t(vofp_ctx* c, cudaStream_t st, const float* po, float* pn, bool pdl) {
+    using G = RbcGeomT<RPT>;
     const Dims d = c->d;
     const int nh = d.nx / 2;
-    const CUtensorMap *mr = tensor_map_f32_x(c, c->rbc_r, nh, G::BWC, kBY + 4),
-                      *mp = tensor_map_f32_x(c, po, nh, G::BWC, kBY + 4),
-                      *mx = tensor_map_f32(c, c->Txf, G::BWF, kBY + 2), *my = tensor_map_f32(c, c->Tyf, G::BWF, kBY + 3),
-                      *mz = tensor_map_f32(c, c->Tzf, G::BWF, kBY + 2);
+    const CUtensorMap *mr = tensor_map_f32_x(c, c->rbc_r, nh, G::BWC, G::TH + 4),
+                      *mp = tensor_map_f32_x(c, po, nh, G::BWC, G::TH + 4),
+                      *mx = tensor_map_f32(c, c->Txf, G::BWF, G::TH + 2),
+                      *my = tensor_map_f32(c, c->Tyf, G::BWF, G::TH + 3),
+                      *mz = tensor_map_f32(c, c->Tzf, G::BWF, G::TH + 2);
     if (!(mr && mp && mx && my && mz)) {
         c->set_error("tensor map of the compact red-black vectors could not be built");
         return;
@@ -639,8 +654,15 @@ void launch_main(vofp_ctx* c, cudaStream_t st, const float* po, float* pn, bool 
     maps.tx = *mx;
     maps.ty = *my;
     maps.tz = *mz;
-    launch_dep(c, pdl, k_rbc_tma<kRbcStages>, dim3(c->rbc_nblocks), dim3(kBX, kBY), cg_rbc_smem<kRbcStages>(), st,
-               maps, d, c->rbc_per, c->rbc_pad, po, pn, c->rbc_x, c->rbc_q, c->sc, c->partials, c->counters);
+    launch_dep(c, pdl, k_rbc_tma<kRbcStages, RPT>, dim3(c->rbc_nblocks), dim3(kBX, kBY),
+               cg_rbc_smem<kRbcStages, RPT>(), st, maps, d, c->rbc_per, c->rbc_pad, po, pn, c->rbc_x, c->rbc_q,
+               c->sc, c->partials, c->counters);
+}
+void launch_main(vofp_ctx* c, cudaStream_t st, const float* po, float* pn, bool pdl) {
+    if (c->rbc_rpt == 1)
+        launch_main_t<1>(c, st, po, pn, pdl);
+    else
+        launch_main_t<2>(c, st, po, pn, pdl);
 }
 }  // namespace
 

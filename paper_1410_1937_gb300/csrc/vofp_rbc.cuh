@@ -29,16 +29,20 @@ struct RbcMaps {
 
 constexpr size_t rbc_al(size_t b) { return (b + 127) / 128 * 128; }
 
-struct RbcGeom {
+// Tile of RPT x 8 rows of 32 pairs; thread (tx, ty) owns pair h0 + tx in rows j0 + ty + 8 q,
+// q < RPT.
+template <int RPT>
+struct RbcGeomT {
+    static constexpr int TH = kBY * RPT;              // rows of a tile
     static constexpr int NP = kBX;                    // pairs of a tile row (64 cells)
     static constexpr int HXC = 4;                     // compact box x origin h0 - 4 (16-byte aligned)
     static constexpr int BWC = NP + 2 * HXC;          // 40 pairs: h0-4 .. h0+35
     static constexpr int HXF = 4;                     // full-grid box x origin i0 - 4
     static constexpr int BWF = 2 * NP + 2 * HXF;      // 72 cells: i0-4 .. i0+67
-    static constexpr int RN = BWC * (kBY + 4);        // compact r, p_old: rows j0-2 .. j0+9
-    static constexpr int XN = BWF * (kBY + 2);        // Tx: rows j0-1 .. j0+8
-    static constexpr int YN = BWF * (kBY + 3);        // Ty: rows j0-2 .. j0+8
-    static constexpr int ZN = BWF * (kBY + 2);        // Tz: rows j0-1 .. j0+8
+    static constexpr int RN = BWC * (TH + 4);         // compact r, p_old: rows j0-2 .. j0+TH+1
+    static constexpr int XN = BWF * (TH + 2);         // Tx: rows j0-1 .. j0+TH
+    static constexpr int YN = BWF * (TH + 3);         // Ty: rows j0-2 .. j0+TH
+    static constexpr int ZN = BWF * (TH + 2);         // Tz: rows j0-1 .. j0+TH
     static constexpr size_t oR = 0;
     static constexpr size_t oP = oR + rbc_al(RN * 4);
     static constexpr size_t oX = oP + rbc_al(RN * 4);
@@ -46,30 +50,33 @@ struct RbcGeom {
     static constexpr size_t oZ = oY + rbc_al(YN * 4);
     static constexpr size_t kStage = oZ + rbc_al(ZN * 4);
     static constexpr uint32_t kTx = (uint32_t)((2 * RN + XN + YN + ZN) * 4);
-    // p ring plane (black cells): index xr <-> pair h0 + xr - 2 (36), row yr <-> j0 + yr - 2 (12)
+    // p ring plane (black cells): index xr <-> pair h0 + xr - 2 (36), row yr <-> j0 + yr - 2
     static constexpr int PW = NP + 4;
-    static constexpr int PN = PW * (kBY + 4);
-    // w ring plane (even cells): same pair index, row yw <-> j0 + yw - 1 (10)
-    static constexpr int WN = PW * (kBY + 2);
+    static constexpr int PN = PW * (TH + 4);
+    // w ring plane (even cells): same pair index, row yw <-> j0 + yw - 1
+    static constexpr int WN = PW * (TH + 2);
     static constexpr int kPItems = PN;                // p values formed per plane
+    static constexpr int kPPer = (PN + kBX * kBY - 1) / (kBX * kBY);   // per thread
+    static constexpr int kRing = 2 * NP + 2 * TH;     // even cells of the w halo ring
 };
+using RbcGeom = RbcGeomT<1>;
 
-template <int NS>
+template <int NS, int RPT>
 constexpr size_t cg_rbc_smem() {
-    using G = RbcGeom;
+    using G = RbcGeomT<RPT>;
     return 128 + NS * G::kStage + 3 * G::PN * 4 + 3 * G::WN * 4 + NS * sizeof(uint64_t);
 }
 
 // A stage of step s carries compact r and p_old of plane s+2 and Tx, Ty, Tz of plane s+1; a step
 // forms p of plane s+2, w of plane s+1 and t of plane s-1 (two barriers per step).
-template <int NS>
-__global__ void __launch_bounds__(kBX* kBY, 3)
+template <int NS, int RPT>
+__global__ void __launch_bounds__(kBX* kBY, RPT == 1 ? 3 : 2)
 k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_block, const int pad,
           const float* __restrict__ pold,
           float* __restrict__ pnew, float* __restrict__ xv, float* __restrict__ out, CgScalars* __restrict__ sc,
           double* __restrict__ partials, unsigned int* __restrict__ counter) {
-    using G = RbcGeom;
-    constexpr int PW = G::PW, BWF = G::BWF, BWC = G::BWC;
+    using G = RbcGeomT<RPT>;
+    constexpr int PW = G::PW, BWF = G::BWF, BWC = G::BWC, TH = G::TH;
     extern __shared__ __align__(128) unsigned char rbc_smem[];
     unsigned char* base = rbc_smem + ((128u - (smem_addr(rbc_smem) & 127u)) & 127u);
     float* pring = reinterpret_cast<float*>(base + NS * G::kStage);
@@ -89,32 +96,32 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_bloc
     auto pl = [&](int kk) -> float* { return pring + ((kk + 6) % 3) * G::PN; };
     auto wl = [&](int kk) -> float* { return wring + ((kk + 6) % 3) * G::WN; };
 
-    // p items: ring index e = tid + 256 q of the 36 x 12 plane (row e / PW, pair e % PW); box
-    // index of the same pair e + (BWC - PW) (e / PW) + 2
-    int pi_src[2];
-    bool pi_on[2];
+    // p items: ring index e = tid + 256 q of the 36 x (TH + 4) plane (row e / PW, pair e % PW);
+    // box index of the same pair e + (BWC - PW) (e / PW) + 2
+    int pi_src[G::kPPer];
+    bool pi_on[G::kPPer];
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < G::kPPer; ++q) {
         const int it = tid + q * kBX * kBY;
         pi_on[q] = it < G::kPItems;
         pi_src[q] = it + (BWC - PW) * (it / PW) + 2;
     }
-    // own pair xr = tx + 2 in w row ty + 1; ring items (threads 0..79): the pairs of rows j0-1 and
-    // j0+8 (threads 0..63) and the pairs h0-1 and h0+32 of rows j0 .. j0+7 (threads 64..79)
-    const int xo = tx + 2, yo = ty + 1;
+    // own pair xr = tx + 2 in w rows ty + 8 q + 1; ring items (threads 0 .. 2 NP + 2 TH - 1): the
+    // pairs of rows j0-1 and j0+TH, then the pairs h0-1 and h0+NP of rows j0 .. j0+TH-1
+    const int xo = tx + 2;
     int rx = 0, ry = 0;
-    const bool has_ring = tid < 80;
-    if (tid < 32) { rx = tid + 2; ry = 0; }
-    else if (tid < 64) { rx = tid - 32 + 2; ry = kBY + 1; }
-    else if (tid < 72) { rx = 1; ry = 1 + (tid - 64); }
-    else if (tid < 80) { rx = PW - 2; ry = 1 + (tid - 72); }
+    const bool has_ring = tid < G::kRing;
+    if (tid < G::NP) { rx = tid + 2; ry = 0; }
+    else if (tid < 2 * G::NP) { rx = tid - G::NP + 2; ry = TH + 1; }
+    else if (tid < 2 * G::NP + TH) { rx = 1; ry = 1 + (tid - 2 * G::NP); }
+    else if (tid < G::kRing) { rx = PW - 2; ry = 1 + (tid - 2 * G::NP - TH); }
 
     // everything above is block-local set-up; the scalars and vectors come from the kernels before
     grid_dep_wait();
     const float beta = (float)sc->beta, alpha = (float)sc->alpha;
     const int nh = d.nx >> 1;
     const int tiles_x = (nh + G::NP - 1) / G::NP;
-    const long long ntiles = (long long)tiles_x * ((d.ny + kBY - 1) / kBY);
+    const long long ntiles = (long long)tiles_x * ((d.ny + TH - 1) / TH);
     // work items w = tile * (nz + pad) + pad + plane: every tile column starts with `pad` items
     // that stand for no plane, so that an equal split of w charges each column's first segment
     // for its prologue steps (pad = 0: the plain equal split)
@@ -129,12 +136,18 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_bloc
         w += kp1 - kp0;
         const int k0 = max(kp0 - pad, 0), k1 = kp1 - pad;
         if (k1 <= k0) continue;   // padding only (the same for every thread of the block)
-        const int h0 = int(tile_id % tiles_x) * G::NP, j0 = int(tile_id / tiles_x) * kBY;
+        const int h0 = int(tile_id % tiles_x) * G::NP, j0 = int(tile_id / tiles_x) * TH;
         const int i0 = 2 * h0;
-        const int h = h0 + tx, j = j0 + ty;
-        const bool inside = h < nh && j < d.ny;
-        const long long own = inside ? h + (long long)nh * j : 0;   // compact index within a plane
+        const int h = h0 + tx;
         const long long cplane = (long long)nh * d.ny;
+        bool inside[RPT];
+        long long own[RPT];   // compact index within a plane
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            const int j = j0 + ty + kBY * q;
+            inside[q] = h < nh && j < d.ny;
+            own[q] = inside[q] ? h + (long long)nh * j : 0;
+        }
         const int s_first = k0 - 4, s_last = k1 - 1;
         auto slot = [&](int s) { return (s - s_first) % NS; };
         auto issue = [&](int s) {
@@ -182,9 +195,17 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_bloc
         struct Co {
             float tx, txl, ty, tyd, tz, tzm, p;
         };
-        Co sa{}, sb{};
-        float2 own_tzm = make_float2(0.f, 0.f), ring_tzm = own_tzm;
-        float xa = 0.f, pa = 0.f, xb2 = 0.f, pb = 0.f;
+        Co sa[RPT], sb[RPT];
+        float2 own_tzm[RPT];
+        float xa[RPT], pa[RPT], xb2[RPT], pb[RPT];
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            sa[q] = Co{};
+            sb[q] = Co{};
+            own_tzm[q] = make_float2(0.f, 0.f);
+            xa[q] = pa[q] = xb2[q] = pb[q] = 0.f;
+        }
+        float2 ring_tzm = make_float2(0.f, 0.f);
 
         __syncthreads();
         if (tid == 0) fence_proxy_async_smem();
@@ -207,76 +228,86 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_bloc
                 const float* P = reinterpret_cast<const float*>(b + G::oP);
                 float* op = Pc;
 #pragma unroll
-                for (int q = 0; q < 2; ++q)
+                for (int q = 0; q < G::kPPer; ++q)
                     if (pi_on[q]) op[tid + q * kBX * kBY] = fmav(beta, P[pi_src[q]], R[pi_src[q]]);
             }
-            // P1: t of plane s-1 on the black cell of the own pair
+            // P1: t of plane s-1 on the black cell of each own pair
             const int m = s - 1;
-            if (m >= k0 && m < k1 && inside) {
-                const int rho = (j + m) & 1;
-                const float* W0 = Wc;
-                const int e = yo * PW + xo;
-                float t = sa.p;
-                t = fmav(-sa.tx, W0[e + 1 - rho], t);
-                t = fmav(-sa.txl, W0[e - rho], t);
-                t = fmav(-sa.ty, W0[e + PW], t);
-                t = fmav(-sa.tyd, W0[e - PW], t);
-                t = fmav(-sa.tz, Wa[e], t);
-                t = fmav(-sa.tzm, Wb[e], t);
-                const long long c = (long long)m * cplane + own;
-                out[c] = t;
-                pnew[c] = sa.p;
-                xv[c] = fmav(alpha, pa, xa);
-                acc.add(sa.p, t);
-            }
-            xa = xb2;
-            pa = pb;
-            xb2 = 0.f;
-            pb = 0.f;
-            if (s + 1 >= k0 && s + 1 < k1 && inside) {
-                const long long c = (long long)(s + 1) * cplane + own;
-                xb2 = xv[c];
-                pb = pold[c];
+#pragma unroll
+            for (int q = 0; q < RPT; ++q) {
+                if (m >= k0 && m < k1 && inside[q]) {
+                    const int rho = (j0 + ty + kBY * q + m) & 1;
+                    const float* W0 = Wc;
+                    const int e = (ty + kBY * q + 1) * PW + xo;
+                    float t = sa[q].p;
+                    t = fmav(-sa[q].tx, W0[e + 1 - rho], t);
+                    t = fmav(-sa[q].txl, W0[e - rho], t);
+                    t = fmav(-sa[q].ty, W0[e + PW], t);
+                    t = fmav(-sa[q].tyd, W0[e - PW], t);
+                    t = fmav(-sa[q].tz, Wa[e], t);
+                    t = fmav(-sa[q].tzm, Wb[e], t);
+                    const long long c = (long long)m * cplane + own[q];
+                    out[c] = t;
+                    pnew[c] = sa[q].p;
+                    xv[c] = fmav(alpha, pa[q], xa[q]);
+                    acc.add(sa[q].p, t);
+                }
+                xa[q] = xb2[q];
+                pa[q] = pb[q];
+                xb2[q] = 0.f;
+                pb[q] = 0.f;
+                if (s + 1 >= k0 && s + 1 < k1 && inside[q]) {
+                    const long long c = (long long)(s + 1) * cplane + own[q];
+                    xb2[q] = xv[c];
+                    pb[q] = pold[c];
+                }
             }
             if (__syncthreads_or(!ok)) {
                 bad = true;
                 break;
             }
-            // P2: w of plane s+1 (even cells of the own pair and the ring); before plane k0-1 only
-            // the pair's Tz is carried
+            // P2: w of plane s+1 (even cells of the own pairs and the ring); before plane k0-1 only
+            // the pairs' Tz is carried
             if (s <= s_last && s + 1 >= k0 - 2) {
                 const int mw = s + 1;
                 const float* Z = reinterpret_cast<const float*>(b + G::oZ);
                 if (mw >= k0 - 1) {
-                    float2 tzp;
-                    Wb[yo * PW + xo] = w_even(b, mw, xo, yo, own_tzm, tzp, Pb, Pc, Pa);
-                    // the own black cell's coefficients and p for its t two steps later
-                    const int rho = (j + mw) & 1;
                     const float* X = reinterpret_cast<const float*>(b + G::oX);
                     const float* Y = reinterpret_cast<const float*>(b + G::oY);
-                    const int xbb = 2 * xo + 1 - rho;      // full-grid box index of the black cell
-                    Co co;
-                    co.tx = X[yo * BWF + xbb];
-                    co.txl = X[yo * BWF + xbb - 1];
-                    co.ty = Y[(yo + 1) * BWF + xbb];
-                    co.tyd = Y[yo * BWF + xbb];
-                    co.tz = rho ? tzp.x : tzp.y;
-                    co.tzm = rho ? own_tzm.x : own_tzm.y;
-                    co.p = Pb[(yo + 1) * PW + xo];
-                    own_tzm = tzp;
-                    sa = sb;
-                    sb = co;
+#pragma unroll
+                    for (int q = 0; q < RPT; ++q) {
+                        const int yo = ty + kBY * q + 1;
+                        float2 tzp;
+                        Wb[yo * PW + xo] = w_even(b, mw, xo, yo, own_tzm[q], tzp, Pb, Pc, Pa);
+                        // the own black cell's coefficients and p for its t two steps later
+                        const int rho = (j0 + yo - 1 + mw) & 1;
+                        const int xbb = 2 * xo + 1 - rho;      // full-grid box index of the black cell
+                        Co co;
+                        co.tx = X[yo * BWF + xbb];
+                        co.txl = X[yo * BWF + xbb - 1];
+                        co.ty = Y[(yo + 1) * BWF + xbb];
+                        co.tyd = Y[yo * BWF + xbb];
+                        co.tz = rho ? tzp.x : tzp.y;
+                        co.tzm = rho ? own_tzm[q].x : own_tzm[q].y;
+                        co.p = Pb[(yo + 1) * PW + xo];
+                        own_tzm[q] = tzp;
+                        sa[q] = sb[q];
+                        sb[q] = co;
+                    }
                     if (has_ring) {
                         float2 tzr;
                         Wb[ry * PW + rx] = w_even(b, mw, rx, ry, ring_tzm, tzr, Pb, Pc, Pa);
                         ring_tzm = tzr;
                     }
                 } else {
-                    own_tzm = *reinterpret_cast<const float2*>(Z + yo * BWF + 2 * xo);
+#pragma unroll
+                    for (int q = 0; q < RPT; ++q)
+                        own_tzm[q] = *reinterpret_cast<const float2*>(Z + (ty + kBY * q + 1) * BWF + 2 * xo);
                     if (has_ring) ring_tzm = *reinterpret_cast<const float2*>(Z + ry * BWF + 2 * rx);
                 }
             } else {
-                sa = sb;
+#pragma unroll
+                for (int q = 0; q < RPT; ++q) sa[q] = sb[q];
             }
             {
                 float* const tp = Pa;

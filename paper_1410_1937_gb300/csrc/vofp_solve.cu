@@ -391,6 +391,7 @@ struct FcgScalars {
     long long total;         // iterations of the whole solve
     long long max_total;
     int window;              // stagnation window (iterations)
+    double stag2;            // the residual must fall to stag2 (ratio squared) of rr `window` iterations before
     int done;                // inner solve finished
     int fell_back;           // stagnation, breakdown or a non-finite value
     double hist[kFcgHist];   // rr of the last iterations (ring)
@@ -400,7 +401,7 @@ struct FcgScalars {
 __global__ void __launch_bounds__(kNT)
 k_fcg_start(long long n, const double* __restrict__ r, double inv, float* __restrict__ rf, float* __restrict__ xf,
             const uint32_t* __restrict__ bits, double* __restrict__ partials, unsigned int* __restrict__ counter,
-            FcgScalars* fs, double target2, long long max_total, int window) {
+            FcgScalars* fs, double target2, long long max_total, int window, double stag2) {
     __shared__ double sh[32];
     AccF2 acc;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
@@ -416,6 +417,7 @@ k_fcg_start(long long n, const double* __restrict__ r, double inv, float* __rest
         fs->k = 0;
         fs->max_total = max_total;
         fs->window = window;
+        fs->stag2 = stag2;
         fs->done = (fs->total >= max_total || !(t > 0.0)) ? 1 : 0;
         fs->fell_back = 0;
         fs->pq_prev = 0.0;
@@ -512,7 +514,7 @@ k_fcg_update(long long n, const float* __restrict__ p, const float* __restrict__
             done = 1;
         } else if (t <= fs->target2 * fs->rr0 || fs->total >= fs->max_total) {
             done = 1;
-        } else if (k + 1 > fs->window && !(t < 0.81 * fs->hist[(k + 1 - fs->window) % kFcgHist])) {
+        } else if (k + 1 >= fs->window && !(t < fs->stag2 * fs->hist[(k + 1 - fs->window) % kFcgHist])) {
             fs->fell_back = 1;
             done = 1;
         }
@@ -521,6 +523,42 @@ k_fcg_update(long long n, const float* __restrict__ p, const float* __restrict__
         fs->done = done;
         if (use_h) cudaGraphSetConditional(h, done ? 0u : 1u);
     }
+}
+
+// Relative A-norm error of a network output z against the exact error e of the residual r
+// (A e = r): L = (z - e)' A (z - e) / (e' A e) = (z'q - 2 z'r + e'r) / e'r with q = A z, over the
+// unknowns (cells in no other cell's group).  out[0..2] = z'q, z'r, e'r.
+__global__ void __launch_bounds__(kNT)
+k_anorm_dots(long long n, const float* __restrict__ z, const float* __restrict__ q, const float* __restrict__ r,
+             const float* __restrict__ e, const uint32_t* __restrict__ bits, double* __restrict__ partials,
+             unsigned int* __restrict__ counter, double* out) {
+    __shared__ double sh[32];
+    AccF2 a, b, c2;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        if (is_slave(bits, c)) continue;
+        a.add(z[c], q[c]);
+        b.add(z[c], r[c]);
+        c2.add(e[c], r[c]);
+    }
+    double t;
+    if (grid_reduce(a.value(), partials, counter, sh, &t)) out[0] = t;
+    __syncthreads();
+    if (grid_reduce(b.value(), partials + kMaxPartials / 4, counter + 1, sh, &t)) out[1] = t;
+    __syncthreads();
+    if (grid_reduce(c2.value(), partials + kMaxPartials / 2, counter + 2, sh, &t)) out[2] = t;
+}
+// dL/dz = 2 (q - r) / e'r at the unknowns, 0 at the other cells of a group (their output is
+// replaced by the master's)
+__global__ void k_anorm_grad(long long n, const float* __restrict__ q, const float* __restrict__ r,
+                             const uint32_t* __restrict__ bits, const double* sums, float* __restrict__ dz) {
+    const double er = sums[2];
+    const float f = er > 0.0 ? (float)(2.0 / er) : 0.0f;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+        dz[c] = is_slave(bits, c) ? 0.0f : f * (q[c] - r[c]);
+}
+__global__ void k_copy_f(long long n, const float* __restrict__ a, float* __restrict__ b) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+        b[c] = a[c];
 }
 
 // x_t += scale * x_f (FP64)
@@ -1180,7 +1218,8 @@ vofp_status solve_fcg(vofp_ctx* c, const double* b, double* x, const vofp_solve_
         c->set_error("the network is not bound to this grid (vofp_nn_bind)");
         return VOFP_ERR_INVALID_ARG;
     }
-    const int W = std::min(kFcgHist - 1, std::max(1, o->stag_window > 0 ? o->stag_window : 20));
+    const int W = std::min(kFcgHist - 1, std::max(1, o->stag_window > 0 ? o->stag_window : 2));
+    const double ratio = o->stag_ratio > 0.0 ? o->stag_ratio : 0.6;
     const long long max_iter = o->max_iter > 0 ? o->max_iter : 100000;
     const uint32_t* bits = c->slave_bits;
     // the network's first pass runs before any capture: it sets up its kernels and tensor maps
@@ -1292,7 +1331,7 @@ vofp_status solve_fcg(vofp_ctx* c, const double* b, double* x, const vofp_solve_
         const double target = std::max(o->inner_rtol > 0 ? o->inner_rtol : 1e-3,
                                        std::min(0.5, 0.3 * kMixedLoopMargin * o->rtol * std::sqrt(bnorm2 / rnorm2)));
         launch(c, k_fcg_start, stream_grid(N), kNT, st, N, (const double*)c->r, scale > 0 ? 1.0 / scale : 0.0, c->rf,
-               c->xf, bits, c->partials, c->counters, fs, target * target, max_iter, W);
+               c->xf, bits, c->partials, c->counters, fs, target * target, max_iter, W, ratio * ratio);
         VOFP_CUDA_TRY(c, cudaGraphLaunch(ge, st));
         FcgScalars hf{};
         VOFP_CUDA_TRY(c, cudaMemcpyAsync(&hf, fs, sizeof(hf), cudaMemcpyDeviceToHost, st));
@@ -1344,6 +1383,56 @@ vofp_status solve_fcg(vofp_ctx* c, const double* b, double* x, const vofp_solve_
     }
     if (result != VOFP_OK) c->set_error("learned-preconditioner solve did not reach rtol");
     return result;
+}
+
+// One training step of the network as a preconditioner of this operator: forward on the scaled
+// residual r, q = A_scaled z (FP32, merge groups as in the solve), the relative A-norm error of z
+// against the exact error e and its gradient, backward, Adam.
+vofp_status nn_train_anorm(vofp_ctx* c, vofp_nn* nn, const float* r, const float* e, float lr, int update,
+                           float* loss) {
+    vofp_status s = ensure_workspace(c);
+    if (s) return s;
+    prepare_kernels(c);
+    if (nn::bound_cells(nn) != c->d.n) {
+        c->set_error("the network is not bound to this grid (vofp_nn_bind or vofp_nn_set_geometry)");
+        return VOFP_ERR_INVALID_ARG;
+    }
+    if (!c->qf2) {
+        if ((s = c->alloc(&c->qf2, c->d.n))) return s;
+    }
+    if ((s = nn::prepare_training(nn))) return s;
+    const long long N = c->d.n;
+    cudaStream_t st = c->stream;
+    if ((s = nn::forward_on(nn, st, r))) {
+        c->set_error(std::string("network: ") + vofp_nn_last_error(nn));
+        return s;
+    }
+    float* z = c->pf0;
+    launch(c, k_copy_f, stream_grid(N), kNT, st, N, (const float*)nn::output(nn), z);
+    if (c->ngroups > 0)
+        launch(c, k_group_expand_f, ceil_div(c->ngroups, kNT), kNT, st, c->ngroups, (const int*)c->gptr,
+               (const int*)c->gcells, z);
+    launch(c, k_stencil<float, ST_APPLY_SCALED, 2>, stencil_grid(c), dim3(kBX, kBY), st, c->d, stencil_per_block(c),
+           (const float*)c->Txf, (const float*)c->Tyf, (const float*)c->Tzf, (const double*)nullptr, (const float*)z,
+           (const float*)nullptr, (float*)nullptr, (float*)nullptr, c->qf, c->sc, c->partials, c->counters);
+    if (c->ngroups > 0)
+        launch(c, k_group_patch<float>, ceil_div(c->ngroups, kNT), kNT, st, c->ngroups, (const int*)c->gptr,
+               (const int*)c->gcells, (const double*)c->gcorr, c->qf, (const float*)z, 0, c->sc, c->partials,
+               c->counters);
+    double* sums = c->partials + kMaxPartials - 48;
+    launch(c, k_anorm_dots, stream_grid(N), kNT, st, N, (const float*)z, (const float*)c->qf, r, e,
+           (const uint32_t*)c->slave_bits, c->partials, c->counters, sums);
+    launch(c, k_anorm_grad, stream_grid(N), kNT, st, N, (const float*)c->qf, r, (const uint32_t*)c->slave_bits,
+           (const double*)sums, c->qf2);
+    if ((s = nn::train_from_grad_on(nn, st, c->qf2, lr, update))) {
+        c->set_error(std::string("network: ") + vofp_nn_last_error(nn));
+        return s;
+    }
+    double h[3];
+    VOFP_CUDA_TRY(c, cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, st));
+    VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
+    if (loss) *loss = h[2] > 0.0 ? (float)((h[0] - 2.0 * h[1] + h[2]) / h[2]) : 0.0f;
+    return VOFP_OK;
 }
 
 vofp_status time_iteration_kernels(vofp_ctx* c, int precision, bool rb, int reps, float* stencil_ms,

@@ -106,6 +106,59 @@ def train(net, data, shape=TRAIN_SHAPE, epochs=4, lr=1e-3, seed=0, log=print):
     return hist
 
 
+def train_anorm(net, seeds, shape=TRAIN_SHAPE, epochs=2, lr=1e-3, stages=(0, 16, 64, 256), workers=None,
+                log=print):
+    """Online training as a preconditioner: per sample (seeded geometry, waves and velocities) the
+    plain FP64 Jacobi-PCG solves to 1e-10 on the GPU, and each CG stage k in `stages` gives a
+    scaled residual r_k = S (b_hat - A_hat x_k) with its exact error e_k = S^-1 (x - x_k); one Adam
+    step per pair on the relative A-norm error of the network's output against e_k under the
+    sample's own operator (vofp_nn_train_step_anorm).  The loss is 1 for a zero output and 0 for the
+    exact error, whatever the scale of r_k, so early and late residuals weigh alike.  Inputs are
+    built by a spawned process pool (started before this process touches CUDA); cosine decay."""
+    ctxmp = mp.get_context("spawn")
+    workers = workers or max(1, min(16, (os.cpu_count() or 2) - 1))
+    pool = ctxmp.Pool(workers)
+    import torch
+    from paper_1410_1937_gb300 import vofp
+    total = epochs * len(seeds) * len(stages)
+    step, hist = 0, []
+    t0 = time.perf_counter()
+    try:
+        for ep in range(epochs):
+            losses, by_stage = [], {k: [] for k in stages}
+            for i, (seed, (dx, dy, dz), arr) in enumerate(pool.imap(_geometry_worker, [(s, shape) for s in seeds],
+                                                                    chunksize=1)):
+                d = {k: torch.from_numpy(v).cuda().double() for k, v in arr.items()}
+                ctx = vofp.Context(dx, dy, dz)
+                ctx.vofp_build_operator(d["F"], d["ax"], d["ay"], d["az"], d["vf"],
+                                        (0, 1, 0, 0, 0, 0), 1000.0, 1.2, 0.1, 0, 1.0)
+                b = ctx.vofp_rhs_from_face_velocity(d["u"], d["v"], d["w"])
+                x, info = ctx.vofp_solve(b, rtol=1e-10, mode=vofp.MODE_FP64, raise_on_error=False)
+                net.bind(ctx, d["F"])
+                for k in stages:
+                    if k == 0:
+                        r, e = ctx.vofp_scaled_pair(b, x)
+                    else:
+                        xk, _ = ctx.vofp_solve(b, rtol=1e-30, max_iter=k, mode=vofp.MODE_FP64, check_every=2,
+                                               raise_on_error=False)
+                        r, e = ctx.vofp_scaled_pair(b - ctx.vofp_apply(xk), x - xk)
+                    lr_t = lr * 0.5 * (1 + math.cos(math.pi * step / max(total, 1)))
+                    loss = net.train_step_anorm(ctx, r, e, lr=lr_t)
+                    losses.append(loss)
+                    by_stage[k].append(loss)
+                    step += 1
+                ctx.close()
+                if (i + 1) % 200 == 0:
+                    log(f"epoch {ep + 1}: {i + 1}/{len(seeds)} samples, mean loss of the last 200 "
+                        f"{np.mean(losses[-200 * len(stages):]):.4f} ({time.perf_counter() - t0:.0f} s)")
+            hist.append({"loss": float(np.mean(losses)), "by_stage": {k: float(np.mean(v)) for k, v in by_stage.items()}})
+            log(f"epoch {ep + 1}/{epochs}: mean relative A-norm error {hist[-1]}")
+    finally:
+        pool.close()
+        pool.join()
+    return hist
+
+
 def save(net, path):
     np.savez_compressed(path, params=net.get_params(), layers=np.array([27, 16, 32, 64]))
 
@@ -165,21 +218,26 @@ def main():
     ap.add_argument("--workers", type=int, default=0)
     ap.add_argument("--report", default=None)
     ap.add_argument("--stages", default="0", help="CG stages of the training pairs, e.g. 0,16,64,256")
+    ap.add_argument("--loss", default="mse", choices=["mse", "anorm"],
+                    help="mse: scaled solution error of stored pairs; anorm: relative A-norm error, online")
     args = ap.parse_args()
     shape = tuple(args.shape)
     stages = tuple(int(v) for v in args.stages.split(","))
     hist = []
-    if args.samples > 0:
-        data = generate(range(TRAIN_SEED0, TRAIN_SEED0 + args.samples), shape, workers=args.workers or None,
-                        stages=stages)
+    seeds = range(TRAIN_SEED0, TRAIN_SEED0 + args.samples)
+    if args.samples > 0 and args.loss == "mse":
+        data = generate(seeds, shape, workers=args.workers or None, stages=stages)
     from paper_1410_1937_gb300 import vofp
     net = vofp.Network(seed=1)
     if args.init:
         load(net, args.init)
-    if args.samples > 0:
+    if args.samples > 0 and args.loss == "mse":
         hist = train(net, data, shape, args.epochs, args.lr)
         save(net, args.out)
         del data
+    elif args.samples > 0:
+        hist = train_anorm(net, seeds, shape, args.epochs, args.lr, stages, workers=args.workers or None)
+        save(net, args.out)
     rows = evaluate(net, range(HELD_OUT_SEED0, HELD_OUT_SEED0 + args.eval_seeds), tuple(args.eval_shape))
     if args.report:
         with open(args.report, "w") as f:

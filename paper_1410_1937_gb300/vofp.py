@@ -53,7 +53,8 @@ class _Opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("precond", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("inner_rtol", ctypes.c_double),
                 ("check_every", ctypes.c_int), ("x0_zero", ctypes.c_int), ("host_loop", ctypes.c_int),
-                ("nn", ctypes.c_void_p), ("stag_window", ctypes.c_int), ("inner_restart", ctypes.c_int)]
+                ("nn", ctypes.c_void_p), ("stag_window", ctypes.c_int), ("inner_restart", ctypes.c_int),
+                ("stag_ratio", ctypes.c_double)]
 
 
 class _Info(ctypes.Structure):
@@ -100,6 +101,8 @@ _sig = {
                                            _P(ctypes.c_int), _P(ctypes.c_int), _P(ctypes.c_int)]),
     "vofp_scaled_pair": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "vofp_measure_fma_peaks": (ctypes.c_int, [_vp, _P(ctypes.c_double), _P(ctypes.c_double)]),
+    "vofp_nn_train_step_anorm": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_float, ctypes.c_int,
+                                                _P(ctypes.c_float)]),
     "vofp_nn_create": (ctypes.c_int, [_P(_vp), ctypes.c_ulonglong, _vp]),
     "vofp_nn_destroy": (None, [_vp]),
     "vofp_nn_last_error": (ctypes.c_char_p, [_vp]),
@@ -349,13 +352,14 @@ class Context:
 
     def vofp_solve(self, b, x=None, mode=MODE_FP64, rtol=1e-10, max_iter=100000, inner_rtol=0.0,
                    check_every=8, precond=PRECOND_JACOBI, raise_on_error=True, x0_zero=0, host_loop=0,
-                   nn=None, stag_window=20, inner_restart=0):
+                   nn=None, stag_window=0, inner_restart=0, stag_ratio=0.0):
         import torch
         if x is None:
             x = torch.zeros(self.n, dtype=torch.float64, device=b.device)
             x0_zero = 1
         o = _Opts(int(mode), int(precond), float(rtol), int(max_iter), float(inner_rtol), int(check_every), x0_zero,
-                  int(host_loop), nn.h if nn is not None else None, int(stag_window), int(inner_restart))
+                  int(host_loop), nn.h if nn is not None else None, int(stag_window), int(inner_restart),
+                  float(stag_ratio))
         info = _Info()
         st = _lib.vofp_solve(self.h, _dev(b, self.n, "b"), _dev(x, self.n, "x"), ctypes.byref(o), ctypes.byref(info))
         out = {"iterations": info.iterations, "outer_iterations": info.outer_iterations,
@@ -385,7 +389,7 @@ class Context:
         b = self._bc(bc, None)
         ph = _Phys(rho_liquid, rho_gas, merge_threshold, int(density_smoothing), dt)
         o = _Opts(int(mode), int(precond), float(rtol), int(max_iter), float(inner_rtol), int(check_every), 1, 0,
-                  None, 20, int(inner_restart))
+                  None, 0, int(inner_restart), 0.0)
         info = _Info()
         st = _lib.vofp_solve_host(self.h, hp(F, self.n, "F"), hp(ax, self.nfx, "ax"), hp(ay, self.nfy, "ay"),
                                   hp(az, self.nfz, "az"), hp(vol_frac, self.n, "vol_frac"), hp(u, self.nfx, "u"),
@@ -501,6 +505,17 @@ class Network:
         self._check(_lib.vofp_nn_train_step(self.h, _dev(r, self.n, "r", "float32"),
                                             _dev(target, self.n, "target", "float32"), float(lr), int(update),
                                             ctypes.byref(loss)))
+        return loss.value
+
+    def train_step_anorm(self, ctx, r, e, lr=1e-3, update=True):
+        """One step on the relative A-norm error of the output against the exact error e of the
+        scaled residual r under ctx's operator (vofp_nn_train_step_anorm); returns the loss."""
+        loss = ctypes.c_float(0.0)
+        st = _lib.vofp_nn_train_step_anorm(self.h, ctx.h, _dev(r, self.n, "r", "float32"),
+                                           _dev(e, self.n, "e", "float32"), float(lr), int(update),
+                                           ctypes.byref(loss))
+        if st != OK:
+            raise VofpError(st, _lib.vofp_last_error(ctx.h).decode())
         return loss.value
 
 

@@ -245,6 +245,56 @@ def test_gpu_adam_step_matches_reference(gpu):
 
 
 @pytest.mark.gpu
+def test_gpu_anorm_step_matches_oracle(gpu, oracle):
+    """Relative A-norm error step: loss and parameter gradients against the oracle.  The oracle's
+    scaled operator S A_hat S (S = diag(A_hat)^-1/2) and exact error e = (S A_hat S)^-1 r give the
+    output gradient 2 (A z - r) / e'r; the oracle network backward is driven with it through its
+    mean-squared-error form (target = z - dz rms^2 count / 2 has that gradient)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+    torch, vofp = gpu
+    prob = _tiny_hull()
+    s = oracle.System(prob)
+    ctx, t = vofp.context_for(prob)
+    net = vofp.Network(seed=17)
+    net.bind(ctx, t["F"])
+    sc = 1.0 / np.sqrt(s.Ahat.diagonal())
+    As = (sp.diags(sc) @ s.Ahat @ sp.diags(sc)).tocsc()
+    rng = np.random.default_rng(18)
+    r_hat = rng.normal(size=s.M)
+    e_hat = spl.spsolve(As, r_hat)
+    full = lambda v: s.expand(v).ravel()
+    r = full(r_hat).astype(np.float32)
+    e = full(e_hat).astype(np.float32)
+    mask = (s.root >= 0).reshape(prob.shape).astype(float)
+    params = net.get_params().astype(np.float64)
+    geo = R.geometry(prob.F, s.apertures, prob.dx, prob.dy, prob.dz)
+    z_ref, cache = R.forward(params, geo, mask, r.reshape(prob.shape).astype(np.float64))
+    zm = s.restrict(z_ref)
+    q = As @ zm
+    er = float(e_hat @ r_hat)
+    loss_ref = (zm @ q - 2 * zm @ r_hat + er) / er
+    dz = np.zeros(prob.n)
+    dz[s.masters] = 2 * (q - r_hat) / er
+    count = mask.sum()
+    target = z_ref - dz.reshape(prob.shape) * cache["rms"] ** 2 * count / 2
+    _, g_ref, _ = R.loss_and_grads(params, geo, mask, r.reshape(prob.shape).astype(np.float64), target)
+    loss = net.train_step_anorm(ctx, torch.from_numpy(r).cuda(), torch.from_numpy(e).cuda(), update=False)
+    assert abs(loss - loss_ref) <= 2e-2 * abs(loss_ref) + 1e-3, (loss, loss_ref)
+    g = net.get_params(grads=True).astype(np.float64)
+    errs, off = [], 0
+    for i, (cin, cout) in enumerate(R.LAYERS):
+        nw = 27 * cin * cout
+        errs.append((i, _rel(g[off:off + nw], g_ref[off:off + nw])))
+        off += nw + cout
+    errs.append(("head", _rel(g[off:], g_ref[off:])))
+    print("A-norm step: loss", loss, "oracle", loss_ref, "gradient errors", errs)
+    assert all(err < 5e-2 for _, err in errs), errs
+    # z = e makes the loss 0 and z = 0 makes it 1 (the definition, on the oracle side)
+    assert abs((e_hat @ (As @ e_hat) - 2 * e_hat @ r_hat + er) / er) < 1e-10
+
+
+@pytest.mark.gpu
 def test_gpu_training_reduces_loss(gpu):
     torch, vofp = gpu
     prob = _tiny_hull()
