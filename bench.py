@@ -508,8 +508,20 @@ def learned_timing(vofp, ctx, t, b, stream, args, solutions):
     learned.load(net, learned.WEIGHTS)
     net.bind(ctx, t["F"])
     xl = torch.zeros_like(b)
-    ctx.vofp_solve(b, x=xl, rtol=RTOL, mode=vofp.MODE_FCG_NN, nn=net, x0_zero=1, raise_on_error=False)
-    _, il = ctx.vofp_solve(b, x=xl, rtol=RTOL, mode=vofp.MODE_FCG_NN, nn=net, x0_zero=1, raise_on_error=False)
+    kw = dict(rtol=RTOL, mode=vofp.MODE_FCG_NN, nn=net, precond=vofp.PRECOND_RBSGS, raise_on_error=False)
+    ctx.vofp_solve(b, x=xl, x0_zero=1, **kw)
+    _, il = ctx.vofp_solve(b, x=xl, x0_zero=1, **kw)
+    # what the network's steps do before the hand-over: relative residual after k flexible-CG
+    # iterations with the network (hand-over disabled) against k mixed Jacobi and red-black iterations
+    curve = {}
+    for k in (1, 2, 4, 10, 40):
+        _, a = ctx.vofp_solve(b, x=torch.zeros_like(b), x0_zero=1, max_iter=k, stag_window=10 ** 6,
+                              **{**kw, "rtol": 1e-12})
+        _, cj = ctx.vofp_solve(b, x=torch.zeros_like(b), x0_zero=1, max_iter=k, rtol=1e-12, mode=vofp.MODE_MIXED,
+                               check_every=2, raise_on_error=False)
+        _, cr = ctx.vofp_solve(b, x=torch.zeros_like(b), x0_zero=1, max_iter=k, rtol=1e-12, mode=vofp.MODE_MIXED,
+                               precond=vofp.PRECOND_RBSGS, check_every=2, raise_on_error=False)
+        curve[k] = {"fcg_nn": a["rel_residual"], "mixed_jacobi": cj["rel_residual"], "mixed_rbsgs": cr["rel_residual"]}
     # one network application on a scaled residual of the workload's size, CUDA events on its stream
     r = torch.randn(b.numel(), dtype=torch.float32, device=b.device)
     z = torch.empty_like(r)
@@ -526,7 +538,9 @@ def learned_timing(vofp, ctx, t, b, stream, args, solutions):
     rec = {"time_to_tol_ms": il["seconds"] * 1e3, "iterations": il["iterations"],
            "outer_iterations": il["outer_iterations"], "nn_applications": il["nn_applications"],
            "fell_back": il["fell_back"], "rel_residual": il["rel_residual"], "status": il["status_name"],
-           "weights": os.path.basename(learned.WEIGHTS), "network_forward_ms": fwd_ms}
+           "weights": os.path.basename(learned.WEIGHTS), "network_forward_ms": fwd_ms,
+           "hand_over": "to mixed red-black PCG when two network steps cut the residual norm by less than 0.4",
+           "residual_after_k_iterations": curve}
     net.close()
     del xl
     return rec
@@ -574,7 +588,8 @@ def c4_record(vofp, stream, args):
         learned.load(net, learned.WEIGHTS)
         net.bind(ctx, t["F"])
         sample()
-        _, inf = ctx.vofp_solve(b, x=x, rtol=RTOL, mode=vofp.MODE_FCG_NN, nn=net, x0_zero=1, raise_on_error=False)
+        _, inf = ctx.vofp_solve(b, x=x, rtol=RTOL, mode=vofp.MODE_FCG_NN, nn=net, precond=vofp.PRECOND_RBSGS,
+                                x0_zero=1, raise_on_error=False)
         sample()
         out["fcg+nn"] = {"time_to_tol_ms": inf["seconds"] * 1e3, "iterations": inf["iterations"],
                          "outer_iterations": inf["outer_iterations"], "nn_applications": inf["nn_applications"],
@@ -732,6 +747,31 @@ def run_profile(args):
                       "status": info["status_name"], "launches": ctx.vofp_launch_count()}), flush=True)
 
 
+def run_profile_nn(args):
+    """Profiling run of the learned preconditioner: the committed network bound to the workload,
+    --profile-nn forward passes (one per scaled residual), timed with CUDA events."""
+    import torch
+    from paper_1410_1937_gb300 import learned
+    from paper_1410_1937_gb300 import vofp
+    prob = make_problem(tuple(args.shape))
+    ctx, t = vofp.context_for(prob)
+    net = vofp.Network(seed=0)
+    learned.load(net, learned.WEIGHTS)
+    net.bind(ctx, t["F"])
+    r = torch.randn(prob.n, dtype=torch.float32, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+    z = net.forward(r)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.profile_nn):
+        net.forward(r, out=z)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.profile_nn
+    print(json.dumps({"profile_nn": True, "shape": args.shape, "forward_ms": ms,
+                      "z_rms": float(z.square().mean().sqrt())}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -761,6 +801,8 @@ def main():
                     help="profiling run: also one VOF step after the capped solve")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiling run: one step whose solve stops after this many CG iterations")
+    ap.add_argument("--profile-nn", type=int, default=0,
+                    help="profiling run: this many forward passes of the committed network")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -770,6 +812,9 @@ def main():
         return
     if args.profile_iters > 0:
         run_profile(args)
+        return
+    if args.profile_nn > 0:
+        run_profile_nn(args)
         return
     if world > 1:
         import torch

@@ -155,6 +155,112 @@ __global__ void k_face_coeffs(Dims d, const double* __restrict__ dx, const doubl
     }
 }
 
+// The same two kernels on x-pairs of cells (nx even): a thread takes cells c and c + 1 of one row
+// (c even, so every cell-indexed and y/z-face stream is 16-byte aligned) and moves the
+// structure-of-arrays streams as double2 words; the x-face apertures (rows of nx + 1) stay
+// scalar.  Each cell's arithmetic is that of the scalar kernels, operation for operation.
+__device__ __forceinline__ double2 ld2(const double* __restrict__ p, long long c) {
+    return *reinterpret_cast<const double2*>(p + c);
+}
+__device__ __forceinline__ void st2(double* __restrict__ p, long long c, double a, double b) {
+    *reinterpret_cast<double2*>(p + c) = make_double2(a, b);
+}
+__global__ void k_face_coeffs2(Dims d, const double* __restrict__ dx, const double* __restrict__ dy,
+                               const double* __restrict__ dz, const double* __restrict__ rho,
+                               const double* __restrict__ axe, const double* __restrict__ aye,
+                               const double* __restrict__ aze, double* __restrict__ Tx,
+                               double* __restrict__ Ty, double* __restrict__ Tz, double* __restrict__ kx,
+                               double* __restrict__ ky, double* __restrict__ kz) {
+    const long long npairs = d.n / 2;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < npairs;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long c = 2 * q;
+        int i, j, k;
+        cell_ijk(d, c, i, j, k);
+        const double2 r2 = ld2(rho, c);
+        const double rc[2] = {r2.x, r2.y};
+        double tx[2] = {0.0, 0.0}, ty[2] = {0.0, 0.0}, tz[2] = {0.0, 0.0};
+        double qx[2] = {0.0, 0.0}, qy[2] = {0.0, 0.0}, qz[2] = {0.0, 0.0};
+        // +x faces: cell c's is interior (i + 1 < nx), cell c + 1's when i + 2 < nx
+        {
+            const double a0 = axe[fx_idx(d, i + 1, j, k)];
+            const double inv0 = 1.0 / (0.5 * (dx[i] * rc[0] + dx[i + 1] * rc[1]));
+            tx[0] = (a0 * (dz[k] * dy[j])) * inv0;
+            qx[0] = a0 > 0.0 ? inv0 : 0.0;
+            if (i + 1 < d.nx - 1) {
+                const double a1 = axe[fx_idx(d, i + 2, j, k)];
+                const double inv1 = 1.0 / (0.5 * (dx[i + 1] * rc[1] + dx[i + 2] * rho[c + 2]));
+                tx[1] = (a1 * (dz[k] * dy[j])) * inv1;
+                qx[1] = a1 > 0.0 ? inv1 : 0.0;
+            }
+        }
+        if (j < d.ny - 1) {
+            const double2 a = ld2(aye, fy_idx(d, i, j + 1, k)), rn = ld2(rho, c + d.nx);
+            const double av[2] = {a.x, a.y}, rv[2] = {rn.x, rn.y};
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const double inv = 1.0 / (0.5 * (dy[j] * rc[e] + dy[j + 1] * rv[e]));
+                ty[e] = (av[e] * (dz[k] * dx[i + e])) * inv;
+                qy[e] = av[e] > 0.0 ? inv : 0.0;
+            }
+        }
+        if (k < d.nz - 1) {
+            const double2 a = ld2(aze, fz_idx(d, i, j, k + 1)), rn = ld2(rho, c + d.plane);
+            const double av[2] = {a.x, a.y}, rv[2] = {rn.x, rn.y};
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const double inv = 1.0 / (0.5 * (dz[k] * rc[e] + dz[k + 1] * rv[e]));
+                tz[e] = (av[e] * (dy[j] * dx[i + e])) * inv;
+                qz[e] = av[e] > 0.0 ? inv : 0.0;
+            }
+        }
+        st2(Tx, c, tx[0], tx[1]);
+        st2(Ty, c, ty[0], ty[1]);
+        st2(Tz, c, tz[0], tz[1]);
+        st2(kx, c, qx[0], qx[1]);
+        st2(ky, c, qy[0], qy[1]);
+        st2(kz, c, qz[0], qz[1]);
+    }
+}
+
+__global__ void k_diag2(Dims d, Bc6 bc, const double* __restrict__ dx, const double* __restrict__ dy,
+                        const double* __restrict__ dz, const double* __restrict__ rho,
+                        const double* __restrict__ axe, const double* __restrict__ aye,
+                        const double* __restrict__ aze, const double* __restrict__ Tx,
+                        const double* __restrict__ Ty, const double* __restrict__ Tz, double* __restrict__ diag) {
+    const long long npairs = d.n / 2;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < npairs;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long c = 2 * q;
+        int i, j, k;
+        cell_ijk(d, c, i, j, k);
+        const double2 x2 = ld2(Tx, c), y2 = ld2(Ty, c), z2 = ld2(Tz, c), r2 = ld2(rho, c);
+        const double2 ym = j > 0 ? ld2(Ty, c - d.nx) : make_double2(0.0, 0.0);
+        const double2 zm = k > 0 ? ld2(Tz, c - d.plane) : make_double2(0.0, 0.0);
+        const double txs[2] = {x2.x, x2.y}, tys[2] = {y2.x, y2.y}, tzs[2] = {z2.x, z2.y}, rcs[2] = {r2.x, r2.y};
+        const double tym[2] = {ym.x, ym.y}, tzm[2] = {zm.x, zm.y};
+        const double txm[2] = {i > 0 ? Tx[c - 1] : 0.0, x2.x};
+        double out[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int ii = i + e;
+            const double rc = rcs[e];
+            double s = txs[e] + tys[e] + tzs[e];
+            if (ii > 0) s += txm[e];
+            if (j > 0) s += tym[e];
+            if (k > 0) s += tzm[e];
+            if (ii == 0 && bc.k[0] == VOFP_BC_DIRICHLET) s += (axe[fx_idx(d, 0, j, k)] * (dz[k] * dy[j])) / (0.5 * dx[0] * rc);
+            if (ii == d.nx - 1 && bc.k[1] == VOFP_BC_DIRICHLET) s += (axe[fx_idx(d, d.nx, j, k)] * (dz[k] * dy[j])) / (0.5 * dx[ii] * rc);
+            if (j == 0 && bc.k[2] == VOFP_BC_DIRICHLET) s += (aye[fy_idx(d, ii, 0, k)] * (dz[k] * dx[ii])) / (0.5 * dy[0] * rc);
+            if (j == d.ny - 1 && bc.k[3] == VOFP_BC_DIRICHLET) s += (aye[fy_idx(d, ii, d.ny, k)] * (dz[k] * dx[ii])) / (0.5 * dy[j] * rc);
+            if (k == 0 && bc.k[4] == VOFP_BC_DIRICHLET) s += (aze[fz_idx(d, ii, j, 0)] * (dy[j] * dx[ii])) / (0.5 * dz[0] * rc);
+            if (k == d.nz - 1 && bc.k[5] == VOFP_BC_DIRICHLET) s += (aze[fz_idx(d, ii, j, d.nz)] * (dy[j] * dx[ii])) / (0.5 * dz[k] * rc);
+            out[e] = s;
+        }
+        st2(diag, c, out[0], out[1]);
+    }
+}
+
 // diagonal of the unmerged operator: sum of the six face coefficients plus p = 0 faces
 __global__ void k_diag(Dims d, Bc6 bc, const double* __restrict__ dx, const double* __restrict__ dy,
                        const double* __restrict__ dz, const double* __restrict__ rho,
@@ -640,9 +746,19 @@ vofp_status build_operator(vofp_ctx* c, const double* F, const double* ax, const
         }
     }
     launch(c, k_eff_apertures, grid_for(nfx + nfy + nfz), kNT, st, d, ax, ay, az, c->inactive, c->axe, c->aye, c->aze);
-    launch(c, k_face_coeffs, gN, kNT, st, d, c->dx, c->dy, c->dz, rho, c->axe, c->aye, c->aze, c->Tx, c->Ty, c->Tz,
-           c->kx, c->ky, c->kz);
-    launch(c, k_diag, gN, kNT, st, d, b6, c->dx, c->dy, c->dz, rho, c->axe, c->aye, c->aze, c->Tx, c->Ty, c->Tz, c->diag);
+    if (d.nx % 2 == 0) {
+        // x-pairs of cells, 16-byte words on the cell and y/z-face streams
+        const int gP = grid_for(d.n / 2);
+        launch(c, k_face_coeffs2, gP, kNT, st, d, c->dx, c->dy, c->dz, rho, c->axe, c->aye, c->aze, c->Tx, c->Ty,
+               c->Tz, c->kx, c->ky, c->kz);
+        launch(c, k_diag2, gP, kNT, st, d, b6, c->dx, c->dy, c->dz, rho, c->axe, c->aye, c->aze, c->Tx, c->Ty, c->Tz,
+               c->diag);
+    } else {
+        launch(c, k_face_coeffs, gN, kNT, st, d, c->dx, c->dy, c->dz, rho, c->axe, c->aye, c->aze, c->Tx, c->Ty,
+               c->Tz, c->kx, c->ky, c->kz);
+        launch(c, k_diag, gN, kNT, st, d, b6, c->dx, c->dy, c->dz, rho, c->axe, c->aye, c->aze, c->Tx, c->Ty, c->Tz,
+               c->diag);
+    }
 
     // merge map (Sec. 2.3): small cells listed on the device, chains resolved on the host
     std::vector<long long> cells, targets, roots;

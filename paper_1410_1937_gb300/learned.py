@@ -106,6 +106,14 @@ def train(net, data, shape=TRAIN_SHAPE, epochs=4, lr=1e-3, seed=0, log=print):
     return hist
 
 
+def _bounded_imap(pool, args, batch=64):
+    """pool.imap over `args` in batches: the workers build inputs faster than the GPU trains on
+    them, and an unbounded imap would queue every sample's arrays (~70 MB at 256x128x64) in host
+    memory."""
+    for i in range(0, len(args), batch):
+        yield from pool.imap(_geometry_worker, args[i:i + batch], chunksize=1)
+
+
 def train_anorm(net, seeds, shape=TRAIN_SHAPE, epochs=2, lr=1e-3, stages=(0, 16, 64, 256), workers=None,
                 log=print):
     """Online training as a preconditioner: per sample (seeded geometry, waves and velocities) the
@@ -126,8 +134,7 @@ def train_anorm(net, seeds, shape=TRAIN_SHAPE, epochs=2, lr=1e-3, stages=(0, 16,
     try:
         for ep in range(epochs):
             losses, by_stage = [], {k: [] for k in stages}
-            for i, (seed, (dx, dy, dz), arr) in enumerate(pool.imap(_geometry_worker, [(s, shape) for s in seeds],
-                                                                    chunksize=1)):
+            for i, (seed, (dx, dy, dz), arr) in enumerate(_bounded_imap(pool, [(s, shape) for s in seeds])):
                 d = {k: torch.from_numpy(v).cuda().double() for k, v in arr.items()}
                 ctx = vofp.Context(dx, dy, dz)
                 ctx.vofp_build_operator(d["F"], d["ax"], d["ay"], d["az"], d["vf"],
