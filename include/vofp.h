@@ -433,15 +433,20 @@ vofp_status vofp_time_iteration_kernels(vofp_ctx* ctx, int precision, int precon
 vofp_status vofp_measure_fma_peaks(vofp_stream stream, double* fp64_tflops, double* fp32_tflops);
 
 /* Host-only planning query (no context, no device): how the colour-compact red-black iteration
- * kernel splits its work over `slots` resident blocks for tiles_x x tiles_y tiles (32 pairs x 8
- * rows each) and nz planes.  Block b marches the work items [b per, (b+1) per) of
- * w = tile (nz + pad) + pad + plane (tiles in x-fastest order; the first `pad` items of a tile
- * column stand for no plane); *blocks = number of blocks (<= slots).  The plan minimises the
- * plane steps of the costliest block (each tile-column segment adds five steps to its planes)
- * and keeps a tile's y-neighbour tiles marched at the same plane in the same step where it can
- * (their halo rows then come from L2).  VOFP_ERR_INVALID_ARG for null outputs, non-positive
- * sizes, or more work items than an int holds. */
-vofp_status vofp_rbc_split_plan(int tiles_x, int tiles_y, int nz, int slots, int* blocks, int* per, int* pad);
+ * kernel splits its work over `slots` resident blocks for tiles_x x tiles_y tiles (32 pairs x 16
+ * rows each by default) and nz planes.  The tiles form groups of *gx x *gy neighbours (*gx divides
+ * tiles_x, *gy divides tiles_y); block b is member b % (gx gy) of group g = b / (gx gy), which
+ * marches the work items [g per, (g+1) per) of w = column (nz + pad) + pad + plane over the
+ * (tiles_x / gx) x (tiles_y / gy) group columns (x-fastest; the first `pad` items of a column
+ * stand for no plane); member m takes tile (column x gx + m % gx, column y gy + m / gx).
+ * *blocks = number of blocks (<= slots, a multiple of gx gy).  The plan minimises the plane steps
+ * of the costliest block (each column segment adds five steps to its planes) weighted by the DRAM
+ * bytes of the tile edges whose two sides are not marched at the same plane in the same step
+ * (inside a group they always are; their halo otherwise comes from DRAM instead of L2).
+ * VOFP_ERR_INVALID_ARG for null outputs, non-positive sizes, or more work items than an int
+ * holds.  (The library's own plan takes the group from VOFP_RBC_GROUP="gx,gy" when set.) */
+vofp_status vofp_rbc_split_plan(int tiles_x, int tiles_y, int nz, int slots, int* blocks, int* per, int* pad,
+                                int* gx, int* gy);
 
 #ifdef __cplusplus
 }

@@ -54,6 +54,13 @@ struct CgScalars {
     int dir_valid;      // the inner direction buffer holds a direction of this solve
 };
 
+// Work split of the compact red-black iteration kernel (chosen on the host): groups of gx x gy
+// tiles (gx divides the tile columns along x, gy the tile rows), each group taking `per` work items
+// of its columns, `pad` of them at the head of every column standing for no plane.
+struct RbcSplit {
+    int per, pad, gx, gy;
+};
+
 struct Dims {
     int nx, ny, nz;
     long long n;
@@ -169,7 +176,8 @@ struct vofp_ctx {
     long long rbc_cap = 0;            // allocated compact length
     int rbc_blocks_per_sm = 0;
     int rbc_rpt = 2;                  // rows per thread of the compact iteration kernel (tile 32 x 8 rpt)
-    int rbc_nblocks = 0, rbc_per = 0, rbc_pad = 0;  // iteration kernel split (see rbc_split)
+    int rbc_nblocks = 0;              // iteration kernel blocks and work split (see rbc_split)
+    vofp::RbcSplit rbc_split{};
     int tma_blocks_deep32 = 0;        // resident blocks per SM of the six-stage FP32 stencil
     int rb_tma_blocks_per_sm = 0;
     std::map<std::tuple<const void*, int, int>, CUtensorMap> tma_maps;

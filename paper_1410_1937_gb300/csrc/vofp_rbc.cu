@@ -14,6 +14,7 @@
 // formula; merge groups summed and their value written to every member) and the vector update on
 // the compact vectors.
 #include <algorithm>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 
@@ -442,29 +443,38 @@ __global__ void k_rbc_expand_exc(long long nh, int ne, const int* __restrict__ e
     if (e < ne) xf[exc[e]] = __fmaf_rn(alpha, p0[nh + e], x[nh + e]);
 }
 
-// Split of the iteration kernel's work over at most `slots` resident blocks. Block b takes the
-// items [b per, (b+1) per) of w = tile * (nz + pad) + pad + plane, tiles in x-fastest order, so
-// every tile column starts with `pad` items that stand for no plane. Two things set the kernel's
-// time:
-//  - its costliest block: a block marches each tile-column segment it holds with kSegSteps plane
-//    steps besides its planes (four prologue steps that fill the p and w rings before the first
-//    output plane, and the closing t step); padding charges a column's first segment for them in
-//    the split itself, so that fewer blocks pay for two segments;
-//  - whether the two y-neighbour tiles of a tile (tiles_x tile columns away, w + tiles_x (nz + pad))
-//    are marched at the same plane in the same step, so that the y-halo rows of the boxes come from
-//    L2: that holds when tiles_x (nz + pad) is within kAlignSteps of a multiple of per. Without it
-//    the halo rows come from DRAM (measured at 512x256x128: 0.115-0.122 ms against 0.101 ms).
-// Candidates: pad 0 .. 2 kSegSteps, per from the fewest planes that fit in `slots` blocks up to
-// four more; score = costliest block x kMisaligned when the y-neighbours drift apart; ties keep
-// the smaller pad, then the smaller per.
-constexpr int kSegSteps = 5;
+// Split of the iteration kernel's work over at most `slots` resident blocks. The tiles form groups
+// of gx x gy neighbours (gx dividing the tile columns along x, gy the tile rows); the blocks of a
+// group march the same planes in the same steps, one tile each. Group g takes the items
+// [g per, (g+1) per) of w = column * (nz + pad) + pad + plane over the group columns (x-fastest),
+// so that every column starts with `pad` items that stand for no plane. Three things set the
+// kernel's time:
+//  - its costliest block: a block marches each column segment it holds with kSegSteps plane steps
+//    besides its planes (four prologue steps that fill the p and w rings before the first output
+//    plane, and the two closing t steps); padding charges a column's first segment for them in the
+//    split itself, so that fewer blocks pay for two segments;
+//  - whether the tiles on either side of a group edge are marched at the same plane in the same
+//    step, so that the halo of their boxes comes from L2. Inside a group that always holds; across
+//    an x edge (the next column, nz + pad items on) or a y edge (ncx columns on) it holds when that
+//    distance is within kAlignSteps of a multiple of per. Otherwise the halo of that edge comes
+//    from DRAM. Measured at 512x256x128 with 32 x 16 tiles (DRAM bytes of one launch for three
+//    groupings, fitted per misaligned edge): 9.7 B per cell when every x edge is apart (the x halo
+//    is two partial sectors per box row on each side), 3.5 B per cell when every y edge is (two
+//    rows of r and p_old, seven coefficient rows), against 24 B per cell of the iteration itself;
+//  - the slots a group size leaves unused (slots / (gx gy) groups).
+// Candidates: every (gx, gy) with gx gy <= kMaxGroup, pad 0 .. 2 kSegSteps, per from the fewest
+// items that fit in the groups up to four more; score = costliest block x (1 + the DRAM bytes of
+// the misaligned edges' halo per 24 B); ties keep the smaller group, pad, per.
+// VOFP_RBC_GROUP="gx,gy" fixes the group (when both divide).
+constexpr int kSegSteps = 6;
 constexpr long long kAlignSteps = 3;
-constexpr double kMisaligned = 1.15;
+constexpr double kHaloX = 9.7 / 24.0, kHaloY = 3.5 / 24.0;
+constexpr long long kMaxGroup = 16;
 
-long long split_cost(long long tiles, long long nz, long long per, int pad, long long* nb) {
-    const long long nzp = nz + pad, total = tiles * nzp;
-    long long worst = 0, blocks = 0;
-    for (long long w0 = 0; w0 < total; w0 += per, ++blocks) {
+long long split_cost(long long cols, long long nz, long long per, int pad, long long* nb) {
+    const long long nzp = nz + pad, total = cols * nzp;
+    long long worst = 0, groups = 0;
+    for (long long w0 = 0; w0 < total; w0 += per, ++groups) {
         const long long w1 = std::min(w0 + per, total);
         long long cost = 0;
         for (long long w = w0; w < w1;) {
@@ -475,32 +485,56 @@ long long split_cost(long long tiles, long long nz, long long per, int pad, long
         }
         worst = std::max(worst, cost);
     }
-    *nb = blocks;
+    *nb = groups;
     return worst;
 }
 
-void rbc_split(long long tiles_x, long long tiles_y, long long nz, long long slots, int* nblocks, int* per_out,
-               int* pad_out) {
-    const long long tiles = tiles_x * tiles_y;
+bool aligned(long long dist_items, long long per) {
+    const long long r = dist_items % per;
+    return std::min(r, per - r) <= kAlignSteps;
+}
+
+void rbc_split(long long tiles_x, long long tiles_y, long long nz, long long slots, int force_gx, int force_gy,
+               RbcSplit* out, int* nblocks) {
     double best = 0.0;
     bool have = false;
-    for (int pad = 0; pad <= 2 * kSegSteps; ++pad) {
-        const long long nzp = nz + pad, total = tiles * nzp;
-        const long long pmin = std::max(1LL, (total + slots - 1) / slots);
-        for (long long per = pmin; per <= pmin + 4 && per <= total; ++per) {
-            const long long dy = (tiles_x * nzp) % per, dist = std::min(dy, per - dy);
-            const bool misaligned = tiles_y > 1 && dist > kAlignSteps;
-            long long nb = 0;
-            const double score = (double)split_cost(tiles, nz, per, pad, &nb) * (misaligned ? kMisaligned : 1.0);
-            if (!have || score < best) {
-                have = true;
-                best = score;
-                *nblocks = (int)nb;
-                *per_out = (int)per;
-                *pad_out = pad;
+    for (long long gy = 1; gy <= tiles_y && gy <= kMaxGroup; ++gy) {
+        if (tiles_y % gy) continue;
+        for (long long gx = 1; gx <= tiles_x && gx * gy <= kMaxGroup; ++gx) {
+            if (tiles_x % gx || gx * gy > slots) continue;
+            if (force_gx > 0 && (gx != force_gx || gy != force_gy)) continue;
+            const long long ncx = tiles_x / gx, ncy = tiles_y / gy, cols = ncx * ncy, gslots = slots / (gx * gy);
+            for (int pad = 0; pad <= 2 * kSegSteps; ++pad) {
+                const long long nzp = nz + pad, total = cols * nzp;
+                const long long pmin = std::max(1LL, (total + gslots - 1) / gslots);
+                for (long long per = pmin; per <= pmin + 4 && per <= total; ++per) {
+                    // fraction of the x and y tile edges whose two sides drift apart
+                    const double fx = (ncx > 1 && !aligned(nzp, per)) ? double(ncx - 1) / double(tiles_x - 1) : 0.0;
+                    const double fy =
+                        (ncy > 1 && !aligned(ncx * nzp, per)) ? double(ncy - 1) / double(tiles_y - 1) : 0.0;
+                    long long ng = 0;
+                    const double score = (double)split_cost(cols, nz, per, pad, &ng) * (1.0 + kHaloX * fx + kHaloY * fy);
+                    if (!have || score < best) {
+                        have = true;
+                        best = score;
+                        *nblocks = (int)(ng * gx * gy);
+                        *out = RbcSplit{(int)per, pad, (int)gx, (int)gy};
+                    }
+                }
             }
         }
     }
+}
+
+bool parse_group(int* gx, int* gy) {
+    const char* env = std::getenv("VOFP_RBC_GROUP");
+    *gx = *gy = 0;
+    if (!env) return false;
+    int a = 0, b = 0;
+    if (std::sscanf(env, "%d,%d", &a, &b) != 2 || a < 1 || b < 1) return false;
+    *gx = a;
+    *gy = b;
+    return true;
 }
 
 }  // namespace
@@ -617,7 +651,11 @@ vofp_status rbc_ensure(vofp_ctx* c) {
         const long long tiles_x = ceil_div(d.nx / 2, RbcGeom::NP), tiles_y = ceil_div(d.ny, th);
         // the kernel's work index is an int
         if (tiles_x * tiles_y * (d.nz + 2 * kSegSteps) > 0x7fffffffLL) return VOFP_OK;
-        rbc_split(tiles_x, tiles_y, d.nz, (long long)num_sms() * nb, &c->rbc_nblocks, &c->rbc_per, &c->rbc_pad);
+        int fgx = 0, fgy = 0;
+        if (parse_group(&fgx, &fgy) && (tiles_x % fgx || tiles_y % fgy || (long long)fgx * fgy > kMaxGroup)) fgx = fgy = 0;
+        c->rbc_nblocks = 0;
+        rbc_split(tiles_x, tiles_y, d.nz, (long long)num_sms() * nb, fgx, fgy, &c->rbc_split, &c->rbc_nblocks);
+        if (c->rbc_nblocks <= 0) return VOFP_OK;
     }
     c->rbc_blocks_per_sm = nb;
     c->rbc_nh = nh;
@@ -655,7 +693,7 @@ void launch_main_t(vofp_ctx* c, cudaStream_t st, const float* po, float* pn, boo
     maps.ty = *my;
     maps.tz = *mz;
     launch_dep(c, pdl, k_rbc_tma<kRbcStages, RPT>, dim3(c->rbc_nblocks), dim3(kBX, kBY),
-               cg_rbc_smem<kRbcStages, RPT>(), st, maps, d, c->rbc_per, c->rbc_pad, po, pn, c->rbc_x, c->rbc_q,
+               cg_rbc_smem<kRbcStages, RPT>(), st, maps, d, c->rbc_split, po, pn, c->rbc_x, c->rbc_q,
                c->sc, c->partials, c->counters);
 }
 void launch_main(vofp_ctx* c, cudaStream_t st, const float* po, float* pn, bool pdl) {
@@ -715,9 +753,17 @@ void rbc_time_aux(vofp_ctx* c, cudaStream_t st) { rbc_aux(c, st, c->rbc_p0, c->r
 }  // namespace vofp
 
 extern "C" vofp_status vofp_rbc_split_plan(int tiles_x, int tiles_y, int nz, int slots, int* blocks, int* per,
-                                           int* pad) {
-    if (tiles_x <= 0 || tiles_y <= 0 || nz <= 0 || slots <= 0 || !blocks || !per || !pad) return VOFP_ERR_INVALID_ARG;
+                                           int* pad, int* gx, int* gy) {
+    if (tiles_x <= 0 || tiles_y <= 0 || nz <= 0 || slots <= 0 || !blocks || !per || !pad || !gx || !gy)
+        return VOFP_ERR_INVALID_ARG;
     if ((long long)tiles_x * tiles_y * (nz + 2 * vofp::kSegSteps) > 0x7fffffffLL) return VOFP_ERR_INVALID_ARG;
-    vofp::rbc_split(tiles_x, tiles_y, nz, slots, blocks, per, pad);
+    vofp::RbcSplit sp{};
+    int nb = 0;
+    vofp::rbc_split(tiles_x, tiles_y, nz, slots, 0, 0, &sp, &nb);
+    *blocks = nb;
+    *per = sp.per;
+    *pad = sp.pad;
+    *gx = sp.gx;
+    *gy = sp.gy;
     return VOFP_OK;
 }

@@ -27,6 +27,7 @@ struct RbcMaps {
     CUtensorMap r, p, tx, ty, tz;
 };
 
+
 constexpr size_t rbc_al(size_t b) { return (b + 127) / 128 * 128; }
 
 // Tile of RPT x 8 rows of 32 pairs; thread (tx, ty) owns pair h0 + tx in rows j0 + ty + 8 q,
@@ -64,14 +65,16 @@ using RbcGeom = RbcGeomT<1>;
 template <int NS, int RPT>
 constexpr size_t cg_rbc_smem() {
     using G = RbcGeomT<RPT>;
-    return 128 + NS * G::kStage + 3 * G::PN * 4 + 3 * G::WN * 4 + NS * sizeof(uint64_t);
+    return 128 + NS * G::kStage + 4 * G::PN * 4 + 4 * G::WN * 4 + NS * sizeof(uint64_t);
 }
 
-// A stage of step s carries compact r and p_old of plane s+2 and Tx, Ty, Tz of plane s+1; a step
-// forms p of plane s+2, w of plane s+1 and t of plane s-1 (two barriers per step).
+// A stage of step s carries compact r and p_old of plane s+2 and Tx, Ty, Tz of plane s; a step
+// forms p of plane s+2, t of plane s-2 and w of plane s, each from ring planes that earlier steps
+// wrote, so that one barrier per step orders it: p and w live in rings of four planes (p: s-1 .. s+2,
+// w: s-3 .. s).
 template <int NS, int RPT>
 __global__ void __launch_bounds__(kBX* kBY, RPT == 1 ? 3 : 2)
-k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_block, const int pad,
+k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const RbcSplit sp,
           const float* __restrict__ pold,
           float* __restrict__ pnew, float* __restrict__ xv, float* __restrict__ out, CgScalars* __restrict__ sc,
           double* __restrict__ partials, unsigned int* __restrict__ counter) {
@@ -80,8 +83,8 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_bloc
     extern __shared__ __align__(128) unsigned char rbc_smem[];
     unsigned char* base = rbc_smem + ((128u - (smem_addr(rbc_smem) & 127u)) & 127u);
     float* pring = reinterpret_cast<float*>(base + NS * G::kStage);
-    float* wring = pring + 3 * G::PN;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(wring + 3 * G::WN);
+    float* wring = pring + 4 * G::PN;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(wring + 4 * G::WN);
     __shared__ double sh[32];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + kBX * ty;
     AccF2 acc;
@@ -93,8 +96,9 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_bloc
     uint32_t phase = 0u, pending = 0u;
     bool bad = false;
     auto stage = [&](int s) -> unsigned char* { return base + s * G::kStage; };
-    auto pl = [&](int kk) -> float* { return pring + ((kk + 6) % 3) * G::PN; };
-    auto wl = [&](int kk) -> float* { return wring + ((kk + 6) % 3) * G::WN; };
+    // ring planes by plane index (planes >= -8)
+    auto pl = [&](int kk) -> float* { return pring + ((kk + 8) & 3) * G::PN; };
+    auto wl = [&](int kk) -> float* { return wring + ((kk + 8) & 3) * G::WN; };
 
     // p items: ring index e = tid + 256 q of the 36 x (TH + 4) plane (row e / PW, pair e % PW);
     // box index of the same pair e + (BWC - PW) (e / PW) + 2
@@ -120,23 +124,28 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_bloc
     grid_dep_wait();
     const float beta = (float)sc->beta, alpha = (float)sc->alpha;
     const int nh = d.nx >> 1;
-    const int tiles_x = (nh + G::NP - 1) / G::NP;
-    const long long ntiles = (long long)tiles_x * ((d.ny + TH - 1) / TH);
-    // work items w = tile * (nz + pad) + pad + plane: every tile column starts with `pad` items
-    // that stand for no plane, so that an equal split of w charges each column's first segment
-    // for its prologue steps (pad = 0: the plain equal split)
+    const int pad = sp.pad;
+    // groups of gx x gy neighbouring tiles march the same planes in the same steps (their shared
+    // halo sectors then come from L2); group g, member jg of the block
+    const int gsz = sp.gx * sp.gy;
+    const int grp = (int)blockIdx.x / gsz, jg = (int)blockIdx.x - grp * gsz;
+    const int ncx = (nh + G::NP - 1) / G::NP / sp.gx;   // group columns along x
+    const long long ncols = (long long)ncx * (((d.ny + TH - 1) / TH) / sp.gy);
+    // work items w = column * (nz + pad) + pad + plane of the group columns: every column starts
+    // with `pad` items that stand for no plane, so that an equal split of w charges each column's
+    // first segment for its prologue steps (pad = 0: the plain equal split)
     const int nzp = d.nz + pad;
-    const int total = (int)ntiles * nzp;
-    const int w0 = min((int)blockIdx.x * per_block, total);
-    const int w1 = min(w0 + per_block, total);
+    const int total = (int)ncols * nzp;
+    const int w0 = min(grp * sp.per, total);
+    const int w1 = min(w0 + sp.per, total);
     for (int w = w0; w < w1 && !bad;) {
-        const int tile_id = w / nzp;
-        const int kp0 = w - tile_id * nzp;
+        const int col = w / nzp;
+        const int kp0 = w - col * nzp;
         const int kp1 = min(nzp, kp0 + (w1 - w));
         w += kp1 - kp0;
         const int k0 = max(kp0 - pad, 0), k1 = kp1 - pad;
         if (k1 <= k0) continue;   // padding only (the same for every thread of the block)
-        const int h0 = int(tile_id % tiles_x) * G::NP, j0 = int(tile_id / tiles_x) * TH;
+        const int h0 = ((col % ncx) * sp.gx + jg % sp.gx) * G::NP, j0 = ((col / ncx) * sp.gy + jg / sp.gx) * TH;
         const int i0 = 2 * h0;
         const int h = h0 + tx;
         const long long cplane = (long long)nh * d.ny;
@@ -148,7 +157,10 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_bloc
             inside[q] = h < nh && j < d.ny;
             own[q] = inside[q] ? h + (long long)nh * j : 0;
         }
-        const int s_first = k0 - 4, s_last = k1 - 1;
+        // steps s_first .. k1 + 1: p of planes k0-2 .. k1+1 (steps s_first .. k1-1), w of planes
+        // k0-1 .. k1 (steps k0-1 .. k1), t of planes k0 .. k1-1 (steps k0+2 .. k1+1); stages are
+        // loaded for steps s_first .. k1
+        const int s_first = k0 - 4, s_last = k1;
         auto slot = [&](int s) { return (s - s_first) % NS; };
         auto issue = [&](int s) {
             const int q = slot(s);
@@ -158,9 +170,9 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_bloc
                 mbar_expect_tx(&bars[q], G::kTx);
                 tma_load_3d(b + G::oR, &maps.r, &bars[q], h0 - G::HXC, j0 - 2, s + 2);
                 tma_load_3d(b + G::oP, &maps.p, &bars[q], h0 - G::HXC, j0 - 2, s + 2);
-                tma_load_3d(b + G::oX, &maps.tx, &bars[q], i0 - G::HXF, j0 - 1, s + 1);
-                tma_load_3d(b + G::oY, &maps.ty, &bars[q], i0 - G::HXF, j0 - 2, s + 1);
-                tma_load_3d(b + G::oZ, &maps.tz, &bars[q], i0 - G::HXF, j0 - 1, s + 1);
+                tma_load_3d(b + G::oX, &maps.tx, &bars[q], i0 - G::HXF, j0 - 1, s);
+                tma_load_3d(b + G::oY, &maps.ty, &bars[q], i0 - G::HXF, j0 - 2, s);
+                tma_load_3d(b + G::oZ, &maps.tz, &bars[q], i0 - G::HXF, j0 - 1, s);
             }
         };
         auto wait = [&](int s) -> bool {
@@ -197,88 +209,93 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_bloc
         };
         Co sa[RPT], sb[RPT];
         float2 own_tzm[RPT];
-        float xa[RPT], pa[RPT], xb2[RPT], pb[RPT];
+        float xa[RPT], pa[RPT], xn[RPT], pn2[RPT];
 #pragma unroll
         for (int q = 0; q < RPT; ++q) {
             sa[q] = Co{};
             sb[q] = Co{};
             own_tzm[q] = make_float2(0.f, 0.f);
-            xa[q] = pa[q] = xb2[q] = pb[q] = 0.f;
+            xa[q] = pa[q] = xn[q] = pn2[q] = 0.f;
         }
         float2 ring_tzm = make_float2(0.f, 0.f);
 
         __syncthreads();
         if (tid == 0) fence_proxy_async_smem();
         for (int s = s_first; s <= min(s_first + NS - 1, s_last); ++s) issue(s);
-        // ring slots of planes s, s+1, s+2 (slot s+2 of w still holds plane s-1 until P2), rotated
-        // once per step
-        float *Pa = pl(s_first), *Pb = pl(s_first + 1), *Pc = pl(s_first + 2);
-        float *Wa = wl(s_first), *Wb = wl(s_first + 1), *Wc = wl(s_first + 2);
-        for (int s = s_first; s <= k1; ++s) {
+        for (int s = s_first; s <= k1 + 1; ++s) {
+            // the slot of step s-1 is free (every thread passed the barrier that closed it)
             if (s - 1 >= s_first && s - 1 + NS <= s_last) {
                 if (tid == 0) fence_proxy_async_smem();
                 issue(s - 1 + NS);
             }
+            // x and p_old of the own black cells of plane s-1, for its t step (the next one)
+#pragma unroll
+            for (int q = 0; q < RPT; ++q) {
+                xn[q] = 0.f;
+                pn2[q] = 0.f;
+                if (s - 1 >= k0 && s - 1 < k1 && inside[q]) {
+                    const long long c = (long long)(s - 1) * cplane + own[q];
+                    xn[q] = xv[c];
+                    pn2[q] = pold[c];
+                }
+            }
             bool ok = true;
             if (s <= s_last) ok = wait(s);
             const unsigned char* b = stage(slot(s));
-            // P1: p of plane s+2
-            if (s <= s_last) {
+            // A: p of plane s+2
+            if (s + 2 <= k1 + 1 && ok) {
                 const float* R = reinterpret_cast<const float*>(b + G::oR);
                 const float* P = reinterpret_cast<const float*>(b + G::oP);
-                float* op = Pc;
+                float* op = pl(s + 2);
 #pragma unroll
                 for (int q = 0; q < G::kPPer; ++q)
                     if (pi_on[q]) op[tid + q * kBX * kBY] = fmav(beta, P[pi_src[q]], R[pi_src[q]]);
             }
-            // P1: t of plane s-1 on the black cell of each own pair
-            const int m = s - 1;
+            // B: t of plane s-2 on the black cell of each own pair (w of planes s-3, s-2, s-1)
+            const int m = s - 2;
+            {
+                const float* W0 = wl(m);
+                const float* Wu = wl(m + 1);
+                const float* Wd = wl(m - 1);
 #pragma unroll
-            for (int q = 0; q < RPT; ++q) {
-                if (m >= k0 && m < k1 && inside[q]) {
-                    const int rho = (j0 + ty + kBY * q + m) & 1;
-                    const float* W0 = Wc;
-                    const int e = (ty + kBY * q + 1) * PW + xo;
-                    float t = sa[q].p;
-                    t = fmav(-sa[q].tx, W0[e + 1 - rho], t);
-                    t = fmav(-sa[q].txl, W0[e - rho], t);
-                    t = fmav(-sa[q].ty, W0[e + PW], t);
-                    t = fmav(-sa[q].tyd, W0[e - PW], t);
-                    t = fmav(-sa[q].tz, Wa[e], t);
-                    t = fmav(-sa[q].tzm, Wb[e], t);
-                    const long long c = (long long)m * cplane + own[q];
-                    out[c] = t;
-                    pnew[c] = sa[q].p;
-                    xv[c] = fmav(alpha, pa[q], xa[q]);
-                    acc.add(sa[q].p, t);
-                }
-                xa[q] = xb2[q];
-                pa[q] = pb[q];
-                xb2[q] = 0.f;
-                pb[q] = 0.f;
-                if (s + 1 >= k0 && s + 1 < k1 && inside[q]) {
-                    const long long c = (long long)(s + 1) * cplane + own[q];
-                    xb2[q] = xv[c];
-                    pb[q] = pold[c];
+                for (int q = 0; q < RPT; ++q) {
+                    if (m >= k0 && m < k1 && inside[q]) {
+                        const int rho = (j0 + ty + kBY * q + m) & 1;
+                        const int e = (ty + kBY * q + 1) * PW + xo;
+                        float t = sa[q].p;
+                        t = fmav(-sa[q].tx, W0[e + 1 - rho], t);
+                        t = fmav(-sa[q].txl, W0[e - rho], t);
+                        t = fmav(-sa[q].ty, W0[e + PW], t);
+                        t = fmav(-sa[q].tyd, W0[e - PW], t);
+                        t = fmav(-sa[q].tz, Wu[e], t);
+                        t = fmav(-sa[q].tzm, Wd[e], t);
+                        const long long c = (long long)m * cplane + own[q];
+                        out[c] = t;
+                        pnew[c] = sa[q].p;
+                        xv[c] = fmav(alpha, pa[q], xa[q]);
+                        acc.add(sa[q].p, t);
+                    }
+                    xa[q] = xn[q];
+                    pa[q] = pn2[q];
                 }
             }
-            if (__syncthreads_or(!ok)) {
-                bad = true;
-                break;
-            }
-            // P2: w of plane s+1 (even cells of the own pairs and the ring); before plane k0-1 only
-            // the pairs' Tz is carried
-            if (s <= s_last && s + 1 >= k0 - 2) {
-                const int mw = s + 1;
+            // C: w of plane s (even cells of the own pairs and the ring; p of planes s-1, s, s+1);
+            // at plane k0-2 only the pairs' Tz is carried
+            if (ok && s >= k0 - 2 && s <= k1) {
+                const int mw = s;
                 const float* Z = reinterpret_cast<const float*>(b + G::oZ);
                 if (mw >= k0 - 1) {
                     const float* X = reinterpret_cast<const float*>(b + G::oX);
                     const float* Y = reinterpret_cast<const float*>(b + G::oY);
+                    const float* P0 = pl(mw);
+                    const float* Pu = pl(mw + 1);
+                    const float* Pd = pl(mw - 1);
+                    float* Wo = wl(mw);
 #pragma unroll
                     for (int q = 0; q < RPT; ++q) {
                         const int yo = ty + kBY * q + 1;
                         float2 tzp;
-                        Wb[yo * PW + xo] = w_even(b, mw, xo, yo, own_tzm[q], tzp, Pb, Pc, Pa);
+                        Wo[yo * PW + xo] = w_even(b, mw, xo, yo, own_tzm[q], tzp, P0, Pu, Pd);
                         // the own black cell's coefficients and p for its t two steps later
                         const int rho = (j0 + yo - 1 + mw) & 1;
                         const int xbb = 2 * xo + 1 - rho;      // full-grid box index of the black cell
@@ -289,14 +306,14 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_bloc
                         co.tyd = Y[yo * BWF + xbb];
                         co.tz = rho ? tzp.x : tzp.y;
                         co.tzm = rho ? own_tzm[q].x : own_tzm[q].y;
-                        co.p = Pb[(yo + 1) * PW + xo];
+                        co.p = P0[(yo + 1) * PW + xo];
                         own_tzm[q] = tzp;
                         sa[q] = sb[q];
                         sb[q] = co;
                     }
                     if (has_ring) {
                         float2 tzr;
-                        Wb[ry * PW + rx] = w_even(b, mw, rx, ry, ring_tzm, tzr, Pb, Pc, Pa);
+                        Wo[ry * PW + rx] = w_even(b, mw, rx, ry, ring_tzm, tzr, P0, Pu, Pd);
                         ring_tzm = tzr;
                     }
                 } else {
@@ -309,17 +326,10 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const int per_bloc
 #pragma unroll
                 for (int q = 0; q < RPT; ++q) sa[q] = sb[q];
             }
-            {
-                float* const tp = Pa;
-                Pa = Pb;
-                Pb = Pc;
-                Pc = tp;
-                float* const tw = Wa;
-                Wa = Wb;
-                Wb = Wc;
-                Wc = tw;
+            if (__syncthreads_or(!ok)) {
+                bad = true;
+                break;
             }
-            __syncthreads();
         }
     }
     if (bad) {

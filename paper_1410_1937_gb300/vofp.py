@@ -98,7 +98,8 @@ _sig = {
     "vofp_residual_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _P(ctypes.c_double)]),
     "vofp_launch_count": (ctypes.c_int, [_vp, _P(ctypes.c_longlong)]),
     "vofp_rbc_split_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                           _P(ctypes.c_int), _P(ctypes.c_int), _P(ctypes.c_int)]),
+                                           _P(ctypes.c_int), _P(ctypes.c_int), _P(ctypes.c_int),
+                                           _P(ctypes.c_int), _P(ctypes.c_int)]),
     "vofp_scaled_pair": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "vofp_measure_fma_peaks": (ctypes.c_int, [_vp, _P(ctypes.c_double), _P(ctypes.c_double)]),
     "vofp_nn_train_step_anorm": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_float, ctypes.c_int,
@@ -154,11 +155,12 @@ def vofp_version() -> str:
 
 
 def vofp_rbc_split_plan(tiles_x, tiles_y, nz, slots):
-    """(blocks, per, pad) of the colour-compact red-black iteration kernel's work split (host only)."""
-    b, p, q = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
-    _check(None, _lib.vofp_rbc_split_plan(int(tiles_x), int(tiles_y), int(nz), int(slots), ctypes.byref(b),
-                                          ctypes.byref(p), ctypes.byref(q)))
-    return b.value, p.value, q.value
+    """(blocks, per, pad, gx, gy) of the colour-compact red-black iteration kernel's work split
+    (host only)."""
+    v = [ctypes.c_int(0) for _ in range(5)]
+    _check(None, _lib.vofp_rbc_split_plan(int(tiles_x), int(tiles_y), int(nz), int(slots),
+                                          *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
 
 
 def vofp_measure_fma_peaks(stream=None):
