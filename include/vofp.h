@@ -418,7 +418,8 @@ vofp_status vofp_launch_count(vofp_ctx* ctx, long long* count);
  * the context stream -- FP64 (precision 64) or FP32 (precision 32), Jacobi or red-black (precond)
  * -- and records the average device time of the fused stencil kernel in *stencil_ms, of the
  * vector-update kernel in *update_ms and, for the FP32 red-black iteration on colour-compact
- * vectors (else 0), of its exception-row and merge-group kernels together in *aux_ms.  Step
+ * vectors (else 0), of its fix-row and merge-group kernel in *aux_ms (the exception rows run
+ * inside the stencil kernel there).  Step
  * sizes are held at zero, so every byte is read and written but the vectors keep their values;
  * the solution returned by the solve is untouched. */
 vofp_status vofp_time_iteration_kernels(vofp_ctx* ctx, int precision, int precond, int reps,

@@ -301,46 +301,6 @@ __global__ void k_rbc_prep(Dims d, long long nh, int ne, const int* __restrict__
     if (grid_reduce(acc.value(), partials, counter, sh, &tot)) inner_start_scalars(sc, tot, rr, keep);
 }
 
-// After the TMA iteration kernel, per exception e (compact entry N/2 + e): p = r + beta p_old,
-// x += alpha p_old, the exception row t_e = p_e - sum_f T_f p_nb, and dE_e = w_red - p_e, the
-// difference between the red formula the black neighbours took in the TMA kernel (same order of
-// operations) and the exception's p.  p.t of the rows into pq_raw.
-__global__ void __launch_bounds__(kNT)
-k_rbc_exc_rows(long long nh, int ne, const int* __restrict__ enb, const float* __restrict__ eT,
-               const float* __restrict__ r, const float* __restrict__ po, float* __restrict__ pn,
-               float* __restrict__ xv, float* __restrict__ q, float* __restrict__ dE, CgScalars* sc,
-               double* __restrict__ partials, unsigned int* __restrict__ counter) {
-    __shared__ double sh[32];
-    grid_dep_wait();
-    grid_dep_trigger();
-    const float beta = (float)sc->beta, alpha = (float)sc->alpha;
-    AccF2 acc;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
-        const long long ie = nh + e;
-        const float pold = po[ie];
-        const float pe = fmav(beta, pold, r[ie]);
-        pn[ie] = pe;
-        xv[ie] = fmav(alpha, pold, xv[ie]);
-        float T[6], p[6];
-#pragma unroll
-        for (int f = 0; f < 6; ++f) {
-            T[f] = eT[6 * e + f];
-            p[f] = pn[enb[6 * e + f]];
-        }
-        float w = 0.0f, t = pe;
-#pragma unroll
-        for (int f = 0; f < 6; ++f) {
-            w = fmav(T[f], p[f], w);
-            t = fmav(-T[f], p[f], t);
-        }
-        dE[e] = w - pe;
-        q[ie] = t;
-        acc.add(pe, t);
-    }
-    double tot;
-    if (grid_reduce(acc.value(), partials, counter, sh, &tot)) sc->pq_raw += tot;
-}
-
 // correction of fix row rr: the black row took the red formula at each neighbouring exception,
 // T_f (w_red - p_e) puts the exception's p back (faces without one point at a zero entry)
 __device__ __forceinline__ float fix_delta(int rr, const int* __restrict__ fexc, const float* __restrict__ fT,
@@ -358,7 +318,8 @@ __device__ __forceinline__ float fix_delta(int rr, const int* __restrict__ fexc,
     return delta;
 }
 
-// After k_rbc_exc_rows.  Fix rows that are not merge-group members (threads 0..nf-1): q += delta.
+// After the iteration kernel (which also forms the exception rows and dE).  Fix rows that are not
+// merge-group members (threads 0..nf-1): q += delta.
 // Merge groups (threads nf..nf+ng-1): every member's final row (the exception row, or the black
 // row plus its correction), then the group value sum + gcorr p_G written to every member.
 // p.delta of the corrections and gcorr p_G^2 into pq_raw.
@@ -692,8 +653,10 @@ void launch_main_t(vofp_ctx* c, cudaStream_t st, const float* po, float* pn, boo
     maps.tx = *mx;
     maps.ty = *my;
     maps.tz = *mz;
+    const RbcExc ex{(const float*)c->rbc_r, (const int*)c->rbc_enb, (const float*)c->rbc_eT, c->rbc_dE,
+                    c->rbc_nh, c->rbc_ne};
     launch_dep(c, pdl, k_rbc_tma<kRbcStages, RPT>, dim3(c->rbc_nblocks), dim3(kBX, kBY),
-               cg_rbc_smem<kRbcStages, RPT>(), st, maps, d, c->rbc_split, po, pn, c->rbc_x, c->rbc_q,
+               cg_rbc_smem<kRbcStages, RPT>(), st, maps, d, c->rbc_split, ex, po, pn, c->rbc_x, c->rbc_q,
                c->sc, c->partials, c->counters);
 }
 void launch_main(vofp_ctx* c, cudaStream_t st, const float* po, float* pn, bool pdl) {
@@ -704,13 +667,11 @@ void launch_main(vofp_ctx* c, cudaStream_t st, const float* po, float* pn, bool 
 }
 }  // namespace
 
-// exception rows, then the rows next to exceptions and the merge groups
+// the rows next to exceptions and the merge groups (the exception rows are formed in the
+// iteration kernel)
 void rbc_aux(vofp_ctx* c, cudaStream_t st, const float* po, float* pn, bool pdl) {
+    (void)po;
     const int ng = c->rbc_gm ? c->ngroups : 0;
-    if (c->rbc_ne > 0)
-        launch_dep(c, pdl, k_rbc_exc_rows, dim3(ceil_div(c->rbc_ne, kNT)), dim3(kNT), 0, st, c->rbc_nh, c->rbc_ne,
-                   (const int*)c->rbc_enb, (const float*)c->rbc_eT, (const float*)c->rbc_r, po, pn, c->rbc_x,
-                   c->rbc_q, c->rbc_dE, c->sc, c->partials, c->counters);
     if (c->rbc_nf + ng > 0)
         launch_dep(c, pdl, k_rbc_fix_rows, dim3(ceil_div(c->rbc_nf + ng, kNT)), dim3(kNT), 0, st, c->rbc_nf, ng,
                    (const int*)c->rbc_fh, (const int*)c->rbc_fexc, (const float*)c->rbc_fT, (const float*)c->rbc_dE,
@@ -721,14 +682,15 @@ void rbc_aux(vofp_ctx* c, cudaStream_t st, const float* po, float* pn, bool pdl)
 
 void rbc_iteration(vofp_ctx* c, cudaStream_t st, const float* po, float* pn, cudaGraphConditionalHandle h,
                    int use_h) {
-    // In the solve's graph (use_h set; a refused launch is caught when the capture ends) the four
-    // kernels of an iteration, and the next iteration's first, are chained by programmatic
-    // dependent launch: each waits for its predecessor before it reads, so only the launch
-    // latency and the block set-up overlap the predecessor's drain. The two short exception and
-    // fix kernels release their successor's blocks at once; the iteration kernel and the update
-    // release theirs as their own blocks end (blocks of the next kernel resident early beside the
-    // streaming ones slowed the solve: 395.2 ms with every kernel releasing early, 387.8 ms with
-    // the update also releasing, 386.2 ms as here, 388.2 ms without the chaining). The
+    // In the solve's graph (use_h set; a refused launch is caught when the capture ends) the three
+    // kernels of an iteration (iteration kernel with the exception rows, fix rows, update), and
+    // the next iteration's first, are chained by programmatic dependent launch: each waits for its
+    // predecessor before it reads, so only the launch latency and the block set-up overlap the
+    // predecessor's drain. The short fix kernel releases its successor's blocks at once; the
+    // iteration kernel and the update release theirs as their own blocks end (blocks of the next
+    // kernel resident early beside the streaming ones slowed the solve: 395.2 ms with every kernel
+    // releasing early, 387.8 ms with the update also releasing, 386.2 ms with the short kernels
+    // only, 388.2 ms without the chaining, measured with a separate exception kernel). The
     // host-driven loop launches them as ordinary kernels.
     const bool pdl = c->pdl != 0 && use_h != 0;
     launch_main(c, st, po, pn, pdl);

@@ -27,6 +27,20 @@ struct RbcMaps {
     CUtensorMap r, p, tx, ty, tz;
 };
 
+// The exception rows (compact entries base + e, e < ne: even cells that belong to merge groups),
+// handled by the iteration kernel's blocks beside their tiles: per exception the compact index of
+// the black cell behind each face (enb, the own pair and coefficient 0 where there is none) and the
+// face coefficient (eT), six each in the order of the red formula; r the compact residual; dE the
+// difference w_red - p_e per exception.
+struct RbcExc {
+    const float* r;
+    const int* enb;
+    const float* eT;
+    float* dE;
+    long long base;
+    int ne;
+};
+
 
 constexpr size_t rbc_al(size_t b) { return (b + 127) / 128 * 128; }
 
@@ -74,7 +88,7 @@ constexpr size_t cg_rbc_smem() {
 // w: s-3 .. s).
 template <int NS, int RPT>
 __global__ void __launch_bounds__(kBX* kBY, RPT == 1 ? 3 : 2)
-k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const RbcSplit sp,
+k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const RbcSplit sp, const RbcExc ex,
           const float* __restrict__ pold,
           float* __restrict__ pnew, float* __restrict__ xv, float* __restrict__ out, CgScalars* __restrict__ sc,
           double* __restrict__ partials, unsigned int* __restrict__ counter) {
@@ -124,6 +138,43 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const RbcSplit sp,
     grid_dep_wait();
     const float beta = (float)sc->beta, alpha = (float)sc->alpha;
     const int nh = d.nx >> 1;
+    // This block's share of the exception rows: p = r + beta p_old, x += alpha p_old, the row
+    // t_e = p_e - sum_f T_f p_nb and dE_e = w_red - p_e, where w_red is the red formula the tiles
+    // take at the exception's cell (same operands, same order) and p_nb the black neighbours' p
+    // formed here from r and p_old exactly as the tiles form them.  Run once per block, while the
+    // first stages of its first segment are in flight.
+    bool exc_done = false;
+    auto exception_rows = [&]() {
+        const int per_b = (ex.ne + (int)gridDim.x - 1) / (int)gridDim.x;
+        const int e0 = (int)blockIdx.x * per_b, e1 = min(ex.ne, e0 + per_b);
+        for (int e = e0 + tid; e < e1; e += kBX * kBY) {
+            const long long ie = ex.base + e;
+            int nb[6];
+            float T[6];
+#pragma unroll
+            for (int f = 0; f < 6; ++f) {
+                nb[f] = ex.enb[6 * e + f];
+                T[f] = ex.eT[6 * e + f];
+            }
+            const float po_e = pold[ie];
+            const float pe = fmav(beta, po_e, ex.r[ie]);
+            float p[6];
+#pragma unroll
+            for (int f = 0; f < 6; ++f) p[f] = fmav(beta, pold[nb[f]], ex.r[nb[f]]);
+            float w = 0.0f, t = pe;
+#pragma unroll
+            for (int f = 0; f < 6; ++f) {
+                w = fmav(T[f], p[f], w);
+                t = fmav(-T[f], p[f], t);
+            }
+            pnew[ie] = pe;
+            xv[ie] = fmav(alpha, po_e, xv[ie]);
+            ex.dE[e] = w - pe;
+            out[ie] = t;
+            acc.add(pe, t);
+        }
+        exc_done = true;
+    };
     const int pad = sp.pad;
     // groups of gx x gy neighbouring tiles march the same planes in the same steps (their shared
     // halo sectors then come from L2); group g, member jg of the block
@@ -222,6 +273,7 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const RbcSplit sp,
         __syncthreads();
         if (tid == 0) fence_proxy_async_smem();
         for (int s = s_first; s <= min(s_first + NS - 1, s_last); ++s) issue(s);
+        if (!exc_done) exception_rows();
         for (int s = s_first; s <= k1 + 1; ++s) {
             // the slot of step s-1 is free (every thread passed the barrier that closed it)
             if (s - 1 >= s_first && s - 1 + NS <= s_last) {
@@ -337,6 +389,7 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const RbcSplit sp,
             if (pending & (1u << s)) mbar_wait_bounded(&bars[s], (phase >> s) & 1u);
         if (tid == 0) atomicCAS(&sc->status, (int)VOFP_OK, (int)VOFP_ERR_DEVICE_TIMEOUT);
     }
+    if (!exc_done) exception_rows();   // blocks without planes (or that stopped early)
     double tot;
     if (grid_reduce(acc.value(), partials, counter, sh, &tot)) sc->pq_raw = tot;
 }

@@ -429,7 +429,7 @@ class Context:
         return n.value
 
     def vofp_time_iteration_kernels(self, precision=64, reps=20, precond=PRECOND_JACOBI):
-        """Average device ms of one iteration's (stencil, update, exception + group) kernels; the
+        """Average device ms of one iteration's (stencil, update, fix-row + group) kernels; the
         third is 0 except for the FP32 red-black iteration on colour-compact vectors."""
         a, b, r = ctypes.c_float(0), ctypes.c_float(0), ctypes.c_float(0)
         _check(self.h, _lib.vofp_time_iteration_kernels(self.h, int(precision), int(precond), int(reps),
