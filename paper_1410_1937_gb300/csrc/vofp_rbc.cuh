@@ -70,8 +70,9 @@ struct RbcGeomT {
     static constexpr int PN = PW * (TH + 4);
     // w ring plane (even cells): same pair index, row yw <-> j0 + yw - 1
     static constexpr int WN = PW * (TH + 2);
-    static constexpr int kPItems = PN;                // p values formed per plane
-    static constexpr int kPPer = (PN + kBX * kBY - 1) / (kBX * kBY);   // per thread
+    static_assert(PW % 2 == 0 && BWC % 2 == 0, "p items are formed two pairs at a time");
+    static constexpr int kPItems = PN / 2;            // p items per plane: two neighbouring pairs each
+    static constexpr int kPPer = (kPItems + kBX * kBY - 1) / (kBX * kBY);   // per thread
     static constexpr int kRing = 2 * NP + 2 * TH;     // even cells of the w halo ring
 };
 using RbcGeom = RbcGeomT<1>;
@@ -114,15 +115,16 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const RbcSplit sp,
     auto pl = [&](int kk) -> float* { return pring + ((kk + 8) & 3) * G::PN; };
     auto wl = [&](int kk) -> float* { return wring + ((kk + 8) & 3) * G::WN; };
 
-    // p items: ring index e = tid + 256 q of the 36 x (TH + 4) plane (row e / PW, pair e % PW);
-    // box index of the same pair e + (BWC - PW) (e / PW) + 2
+    // p items: item it = tid + 256 q covers ring indices 2 it and 2 it + 1 of the 36 x (TH + 4)
+    // plane (row 2 it / PW, pairs 2 it % PW and the next); box index of the same pairs
+    // 2 it + (BWC - PW) (2 it / PW) + 2 (both even, so each item is one 8-byte word)
     int pi_src[G::kPPer];
     bool pi_on[G::kPPer];
 #pragma unroll
     for (int q = 0; q < G::kPPer; ++q) {
         const int it = tid + q * kBX * kBY;
         pi_on[q] = it < G::kPItems;
-        pi_src[q] = it + (BWC - PW) * (it / PW) + 2;
+        pi_src[q] = 2 * it + (BWC - PW) * ((2 * it) / PW) + 2;
     }
     // own pair xr = tx + 2 in w rows ty + 8 q + 1; ring items (threads 0 .. 2 NP + 2 TH - 1): the
     // pairs of rows j0-1 and j0+TH, then the pairs h0-1 and h0+NP of rows j0 .. j0+TH-1
@@ -301,7 +303,12 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const RbcSplit sp,
                 float* op = pl(s + 2);
 #pragma unroll
                 for (int q = 0; q < G::kPPer; ++q)
-                    if (pi_on[q]) op[tid + q * kBX * kBY] = fmav(beta, P[pi_src[q]], R[pi_src[q]]);
+                    if (pi_on[q]) {
+                        const float2 pv = *reinterpret_cast<const float2*>(P + pi_src[q]);
+                        const float2 rv = *reinterpret_cast<const float2*>(R + pi_src[q]);
+                        *reinterpret_cast<float2*>(op + 2 * (tid + q * kBX * kBY)) =
+                            make_float2(fmav(beta, pv.x, rv.x), fmav(beta, pv.y, rv.y));
+                    }
             }
             // B: t of plane s-2 on the black cell of each own pair (w of planes s-3, s-2, s-1)
             const int m = s - 2;
@@ -345,20 +352,35 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const RbcSplit sp,
                     float* Wo = wl(mw);
 #pragma unroll
                     for (int q = 0; q < RPT; ++q) {
+                        // the own pair (cells 2 xo, 2 xo + 1 of box row yo): its even cell's w
+                        // (the terms of w_even, same order) and its black cell's coefficients and
+                        // p for the t step two steps later, from the coefficients of both cells
+                        // read as 8-byte words
                         const int yo = ty + kBY * q + 1;
-                        float2 tzp;
-                        Wo[yo * PW + xo] = w_even(b, mw, xo, yo, own_tzm[q], tzp, P0, Pu, Pd);
-                        // the own black cell's coefficients and p for its t two steps later
                         const int rho = (j0 + yo - 1 + mw) & 1;
-                        const int xbb = 2 * xo + 1 - rho;      // full-grid box index of the black cell
+                        const float xl = X[yo * BWF + 2 * xo - 1];
+                        const float2 x2 = *reinterpret_cast<const float2*>(X + yo * BWF + 2 * xo);
+                        const float2 ya = *reinterpret_cast<const float2*>(Y + yo * BWF + 2 * xo);
+                        const float2 yb = *reinterpret_cast<const float2*>(Y + (yo + 1) * BWF + 2 * xo);
+                        const float2 tzp = *reinterpret_cast<const float2*>(Z + yo * BWF + 2 * xo);
+                        const int e = (yo + 1) * PW + xo;
+                        const float pm = P0[e - 1], pc = P0[e], pp = P0[e + 1];
+                        float u = 0.0f;
+                        u = fmav(rho ? x2.y : x2.x, rho ? pp : pc, u);
+                        u = fmav(rho ? x2.x : xl, rho ? pc : pm, u);
+                        u = fmav(rho ? yb.y : yb.x, P0[e + PW], u);
+                        u = fmav(rho ? ya.y : ya.x, P0[e - PW], u);
+                        u = fmav(rho ? tzp.y : tzp.x, Pu[e], u);
+                        u = fmav(rho ? own_tzm[q].y : own_tzm[q].x, Pd[e], u);
+                        Wo[yo * PW + xo] = u;
                         Co co;
-                        co.tx = X[yo * BWF + xbb];
-                        co.txl = X[yo * BWF + xbb - 1];
-                        co.ty = Y[(yo + 1) * BWF + xbb];
-                        co.tyd = Y[yo * BWF + xbb];
+                        co.tx = rho ? x2.x : x2.y;
+                        co.txl = rho ? xl : x2.x;
+                        co.ty = rho ? yb.x : yb.y;
+                        co.tyd = rho ? ya.x : ya.y;
                         co.tz = rho ? tzp.x : tzp.y;
                         co.tzm = rho ? own_tzm[q].x : own_tzm[q].y;
-                        co.p = P0[(yo + 1) * PW + xo];
+                        co.p = pc;
                         own_tzm[q] = tzp;
                         sa[q] = sb[q];
                         sb[q] = co;
