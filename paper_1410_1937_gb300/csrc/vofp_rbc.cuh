@@ -310,33 +310,43 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const RbcSplit sp,
                             make_float2(fmav(beta, pv.x, rv.x), fmav(beta, pv.y, rv.y));
                     }
             }
-            // B: t of plane s-2 on the black cell of each own pair (w of planes s-3, s-2, s-1)
+            // B: t of plane s-2 on the black cell of each own pair (w of planes s-3, s-2, s-1); the
+            // rows' sums are formed together (every ring read is in bounds) and only the stores
+            // and the dot product wait on whether the cell is inside the grid
             const int m = s - 2;
-            {
+            if (m >= k0 && m < k1) {
                 const float* W0 = wl(m);
                 const float* Wu = wl(m + 1);
                 const float* Wd = wl(m - 1);
+                float t[RPT];
 #pragma unroll
                 for (int q = 0; q < RPT; ++q) {
-                    if (m >= k0 && m < k1 && inside[q]) {
-                        const int rho = (j0 + ty + kBY * q + m) & 1;
-                        const int e = (ty + kBY * q + 1) * PW + xo;
-                        float t = sa[q].p;
-                        t = fmav(-sa[q].tx, W0[e + 1 - rho], t);
-                        t = fmav(-sa[q].txl, W0[e - rho], t);
-                        t = fmav(-sa[q].ty, W0[e + PW], t);
-                        t = fmav(-sa[q].tyd, W0[e - PW], t);
-                        t = fmav(-sa[q].tz, Wu[e], t);
-                        t = fmav(-sa[q].tzm, Wd[e], t);
+                    const int rho = (j0 + ty + kBY * q + m) & 1;
+                    const int e = (ty + kBY * q + 1) * PW + xo;
+                    float u = sa[q].p;
+                    u = fmav(-sa[q].tx, W0[e + 1 - rho], u);
+                    u = fmav(-sa[q].txl, W0[e - rho], u);
+                    u = fmav(-sa[q].ty, W0[e + PW], u);
+                    u = fmav(-sa[q].tyd, W0[e - PW], u);
+                    u = fmav(-sa[q].tz, Wu[e], u);
+                    u = fmav(-sa[q].tzm, Wd[e], u);
+                    t[q] = u;
+                }
+#pragma unroll
+                for (int q = 0; q < RPT; ++q) {
+                    if (inside[q]) {
                         const long long c = (long long)m * cplane + own[q];
-                        out[c] = t;
+                        out[c] = t[q];
                         pnew[c] = sa[q].p;
                         xv[c] = fmav(alpha, pa[q], xa[q]);
-                        acc.add(sa[q].p, t);
+                        acc.add(sa[q].p, t[q]);
                     }
-                    xa[q] = xn[q];
-                    pa[q] = pn2[q];
                 }
+            }
+#pragma unroll
+            for (int q = 0; q < RPT; ++q) {
+                xa[q] = xn[q];
+                pa[q] = pn2[q];
             }
             // C: w of plane s (even cells of the own pairs and the ring; p of planes s-1, s, s+1);
             // at plane k0-2 only the pairs' Tz is carried
