@@ -62,8 +62,9 @@ def iter_elems(variant):
 # only while the sources of that kernel and its launch hash to the value stored with it (else null):
 #   (32, "jacobi"): k_cg_tma<float, 6, 2> (column split), 561.8 MB over 16777216 cells
 #   (32, "rbsgs"):  k_cg_rb_tma<3, 8>, 885.6 MB over 16777216 cells
-#   (32, "rbsgs-compact"): k_rbc_tma<3, 2> (32 x 16 tiles), 563.2 MB over 16777216 cells
-TRAFFIC_PER_CELL = {(32, "jacobi"): (33.49, "7d8c8dd1b0cef8cd"), (32, "rbsgs"): (52.78, "987a1d6fd554bdf8"), (32, "rbsgs-compact"): (33.51, "694440ac59da758e")}
+#   (32, "rbsgs-compact"): k_rbc_tma<3, 2> (32 x 16 tiles in 8 x 2 groups, one barrier per step),
+#                          425.8 MB over 16777216 cells (mean of two launches)
+TRAFFIC_PER_CELL = {(32, "jacobi"): (33.49, "7d8c8dd1b0cef8cd"), (32, "rbsgs"): (52.78, "987a1d6fd554bdf8"), (32, "rbsgs-compact"): (25.38, "b40f011a8d0f9bce")}
 KERNEL_FILES = {(32, "jacobi"): ('vofp_kernels.cuh', 'vofp_tma.cuh', 'vofp_tma.cu'),
                 (32, "rbsgs"): ('vofp_kernels.cuh', 'vofp_tma.cuh', 'vofp_rb_tma.cuh', 'vofp_rb_tma.cu'),
                 (32, "rbsgs-compact"): ('vofp_kernels.cuh', 'vofp_tma.cuh', 'vofp_rbc.cuh', 'vofp_rbc.cu')}
@@ -416,7 +417,8 @@ def run_ours(args, rank, world, local_rank):
         variant = args.precond
         if args.precond == "rbsgs":
             if prec == 32 and stats["rb_compact"]:
-                kernel_name = "k_rbc_tma<3, 2> (TMA-fed red-black iteration on colour-compact vectors, 32x16 tiles)"
+                kernel_name = ("k_rbc_tma<3, 2> (TMA-fed red-black iteration on colour-compact vectors, 32x16 tiles "
+                               "in groups of neighbouring tiles, exception rows inside)")
                 variant = "rbsgs-compact"
             elif prec == 32 and stats["tma_stencil_fp32"]:
                 kernel_name = "k_cg_rb_tma<3, 8> (TMA-fed fused red-black iteration)"
