@@ -829,6 +829,39 @@ def run_profile_nn(args):
                       "z_rms": float(z.square().mean().sqrt())}), flush=True)
 
 
+def run_profile_train(args):
+    """Profiling run of the learned preconditioner's training: the committed network bound to the
+    workload, --profile-train training steps (forward, backward, Adam update; loss on the solution,
+    vofp_nn_train_step) after two untimed ones, timed with CUDA events, beside the forward alone."""
+    import torch
+    from paper_1410_1937_gb300 import learned
+    from paper_1410_1937_gb300 import vofp
+    prob = make_problem(tuple(args.shape))
+    ctx, t = vofp.context_for(prob)
+    net = vofp.Network(seed=0)
+    learned.load(net, learned.WEIGHTS)
+    net.bind(ctx, t["F"])
+    g = torch.Generator("cuda").manual_seed(5)
+    r = torch.randn(prob.n, dtype=torch.float32, device="cuda", generator=g)
+    target = torch.randn(prob.n, dtype=torch.float32, device="cuda", generator=g)
+    z = net.forward(r)
+    for _ in range(2):
+        net.train_step(r, target, lr=1e-4)
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record()
+    for _ in range(args.profile_train):
+        net.forward(r, out=z)
+    e1.record()
+    for _ in range(args.profile_train):
+        loss = net.train_step(r, target, lr=1e-4)
+    e2.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_train": True, "shape": args.shape,
+                      "forward_ms": e0.elapsed_time(e1) / args.profile_train,
+                      "train_step_ms": e1.elapsed_time(e2) / args.profile_train, "loss": loss}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -858,6 +891,8 @@ def main():
                     help="profiling run: also one VOF step after the capped solve")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiling run: one step whose solve stops after this many CG iterations")
+    ap.add_argument("--profile-train", type=int, default=0,
+                    help="profiling run: this many timed training steps of the network, then exit")
     ap.add_argument("--profile-nn", type=int, default=0,
                     help="profiling run: this many forward passes of the committed network")
     args = ap.parse_args()
@@ -872,6 +907,9 @@ def main():
         return
     if args.profile_nn > 0:
         run_profile_nn(args)
+        return
+    if args.profile_train > 0:
+        run_profile_train(args)
         return
     if world > 1:
         import torch

@@ -17,7 +17,8 @@
 // tcgen05.mma instructions whose A operand is the halo'd plane shifted by the tap (a different
 // descriptor start address) and whose B operand is that tap's weights, accumulating in FP32 in
 // tensor memory; four warps read the accumulator back, add the bias, apply ReLU and store BF16.
-// Weight gradients use warp-level mma.sync over voxel rows (a training-only path).
+// Weight gradients are tcgen05 GEMMs over the voxels with both operands read MN-major from the
+// same chunk-planar tiles (k_conv3_wgrad_umma).
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
@@ -302,77 +303,184 @@ __global__ void k_blob_dgrad(const float* __restrict__ w, int cout, int cin, int
     }
 }
 
-__device__ __forceinline__ uint32_t ld32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
-__device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi) {
-    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
+// ---- 3x3x3 convolution, weight gradient, on the tensor cores ----------------------------------
+// dW[tap][co][ci] = sum over voxels v of dy[v][co] x[v + tap - 1][ci].  Per (y, x) tap it is one
+// GEMM over the voxels, D[(z tap, ci)][co] = sum_k A[(z tap, ci)][k] B[co][k] with K = voxels: A is
+// the input x at the three planes z-1, z, z+1 shifted by the (y, x) tap and B the output gradient
+// dy at plane z, both read MN-major straight from their chunk-planar tiles (a row of a core matrix
+// is one voxel's 8 channels of a group, consecutive rows are consecutive voxels along x).  The
+// input box of a tile plane is 10 x 18 voxels x 3 planes x CIC channels; its group planes, plane
+// fastest, are one box plane apart, so one instruction's M rows (8 per group plane) cover the three
+// z taps of CIC input channels: M = 64 for 16 channels (48 rows used), 128 for 32 (96 rows).  A
+// block owns a chunk of CIC input channels and a slice of NCO output channels; for each 8 x 16 tile
+// plane of its share of the work it receives, by two tensor copies, that input box and the
+// gradient's 8 x 16 tile (the slice's groups), and one thread issues, per K step of 16 voxels (two
+// tile rows), one instruction per (y, x) tap whose A start address is the box shifted by the tap.
+// The nine accumulators stay in tensor memory (9 NCO FP32 columns) over all of the block's tiles;
+// four warps add them to the FP32 gradient once at the end.  The M rows past the used ones read
+// other shared memory and are not used.
+template <int CIC, int NCO, int M>
+struct WgCfg {
+    static_assert((CIC == 16 && M == 64) || (CIC == 32 && M == 128), "input-channel chunk and rows");
+    static_assert(NCO % 16 == 0, "output-channel slice");
+    static constexpr int XG = 3 * CIC / 8;                               // group planes of a box
+    static constexpr int MG = M / 8, DG = NCO / 8;
+    static constexpr int R = 4;                                          // ring slots
+    static constexpr uint32_t XSLOT = (uint32_t)XG * kGroupBytes;        // input box (3 planes, halo)
+    static constexpr uint32_t DGB = kTileX * kTileY * 16;                // one gradient group
+    static constexpr uint32_t DSLOT = (uint32_t)DG * DGB;
+    static constexpr uint32_t TCOLS = pow2_at_least(9u * NCO);
+    static constexpr size_t oX = 0;
+    // the unused rows of the last slot read up to (MG - XG) group planes further on
+    static constexpr size_t oD = al128((size_t)R * XSLOT + (size_t)(MG - XG) * kGroupBytes);
+    static constexpr size_t oBar = oD + al128((size_t)R * DSLOT);
+    static constexpr size_t SMEM_USED = al128(oBar + 8 * (2 * R + 1) + 8) + 128;   // + alignment slack
+    // no more blocks per SM than tensor memory holds (512 columns per SM)
+    static constexpr size_t SMEM = TCOLS == 512 ? (SMEM_USED > 120 * 1024 ? SMEM_USED : 120 * 1024)
+                                 : TCOLS == 256 ? (SMEM_USED > 80 * 1024 ? SMEM_USED : 80 * 1024) : SMEM_USED;
+    static_assert(SMEM <= 232448, "shared memory per block");
+    static_assert(TCOLS <= 512, "tensor memory");
+};
 
-// ---- 3x3x3 convolution, weight gradient (training) ----------------------------------------------
-// dw[tap][co][ci] += sum over voxels v of dy[v][co] * x[v + tap - 1][ci] (FP32 atomics into dw).
-// GEMM per tap: M = 16 output channels (co tile), N = input channels, K = 16 voxels of an x-row.
-template <int CIN>
-__global__ void __launch_bounds__(128)
-k_conv3_wgrad(const bf16* __restrict__ x, const bf16* __restrict__ dy, int cout, float* __restrict__ dw,
-              int nx, int ny, int nz, int rows_per_block) {
-    constexpr int NT = CIN / 8;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, t = lane & 3;
-    const int cotiles = cout / 16;
-    const int tap = blockIdx.x / cotiles, co0 = (blockIdx.x % cotiles) * 16;
-    const int dz = tap / 9 - 1, dy_ = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-    const long long V = (long long)nx * ny * nz;
-    float acc[NT][4];
+struct WgArgs {
+    int tiles_x, tiles_y;
+    long long items;          // tile planes: tiles_x tiles_y nz
+    long long per;            // tile planes per block
+    int nchunks, nslices;     // input-channel chunks of CIC, output-channel slices of NCO
+    int cin, cout;
+    float* gw;                // [27][cout][cin], added to
+    int* err;                 // set to 1 when a bounded wait runs out
+};
+
+// Block order: input-channel chunk fastest, then output slice, then the block's range of tile
+// planes (the chunks and slices of a range read the same gradient and input tiles at nearly the
+// same time, through L2).
+template <int CIC, int NCO, int M>
+__global__ void __launch_bounds__(kConvThreads, 1)
+k_conv3_wgrad_umma(const __grid_constant__ CUtensorMap x_map, const __grid_constant__ CUtensorMap dy_map,
+                   const WgArgs a) {
+    using G = WgCfg<CIC, NCO, M>;
+    constexpr int R = G::R;
+    extern __shared__ unsigned char smraw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 127) & ~uintptr_t(127));
+    unsigned char* xs = sm + G::oX;
+    unsigned char* ds = sm + G::oD;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + G::oBar);
+    uint64_t* empty = full + R;
+    uint64_t* done = empty + R;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int b = blockIdx.x;
+    const int chunk = b % a.nchunks;
+    b /= a.nchunks;
+    const int slice = b % a.nslices;
+    const long long blk = b / a.nslices;
+    const long long it0 = blk * a.per;
+    const int nitems = (int)max(0LL, min(a.items, it0 + a.per) - it0);
+    const int ntiles = a.tiles_x * a.tiles_y;
+    if (tid == 0) {
+        for (int i = 0; i < R; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        mbar_init(done, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) umma::tmem_alloc(tslot, G::TCOLS);
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    bool fail = false;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int i = 0; i < nitems; ++i) {
+                const int s = i % R;
+                if (i >= R && !mbar_wait_bounded(&empty[s], (uint32_t)((i / R) - 1) & 1u)) {
+                    fail = true;
+                    break;
+                }
+                const long long item = it0 + i;
+                const int tile = (int)(item % ntiles), z = (int)(item / ntiles);
+                const int x0 = (tile % a.tiles_x) * kTileX, y0 = (tile / a.tiles_x) * kTileY;
+                mbar_expect_tx(&full[s], G::XSLOT + G::DSLOT);
+                umma::tma_load_5d(xs + (size_t)s * G::XSLOT, &x_map, &full[s], 0, x0 - 1, y0 - 1, z - 1, chunk * (CIC / 8));
+                umma::tma_load_5d(ds + (size_t)s * G::DSLOT, &dy_map, &full[s], 0, x0, y0, z, slice * G::DG);
+                ++issued;
+            }
+            // every copy issued must have landed before the block may leave
+            for (int i = max(0, issued - R); i < issued; ++i)
+                if (!mbar_wait_bounded(&full[i % R], (uint32_t)(i / R) & 1u)) fail = true;
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t id = umma::idesc_bf16_mn(M, NCO);
+            const uint32_t xbase = umma::saddr(xs), dbase = umma::saddr(ds);
+            for (int i = 0; i < nitems && !fail; ++i) {
+                const int s = i % R;
+                if (!mbar_wait_bounded(&full[s], (uint32_t)(i / R) & 1u)) {
+                    fail = true;
+                    break;
+                }
+                umma::fence_after_sync();
+                const uint32_t xslot = xbase + (uint32_t)s * G::XSLOT, dslot = dbase + (uint32_t)s * G::DSLOT;
+                // K steps outermost: consecutive instructions go to the nine taps' separate
+                // accumulators
+#pragma unroll 1
+                for (int ks = 0; ks < kTileY / 2; ++ks) {
+                    // K = tile rows 2 ks and 2 ks + 1 (8 voxels each): gradient tile rows one tile row
+                    // apart, channel groups one group plane apart
+                    const uint64_t bd = umma::smem_desc(dslot + (uint32_t)(ks * 2 * kTileX * 16), kTileX * 16, G::DGB);
 #pragma unroll
-    for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-    const long long rows = (long long)ny * nz;
-    const long long r0 = (long long)blockIdx.y * rows_per_block;
-    const long long r1 = min(rows, r0 + rows_per_block);
-    const bf16 zero = __float2bfloat16(0.f);
-    for (long long row = r0; row < r1; ++row) {
-        const int y = int(row % ny), z = int(row / ny);
-        const int iy = y + dy_, iz = z + dz;
-        const bool rowok = iy >= 0 && iy < ny && iz >= 0 && iz < nz;
-        const long long ob = row * nx, ib = ((long long)iz * ny + iy) * nx;
-        for (int xs = warp * 16; xs < nx; xs += 64) {
-            // K index k = voxel xs + k of this row
-            auto dyv = [&](int k, int mm) -> bf16 {
-                const int xx = xs + k;
-                return xx < nx ? dy[aidx(ob + xx, co0 + mm, V)] : zero;
-            };
-            auto xv = [&](int k, int ci) -> bf16 {
-                const int xx = xs + k, ix = xx + dx;
-                return (rowok && xx < nx && ix >= 0 && ix < nx) ? x[aidx(ib + ix, ci, V)] : zero;
-            };
-            uint32_t a[4];
-            a[0] = pack2(dyv(2 * t, g), dyv(2 * t + 1, g));
-            a[1] = pack2(dyv(2 * t, g + 8), dyv(2 * t + 1, g + 8));
-            a[2] = pack2(dyv(2 * t + 8, g), dyv(2 * t + 9, g));
-            a[3] = pack2(dyv(2 * t + 8, g + 8), dyv(2 * t + 9, g + 8));
+                    for (int t = 0; t < 9; ++t) {
+                        const int ty = t / 3, tx = t % 3;
+                        // input box rows shifted by the tap, one box row (kBoxX voxels) apart; M
+                        // groups (plane, channel group) one box plane apart
+                        const uint64_t ad =
+                            umma::smem_desc(xslot + (uint32_t)(((2 * ks + ty) * kBoxX + tx) * 16), kBoxX * 16, kGroupBytes);
+                        umma::mma_bf16(tmem + (uint32_t)(t * NCO), ad, bd, id, (i > 0 || ks > 0) ? 1u : 0u);
+                    }
+                }
+                umma::commit(&empty[s]);   // the slot may be refilled
+            }
+            umma::commit(done);            // every MMA issued has completed
+        }
+    } else {
+        // epilogue: warp quarter q of the TMEM lanes; accumulator row of this lane (M = 64: the
+        // first 16 lanes of each quarter), its group plane m (channel group m / 3, z tap m % 3)
+        const int q = warp & 3;
+        const int row = M == 128 ? q * 32 + lane : (lane < 16 ? q * 16 + lane : M);
+        const int m = row >> 3;
+        const bool used = row < M && m < G::XG;
+        const int ci = chunk * CIC + (m / 3) * 8 + (row & 7), tz = m % 3;
+        if (!mbar_wait_bounded(done, 0u)) fail = true;
+        if (!__any_sync(0xffffffffu, fail) && nitems > 0) {
+            umma::fence_after_sync();
+#pragma unroll 1
+            for (int t = 0; t < 9; ++t) {
+                const int tap = 9 * tz + t;
 #pragma unroll
-            for (int n = 0; n < NT; ++n) {
-                const int ci = n * 8 + g;
-                const uint32_t b0 = pack2(xv(2 * t, ci), xv(2 * t + 1, ci));
-                const uint32_t b1 = pack2(xv(2 * t + 8, ci), xv(2 * t + 9, ci));
-                mma16816(acc[n], a, b0, b1);
+                for (int c0 = 0; c0 < NCO; c0 += 16) {
+                    uint32_t r[16];
+                    umma::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * NCO + c0), r);
+                    umma::tmem_wait_ld();
+                    if (used) {
+                        float* dst = a.gw + ((long long)tap * a.cout + slice * NCO + c0) * a.cin + ci;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) atomicAdd(dst + (long long)j * a.cin, __uint_as_float(r[j]));
+                    }
+                }
             }
         }
     }
-    // c0,c1: (co0 + g, ci = n*8 + 2t, +1); c2,c3: (co0 + g + 8, same ci)
-    float* base = dw + (long long)tap * cout * CIN;
-#pragma unroll
-    for (int n = 0; n < NT; ++n) {
-        const int ci = n * 8 + 2 * t;
-        atomicAdd(base + (long long)(co0 + g) * CIN + ci, acc[n][0]);
-        atomicAdd(base + (long long)(co0 + g) * CIN + ci + 1, acc[n][1]);
-        atomicAdd(base + (long long)(co0 + g + 8) * CIN + ci, acc[n][2]);
-        atomicAdd(base + (long long)(co0 + g + 8) * CIN + ci + 1, acc[n][3]);
+    if (fail) atomicExch(a.err, 1);
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        umma::fence_after_sync();
+        umma::tmem_dealloc(tmem, G::TCOLS);
     }
 }
 
@@ -384,22 +492,6 @@ __global__ void k_relu_bwd(bf16* __restrict__ dy, const bf16* __restrict__ y, lo
         if (!(__bfloat162float(y[i]) > 0.f)) dy[i] = zero;
 }
 
-// db[c] += sum over voxels of dy[v][c]
-__global__ void k_bias_grad(const bf16* __restrict__ dy, int C, long long nv, float* __restrict__ db) {
-    __shared__ float sh[256];
-    const int c = blockIdx.y;
-    float s = 0.f;
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv; v += (long long)gridDim.x * blockDim.x)
-        s += __bfloat162float(dy[aidx(v, c, nv)]);
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) atomicAdd(db + c, sh[0]);
-}
-
 __device__ __forceinline__ void unpack8(const uint4& u, float (&f)[8]) {
     const uint32_t w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
@@ -408,6 +500,36 @@ __device__ __forceinline__ void unpack8(const uint4& u, float (&f)[8]) {
         f[2 * h + 1] = __uint_as_float(w[h] & 0xFFFF0000u);
     }
 }
+// db[8 g + j] += sum over voxels of dy[v][8 g + j] (channel group g = blockIdx.y): one 16-byte
+// word (the group's 8 channels of a voxel) per thread and voxel, eight sums per thread, reduced
+// over the warp by shuffles and over the block in shared memory
+__global__ void __launch_bounds__(256) k_bias_grad(const bf16* __restrict__ dy, long long nv, float* __restrict__ db) {
+    __shared__ float sh[8][8];
+    const int g = blockIdx.y;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const uint4* src = reinterpret_cast<const uint4*>(dy) + (long long)g * nv;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv; v += (long long)gridDim.x * blockDim.x) {
+        float f[8];
+        unpack8(src[v], f);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[j] += f[j];
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) sh[warp][j] = acc[j];
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        float t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w][threadIdx.x];
+        atomicAdd(db + 8 * g + threadIdx.x, t);
+    }
+}
+
 __device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
     uint32_t w[4];
 #pragma unroll
@@ -609,6 +731,8 @@ struct vofp_nn {
     float *mask = nullptr, *out = nullptr, *scal = nullptr;   // scal: sum r^2, count, scale, inv scale, loss
     bool bound = false, grads_ready = false;
     std::map<std::tuple<const void*, int, int, int, int>, CUtensorMap> maps;
+    // other boxes: (tensor, nx, ny, nz, groups, box x y z, box groups)
+    std::map<std::tuple<const void*, int, int, int, int, int, int>, CUtensorMap> tile_maps;
 
     template <typename T>
     vofp_status alloc(T** p, size_t count, std::vector<void*>& list) {
@@ -793,6 +917,53 @@ const CUtensorMap* act_map(vofp_nn* n, const bf16* ptr, int nx, int ny, int nz, 
     return &(n->maps[key] = m);
 }
 
+// chunk-planar tensor map with a box of bx x by voxels, bz planes and box_groups channel groups
+// (cached per tensor, level and box)
+const CUtensorMap* box_map(vofp_nn* n, const bf16* ptr, int nx, int ny, int nz, int groups, int bx, int by, int bz,
+                           int box_groups) {
+    const auto key = std::make_tuple((const void*)ptr, nx, ny, nz, groups, bx * 1000000 + by * 1000 + bz, box_groups);
+    auto it = n->tile_maps.find(key);
+    if (it != n->tile_maps.end()) return &it->second;
+    auto enc = tensor_map_encoder();
+    if (!enc) return nullptr;
+    CUtensorMap m;
+    std::memset(&m, 0, sizeof(m));
+    const cuuint64_t V = (cuuint64_t)nx * ny * nz;
+    const cuuint64_t dims[5] = {8, (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)groups};
+    const cuuint64_t strides[4] = {16, (cuuint64_t)nx * 16, (cuuint64_t)nx * ny * 16, V * 16};
+    const cuuint32_t box[5] = {8, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, (cuuint32_t)box_groups};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    const CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16*>(ptr), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return nullptr;
+    return &(n->tile_maps[key] = m);
+}
+
+template <int CIC, int NCO, int M>
+vofp_status wgrad_umma(vofp_nn* n, const CUtensorMap* xm, const CUtensorMap* dm, WgArgs a) {
+    using G = WgCfg<CIC, NCO, M>;
+    auto kern = k_conv3_wgrad_umma<CIC, NCO, M>;
+    static int occ = -1;   // resident blocks per SM (per instantiation; one device per process)
+    if (occ < 0) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kConvThreads, G::SMEM) != cudaSuccess || occ < 1) {
+            occ = -1;
+            n->err = "tensor-core weight gradient: shared memory opt-in failed";
+            return VOFP_ERR_CUDA;
+        }
+    }
+    // one wave: the resident blocks shared by the chunks and slices, each block a run of at least
+    // four tile planes
+    const long long groups = (long long)a.nchunks * a.nslices;
+    const long long want = std::max(1LL, (long long)num_sms() * occ / groups);
+    a.per = std::max(4LL, (a.items + want - 1) / want);
+    const long long nb = (a.items + a.per - 1) / a.per;
+    a.err = n->derr;
+    kern<<<(unsigned)(nb * groups), kConvThreads, G::SMEM, n->stream>>>(*xm, *dm, a);
+    return cudaGetLastError() == cudaSuccess ? VOFP_OK : VOFP_ERR_CUDA;
+}
+
 template <int CIN, int NOUT, int R>
 vofp_status conv_umma(vofp_nn* n, const CUtensorMap* map, ConvArgs a, int nsplit) {
     using G = ConvCfg<CIN, NOUT, R>;
@@ -860,23 +1031,38 @@ vofp_status conv_fwd(vofp_nn* n, const Layer& l, const bf16* in, bf16* out, int 
     return conv(n, in, l.cin, l.blob_f, l.cout, l.nout_f, l.b, true, out, out_chunk0, nx, ny, nz);
 }
 
-void conv_wgrad(vofp_nn* n, const bf16* x, const bf16* dy, const Layer& l, int nx, int ny, int nz) {
-    const long long rows = (long long)ny * nz;
-    const int bx = 27 * (l.cout / 16);
-    const long long by = std::max(1LL, std::min(rows, (long long)num_sms() * 8 / bx + 1));
-    const int rpb = (int)((rows + by - 1) / by);
-    dim3 grid(bx, (unsigned)((rows + rpb - 1) / rpb));
-    cudaStream_t st = n->stream;
-    switch (l.cin) {
-        case 16: k_conv3_wgrad<16><<<grid, 128, 0, st>>>(x, dy, l.cout, l.gw, nx, ny, nz, rpb); break;
-        case 32: k_conv3_wgrad<32><<<grid, 128, 0, st>>>(x, dy, l.cout, l.gw, nx, ny, nz, rpb); break;
-        case 48: k_conv3_wgrad<48><<<grid, 128, 0, st>>>(x, dy, l.cout, l.gw, nx, ny, nz, rpb); break;
-        case 64: k_conv3_wgrad<64><<<grid, 128, 0, st>>>(x, dy, l.cout, l.gw, nx, ny, nz, rpb); break;
-        case 96: k_conv3_wgrad<96><<<grid, 128, 0, st>>>(x, dy, l.cout, l.gw, nx, ny, nz, rpb); break;
-        default: break;
+// weight and bias gradients of one layer from its input x and the gradient dy of its output
+// (before the ReLU), added to l.gw and l.gb
+vofp_status conv_wgrad(vofp_nn* n, const bf16* x, const bf16* dy, const Layer& l, int nx, int ny, int nz) {
+    const int nco = l.cout == 16 ? 16 : 32;
+    const int cic = l.cin % 32 == 0 ? 32 : 16;
+    const CUtensorMap* xm = box_map(n, x, nx, ny, nz, l.cin / 8, kBoxX, kBoxY, 3, cic / 8);
+    const CUtensorMap* dm = box_map(n, dy, nx, ny, nz, l.cout / 8, kTileX, kTileY, 1, nco / 8);
+    if (!xm || !dm) {
+        n->err = "tensor map of an activation could not be built";
+        return VOFP_ERR_CUDA;
     }
+    WgArgs a{};
+    a.tiles_x = (nx + kTileX - 1) / kTileX;
+    a.tiles_y = (ny + kTileY - 1) / kTileY;
+    a.items = (long long)a.tiles_x * a.tiles_y * nz;
+    a.nchunks = l.cin / cic;
+    a.nslices = l.cout / nco;
+    a.cin = l.cin;
+    a.cout = l.cout;
+    a.gw = l.gw;
+    vofp_status s;
+    switch (cic * 1000 + nco) {
+        case 16016: s = wgrad_umma<16, 16, 64>(n, xm, dm, a); break;
+        case 16032: s = wgrad_umma<16, 32, 64>(n, xm, dm, a); break;
+        case 32032: s = wgrad_umma<32, 32, 128>(n, xm, dm, a); break;
+        default: n->err = "no tensor-core weight gradient for this shape"; return VOFP_ERR_INVALID_ARG;
+    }
+    if (s) return s;
     const long long nv = (long long)nx * ny * nz;
-    k_bias_grad<<<dim3(gs(nv), l.cout), 256, 0, st>>>(dy, l.cout, nv, l.gb);
+    const int bx = (int)std::max(1LL, std::min((long long)num_sms() * 8 / (l.cout / 8), (nv + 255) / 256));
+    k_bias_grad<<<dim3(bx, l.cout / 8), 256, 0, n->stream>>>(dy, nv, l.gb);
+    return VOFP_OK;
 }
 
 void refresh_blobs(vofp_nn* n) {
@@ -929,7 +1115,7 @@ vofp_status layer_bwd(vofp_nn* n, const Layer& l, const bf16* x, const bf16* y, 
                       int nz) {
     const long long nv = (long long)nx * ny * nz;
     k_relu_bwd<<<gs(nv * l.cout), 256, 0, n->stream>>>(dy, y, nv * l.cout);
-    conv_wgrad(n, x, dy, l, nx, ny, nz);
+    if (vofp_status s = conv_wgrad(n, x, dy, l, nx, ny, nz)) return s;
     if (dx) return conv(n, dy, l.cout, l.blob_b, l.cin, l.nout_b, nullptr, false, dx, 0, nx, ny, nz);
     return VOFP_OK;
 }
@@ -1001,6 +1187,7 @@ vofp_status ensure_grid(vofp_nn* n, int nx, int ny, int nz) {
     free_list(n->grid_allocs);
     free_list(n->grad_allocs);
     n->maps.clear();
+    n->tile_maps.clear();
     n->bound = false;
     n->grads_ready = false;
     n->nx = nx;

@@ -8,6 +8,13 @@
 // matrices adjacent along K (leading byte offset) and between core matrices adjacent along M or N
 // (stride byte offset).  The instruction descriptor selects BF16 inputs, FP32 accumulation, both
 // operands K-major, and the M x N shape of one instruction (K = 16).
+//
+// MN-major operands (idesc_bf16_mn): a core matrix is 8 rows of 16 bytes again, but a row holds 8
+// values along M (or N) at one K, and consecutive rows are consecutive K; the leading byte offset
+// is still the distance between core matrices adjacent along K and the stride byte offset the one
+// along M or N (checked on the GPU: the other reading gives wrong sums).  With M = 128 accumulator
+// row r is TMEM lane r; with M = 64 row r is lane 32 (r / 16) + r % 16 (the first 16 lanes of each
+// warp's quarter).
 #pragma once
 #include <cuda.h>
 #include <cstdint>
@@ -28,6 +35,9 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t k_stride, 
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+
+// the same with both operands MN-major
+__host__ __device__ constexpr uint32_t idesc_bf16_mn(int M, int N) { return idesc_bf16(M, N) | (1u << 15) | (1u << 16); }
 
 // one warp allocates ncols TMEM columns (power of two >= 32) and writes the base address to *slot
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {

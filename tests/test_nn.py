@@ -184,9 +184,13 @@ def test_gpu_geometry_channels_match_oracle(gpu, oracle):
 
 
 @pytest.mark.gpu
-def test_gpu_forward_and_gradients_match_oracle(gpu, oracle):
+@pytest.mark.parametrize("shape", [(32, 32, 16), (44, 40, 24)])
+def test_gpu_forward_and_gradients_match_oracle(gpu, oracle, shape):
+    """Forward output, loss and every parameter gradient against the oracle.  32 x 32 x 16: whole
+    8 x 16 tiles at the finest level; 44 x 40 x 24: ragged tiles in x and y at every level (44 =
+    5 x 8 + 4, 40 = 2 x 16 + 8; 22 x 20 and 11 x 10 below), several tile planes per block."""
     torch, vofp = gpu
-    prob = _tiny_hull()
+    prob = _tiny_hull(shape)
     s = oracle.System(prob)
     ctx, t = vofp.context_for(prob)
     net = vofp.Network(seed=7)
