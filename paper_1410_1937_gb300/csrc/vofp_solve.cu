@@ -759,8 +759,8 @@ int outer_tail_kernels(const vofp_ctx* c, bool rb) {
 }
 // kernels of one mixed inner iteration
 int inner_iteration_kernels(const vofp_ctx* c, bool rb) {
-    if (rb && c->rbc_ok)
-        return 2 + (c->rbc_ne > 0 ? 1 : 0) + (c->rbc_nf + (c->rbc_gm ? c->ngroups : 0) > 0 ? 1 : 0);
+    if (rb && c->rbc_ok)   // iteration kernel (exception rows inside), fix rows, update
+        return 2 + (c->rbc_nf + (c->rbc_gm ? c->ngroups : 0) > 0 ? 1 : 0);
     return iteration_kernels(c, rb);
 }
 
