@@ -395,6 +395,22 @@ vofp_status vofp_nn_export_geometry(vofp_nn* nn, uint16_t* geo, float* mask);
 vofp_status vofp_nn_set_geometry(vofp_nn* nn, int nx, int ny, int nz, const uint16_t* geo, const float* mask);
 /* z = network(r) for a scaled residual r (device FP32, cells) */
 vofp_status vofp_nn_forward(vofp_nn* nn, const float* r, float* z);
+/* Check hooks for one 3x3x3 convolution layer (0..9, forward order) of the network, on caller
+ * tensors of nx x ny x nz voxels (any positive sizes) in the network's chunk-planar BF16 layout:
+ * channel c of voxel v (x fastest) at ((c / 8) * V + v) * 8 + c % 8, device memory, 16-byte aligned.
+ * vofp_nn_conv_apply: data_grad = 0: out = ReLU(conv(in) + bias) with the layer's weights (in: its
+ * input channels, out: its output channels); data_grad = 1: out = the data gradient of the
+ * convolution applied to in (in: output channels, out: input channels; taps mirrored, no bias, no
+ * ReLU).  vofp_nn_conv_wgrad: gw = dW[27][cout][cin] (tap index 9 (dz+1) + 3 (dy+1) + (dx+1)) =
+ * sum over voxels of dy[v][co] x[v + tap][ci] and gb[cout] = sum over voxels of dy (FP32 device,
+ * overwritten) from the layer input x and the output gradient dy.  These are the kernels the
+ * forward pass and vofp_nn_train_step run; the paper has no counterpart.  VOFP_ERR_INVALID_ARG for
+ * a bad layer, size, null or unaligned pointer; VOFP_ERR_DEVICE_TIMEOUT if a bounded wait ran
+ * out. */
+vofp_status vofp_nn_conv_apply(vofp_nn* nn, int layer, int data_grad, int nx, int ny, int nz, const uint16_t* in,
+                               uint16_t* out);
+vofp_status vofp_nn_conv_wgrad(vofp_nn* nn, int layer, int nx, int ny, int nz, const uint16_t* x, const uint16_t* dy,
+                               float* gw, float* gb);
 /* forward, masked mean-squared error against target (both relative to the RMS of r), backward;
  * update = 1 also takes an Adam step with learning rate lr.  *loss (host) may be NULL. */
 vofp_status vofp_nn_train_step(vofp_nn* nn, const float* r, const float* target, float lr, int update,

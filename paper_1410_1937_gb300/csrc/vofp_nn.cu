@@ -1444,6 +1444,36 @@ vofp_status vofp_nn_forward(vofp_nn* n, const float* r, float* z) {
     return cudaGetLastError() == cudaSuccess ? VOFP_OK : VOFP_ERR_CUDA;
 }
 
+vofp_status vofp_nn_conv_apply(vofp_nn* n, int layer, int data_grad, int nx, int ny, int nz, const uint16_t* in,
+                               uint16_t* out) {
+    if (!n || layer < 0 || layer >= 10 || nx <= 0 || ny <= 0 || nz <= 0 || !in || !out ||
+        (reinterpret_cast<uintptr_t>(in) & 15) || (reinterpret_cast<uintptr_t>(out) & 15))
+        return VOFP_ERR_INVALID_ARG;
+    const Layer& l = n->L[layer];
+    const bf16* x = reinterpret_cast<const bf16*>(in);
+    bf16* y = reinterpret_cast<bf16*>(out);
+    vofp_status s = data_grad ? conv(n, x, l.cout, l.blob_b, l.cin, l.nout_b, nullptr, false, y, 0, nx, ny, nz)
+                              : conv(n, x, l.cin, l.blob_f, l.cout, l.nout_f, l.b, true, y, 0, nx, ny, nz);
+    if (s) return s;
+    return read_err(n);
+}
+
+vofp_status vofp_nn_conv_wgrad(vofp_nn* n, int layer, int nx, int ny, int nz, const uint16_t* x, const uint16_t* dy,
+                               float* gw, float* gb) {
+    if (!n || layer < 0 || layer >= 10 || nx <= 0 || ny <= 0 || nz <= 0 || !x || !dy || !gw || !gb ||
+        (reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(dy) & 15))
+        return VOFP_ERR_INVALID_ARG;
+    Layer l = n->L[layer];
+    l.gw = gw;
+    l.gb = gb;
+    if (cudaMemsetAsync(gw, 0, sizeof(float) * l.nw(), n->stream) != cudaSuccess ||
+        cudaMemsetAsync(gb, 0, sizeof(float) * l.cout, n->stream) != cudaSuccess)
+        return VOFP_ERR_CUDA;
+    vofp_status s = conv_wgrad(n, reinterpret_cast<const bf16*>(x), reinterpret_cast<const bf16*>(dy), l, nx, ny, nz);
+    if (s) return s;
+    return read_err(n);
+}
+
 vofp_status vofp_nn_train_step(vofp_nn* n, const float* r, const float* target, float lr, int update, float* loss) {
     if (!n || !r || !target) return VOFP_ERR_INVALID_ARG;
     if (!n->bound) {

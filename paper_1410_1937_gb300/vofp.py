@@ -114,6 +114,10 @@ _sig = {
     "vofp_nn_export_geometry": (ctypes.c_int, [_vp, _vp, _vp]),
     "vofp_nn_set_geometry": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]),
     "vofp_nn_forward": (ctypes.c_int, [_vp, _vp, _vp]),
+    "vofp_nn_conv_apply": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          _vp, _vp]),
+    "vofp_nn_conv_wgrad": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp,
+                                          _vp]),
     "vofp_nn_train_step": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_float, ctypes.c_int, _P(ctypes.c_float)]),
     "vofp_time_iteration_kernels": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                    _P(ctypes.c_float), _P(ctypes.c_float), _P(ctypes.c_float)]),
@@ -437,6 +441,10 @@ class Context:
         return a.value, b.value, r.value
 
 
+# (input, output) channels of the network's ten 3x3x3 convolutions, forward order
+LAYER_CHANNELS = [(16, 16), (16, 16), (16, 32), (32, 32), (32, 64), (64, 64), (96, 32), (32, 32), (48, 16), (16, 16)]
+
+
 class Network:
     """The learned preconditioner (vofp_nn_*): 3-level 3-D conv encoder-decoder, BF16 on tensor cores."""
 
@@ -501,6 +509,39 @@ class Network:
             out = torch.empty(self.n, dtype=torch.float32, device=r.device)
         self._check(_lib.vofp_nn_forward(self.h, _dev(r, self.n, "r", "float32"), _dev(out, self.n, "z", "float32")))
         return out
+
+    def conv_apply(self, layer, x, shape, data_grad=False):
+        """One convolution layer on a chunk-planar BF16 tensor x of shape (nz, ny, nx) voxels
+        (vofp_nn_conv_apply); returns the chunk-planar BF16 output."""
+        import torch
+        nz, ny, nx = shape
+        cin, cout = LAYER_CHANNELS[layer]
+        cout_here = cin if data_grad else cout
+        cin_here = cout if data_grad else cin
+        V = nx * ny * nz
+        if x.dtype != torch.bfloat16 or x.numel() != V * cin_here or not x.is_cuda or not x.is_contiguous():
+            raise ValueError("x must be a contiguous chunk-planar CUDA bfloat16 tensor of the layer's input")
+        out = torch.empty(V * cout_here, dtype=torch.bfloat16, device=x.device)
+        self._check(_lib.vofp_nn_conv_apply(self.h, int(layer), int(bool(data_grad)), int(nx), int(ny), int(nz),
+                                            ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def conv_wgrad(self, layer, x, dy, shape):
+        """Weight and bias gradients of one convolution layer from chunk-planar BF16 tensors x (its
+        input) and dy (its output gradient) (vofp_nn_conv_wgrad); returns (gw [27][cout][cin], gb)."""
+        import torch
+        nz, ny, nx = shape
+        cin, cout = LAYER_CHANNELS[layer]
+        V = nx * ny * nz
+        for t, c in ((x, cin), (dy, cout)):
+            if t.dtype != torch.bfloat16 or t.numel() != V * c or not t.is_cuda or not t.is_contiguous():
+                raise ValueError("x and dy must be contiguous chunk-planar CUDA bfloat16 tensors")
+        gw = torch.empty(27 * cout * cin, dtype=torch.float32, device=x.device)
+        gb = torch.empty(cout, dtype=torch.float32, device=x.device)
+        self._check(_lib.vofp_nn_conv_wgrad(self.h, int(layer), int(nx), int(ny), int(nz),
+                                            ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(dy.data_ptr()),
+                                            ctypes.c_void_p(gw.data_ptr()), ctypes.c_void_p(gb.data_ptr())))
+        return gw.view(27, cout, cin), gb
 
     def train_step(self, r, target, lr=1e-3, update=True):
         loss = ctypes.c_float(0.0)

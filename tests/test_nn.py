@@ -224,6 +224,54 @@ def test_gpu_forward_and_gradients_match_oracle(gpu, oracle, shape):
     assert all(ew < 1e-2 for i, ew, _ in errs if i in (0, 1, 8, 9, "head")), errs
 
 
+def _to_planar(a):
+    """(nz, ny, nx, C) channels-last -> the network's chunk-planar order (C/8, voxels, 8)."""
+    nz, ny, nx, C = a.shape
+    return np.ascontiguousarray(a.reshape(nz * ny * nx, C // 8, 8).transpose(1, 0, 2)).ravel()
+
+
+def _from_planar(flat, shape, C):
+    nz, ny, nx = shape
+    return np.asarray(flat, dtype=np.float64).reshape(C // 8, nz * ny * nx, 8).transpose(1, 0, 2).reshape(
+        nz, ny, nx, C)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("layer", range(10))
+def test_gpu_conv_layer_matches_oracle(gpu, layer):
+    """One convolution layer's three tensor-core kernels (forward with bias and ReLU, data gradient,
+    weight and bias gradients) element by element against the oracle's definitions on the same BF16
+    inputs and weights, at 20 x 36 x 10 voxels: ragged tiles in x (2 x 8 + 4) and y (2 x 16 + 4).
+    The GPU accumulates in FP32; the forward and data-gradient outputs are rounded to BF16 once
+    (within one BF16 unit, 2^-8 relative), the weight gradients stay FP32 (sums over 7200 voxels)."""
+    torch, vofp = gpu
+    shape = (10, 36, 20)
+    cin, cout = R.LAYERS[layer]
+    net = vofp.Network(seed=3)
+    layers, _, _ = R.unpack(net.get_params().astype(np.float64))
+    W, b = layers[layer]
+    Wb = R.bf16_round(W)
+    rng = np.random.default_rng(40 + layer)
+    x = R.bf16_round(rng.normal(size=shape + (cin,)))
+    dy = R.bf16_round(rng.normal(size=shape + (cout,)))
+
+    def dev(a):
+        return torch.from_numpy(_to_planar(a).astype(np.float32)).to(torch.bfloat16).cuda()
+
+    def close(got, ref, rtol, rel_atol):
+        atol = rel_atol * np.abs(ref).max()
+        bad = np.abs(got - ref) > rtol * np.abs(ref) + atol
+        assert not bad.any(), (layer, int(bad.sum()), float(np.abs(got - ref).max()))
+
+    y = net.conv_apply(layer, dev(x), shape).float().cpu().numpy()
+    close(_from_planar(y, shape, cout), np.maximum(R.conv3(x, Wb, b), 0.0), 2.0 ** -8, 1e-5)
+    dx = net.conv_apply(layer, dev(dy), shape, data_grad=True).float().cpu().numpy()
+    close(_from_planar(dx, shape, cin), R.conv3_data_grad(dy, Wb, shape), 2.0 ** -8, 1e-5)
+    gw, gb = net.conv_wgrad(layer, dev(x), dev(dy), shape)
+    close(gw.cpu().numpy().astype(np.float64), R.conv3_weight_grad(x, dy), 1e-4, 1e-5)
+    close(gb.cpu().numpy().astype(np.float64), dy.reshape(-1, cout).sum(axis=0), 1e-4, 1e-5)
+
+
 @pytest.mark.gpu
 def test_gpu_adam_step_matches_reference(gpu):
     torch, vofp = gpu
