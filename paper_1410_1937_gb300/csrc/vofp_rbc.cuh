@@ -8,12 +8,15 @@
 // iteration then streams half of each vector instead of all of it: about 24 B per cell for the
 // iteration kernel instead of 36.
 //
-// Per plane m, for a tile of 32 pairs (64 cells) x 8 rows:
+// Per plane m, for a tile of 32 pairs (64 cells) x 8 RPT rows:
 //   p = r + beta p_old on the pairs of the tile with a two-pair / two-row halo (compact);
 //   w on the even cell of each pair of the tile with a one-cell halo: the red formula
 //     w = sum_f T_f p_nb for every even cell (all its neighbours are black); an exception's w must
-//     be its own p instead, which the fix kernels of vofp_rbc.cu put back afterwards;
+//     be its own p instead, which the fix-row kernel of vofp_rbc.cu puts back afterwards from the
+//     differences dE that the blocks form with the exceptions' own rows;
 //   t = p - sum_f T_f w_nb on the black cell of each own pair, p.t, x += alpha p_old.
+// Blocks march groups of neighbouring tiles in step (RbcSplit), so that the halos they share
+// come from L2.
 // The even cell of pair h in row j, plane m sits at x = 2h + rho with rho = (j + m) & 1, the black
 // one at 2h + 1 - rho; x-neighbours of the even cell are the black cells of pairs h - 1 + rho and
 // h + rho, those of the black cell the even cells of pairs h - rho and h + 1 - rho; y- and
