@@ -319,15 +319,25 @@ __global__ void k_blob_dgrad(const float* __restrict__ w, int cout, int cin, int
 // The nine accumulators stay in tensor memory (9 NCO FP32 columns) over all of the block's tiles;
 // four warps add them to the FP32 gradient once at the end.  The M rows past the used ones read
 // other shared memory and are not used.
+//
+// With M = 64 and 16 output channels (the finest layers) the x taps go into N as well: the
+// gradient tile is received 10 voxels wide, and one instruction's N = 24 columns are its 8 channels
+// of one group at three one-voxel shifts j = 0, 1, 2 (stride byte offset 16: the three core
+// matrices overlap), paired with the input box at x offset 2, so that column group j holds x tap
+// 2 - j; per K step that is 3 y taps x 2 groups = 6 instructions instead of 9.  Each shift sums the
+// gradient over its tile's 8 voxels moved by j, so the tiles start one tile further left (x0 =
+// -8, ...) to count every gradient voxel once at every shift.
 template <int CIC, int NCO, int M>
 struct WgCfg {
     static_assert((CIC == 16 && M == 64) || (CIC == 32 && M == 128), "input-channel chunk and rows");
     static_assert(NCO % 16 == 0, "output-channel slice");
+    static constexpr bool XN = M == 64 && NCO == 16;                     // x taps in N
+    static constexpr int DW = XN ? kBoxX : kTileX;                       // gradient box width
     static constexpr int XG = 3 * CIC / 8;                               // group planes of a box
     static constexpr int MG = M / 8, DG = NCO / 8;
     static constexpr int R = 4;                                          // ring slots
     static constexpr uint32_t XSLOT = (uint32_t)XG * kGroupBytes;        // input box (3 planes, halo)
-    static constexpr uint32_t DGB = kTileX * kTileY * 16;                // one gradient group
+    static constexpr uint32_t DGB = DW * kTileY * 16;                    // one gradient group
     static constexpr uint32_t DSLOT = (uint32_t)DG * DGB;
     static constexpr uint32_t TCOLS = pow2_at_least(9u * NCO);
     static constexpr size_t oX = 0;
@@ -343,7 +353,8 @@ struct WgCfg {
 };
 
 struct WgArgs {
-    int tiles_x, tiles_y;
+    int tiles_x, tiles_y;     // tile columns along x (one more, starting at x0 = -8, with x taps in N)
+    int x_first;              // x of the first tile column: 0, or -8 with x taps in N
     long long items;          // tile planes: tiles_x tiles_y nz
     long long per;            // tile planes per block
     int nchunks, nslices;     // input-channel chunks of CIC, output-channel slices of NCO
@@ -404,7 +415,7 @@ k_conv3_wgrad_umma(const __grid_constant__ CUtensorMap x_map, const __grid_const
                 }
                 const long long item = it0 + i;
                 const int tile = (int)(item % ntiles), z = (int)(item / ntiles);
-                const int x0 = (tile % a.tiles_x) * kTileX, y0 = (tile / a.tiles_x) * kTileY;
+                const int x0 = a.x_first + (tile % a.tiles_x) * kTileX, y0 = (tile / a.tiles_x) * kTileY;
                 mbar_expect_tx(&full[s], G::XSLOT + G::DSLOT);
                 umma::tma_load_5d(xs + (size_t)s * G::XSLOT, &x_map, &full[s], 0, x0 - 1, y0 - 1, z - 1, chunk * (CIC / 8));
                 umma::tma_load_5d(ds + (size_t)s * G::DSLOT, &dy_map, &full[s], 0, x0, y0, z, slice * G::DG);
@@ -416,7 +427,7 @@ k_conv3_wgrad_umma(const __grid_constant__ CUtensorMap x_map, const __grid_const
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t id = umma::idesc_bf16_mn(M, NCO);
+            constexpr uint32_t id = G::XN ? umma::idesc_bf16_mn(M, 24) : umma::idesc_bf16_mn(M, NCO);
             const uint32_t xbase = umma::saddr(xs), dbase = umma::saddr(ds);
             for (int i = 0; i < nitems && !fail; ++i) {
                 const int s = i % R;
@@ -429,7 +440,25 @@ k_conv3_wgrad_umma(const __grid_constant__ CUtensorMap x_map, const __grid_const
                 // K steps outermost: consecutive instructions go to the nine taps' separate
                 // accumulators
 #pragma unroll 1
-                for (int ks = 0; ks < kTileY / 2; ++ks) {
+                for (int ks = 0; ks < kTileY / 2 && G::XN; ++ks) {
+                    // K = tile rows 2 ks and 2 ks + 1: gradient box rows one box row (10 voxels)
+                    // apart, the three shifts 16 bytes apart; input box at x offset 2, shifted by
+                    // the y tap
+#pragma unroll
+                    for (int ty = 0; ty < 3; ++ty) {
+                        const uint64_t ad =
+                            umma::smem_desc(xslot + (uint32_t)(((2 * ks + ty) * kBoxX + 2) * 16), kBoxX * 16, kGroupBytes);
+#pragma unroll
+                        for (int cg = 0; cg < G::DG; ++cg) {
+                            const uint64_t bd =
+                                umma::smem_desc(dslot + (uint32_t)(cg * G::DGB + ks * 2 * G::DW * 16), G::DW * 16, 16);
+                            umma::mma_bf16(tmem + (uint32_t)((ty * G::DG + cg) * 24), ad, bd, id,
+                                           (i > 0 || ks > 0) ? 1u : 0u);
+                        }
+                    }
+                }
+#pragma unroll 1
+                for (int ks = 0; ks < kTileY / 2 && !G::XN; ++ks) {
                     // K = tile rows 2 ks and 2 ks + 1 (8 voxels each): gradient tile rows one tile row
                     // apart, channel groups one group plane apart
                     const uint64_t bd = umma::smem_desc(dslot + (uint32_t)(ks * 2 * kTileX * 16), kTileX * 16, G::DGB);
@@ -459,17 +488,25 @@ k_conv3_wgrad_umma(const __grid_constant__ CUtensorMap x_map, const __grid_const
         if (!__any_sync(0xffffffffu, fail) && nitems > 0) {
             umma::fence_after_sync();
 #pragma unroll 1
-            for (int t = 0; t < 9; ++t) {
-                const int tap = 9 * tz + t;
+            for (int c0 = 0; c0 < 9 * NCO; c0 += 16) {
+                uint32_t r[16];
+                umma::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
+                umma::tmem_wait_ld();
+                if (used) {
 #pragma unroll
-                for (int c0 = 0; c0 < NCO; c0 += 16) {
-                    uint32_t r[16];
-                    umma::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * NCO + c0), r);
-                    umma::tmem_wait_ld();
-                    if (used) {
-                        float* dst = a.gw + ((long long)tap * a.cout + slice * NCO + c0) * a.cin + ci;
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) atomicAdd(dst + (long long)j * a.cin, __uint_as_float(r[j]));
+                    for (int j = 0; j < 16; ++j) {
+                        // column c: (y tap, group, shift, channel) with x taps in N, else (tap, channel)
+                        const int c = c0 + j;
+                        int tap, co;
+                        if constexpr (G::XN) {
+                            const int blk = c / 24, rem = c % 24;
+                            tap = 9 * tz + 3 * (blk / G::DG) + (2 - rem / 8);
+                            co = 8 * (blk % G::DG) + (rem & 7);
+                        } else {
+                            tap = 9 * tz + c / NCO;
+                            co = c % NCO;
+                        }
+                        atomicAdd(a.gw + ((long long)tap * a.cout + slice * NCO + co) * a.cin + ci, __uint_as_float(r[j]));
                     }
                 }
             }
@@ -1037,13 +1074,15 @@ vofp_status conv_wgrad(vofp_nn* n, const bf16* x, const bf16* dy, const Layer& l
     const int nco = l.cout == 16 ? 16 : 32;
     const int cic = l.cin % 32 == 0 ? 32 : 16;
     const CUtensorMap* xm = box_map(n, x, nx, ny, nz, l.cin / 8, kBoxX, kBoxY, 3, cic / 8);
-    const CUtensorMap* dm = box_map(n, dy, nx, ny, nz, l.cout / 8, kTileX, kTileY, 1, nco / 8);
+    const bool xn = cic == 16 && nco == 16;   // x taps in N (WgCfg::XN): 10-voxel gradient box
+    const CUtensorMap* dm = box_map(n, dy, nx, ny, nz, l.cout / 8, xn ? kBoxX : kTileX, kTileY, 1, nco / 8);
     if (!xm || !dm) {
         n->err = "tensor map of an activation could not be built";
         return VOFP_ERR_CUDA;
     }
     WgArgs a{};
-    a.tiles_x = (nx + kTileX - 1) / kTileX;
+    a.tiles_x = (nx + kTileX - 1) / kTileX + (xn ? 1 : 0);
+    a.x_first = xn ? -kTileX : 0;
     a.tiles_y = (ny + kTileY - 1) / kTileY;
     a.items = (long long)a.tiles_x * a.tiles_y * nz;
     a.nchunks = l.cin / cic;
