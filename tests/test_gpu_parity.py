@@ -598,6 +598,36 @@ def test_single_cell_grid(vofp, oracle):
     np.testing.assert_allclose(host(x, prob.shape), ref, rtol=1e-13)
 
 
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+@pytest.mark.parametrize("precond", ["jacobi", "rbsgs"])
+def test_zero_right_hand_side_gives_zero_solution(vofp, mode, precond):
+    """b = 0 from x = 0: the solution is exactly 0 after no iteration, with status OK (the relative
+    residual of a zero right-hand side is the absolute one, 0)."""
+    prob = CASES["hull-small"]()
+    ctx, t = vofp.context_for(prob)
+    b = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    m = vofp.MODE_FP64 if mode == "fp64" else vofp.MODE_MIXED
+    pc = vofp.PRECOND_JACOBI if precond == "jacobi" else vofp.PRECOND_RBSGS
+    x, info = ctx.vofp_solve(b, rtol=1e-10, mode=m, precond=pc)
+    assert info["status"] == 0 and info["iterations"] == 0 and info["rel_residual"] == 0.0
+    assert int(torch.count_nonzero(x)) == 0
+
+
+def test_operator_without_unknowns(vofp):
+    """Every cell closed (no open volume, no open face): no unknown, a zero right-hand side for any
+    face velocity, and the solve returns x = 0 with status OK in both modes."""
+    prob = CASES["tiny"]()
+    prob.vf = np.zeros_like(prob.vf)
+    prob.ax, prob.ay, prob.az = np.zeros_like(prob.ax), np.zeros_like(prob.ay), np.zeros_like(prob.az)
+    ctx, t = vofp.context_for(prob)
+    b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
+    assert int(torch.count_nonzero(b)) == 0
+    for m in (vofp.MODE_FP64, vofp.MODE_MIXED):
+        x, info = ctx.vofp_solve(b, rtol=1e-10, mode=m)
+        assert info["status"] == 0 and info["iterations"] == 0
+        assert int(torch.count_nonzero(x)) == 0
+
+
 def test_host_buffer_entry_point_matches_device_path(vofp):
     prob = CASES["c1-small"]()
     ctx, t = vofp.context_for(prob)
