@@ -308,16 +308,31 @@ template <typename V, bool INNER>
 __global__ void __launch_bounds__(kRedThreads)
 k_cg_update(long long n, V* __restrict__ r, const V* __restrict__ q, const uint32_t* __restrict__ bits,
             CgScalars* sc, double* __restrict__ partials, unsigned int* __restrict__ counter,
-            cudaGraphConditionalHandle handle, int use_handle) {
+            cudaGraphConditionalHandle handle, int use_handle, const double* __restrict__ pq_part, int npq) {
     using Acc = typename AccFor<V>::type;
     __shared__ double sh[32];
     __shared__ double s_alpha;
     __shared__ int s_flags;
     grid_dep_wait();
+    // p.Ap: with npq > 0 the kernels before left their block partials in pq_part and every block
+    // sums them itself, in the same fixed order (no last-block pass in those kernels); else the
+    // scalars hold it
+    double pq_sum = 0.0;
+    if (npq > 0) {
+        const int nt = blockDim.x;
+        double v = 0.0;
+        for (int i = threadIdx.x; i < npq; i += nt) v += __ldcg(&pq_part[i]);
+        v = warp_sum(v);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int w = 0; w < nt / 32; ++w) pq_sum += sh[w];
+        __syncthreads();
+    }
     // the scalar step is computed once per block (FP64 division is slow on this part)
     if (threadIdx.x == 0) {
         const double rr = sc->rr;
-        const double pq = sc->pq_raw + sc->pq_corr;
+        const double pq = npq > 0 ? pq_sum : sc->pq_raw + sc->pq_corr;
         // rr == 0: the residual vanished exactly (later unrolled iterations are no-ops)
         const bool ok = sc->status == VOFP_OK && (pq > 0.0) && isfinite(pq) && isfinite(rr) && rr > 0.0;
         const bool broke = !ok && !(rr == 0.0 && sc->status == VOFP_OK);

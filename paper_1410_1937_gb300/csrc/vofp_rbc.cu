@@ -25,6 +25,9 @@ namespace {
 
 constexpr int kNT = 256;
 constexpr int kRbcStages = 3;
+// the iteration kernel's and the fix rows' block partials of p.Ap live in the last quarter of the
+// partials buffer (no other reduction of an inner iteration uses it)
+constexpr int kPqBase = 3 * (kMaxPartials / 4);
 constexpr int kChunk = 2048;            // cells per block of the compaction passes (8 per thread)
 
 int grid_n(long long n) {
@@ -328,8 +331,7 @@ k_rbc_fix_rows(int nf, int ng, const int* __restrict__ fh, const int* __restrict
                const float* __restrict__ fT, const float* __restrict__ dE, const int4* __restrict__ gm,
                const int4* __restrict__ gf, const int* __restrict__ gn, const int* __restrict__ gptr,
                const int* __restrict__ gref, const int* __restrict__ gfx, const double* __restrict__ gcorr,
-               const float* __restrict__ pn, float* __restrict__ q, CgScalars* sc, double* __restrict__ partials,
-               unsigned int* __restrict__ counter) {
+               const float* __restrict__ pn, float* __restrict__ q, double* __restrict__ pq_part) {
     __shared__ double sh[32];
     grid_dep_wait();
     grid_dep_trigger();
@@ -382,10 +384,14 @@ k_rbc_fix_rows(int nf, int ng, const int* __restrict__ fh, const int* __restrict
         }
         corr += gc * pm * pm;
     }
-    double tot;
-    if (grid_reduce(acc.value() + corr, partials, counter, sh, &tot)) {
-        sc->pq_raw += tot;
-        sc->pq_corr = 0.0;
+    // this block's p.delta and group terms (fixed order); the update kernel sums the partials
+    const double v = warp_sum(acc.value() + corr);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += sh[w];
+        pq_part[blockIdx.x] = b;
     }
 }
 
@@ -617,6 +623,8 @@ vofp_status rbc_ensure(vofp_ctx* c) {
         c->rbc_nblocks = 0;
         rbc_split(tiles_x, tiles_y, d.nz, (long long)num_sms() * nb, fgx, fgy, &c->rbc_split, &c->rbc_nblocks);
         if (c->rbc_nblocks <= 0) return VOFP_OK;
+        const int ng = c->ngroups;
+        if (c->rbc_nblocks + ceil_div(nf + ng, (long long)kNT) > kMaxPartials / 4 - 16) return VOFP_OK;
     }
     c->rbc_blocks_per_sm = nb;
     c->rbc_nh = nh;
@@ -657,7 +665,7 @@ void launch_main_t(vofp_ctx* c, cudaStream_t st, const float* po, float* pn, boo
                     c->rbc_nh, c->rbc_ne};
     launch_dep(c, pdl, k_rbc_tma<kRbcStages, RPT>, dim3(c->rbc_nblocks), dim3(kBX, kBY),
                cg_rbc_smem<kRbcStages, RPT>(), st, maps, d, c->rbc_split, ex, po, pn, c->rbc_x, c->rbc_q,
-               c->sc, c->partials, c->counters);
+               c->sc, c->partials + kPqBase);
 }
 void launch_main(vofp_ctx* c, cudaStream_t st, const float* po, float* pn, bool pdl) {
     if (c->rbc_rpt == 1)
@@ -677,7 +685,13 @@ void rbc_aux(vofp_ctx* c, cudaStream_t st, const float* po, float* pn, bool pdl)
                    (const int*)c->rbc_fh, (const int*)c->rbc_fexc, (const float*)c->rbc_fT, (const float*)c->rbc_dE,
                    (const int4*)c->rbc_gm, (const int4*)c->rbc_gf, (const int*)c->rbc_gn, (const int*)c->gptr,
                    (const int*)c->rbc_gref, (const int*)c->rbc_gfx, (const double*)c->gcorr, (const float*)pn,
-                   c->rbc_q, c->sc, c->partials, c->counters);
+                   c->rbc_q, c->partials + kPqBase + c->rbc_nblocks);
+}
+
+// block partials of p.Ap that the iteration kernel and the fix rows leave for the update
+int rbc_pq_parts(const vofp_ctx* c) {
+    const int ng = c->rbc_gm ? c->ngroups : 0;
+    return c->rbc_nblocks + (c->rbc_nf + ng > 0 ? ceil_div(c->rbc_nf + ng, kNT) : 0);
 }
 
 void rbc_iteration(vofp_ctx* c, cudaStream_t st, const float* po, float* pn, cudaGraphConditionalHandle h,
@@ -697,7 +711,8 @@ void rbc_iteration(vofp_ctx* c, cudaStream_t st, const float* po, float* pn, cud
     rbc_aux(c, st, po, pn, pdl);
     const long long nc = c->rbc_nh + c->rbc_ne;
     launch_dep(c, pdl, k_cg_update<float, true>, dim3(grid_n(nc / 4 + 1)), dim3(kNT), 0, st, nc, c->rbc_r,
-               (const float*)c->rbc_q, (const uint32_t*)c->rbc_bits, c->sc, c->partials, c->counters, h, use_h);
+               (const float*)c->rbc_q, (const uint32_t*)c->rbc_bits, c->sc, c->partials, c->counters, h, use_h,
+               (const double*)(c->partials + kPqBase), rbc_pq_parts(c));
 }
 
 void rbc_finish_xf(vofp_ctx* c, cudaStream_t st) {

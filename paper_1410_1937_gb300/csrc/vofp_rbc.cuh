@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kBX* kBY, RPT == 1 ? 3 : 2)
 k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const RbcSplit sp, const RbcExc ex,
           const float* __restrict__ pold,
           float* __restrict__ pnew, float* __restrict__ xv, float* __restrict__ out, CgScalars* __restrict__ sc,
-          double* __restrict__ partials, unsigned int* __restrict__ counter) {
+          double* __restrict__ pq_part) {
     using G = RbcGeomT<RPT>;
     constexpr int PW = G::PW, BWF = G::BWF, BWC = G::BWC, TH = G::TH;
     extern __shared__ __align__(128) unsigned char rbc_smem[];
@@ -425,8 +425,15 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const RbcSplit sp,
         if (tid == 0) atomicCAS(&sc->status, (int)VOFP_OK, (int)VOFP_ERR_DEVICE_TIMEOUT);
     }
     if (!exc_done) exception_rows();   // blocks without planes (or that stopped early)
-    double tot;
-    if (grid_reduce(acc.value(), partials, counter, sh, &tot)) sc->pq_raw = tot;
+    // this block's p.t (fixed order); the update kernel sums the blocks' partials
+    const double v = warp_sum(acc.value());
+    if ((tid & 31) == 0) sh[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+        double b = 0.0;
+        for (int w = 0; w < (kBX * kBY) / 32; ++w) b += sh[w];
+        pq_part[blockIdx.x] = b;
+    }
 }
 
 }  // namespace vofp

@@ -623,10 +623,10 @@ void launch_cg_iteration(vofp_ctx* c, cudaStream_t st, V* r, V* po, V* pn, V* xv
                1, c->sc, c->partials, c->counters);
     if (inner)
         launch(c, k_cg_update<V, true>, stream_grid(c->d.n / (sizeof(V) == 8 ? 2 : 4) + 1), kNT, st,
-               c->d.n, r, (const V*)q, bits, c->sc, c->partials, c->counters, h, use_h);
+               c->d.n, r, (const V*)q, bits, c->sc, c->partials, c->counters, h, use_h, (const double*)nullptr, 0);
     else
         launch(c, k_cg_update<V, false>, stream_grid(c->d.n / (sizeof(V) == 8 ? 2 : 4) + 1), kNT, st,
-               c->d.n, r, (const V*)q, bits, c->sc, c->partials, c->counters, h, use_h);
+               c->d.n, r, (const V*)q, bits, c->sc, c->partials, c->counters, h, use_h, (const double*)nullptr, 0);
 }
 
 // kernels of one iteration (for the launch count of graph executions)
@@ -1492,7 +1492,7 @@ vofp_status time_iteration_kernels(vofp_ctx* c, int precision, bool rb, int reps
         auto upd = [&]() {
             launch(c, k_cg_update<float, false>, stream_grid(nc / 4 + 1), kNT, st, nc, c->rbc_r,
                    (const float*)c->rbc_q, (const uint32_t*)c->rbc_bits, c->sc, c->partials, c->counters,
-                   (cudaGraphConditionalHandle)0, 0);
+                   (cudaGraphConditionalHandle)0, 0, (const double*)nullptr, 0);
         };
         auto aux = [&]() { rbc_time_aux(c, st); };
         if ((s = timed(stn, &t1)) || (s = timed(upd, &t2)) || (s = timed(aux, &t3))) return s;
@@ -1505,7 +1505,7 @@ vofp_status time_iteration_kernels(vofp_ctx* c, int precision, bool rb, int reps
         };
         auto upd = [&]() {
             launch(c, k_cg_update<float, false>, stream_grid(N / 4 + 1), kNT, st, N, c->rf, (const float*)c->qf, bits,
-                   c->sc, c->partials, c->counters, (cudaGraphConditionalHandle)0, 0);
+                   c->sc, c->partials, c->counters, (cudaGraphConditionalHandle)0, 0, (const double*)nullptr, 0);
         };
         if ((s = timed(stn, &t1)) || (s = timed(upd, &t2))) return s;
     } else {
@@ -1517,7 +1517,7 @@ vofp_status time_iteration_kernels(vofp_ctx* c, int precision, bool rb, int reps
         };
         auto upd = [&]() {
             launch(c, k_cg_update<double, false>, stream_grid(N / 2 + 1), kNT, st, N, c->r, (const double*)c->q, bits,
-                   c->sc, c->partials, c->counters, (cudaGraphConditionalHandle)0, 0);
+                   c->sc, c->partials, c->counters, (cudaGraphConditionalHandle)0, 0, (const double*)nullptr, 0);
         };
         if ((s = timed(stn, &t1)) || (s = timed(upd, &t2))) return s;
     }
