@@ -499,14 +499,19 @@ def test_solve_is_bitwise_reproducible(vofp):
     assert torch.equal(x1, x2)
 
 
-@pytest.mark.parametrize("mode", ["fp64", "mixed"])
-def test_host_loop_matches_graph_loop(vofp, mode):
+@pytest.mark.parametrize("mode,precond", [("fp64", "jacobi"), ("mixed", "jacobi"), ("fp64", "rbsgs"),
+                                          ("mixed", "rbsgs")])
+def test_host_loop_matches_graph_loop(vofp, mode, precond):
+    """The graph loop (device-side WHILE, chained launches) and the host-driven loop (ordinary
+    launches) run the same kernels in the same order: bitwise the same solution (the mixed
+    red-black case is the colour-compact iteration with its block partials summed by the update)."""
     prob = CASES["hull-small"]()
     ctx, t = vofp.context_for(prob)
     b = ctx.vofp_rhs_from_face_velocity(t["u"], t["v"], t["w"])
     m = vofp.MODE_FP64 if mode == "fp64" else vofp.MODE_MIXED
-    x1, i1 = ctx.vofp_solve(b, rtol=1e-9, mode=m)
-    x2, i2 = ctx.vofp_solve(b, rtol=1e-9, mode=m, host_loop=1)
+    pc = vofp.PRECOND_JACOBI if precond == "jacobi" else vofp.PRECOND_RBSGS
+    x1, i1 = ctx.vofp_solve(b, rtol=1e-9, mode=m, precond=pc)
+    x2, i2 = ctx.vofp_solve(b, rtol=1e-9, mode=m, precond=pc, host_loop=1)
     assert i1["status"] == 0 and i2["status"] == 0
     assert i1["iterations"] == i2["iterations"] and i1["outer_iterations"] == i2["outer_iterations"]
     assert torch.equal(x1, x2)
