@@ -30,7 +30,8 @@ constexpr int kMaxPartials = 1 << 17;
 struct CgScalars {
     double rr;          // r.r of the (scaled) residual over the unknowns
     double rr0;         // r.r at the start of the current (inner) solve
-    double pq_raw;      // p.t summed over all cells by the stencil kernel
+    double pq_raw;      // p.t summed over all cells by the stencil kernel (the colour-compact
+                        // red-black iteration leaves block partials for the update instead)
     double pq_corr;     // merge-group correction to p.Ap
     double alpha;       // step of the last completed iteration (used by the next stencil pass)
     double beta;        // direction coefficient for the next stencil pass

@@ -325,7 +325,8 @@ __device__ __forceinline__ float fix_delta(int rr, const int* __restrict__ fexc,
 // merge-group members (threads 0..nf-1): q += delta.
 // Merge groups (threads nf..nf+ng-1): every member's final row (the exception row, or the black
 // row plus its correction), then the group value sum + gcorr p_G written to every member.
-// p.delta of the corrections and gcorr p_G^2 into pq_raw.
+// p.delta of the corrections and gcorr p_G^2 as this block's partial of p.Ap (after the iteration
+// kernel's partials), which the update kernel sums.
 __global__ void __launch_bounds__(kNT)
 k_rbc_fix_rows(int nf, int ng, const int* __restrict__ fh, const int* __restrict__ fexc,
                const float* __restrict__ fT, const float* __restrict__ dE, const int4* __restrict__ gm,
