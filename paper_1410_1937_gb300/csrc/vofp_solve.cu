@@ -368,6 +368,46 @@ k_inner_finish_rb(const Dims d, const double* __restrict__ Tx, const double* __r
     }
 }
 
+// The same with one thread per x pair of cells (nx even): a pair holds one cell of each parity,
+// so every thread takes both branches in the same order and no warp splits on the colour; the
+// arithmetic of each cell is the same as above (bitwise the same result).
+__global__ void __launch_bounds__(kRedThreads)
+k_inner_finish_rb_pairs(const Dims d, const double* __restrict__ Tx, const double* __restrict__ Ty,
+                        const double* __restrict__ Tz, const uint32_t* __restrict__ red, const float* __restrict__ xf,
+                        const double* __restrict__ r, double* __restrict__ xt, const CgScalars* sc) {
+    const double scale = sc->scale;
+    const long long rows = (long long)d.ny * d.nz;
+    const int nh = d.nx >> 1;
+    for (long long row = blockIdx.y; row < rows; row += gridDim.y) {
+        const int j = int(row % d.ny), k = int(row / d.ny);
+        for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < nh; h += gridDim.x * blockDim.x) {
+            const long long c0 = 2LL * h + (long long)d.nx * row;
+            const double2 xt2 = *reinterpret_cast<const double2*>(xt + c0);
+            const float2 xf2 = *reinterpret_cast<const float2*>(xf + c0);
+            double out[2] = {xt2.x, xt2.y};
+            const float own[2] = {xf2.x, xf2.y};
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const long long c = c0 + u;
+                const int i = 2 * h + u;
+                if (!is_slave(red, c)) {
+                    out[u] = fma(scale, (double)own[u], out[u]);
+                    continue;
+                }
+                double acc = 0.0;
+                if (i > 0) acc = fma(Tx[c - 1], (double)xf[c - 1], acc);
+                if (i < d.nx - 1) acc = fma(Tx[c], (double)xf[c + 1], acc);
+                if (j > 0) acc = fma(Ty[c - d.nx], (double)xf[c - d.nx], acc);
+                if (j < d.ny - 1) acc = fma(Ty[c], (double)xf[c + d.nx], acc);
+                if (k > 0) acc = fma(Tz[c - d.plane], (double)xf[c - d.plane], acc);
+                if (k < d.nz - 1) acc = fma(Tz[c], (double)xf[c + d.plane], acc);
+                if (scale > 0.0) out[u] += r[c] + scale * acc;
+            }
+            *reinterpret_cast<double2*>(xt + c0) = make_double2(out[0], out[1]);
+        }
+    }
+}
+
 dim3 rows_grid(const vofp_ctx* c, int threads) {
     const long long rows = (long long)c->d.ny * c->d.nz;
     const int gx = ceil_div(c->d.nx, threads);
@@ -746,9 +786,14 @@ void launch_outer_tail(vofp_ctx* c, cudaStream_t st, bool rb) {
         else
             launch(c, k_inner_xf, stream_grid(c->d.n), kNT, st, c->d.n, c->xf, (const float*)c->pf0,
                    (const CgScalars*)c->sc);
-        launch(c, k_inner_finish_rb, rows_grid(c, kNT), dim3(kNT), st, c->d, (const double*)c->Txs,
-               (const double*)c->Tys, (const double*)c->Tzs, (const uint32_t*)c->red_bits, (const float*)c->xf,
-               (const double*)c->r, c->xt, (const CgScalars*)c->sc);
+        if (c->d.nx % 2 == 0)
+            launch(c, k_inner_finish_rb_pairs, rows_grid(c, 2 * kNT), dim3(kNT), st, c->d, (const double*)c->Txs,
+                   (const double*)c->Tys, (const double*)c->Tzs, (const uint32_t*)c->red_bits, (const float*)c->xf,
+                   (const double*)c->r, c->xt, (const CgScalars*)c->sc);
+        else
+            launch(c, k_inner_finish_rb, rows_grid(c, kNT), dim3(kNT), st, c->d, (const double*)c->Txs,
+                   (const double*)c->Tys, (const double*)c->Tzs, (const uint32_t*)c->red_bits, (const float*)c->xf,
+                   (const double*)c->r, c->xt, (const CgScalars*)c->sc);
     } else {
         launch(c, k_inner_finish, stream_grid(c->d.n), kNT, st, c->d.n, c->xf, (const float*)c->pf0, c->xt,
                (const CgScalars*)c->sc);
