@@ -677,9 +677,53 @@ int iteration_kernels(const vofp_ctx* c, bool rb) {
 
 // Mixed precision, red-black: the reduced right-hand side r_S + E_SR r_R of the correction
 // equation (folded over merge groups) into c->q, its norm into sc->rr0.
+// k_rb_gather with to_red = 0 and no base, one thread per x pair of cells (nx even; bitwise the
+// same): dst_c = sum over the red neighbours of T_f src_nb for non-red cells, 0 at red cells
+__global__ void __launch_bounds__(kRedThreads)
+k_rb_gather_pairs(const Dims d, const double* __restrict__ Tx, const double* __restrict__ Ty,
+                  const double* __restrict__ Tz, const uint32_t* __restrict__ red, const double* __restrict__ src,
+                  double* __restrict__ dst) {
+    const long long rows = (long long)d.ny * d.nz;
+    const int nh = d.nx >> 1;
+    auto is_red = [&](long long c) { return (red[c >> 5] >> (c & 31)) & 1u; };
+    for (long long row = blockIdx.y; row < rows; row += gridDim.y) {
+        const int j = int(row % d.ny), k = int(row / d.ny);
+        for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < nh; h += gridDim.x * blockDim.x) {
+            const long long c0 = 2LL * h + (long long)d.nx * row;
+            double out[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const long long c = c0 + u;
+                const int i = 2 * h + u;
+                if (is_red(c)) {
+                    out[u] = 0.0;
+                    continue;
+                }
+                double acc = 0.0;
+                auto term = [&](long long n, double T) {
+                    if (is_red(n)) acc = fma(T, src[n], acc);
+                };
+                if (i > 0) term(c - 1, Tx[c - 1]);
+                if (i < d.nx - 1) term(c + 1, Tx[c]);
+                if (j > 0) term(c - d.nx, Ty[c - d.nx]);
+                if (j < d.ny - 1) term(c + d.nx, Ty[c]);
+                if (k > 0) term(c - d.plane, Tz[c - d.plane]);
+                if (k < d.nz - 1) term(c + d.plane, Tz[c]);
+                out[u] = acc;
+            }
+            *reinterpret_cast<double2*>(dst + c0) = make_double2(out[0], out[1]);
+        }
+    }
+}
+
 void launch_reduced_rhs(vofp_ctx* c, cudaStream_t st) {
-    launch(c, k_rb_gather, rows_grid(c, kNT), dim3(kNT), st, c->d, (const double*)c->Txs, (const double*)c->Tys,
-           (const double*)c->Tzs, (const uint32_t*)c->red_bits, (const double*)c->r, (const double*)nullptr, c->q, 0);
+    if (c->d.nx % 2 == 0)
+        launch(c, k_rb_gather_pairs, rows_grid(c, 2 * kNT), dim3(kNT), st, c->d, (const double*)c->Txs,
+               (const double*)c->Tys, (const double*)c->Tzs, (const uint32_t*)c->red_bits, (const double*)c->r, c->q);
+    else
+        launch(c, k_rb_gather, rows_grid(c, kNT), dim3(kNT), st, c->d, (const double*)c->Txs, (const double*)c->Tys,
+               (const double*)c->Tzs, (const uint32_t*)c->red_bits, (const double*)c->r, (const double*)nullptr, c->q,
+               0);
     if (c->ngroups > 0)
         launch(c, k_group_fold_d, ceil_div(c->ngroups, kNT), kNT, st, c->ngroups, (const int*)c->gptr,
                (const int*)c->gcells, c->q);
