@@ -362,18 +362,24 @@ def run_ours(args, rank, world, local_rank):
                                          host["v"], host["w"], prob.bc, xh, mode=mode, rtol=RTOL,
                                          check_every=args.check_every, inner_rtol=args.inner_rtol,
                                          rho_liquid=prob.rho_liquid, rho_gas=prob.rho_gas,
-                                         merge_threshold=prob.merge_threshold, dt=prob.dt, precond=pc)
+                                         merge_threshold=prob.merge_threshold,
+                                         density_smoothing=prob.density_smoothing, dt=prob.dt, precond=pc)
                 assert r["status"] == 0, r
+                return r
             for _ in range(max(1, args.warmup)):
                 host_step()
             if world > 1:
                 dist.barrier()
             torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for _ in range(args.steps):
-                host_step()
-            torch.cuda.synchronize()
-            e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+            stamps, solve_ms = [], []
+            with ClockSampler(local_rank) as clk_e2e:
+                t0 = time.perf_counter()
+                for _ in range(args.steps):
+                    solve_ms.append(host_step()["seconds"] * 1e3)
+                    stamps.append(time.perf_counter())
+                torch.cuda.synchronize()
+                e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+            step_ms = [(b1 - a1) * 1e3 for a1, b1 in zip([t0] + stamps[:-1], stamps)]
             te_ms = max_over_ranks(e2e_ms, world, "cuda")
             h2d = sum(v.numel() * 8 for v in host.values())
             solutions["e2e"] = xh.numpy().copy()
@@ -391,6 +397,7 @@ def run_ours(args, rank, world, local_rank):
             e2e = {"value": job_rate(world, te_ms), "unit": "solves/s", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": n * 8, "ms_per_step": te_ms,
                    "h2d_ms": c0.elapsed_time(c1), "d2h_ms": c1.elapsed_time(c2),
+                   "step_ms": step_ms, "solve_ms": solve_ms, "clocks": clk_e2e.summary(),
                    "host_cpus": affinity_note}
             del dev, back
             ctx2.close()
