@@ -114,7 +114,9 @@ typedef struct {
  *   inner_restart  mixed mode: 0 (default) keeps the FP32 search direction across refinement
  *               steps (the FP64 residual replaces the FP32 one, a "reliable update"); 1 restarts
  *               the inner PCG from p = r at every refinement step.
- *   check_every convergence is tested every check_every iterations (even, >= 2; 0 = default 8).
+ *   check_every convergence is tested every check_every iterations (even, 2 .. 64; 0 = default:
+ *               64 in mixed mode from 2^20 cells on, where an inner solve runs on to the end of
+ *               its 64 iterations past its stop and saves refinement steps, 8 otherwise).
  *   x0_zero     1: ignore the contents of x and start from 0.
  *   host_loop   0: the loop runs as a CUDA graph with a device-side WHILE condition (no host round
  *               trip per iteration).  1: the host launches each kernel and reads the convergence

@@ -304,16 +304,41 @@ __device__ __forceinline__ bool is_slave(const uint32_t* __restrict__ bits, long
 // alpha = r.r / p.Ap;  r -= alpha q;  r.r over the unknowns (cells that are not another cell's
 // group member).  The last block stores rr, beta = rr_new / rr_old, alpha, counts the iteration
 // and, for an inner (mixed-precision) loop, ends it when rr <= inner_rtol^2 rr0 or max_iter.
+// At most 64 registers (four 256-thread blocks per SM), so that a grid of four blocks per SM is one
+// wave.
 template <typename V, bool INNER>
-__global__ void __launch_bounds__(kRedThreads)
+__global__ void __launch_bounds__(kRedThreads, 4)
 k_cg_update(long long n, V* __restrict__ r, const V* __restrict__ q, const uint32_t* __restrict__ bits,
             CgScalars* sc, double* __restrict__ partials, unsigned int* __restrict__ counter,
             cudaGraphConditionalHandle handle, int use_handle, const double* __restrict__ pq_part, int npq) {
-    using Acc = typename AccFor<V>::type;
     __shared__ double sh[32];
     __shared__ double s_alpha;
     __shared__ int s_flags;
     grid_dep_wait();
+    using Acc = typename AccFor<V>::type;
+    constexpr int VW = sizeof(V) == 8 ? 2 : 4;
+    using VV = typename std::conditional<sizeof(V) == 8, double2, float4>::type;
+    constexpr int UN = 4;
+    const long long nv = n / VW;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    VV* rvp = reinterpret_cast<VV*>(r);
+    const VV* qvp = reinterpret_cast<const VV*>(q);
+    long long vi = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    VV rv[UN], qv[UN];
+    uint32_t w[UN];
+    auto load = [&]() {
+#pragma unroll
+        for (int u = 0; u < UN; ++u) {
+            rv[u] = rvp[vi + u * stride];
+            qv[u] = qvp[vi + u * stride];
+            const long long c0 = (vi + u * stride) * VW;
+            w[u] = bits[c0 >> 5] >> (c0 & 31);
+        }
+    };
+    // the first chunk's loads do not depend on alpha: issued before the scalar step, so that
+    // their latency overlaps the p.Ap sum and the division
+    bool full = vi + (UN - 1) * stride < nv;
+    if (full) load();
     // p.Ap: with npq > 0 the kernels before left their block partials in pq_part and every block
     // sums them itself, in the same fixed order (no last-block pass in those kernels); else the
     // scalars hold it
@@ -326,7 +351,7 @@ k_cg_update(long long n, V* __restrict__ r, const V* __restrict__ q, const uint3
         if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
         __syncthreads();
         if (threadIdx.x == 0)
-            for (int w = 0; w < nt / 32; ++w) pq_sum += sh[w];
+            for (int wi = 0; wi < nt / 32; ++wi) pq_sum += sh[wi];
         __syncthreads();
     }
     // the scalar step is computed once per block (FP64 division is slow on this part)
@@ -344,59 +369,45 @@ k_cg_update(long long n, V* __restrict__ r, const V* __restrict__ q, const uint3
     const bool broke = (s_flags & 2) != 0;
     const V alpha = (V)alpha_d;
     Acc acc;
-    constexpr int VW = sizeof(V) == 8 ? 2 : 4;
-    using VV = typename std::conditional<sizeof(V) == 8, double2, float4>::type;
-    constexpr int UN = 4;
-    const long long nv = n / VW;
-    const long long stride = (long long)gridDim.x * blockDim.x;
     const V na = -alpha;
-    auto upd = [&](VV& rv, const VV& qv, uint32_t w) {
+    auto upd = [&](VV& a, const VV& b, uint32_t m) {
         if constexpr (VW == 2) {
-            rv.x = fmav(na, qv.x, rv.x);
-            rv.y = fmav(na, qv.y, rv.y);
-            if (!(w & 1u)) acc.add(rv.x, rv.x);
-            if (!(w & 2u)) acc.add(rv.y, rv.y);
+            a.x = fmav(na, b.x, a.x);
+            a.y = fmav(na, b.y, a.y);
+            if (!(m & 1u)) acc.add(a.x, a.x);
+            if (!(m & 2u)) acc.add(a.y, a.y);
         } else {
-            rv.x = fmav(na, qv.x, rv.x);
-            rv.y = fmav(na, qv.y, rv.y);
-            rv.z = fmav(na, qv.z, rv.z);
-            rv.w = fmav(na, qv.w, rv.w);
-            if (!(w & 1u)) acc.add(rv.x, rv.x);
-            if (!(w & 2u)) acc.add(rv.y, rv.y);
-            if (!(w & 4u)) acc.add(rv.z, rv.z);
-            if (!(w & 8u)) acc.add(rv.w, rv.w);
+            a.x = fmav(na, b.x, a.x);
+            a.y = fmav(na, b.y, a.y);
+            a.z = fmav(na, b.z, a.z);
+            a.w = fmav(na, b.w, a.w);
+            if (!(m & 1u)) acc.add(a.x, a.x);
+            if (!(m & 2u)) acc.add(a.y, a.y);
+            if (!(m & 4u)) acc.add(a.z, a.z);
+            if (!(m & 8u)) acc.add(a.w, a.w);
         }
     };
-    VV* rvp = reinterpret_cast<VV*>(r);
-    const VV* qvp = reinterpret_cast<const VV*>(q);
-    long long vi = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    for (; vi + (UN - 1) * stride < nv; vi += UN * stride) {
-        VV rv[UN], qv[UN];
-        uint32_t w[UN];
-#pragma unroll
-        for (int u = 0; u < UN; ++u) {
-            rv[u] = rvp[vi + u * stride];
-            qv[u] = qvp[vi + u * stride];
-            const long long c0 = (vi + u * stride) * VW;
-            w[u] = bits[c0 >> 5] >> (c0 & 31);
-        }
+    while (full) {
 #pragma unroll
         for (int u = 0; u < UN; ++u) {
             upd(rv[u], qv[u], w[u]);
             rvp[vi + u * stride] = rv[u];
         }
+        vi += UN * stride;
+        full = vi + (UN - 1) * stride < nv;
+        if (full) load();
     }
     for (; vi < nv; vi += stride) {
-        VV rv = rvp[vi];
-        const VV qv = qvp[vi];
+        VV a = rvp[vi];
+        const VV b = qvp[vi];
         const long long c0 = vi * VW;
-        upd(rv, qv, bits[c0 >> 5] >> (c0 & 31));
-        rvp[vi] = rv;
+        upd(a, b, bits[c0 >> 5] >> (c0 & 31));
+        rvp[vi] = a;
     }
     for (long long c = nv * VW + blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += stride) {
-        V rv = fmav(-alpha, q[c], r[c]);
-        r[c] = rv;
-        if (!is_slave(bits, c)) acc.add(rv, rv);
+        V a = fmav(-alpha, q[c], r[c]);
+        r[c] = a;
+        if (!is_slave(bits, c)) acc.add(a, a);
     }
     double tot;
     if (grid_reduce(acc.value(), partials, counter, sh, &tot)) {

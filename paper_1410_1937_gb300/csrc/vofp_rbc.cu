@@ -711,7 +711,10 @@ void rbc_iteration(vofp_ctx* c, cudaStream_t st, const float* po, float* pn, cud
     launch_main(c, st, po, pn, pdl);
     rbc_aux(c, st, po, pn, pdl);
     const long long nc = c->rbc_nh + c->rbc_ne;
-    launch_dep(c, pdl, k_cg_update<float, true>, dim3(grid_n(nc / 4 + 1)), dim3(kNT), 0, st, nc, c->rbc_r,
+    // the update: one wave of four 256-thread blocks per SM (its register cap); two waves of eight
+    // per SM took 7.5 us more per iteration at 512x256x128
+    const int ug = std::min(grid_n(nc / 4 + 1), num_sms() * 4);
+    launch_dep(c, pdl, k_cg_update<float, true>, dim3(ug), dim3(kNT), 0, st, nc, c->rbc_r,
                (const float*)c->rbc_q, (const uint32_t*)c->rbc_bits, c->sc, c->partials, c->counters, h, use_h,
                (const double*)(c->partials + kPqBase), rbc_pq_parts(c));
 }

@@ -1090,7 +1090,15 @@ vofp_status solve_pass(vofp_ctx* c, const double* b, double* x, const vofp_solve
     if (o->mode == VOFP_MODE_MIXED && o->precond == VOFP_PRECOND_RBSGS && (s = rbc_ensure(c))) return s;
     const long long N = c->d.n;
     cudaStream_t st = c->stream;
-    const int U = o->check_every > 0 ? o->check_every : 8;
+    // Default: the FP64 loop checks its true residual every 8 iterations, and so does the mixed
+    // solve's inner loop below 2^20 cells; from 2^20 cells on it tests its stop every 64. An inner
+    // solve runs on to the end of its unrolled body past its target, and on large systems, where
+    // one takes hundreds of iterations, that overshoot saves refinement steps (512x256x128: 2560
+    // iterations in 8 steps, 290 ms, against 2640 in 12, 303 ms, testing every 8). On small ones
+    // an inner solve can reach the FP32 rounding floor within 64 iterations, and the steps taken
+    // there, kept as the next inner solve's direction, stalled it (a 16^3 sphere, Jacobi: 100032
+    // iterations without converging).
+    const int U = o->check_every > 0 ? o->check_every : (o->mode == VOFP_MODE_MIXED && N >= (1LL << 20) ? 64 : 8);
     VOFP_CUDA_TRY(c, cudaEventRecord(c->ev0, st));
     double sums[3];
     if ((s = prepare_rhs(c, b, sums))) return s;

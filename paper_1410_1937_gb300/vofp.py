@@ -313,7 +313,7 @@ class Context:
     def vofp_rk2_step(self, F, ax, ay, az, vol_frac, u, v, w, bc, p, order=0, R=None, neumann_flux=None,
                       rho_liquid=1000.0, rho_gas=1.2, merge_threshold=0.1, density_smoothing=0, dt=1.0,
                       mode=MODE_MIXED, precond=PRECOND_RBSGS, rtol=1e-8, max_iter=100000, inner_rtol=0.0,
-                      check_every=8, raise_on_error=True):
+                      check_every=0, raise_on_error=True):
         """One RK2 step of Sec. 2.1 (two solves, two projections, two VOF steps); F, u, v, w and p
         are updated in place.  Returns the two solves' info dicts and the largest group divergence."""
         b = self._bc(bc, neumann_flux)
@@ -357,7 +357,7 @@ class Context:
         return r.value
 
     def vofp_solve(self, b, x=None, mode=MODE_FP64, rtol=1e-10, max_iter=100000, inner_rtol=0.0,
-                   check_every=8, precond=PRECOND_JACOBI, raise_on_error=True, x0_zero=0, host_loop=0,
+                   check_every=0, precond=PRECOND_JACOBI, raise_on_error=True, x0_zero=0, host_loop=0,
                    nn=None, stag_window=0, inner_restart=0, stag_ratio=0.0):
         import torch
         if x is None:
@@ -378,7 +378,7 @@ class Context:
         return x, out
 
     def vofp_solve_host(self, F, ax, ay, az, vol_frac, u, v, w, bc, x_out, mode=MODE_FP64, rtol=1e-10,
-                        max_iter=100000, inner_rtol=0.0, check_every=8, rho_liquid=1000.0, rho_gas=1.2,
+                        max_iter=100000, inner_rtol=0.0, check_every=0, rho_liquid=1000.0, rho_gas=1.2,
                         merge_threshold=0.1, density_smoothing=0, dt=1.0, precond=PRECOND_JACOBI, inner_restart=0):
         """Host-buffer end-to-end call: numpy (or pinned torch CPU) float64 arrays in, x_out out."""
         def hp(a, n, name):
