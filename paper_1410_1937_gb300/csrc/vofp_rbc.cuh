@@ -363,40 +363,54 @@ k_rbc_tma(const __grid_constant__ RbcMaps maps, const Dims d, const RbcSplit sp,
                     const float* Pu = pl(mw + 1);
                     const float* Pd = pl(mw - 1);
                     float* Wo = wl(mw);
-#pragma unroll
-                    for (int q = 0; q < RPT; ++q) {
-                        // the own pair (cells 2 xo, 2 xo + 1 of box row yo): its even cell's w
-                        // (the terms of w_even, same order) and its black cell's coefficients and
-                        // p for the t step two steps later, from the coefficients of both cells
-                        // read as 8-byte words
+                    // the own pair (cells 2 xo, 2 xo + 1 of box row yo): its even cell's w (the
+                    // terms of w_even, same order) and its black cell's coefficients and p for the
+                    // t step two steps later, from the coefficients of both cells read as 8-byte
+                    // words. The even cell's side rho is the same for the RPT rows of a thread
+                    // (kBY rows apart) and for the 32 threads of a warp (one row): a branch per
+                    // warp instead of a select per operand
+                    auto own_row = [&](auto rho_c, int q) {
+                        constexpr int RHO = decltype(rho_c)::value;
                         const int yo = ty + kBY * q + 1;
-                        const int rho = (j0 + yo - 1 + mw) & 1;
                         const float xl = X[yo * BWF + 2 * xo - 1];
                         const float2 x2 = *reinterpret_cast<const float2*>(X + yo * BWF + 2 * xo);
                         const float2 ya = *reinterpret_cast<const float2*>(Y + yo * BWF + 2 * xo);
                         const float2 yb = *reinterpret_cast<const float2*>(Y + (yo + 1) * BWF + 2 * xo);
                         const float2 tzp = *reinterpret_cast<const float2*>(Z + yo * BWF + 2 * xo);
+                        const float2 tzm = own_tzm[q];
                         const int e = (yo + 1) * PW + xo;
-                        const float pm = P0[e - 1], pc = P0[e], pp = P0[e + 1];
+                        const float pc = P0[e];
                         float u = 0.0f;
-                        u = fmav(rho ? x2.y : x2.x, rho ? pp : pc, u);
-                        u = fmav(rho ? x2.x : xl, rho ? pc : pm, u);
-                        u = fmav(rho ? yb.y : yb.x, P0[e + PW], u);
-                        u = fmav(rho ? ya.y : ya.x, P0[e - PW], u);
-                        u = fmav(rho ? tzp.y : tzp.x, Pu[e], u);
-                        u = fmav(rho ? own_tzm[q].y : own_tzm[q].x, Pd[e], u);
-                        Wo[yo * PW + xo] = u;
                         Co co;
-                        co.tx = rho ? x2.x : x2.y;
-                        co.txl = rho ? xl : x2.x;
-                        co.ty = rho ? yb.x : yb.y;
-                        co.tyd = rho ? ya.x : ya.y;
-                        co.tz = rho ? tzp.x : tzp.y;
-                        co.tzm = rho ? own_tzm[q].x : own_tzm[q].y;
-                        co.p = pc;
+                        if constexpr (RHO == 1) {
+                            u = fmav(x2.y, P0[e + 1], u);
+                            u = fmav(x2.x, pc, u);
+                            u = fmav(yb.y, P0[e + PW], u);
+                            u = fmav(ya.y, P0[e - PW], u);
+                            u = fmav(tzp.y, Pu[e], u);
+                            u = fmav(tzm.y, Pd[e], u);
+                            co = Co{x2.x, xl, yb.x, ya.x, tzp.x, tzm.x, pc};
+                        } else {
+                            u = fmav(x2.x, pc, u);
+                            u = fmav(xl, P0[e - 1], u);
+                            u = fmav(yb.x, P0[e + PW], u);
+                            u = fmav(ya.x, P0[e - PW], u);
+                            u = fmav(tzp.x, Pu[e], u);
+                            u = fmav(tzm.x, Pd[e], u);
+                            co = Co{x2.y, x2.x, yb.y, ya.y, tzp.y, tzm.y, pc};
+                        }
+                        Wo[yo * PW + xo] = u;
                         own_tzm[q] = tzp;
                         sa[q] = sb[q];
                         sb[q] = co;
+                    };
+                    static_assert(kBY % 2 == 0, "the rows of a thread share their parity");
+                    if ((j0 + ty + mw) & 1) {
+#pragma unroll
+                        for (int q = 0; q < RPT; ++q) own_row(std::integral_constant<int, 1>{}, q);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < RPT; ++q) own_row(std::integral_constant<int, 0>{}, q);
                     }
                     if (has_ring) {
                         float2 tzr;
