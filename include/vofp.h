@@ -344,6 +344,34 @@ vofp_status vofp_solve_host(vofp_ctx* ctx, const double* F, const double* ax, co
                             const vofp_phys* phys, const vofp_solve_opts* opts, double* x_host,
                             vofp_solve_info* info);
 
+/* One step of vofp_solve_host_batch: the inputs of vofp_solve_host (host buffers; vol_frac may be
+ * NULL) and where that step's pressure goes. */
+typedef struct vofp_host_step {
+    const double* F;
+    const double* ax;
+    const double* ay;
+    const double* az;
+    const double* vol_frac;
+    const double* u;
+    const double* v;
+    const double* w;
+    double* x_host;
+} vofp_host_step;
+
+/* nsteps independent end-to-end solves on this context's grid, with one boundary set, physics and
+ * options for all: step i gives the same x_host and infos[i] as vofp_solve_host on its buffers
+ * (steps run in order; each builds the operator from its own inputs).  Step i + 1's uploads run
+ * on a copy stream, into a second staging set, while step i solves (issued once its operator is
+ * built), so with pinned host buffers a step costs about its device time plus the download of its
+ * pressure; the copy stream waits for step 0's own uploads first.  Device staging: b and x (2 N
+ * doubles) and two input sets of 2 N + 2 x (faces) doubles each, allocated on first use and kept
+ * (one set with nsteps = 1).  infos: nsteps records, or NULL.  Returns OK, or the first
+ * NOT_CONVERGED / BREAKDOWN among the steps (the batch goes on past those); any other error ends
+ * the batch at that step, leaving its later x_host and infos untouched.  Every return comes after
+ * the last copy that reads a caller's buffer.  vofp_solve_host is this call with one step. */
+vofp_status vofp_solve_host_batch(vofp_ctx* ctx, int nsteps, const vofp_host_step* steps, const vofp_bc* bc,
+                                  const vofp_phys* phys, const vofp_solve_opts* opts, vofp_solve_info* infos);
+
 /* master[c] (device int32, cells) = root cell of c's merge group, -1 for cells without unknown. */
 vofp_status vofp_merge_map(vofp_ctx* ctx, int32_t* master);
 

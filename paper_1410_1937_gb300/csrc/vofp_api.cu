@@ -93,6 +93,9 @@ void vofp_destroy(vofp_ctx* c) {
         cudaStreamDestroy(c->copy_stream);
     }
     if (c->copy_done) cudaEventDestroy(c->copy_done);
+    if (c->ops_done) cudaEventDestroy(c->ops_done);
+    for (cudaEvent_t e : c->set_ready)
+        if (e) cudaEventDestroy(e);
     for (void* p : c->allocs) cudaFree(p);
     delete c;
 }
@@ -210,57 +213,148 @@ vofp_status vofp_solve(vofp_ctx* c, const double* b, double* x, const vofp_solve
     return vofp::solve(c, b, x, o, info);
 }
 
-vofp_status vofp_solve_host(vofp_ctx* c, const double* F, const double* ax, const double* ay, const double* az,
-                            const double* vf, const double* u, const double* v, const double* w, const vofp_bc* bc,
-                            const vofp_phys* phys, const vofp_solve_opts* o, double* x_host, vofp_solve_info* info) {
-    vofp_status s = check_ctx(c, false);
-    if (s) return s;
-    if (!F || !ax || !ay || !az || !u || !v || !w || !x_host || !o) return invalid(c, "null input");
+namespace {
+// One set of a host call's inputs in device staging: cells F, vol_frac; faces ax, ay, az, u, v, w.
+struct HostSet {
+    double *F, *vf, *ax, *ay, *az, *u, *v, *w;
+};
+long long host_set_len(const vofp::Dims& d) {
+    const long long nfx = (long long)(d.nx + 1) * d.ny * d.nz;
+    const long long nfy = (long long)d.nx * (d.ny + 1) * d.nz;
+    const long long nfz = (long long)d.nx * d.ny * (d.nz + 1);
+    return 2 * d.n + 2 * (nfx + nfy + nfz);
+}
+HostSet host_set(const vofp::Dims& d, double* p) {
+    const long long N = d.n;
+    const long long nfx = (long long)(d.nx + 1) * d.ny * d.nz;
+    const long long nfy = (long long)d.nx * (d.ny + 1) * d.nz;
+    const long long nfz = (long long)d.nx * d.ny * (d.nz + 1);
+    HostSet h;
+    h.F = p;
+    h.vf = p + N;
+    h.ax = p + 2 * N;
+    h.ay = h.ax + nfx;
+    h.az = h.ay + nfy;
+    h.u = h.az + nfz;
+    h.v = h.u + nfx;
+    h.w = h.v + nfy;
+    return h;
+}
+
+// staging (b and x, then `sets` input sets), the copy stream and its events
+vofp_status host_staging(vofp_ctx* c, int sets) {
+    vofp_status s;
+    const long long in = host_set_len(c->d);
+    if (!c->dstage) {
+        if ((s = c->alloc(&c->dstage, 2 * c->d.n + in))) return s;
+        c->dstage_bytes += sizeof(double) * (2 * c->d.n + in);
+    }
+    if (sets > 1 && !c->dstage2) {
+        if ((s = c->alloc(&c->dstage2, in))) return s;
+        c->dstage_bytes += sizeof(double) * in;
+    }
+    if (!c->copy_stream) VOFP_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    if (!c->copy_done) VOFP_CUDA_TRY(c, cudaEventCreateWithFlags(&c->copy_done, cudaEventDisableTiming));
+    if (!c->ops_done) VOFP_CUDA_TRY(c, cudaEventCreateWithFlags(&c->ops_done, cudaEventDisableTiming));
+    for (cudaEvent_t& e : c->set_ready)
+        if (!e) VOFP_CUDA_TRY(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return VOFP_OK;
+}
+
+// the operator's inputs (cells and apertures) and the face velocities of one step, each group on
+// its own stream
+vofp_status upload_ops(vofp_ctx* c, const HostSet& h, const vofp_host_step& in, cudaStream_t st) {
     const vofp::Dims d = c->d;
     const long long N = d.n;
     const long long nfx = (long long)(d.nx + 1) * d.ny * d.nz;
     const long long nfy = (long long)d.nx * (d.ny + 1) * d.nz;
     const long long nfz = (long long)d.nx * d.ny * (d.nz + 1);
-    const long long total = 4 * N + 2 * (nfx + nfy + nfz);
-    if (!c->dstage) {
-        if ((s = c->alloc(&c->dstage, total))) return s;
-        c->dstage_bytes = sizeof(double) * total;
-    }
-    double* p = c->dstage;
-    double *dF = p, *dvf = p + N, *db = p + 2 * N, *dx = p + 3 * N;
-    double *dax = p + 4 * N, *day = dax + nfx, *daz = day + nfy;
-    double *du = daz + nfz, *dv = du + nfx, *dw = dv + nfy;
-    cudaStream_t st = c->stream;
-    if (!c->copy_stream) {
-        VOFP_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
-        VOFP_CUDA_TRY(c, cudaEventCreateWithFlags(&c->copy_done, cudaEventDisableTiming));
-    }
-    // the operator's inputs on the context stream; the face velocities on the copy stream while
-    // the operator builds (the previous call ended with both streams idle)
-    VOFP_CUDA_TRY(c, cudaMemcpyAsync(dF, F, sizeof(double) * N, cudaMemcpyHostToDevice, st));
-    if (vf) VOFP_CUDA_TRY(c, cudaMemcpyAsync(dvf, vf, sizeof(double) * N, cudaMemcpyHostToDevice, st));
-    VOFP_CUDA_TRY(c, cudaMemcpyAsync(dax, ax, sizeof(double) * nfx, cudaMemcpyHostToDevice, st));
-    VOFP_CUDA_TRY(c, cudaMemcpyAsync(day, ay, sizeof(double) * nfy, cudaMemcpyHostToDevice, st));
-    VOFP_CUDA_TRY(c, cudaMemcpyAsync(daz, az, sizeof(double) * nfz, cudaMemcpyHostToDevice, st));
-    cudaStream_t cs = c->copy_stream;
-    VOFP_CUDA_TRY(c, cudaMemcpyAsync(du, u, sizeof(double) * nfx, cudaMemcpyHostToDevice, cs));
-    VOFP_CUDA_TRY(c, cudaMemcpyAsync(dv, v, sizeof(double) * nfy, cudaMemcpyHostToDevice, cs));
-    VOFP_CUDA_TRY(c, cudaMemcpyAsync(dw, w, sizeof(double) * nfz, cudaMemcpyHostToDevice, cs));
+    VOFP_CUDA_TRY(c, cudaMemcpyAsync(h.F, in.F, sizeof(double) * N, cudaMemcpyHostToDevice, st));
+    if (in.vol_frac) VOFP_CUDA_TRY(c, cudaMemcpyAsync(h.vf, in.vol_frac, sizeof(double) * N, cudaMemcpyHostToDevice, st));
+    VOFP_CUDA_TRY(c, cudaMemcpyAsync(h.ax, in.ax, sizeof(double) * nfx, cudaMemcpyHostToDevice, st));
+    VOFP_CUDA_TRY(c, cudaMemcpyAsync(h.ay, in.ay, sizeof(double) * nfy, cudaMemcpyHostToDevice, st));
+    VOFP_CUDA_TRY(c, cudaMemcpyAsync(h.az, in.az, sizeof(double) * nfz, cudaMemcpyHostToDevice, st));
+    return VOFP_OK;
+}
+vofp_status upload_vel(vofp_ctx* c, const HostSet& h, const vofp_host_step& in, cudaStream_t st) {
+    const vofp::Dims d = c->d;
+    const long long nfx = (long long)(d.nx + 1) * d.ny * d.nz;
+    const long long nfy = (long long)d.nx * (d.ny + 1) * d.nz;
+    const long long nfz = (long long)d.nx * d.ny * (d.nz + 1);
+    VOFP_CUDA_TRY(c, cudaMemcpyAsync(h.u, in.u, sizeof(double) * nfx, cudaMemcpyHostToDevice, st));
+    VOFP_CUDA_TRY(c, cudaMemcpyAsync(h.v, in.v, sizeof(double) * nfy, cudaMemcpyHostToDevice, st));
+    VOFP_CUDA_TRY(c, cudaMemcpyAsync(h.w, in.w, sizeof(double) * nfz, cudaMemcpyHostToDevice, st));
+    return VOFP_OK;
+}
+
+// The steps in order. Step 0: the operator's inputs on the context stream and the face velocities
+// on the copy stream, so that the velocities arrive while the operator builds. Step i + 1's inputs
+// go to the other staging set on the copy stream while step i solves (that set was last read by
+// step i - 1, which has finished); the copy stream starts them only after step 0's own inputs
+// are in, so that they do not share the host link with the uploads step 0 waits for.
+// Returns the first status other than OK (NOT_CONVERGED and BREAKDOWN go on to the next step;
+// any other error ends the batch).
+vofp_status solve_host_steps(vofp_ctx* c, int n, const vofp_host_step* steps, const vofp_bc* bc,
+                             const vofp_phys* phys, const vofp_solve_opts* o, vofp_solve_info* infos) {
+    vofp_status s = host_staging(c, n > 1 ? 2 : 1);
+    if (s) return s;
+    const long long N = c->d.n;
+    double* db = c->dstage;
+    double* dx = c->dstage + N;
+    const HostSet set[2] = {host_set(c->d, c->dstage + 2 * N), host_set(c->d, n > 1 ? c->dstage2 : c->dstage + 2 * N)};
+    const cudaStream_t st = c->stream, cs = c->copy_stream;
+    if ((s = upload_ops(c, set[0], steps[0], st))) return s;
+    VOFP_CUDA_TRY(c, cudaEventRecord(c->ops_done, st));
+    if ((s = upload_vel(c, set[0], steps[0], cs))) return s;
     VOFP_CUDA_TRY(c, cudaEventRecord(c->copy_done, cs));
-    s = vofp_build_operator(c, dF, dax, day, daz, vf ? dvf : nullptr, bc, phys);
-    VOFP_CUDA_TRY(c, cudaStreamWaitEvent(st, c->copy_done, 0));
-    if (s) {
-        cudaStreamSynchronize(cs);
-        return s;
+    if (n > 1) VOFP_CUDA_TRY(c, cudaStreamWaitEvent(cs, c->ops_done, 0));
+    vofp_status first = VOFP_OK;
+    for (int i = 0; i < n; ++i) {
+        const HostSet& h = set[i & 1];
+        if (i > 0) VOFP_CUDA_TRY(c, cudaStreamWaitEvent(st, c->set_ready[i & 1], 0));
+        s = vofp_build_operator(c, h.F, h.ax, h.ay, h.az, steps[i].vol_frac ? h.vf : nullptr, bc, phys);
+        if (i == 0) VOFP_CUDA_TRY(c, cudaStreamWaitEvent(st, c->copy_done, 0));
+        if (s) return s;
+        if ((s = vofp_rhs_from_face_velocity(c, h.u, h.v, h.w, nullptr, db))) return s;
+        // the next step's uploads once this one's operator is built: the build's own small copies
+        // then do not queue behind them, and the solve (kernels only) hides them
+        if (i + 1 < n) {
+            const HostSet& hn = set[(i + 1) & 1];
+            if ((s = upload_ops(c, hn, steps[i + 1], cs)) || (s = upload_vel(c, hn, steps[i + 1], cs))) return s;
+            VOFP_CUDA_TRY(c, cudaEventRecord(c->set_ready[(i + 1) & 1], cs));
+        }
+        vofp_solve_opts o2 = *o;
+        o2.x0_zero = 1;
+        const vofp_status rs = vofp_solve(c, db, dx, &o2, infos ? &infos[i] : nullptr);
+        if (rs != VOFP_OK && rs != VOFP_ERR_NOT_CONVERGED && rs != VOFP_ERR_BREAKDOWN) return rs;
+        VOFP_CUDA_TRY(c, cudaMemcpyAsync(steps[i].x_host, dx, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+        VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
+        if (first == VOFP_OK) first = rs;
     }
-    if ((s = vofp_rhs_from_face_velocity(c, du, dv, dw, nullptr, db))) return s;
-    vofp_solve_opts o2 = *o;
-    o2.x0_zero = 1;
-    vofp_status rs = vofp_solve(c, db, dx, &o2, info);
-    if (rs != VOFP_OK && rs != VOFP_ERR_NOT_CONVERGED && rs != VOFP_ERR_BREAKDOWN) return rs;
-    VOFP_CUDA_TRY(c, cudaMemcpyAsync(x_host, dx, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
-    VOFP_CUDA_TRY(c, cudaStreamSynchronize(st));
-    return rs;
+    return first;
+}
+}  // namespace
+
+vofp_status vofp_solve_host_batch(vofp_ctx* c, int nsteps, const vofp_host_step* steps, const vofp_bc* bc,
+                                  const vofp_phys* phys, const vofp_solve_opts* o, vofp_solve_info* infos) {
+    vofp_status s = check_ctx(c, false);
+    if (s) return s;
+    if (nsteps < 1 || !steps || !o) return invalid(c, "nsteps >= 1, steps and opts required");
+    for (int i = 0; i < nsteps; ++i) {
+        const vofp_host_step& h = steps[i];
+        if (!h.F || !h.ax || !h.ay || !h.az || !h.u || !h.v || !h.w || !h.x_host) return invalid(c, "null input");
+    }
+    s = solve_host_steps(c, nsteps, steps, bc, phys, o, infos);
+    // on every return the copy stream is idle: no copy still reads a caller's buffer
+    if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+    return s;
+}
+
+vofp_status vofp_solve_host(vofp_ctx* c, const double* F, const double* ax, const double* ay, const double* az,
+                            const double* vf, const double* u, const double* v, const double* w, const vofp_bc* bc,
+                            const vofp_phys* phys, const vofp_solve_opts* o, double* x_host, vofp_solve_info* info) {
+    const vofp_host_step step{F, ax, ay, az, vf, u, v, w, x_host};
+    return vofp_solve_host_batch(c, 1, &step, bc, phys, o, info);
 }
 
 vofp_status vofp_scaled_pair(vofp_ctx* c, const double* b, const double* x, float* r_scaled, float* x_scaled) {

@@ -127,7 +127,8 @@ struct vofp_ctx {
     unsigned int* counters = nullptr; // last-block tickets
     vofp::CgScalars* sc = nullptr;
     double* work = nullptr;           // apply / residual scratch (cells)
-    double* dstage = nullptr;         // host-call staging (inputs)
+    double* dstage = nullptr;         // host-call staging: b, x and one set of inputs
+    double* dstage2 = nullptr;        // a second set of inputs (batched host calls)
     size_t dstage_bytes = 0;
 
     // CUDA graphs of the solve loops, keyed by configuration
@@ -136,9 +137,12 @@ struct vofp_ctx {
     cudaGraphExec_t graph_mixed = nullptr;
     int graph_mixed_key = -1;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    // vofp_solve_host: a copy stream that brings the face velocities in while the operator builds
+    // vofp_solve_host(_batch): a copy stream that brings the face velocities in while the operator
+    // builds, and the next step's inputs while a step solves
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t copy_done = nullptr;
+    cudaEvent_t ops_done = nullptr;
+    cudaEvent_t set_ready[2] = {nullptr, nullptr};
 
     size_t bytes = 0;
     std::vector<void*> allocs;

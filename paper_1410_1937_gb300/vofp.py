@@ -63,6 +63,12 @@ class _Info(ctypes.Structure):
                 ("status", ctypes.c_int), ("nn_applications", ctypes.c_int), ("fell_back", ctypes.c_int)]
 
 
+class _HostStep(ctypes.Structure):
+    _fields_ = [("F", ctypes.c_void_p), ("ax", ctypes.c_void_p), ("ay", ctypes.c_void_p), ("az", ctypes.c_void_p),
+                ("vol_frac", ctypes.c_void_p), ("u", ctypes.c_void_p), ("v", ctypes.c_void_p), ("w", ctypes.c_void_p),
+                ("x_host", ctypes.c_void_p)]
+
+
 class _Rk2Info(ctypes.Structure):
     _fields_ = [("solve1", _Info), ("solve2", _Info), ("max_div", ctypes.c_double)]
 
@@ -93,6 +99,8 @@ _sig = {
     "vofp_residual": (ctypes.c_int, [_vp, _vp, _vp, _P(ctypes.c_double)]),
     "vofp_solve": (ctypes.c_int, [_vp, _vp, _vp, _P(_Opts), _P(_Info)]),
     "vofp_solve_host": (ctypes.c_int, [_vp] + [_vp] * 8 + [_P(_Bc), _P(_Phys), _P(_Opts), _vp, _P(_Info)]),
+    "vofp_solve_host_batch": (ctypes.c_int, [_vp, ctypes.c_int, _P(_HostStep), _P(_Bc), _P(_Phys), _P(_Opts),
+                                             _P(_Info)]),
     "vofp_merge_map": (ctypes.c_int, [_vp, _vp]),
     "vofp_get_stats": (ctypes.c_int, [_vp, _P(_Stats)]),
     "vofp_residual_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _P(ctypes.c_double)]),
@@ -377,21 +385,53 @@ class Context:
         out["return_status"] = st
         return x, out
 
+    @staticmethod
+    def _host_ptr(a, n, name):
+        """Address of a host float64 array of n values (numpy, or a torch CPU tensor, pinned or not)."""
+        if a is None:
+            return None
+        if hasattr(a, "data_ptr"):
+            if a.numel() != n or a.is_cuda:
+                raise ValueError(name)
+            return ctypes.c_void_p(a.data_ptr())
+        # an ndarray itself (a converted copy would be freed before the call reads it)
+        if not isinstance(a, np.ndarray) or a.dtype != np.float64 or a.size != n or not a.flags.c_contiguous:
+            raise ValueError(name)
+        return ctypes.c_void_p(a.ctypes.data)
+
+    def vofp_solve_host_batch(self, steps, bc, mode=MODE_FP64, rtol=1e-10, max_iter=100000, inner_rtol=0.0,
+                              check_every=0, rho_liquid=1000.0, rho_gas=1.2, merge_threshold=0.1,
+                              density_smoothing=0, dt=1.0, precond=PRECOND_JACOBI, inner_restart=0):
+        """Independent host-buffer end-to-end solves in one call, the next step's uploads overlapping
+        this step's solve.  steps: sequence of dicts with keys F, ax, ay, az, vol_frac (may be None),
+        u, v, w and x_out (host float64 arrays; pinned torch tensors for the overlap).  Returns one
+        info dict per step and the call's status."""
+        hp = self._host_ptr
+        if len(steps) < 1:
+            raise ValueError("steps")
+        arr = (_HostStep * len(steps))()
+        for i, s in enumerate(steps):
+            ptrs = (hp(s["F"], self.n, "F"), hp(s["ax"], self.nfx, "ax"), hp(s["ay"], self.nfy, "ay"),
+                    hp(s["az"], self.nfz, "az"), hp(s.get("vol_frac"), self.n, "vol_frac"), hp(s["u"], self.nfx, "u"),
+                    hp(s["v"], self.nfy, "v"), hp(s["w"], self.nfz, "w"), hp(s["x_out"], self.n, "x_out"))
+            arr[i] = _HostStep(*[p.value if p is not None else None for p in ptrs])
+        b = self._bc(bc, None)
+        ph = _Phys(rho_liquid, rho_gas, merge_threshold, int(density_smoothing), dt)
+        o = _Opts(int(mode), int(precond), float(rtol), int(max_iter), float(inner_rtol), int(check_every), 1, 0,
+                  None, 0, int(inner_restart), 0.0)
+        infos = (_Info * len(steps))()
+        st = _lib.vofp_solve_host_batch(self.h, len(steps), arr, ctypes.byref(b), ctypes.byref(ph), ctypes.byref(o),
+                                        infos)
+        if st not in (OK, ERR_NOT_CONVERGED):
+            _check(self.h, st)
+        return [{"iterations": f.iterations, "outer_iterations": f.outer_iterations, "rel_residual": f.rel_residual,
+                 "seconds": f.seconds, "status": f.status} for f in infos], st
+
     def vofp_solve_host(self, F, ax, ay, az, vol_frac, u, v, w, bc, x_out, mode=MODE_FP64, rtol=1e-10,
                         max_iter=100000, inner_rtol=0.0, check_every=0, rho_liquid=1000.0, rho_gas=1.2,
                         merge_threshold=0.1, density_smoothing=0, dt=1.0, precond=PRECOND_JACOBI, inner_restart=0):
         """Host-buffer end-to-end call: numpy (or pinned torch CPU) float64 arrays in, x_out out."""
-        def hp(a, n, name):
-            if a is None:
-                return None
-            if hasattr(a, "data_ptr"):
-                if a.numel() != n or a.is_cuda:
-                    raise ValueError(name)
-                return ctypes.c_void_p(a.data_ptr())
-            a = np.asarray(a)
-            if a.dtype != np.float64 or a.size != n or not a.flags.c_contiguous:
-                raise ValueError(name)
-            return ctypes.c_void_p(a.ctypes.data)
+        hp = self._host_ptr
         b = self._bc(bc, None)
         ph = _Phys(rho_liquid, rho_gas, merge_threshold, int(density_smoothing), dt)
         o = _Opts(int(mode), int(precond), float(rtol), int(max_iter), float(inner_rtol), int(check_every), 1, 0,

@@ -649,3 +649,56 @@ def test_host_buffer_entry_point_matches_device_path(vofp):
                                  rtol=1e-10)
     assert info2["status"] == 0
     np.testing.assert_array_equal(xh, x.cpu().numpy())
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_host_batch_matches_single_host_calls(vofp, mode):
+    """vofp_solve_host_batch: three independent steps on one grid (the second with doubled face
+    velocities, the third with another fraction field, reversed velocities and no vol_frac), pinned
+    and pageable buffers mixed; every step's pressure and info equal those of its own
+    vofp_solve_host call, bit for bit (the uploads of the next step overlap a step's solve)."""
+    prob = CASES["c1-small"]()
+    m = vofp.MODE_FP64 if mode == "fp64" else vofp.MODE_MIXED
+    rtol = 1e-10 if mode == "fp64" else 1e-8
+    rng = np.random.default_rng(11)
+    F2 = np.clip(prob.F + 0.05 * rng.standard_normal(prob.F.shape), 0.0, 1.0)
+
+    def arrays(k):
+        u, v, w = prob.u.ravel(), prob.v.ravel(), prob.w.ravel()
+        F, vf = prob.F.ravel(), prob.vf.ravel()
+        if k == 1:
+            u, v, w = 2.0 * u, 2.0 * v, 2.0 * w
+        if k == 2:
+            u, v, w, F, vf = -u, -v, -w, F2.ravel(), None
+        return dict(F=F, ax=prob.ax.ravel(), ay=prob.ay.ravel(), az=prob.az.ravel(), vol_frac=vf, u=u, v=v, w=w)
+
+    steps = []
+    for k in range(3):
+        s = arrays(k)
+        if k != 1:   # pinned copies for two of the steps, pageable numpy for the other
+            s = {key: (None if a is None else torch.from_numpy(np.ascontiguousarray(a)).pin_memory())
+                 for key, a in s.items()}
+            s["x_out"] = torch.zeros(prob.n, dtype=torch.float64).pin_memory()
+        else:
+            s = {key: (None if a is None else np.ascontiguousarray(a)) for key, a in s.items()}
+            s["x_out"] = np.zeros(prob.n)
+        steps.append(s)
+    ctx = vofp.Context(prob.dx, prob.dy, prob.dz)
+    infos, st = ctx.vofp_solve_host_batch(steps, prob.bc, mode=m, rtol=rtol, precond=vofp.PRECOND_RBSGS)
+    assert st == 0 and all(i["status"] == 0 for i in infos), infos
+    ref = vofp.Context(prob.dx, prob.dy, prob.dz)
+    for k in range(3):
+        s = arrays(k)
+        xh = np.zeros(prob.n)
+        info = ref.vofp_solve_host(s["F"], s["ax"], s["ay"], s["az"], s["vol_frac"], s["u"], s["v"], s["w"], prob.bc,
+                                   xh, mode=m, rtol=rtol, precond=vofp.PRECOND_RBSGS)
+        got = steps[k]["x_out"]
+        got = got.numpy() if hasattr(got, "numpy") else got
+        np.testing.assert_array_equal(got, xh)
+        assert (infos[k]["iterations"], infos[k]["outer_iterations"]) == (info["iterations"], info["outer_iterations"])
+        assert infos[k]["rel_residual"] == info["rel_residual"]
+    # the doubled velocities double the pressure (the operator is the same, the solve linear up to
+    # its stopping point): a check that the steps did not read each other's staging set
+    x0 = steps[0]["x_out"].numpy()
+    x1 = steps[1]["x_out"]
+    assert np.linalg.norm(x1 - 2.0 * x0) <= 1e-6 * np.linalg.norm(x1)
