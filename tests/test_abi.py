@@ -68,6 +68,8 @@ def test_null_context_is_rejected_by_every_entry_point():
         "vofp_rk2_step": lambda: L.vofp_rk2_step(*([n] * 15), n, 0, n),
         "vofp_apply": lambda: L.vofp_apply(n, n, n),
         "vofp_solve": lambda: L.vofp_solve(n, n, n, n, n),
+        "vofp_solve_host": lambda: L.vofp_solve_host(*([n] * 14)),
+        "vofp_solve_host_batch": lambda: L.vofp_solve_host_batch(n, 1, n, n, n, n, n),
     }
     for name, call in calls.items():
         assert call() == vofp.ERR_INVALID_ARG, name
@@ -81,3 +83,17 @@ def test_binding_fails_loudly_without_the_library(tmp_path):
     shutil.copy(os.path.join(ROOT, "paper_1410_1937_gb300", "vofp.py"), tmp_path / "vofp.py")
     r = subprocess.run([sys.executable, "-c", "import vofp"], cwd=tmp_path, capture_output=True, text=True)
     assert r.returncode != 0 and "libvofp.so is not built" in r.stderr
+
+
+def test_host_pointers_only_from_arrays_that_outlive_the_call():
+    # a list or another dtype would be converted to a temporary whose memory is freed before the
+    # C call reads it: the binding refuses those instead of passing a dangling address
+    import numpy as np
+    from paper_1410_1937_gb300 import vofp
+    hp = vofp.Context._host_ptr
+    a = np.arange(4, dtype=np.float64)
+    assert hp(a, 4, "a").value == a.ctypes.data
+    assert hp(None, 4, "a") is None
+    for bad in ([0.0, 1.0, 2.0, 3.0], np.arange(4, dtype=np.float32), np.zeros((4, 2))[:, 0], np.zeros(5)):
+        with pytest.raises(ValueError):
+            hp(bad, 4, "a")
